@@ -1,0 +1,151 @@
+/*
+ * rpod.h -- C ABI of librpod: randomized POD (rPOD) of tall-skinny snapshot
+ * matrices on one GB300 (sm_103a).
+ *
+ * The method is Alg. 1 of Sec. 4.2 ("randomized POD with subspace
+ * iterations") of Besabe, Girfoglio, Quaini, Rozza, "Randomized POD-LSTM
+ * ROMs for the quasi-geostrophic equations" (arXiv 2504.15350):
+ *   Lambda (m x l) ~ N(0, 1)        Gaussian sketching matrix
+ *   P = S Lambda                    sampled matrix
+ *   P <- (S S^T)^q P                subspace iterations, orthonormalised after
+ *                                   every product with S or S^T
+ *   P = Q R                         QR (CholeskyQR on the GPU)
+ *   T = Q^T S                       l x m
+ *   T = Uhat Sigma V^T              small SVD
+ *   U = Q Uhat                      basis (first k columns)
+ * with n = N_C grid cells, m = N^s snapshots, k = N^r, l = k + p, plus the
+ * modal coefficients C = U_k^T S of Sec. 4.3.
+ *
+ * Conventions for every entry point
+ *   - Matrices are column-major with an explicit leading dimension (element
+ *     (i, j) of S is S[i + j * lds]).  All matrix pointers are DEVICE pointers
+ *     owned by the caller; the library never allocates device memory.  Work
+ *     memory is a caller-allocated device buffer of rpod_workspace_bytes()
+ *     bytes, 256-byte aligned.
+ *   - Everything is enqueued asynchronously on `stream` (a cudaStream_t, NULL
+ *     for the legacy default stream).  Argument errors are detected on the
+ *     host and returned synchronously; errors detected on the device
+ *     (non-finite input, no convergence, wait timeout) are recorded in a
+ *     status word inside the workspace and reported by rpod_status_sync().
+ *   - Return values are rpod_status codes (0 = success).
+ *   - There is no CPU fallback: without a usable CUDA device every compute
+ *     call returns RPOD_ERR_CUDA.
+ */
+#ifndef RPOD_H
+#define RPOD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Element types.  RPOD_F64/RPOD_F32 select the plain paths; RPOD_BF16 and
+ * RPOD_F16 select the tensor-core precision forms (X in 16-bit, FP32
+ * accumulation, FP64 Cholesky and small SVD). */
+typedef enum { RPOD_F64 = 0, RPOD_F32 = 1, RPOD_BF16 = 2, RPOD_F16 = 3 } rpod_dtype;
+
+typedef enum {
+  RPOD_OK = 0,
+  RPOD_ERR_INVALID_ARG = 1,   /* a size, leading dimension or pointer is invalid */
+  RPOD_ERR_UNSUPPORTED = 2,   /* valid but not supported by this build */
+  RPOD_ERR_NONFINITE = 3,     /* S holds NaN or Inf (device-detected) */
+  RPOD_ERR_BREAKDOWN = 4,     /* every column of a Gram matrix vanished */
+  RPOD_ERR_NO_CONVERGENCE = 5,/* small SVD did not converge */
+  RPOD_ERR_TIMEOUT = 6,       /* a device-side wait gave up */
+  RPOD_ERR_CUDA = 7,          /* a CUDA runtime call failed */
+  RPOD_ERR_WORKSPACE = 8      /* workspace missing, too small or misaligned */
+} rpod_status;
+
+/* Warning bits returned through rpod_status_sync()'s flags_out. */
+enum {
+  RPOD_WARN_RANK_DEFICIENT = 1u  /* a Gram matrix had numerically dependent
+                                    columns; the matching basis columns are 0 */
+};
+
+/* Plan flags. */
+enum {
+  RPOD_FLAG_REFINE_FP32 = 1u,  /* 16-bit forms: T = Q^T S reads an FP32 copy */
+  RPOD_FLAG_RETURN_ALL_L = 4u  /* U gets all l = k + p columns, not k */
+};
+
+typedef struct rpod_plan rpod_plan;
+
+/* Creates a plan for one rPOD of an n x m matrix (Alg. 1 inputs: target rank
+ * k = N^r >= 1, oversampling p >= 0, subspace iterations q >= 0 -- the paper
+ * asks q >= 1; q = 0 is the plain randomized range finder).  Requires
+ * l = k + p <= min(n, m, 128).  `seed` keys the Philox4x64-10 stream of the
+ * sketch: entry (i, j) of Lambda uses the counter (e/2, 0, 0, 0), e = i + j*m,
+ * under the key (seed, 0), and a Box-Muller transform (z0 for even e, z1 for
+ * odd e).  `compute` is an rpod_dtype.  The plan is host memory only.
+ * Errors: RPOD_ERR_INVALID_ARG for bad sizes or a NULL `out`. */
+int rpod_plan_create(rpod_plan** out, int64_t n, int64_t m, int32_t k, int32_t p,
+                     int32_t q, uint64_t seed, int32_t compute, uint32_t flags);
+
+/* Bytes of device workspace the plan needs (for any of its calls). */
+int rpod_workspace_bytes(const rpod_plan* plan, size_t* bytes);
+
+/* Alg. 1 on S (n x m, element type s_dtype, leading dimension lds >= n).
+ *   s_dtype:   RPOD_F64 for compute F64; RPOD_F32 for compute F32; for the
+ *              16-bit forms either that 16-bit type or RPOD_F32 (converted
+ *              into the workspace on the first pass).
+ *   S_refine:  FP32 copy of S (ldr >= n) read by T = Q^T S when
+ *              RPOD_FLAG_REFINE_FP32 is set and S itself is 16-bit; ignored
+ *              otherwise (an FP32 S is its own refinement copy).
+ *   U:         n x k (or n x l with RPOD_FLAG_RETURN_ALL_L), ldu >= n; double
+ *              for compute F64, float otherwise.
+ *   sigma:     l singular values of T, descending, double.
+ *   C:         k x m modal coefficients U_k^T S, ldc >= k; double for F64,
+ *              float otherwise.
+ * Column signs: each column of U has its largest-magnitude entry positive;
+ * C's rows follow.  Columns of U that belong to numerically rank-deficient
+ * directions are zero (flagged by RPOD_WARN_RANK_DEFICIENT). */
+int rpod_basis(rpod_plan* plan, const void* S, int64_t lds, int32_t s_dtype,
+               const float* S_refine, int64_t ldr,
+               void* U, int64_t ldu, double* sigma, void* C, int64_t ldc,
+               void* workspace, size_t workspace_bytes, void* stream);
+
+/* Galerkin projection of new snapshots on a basis (Sec. 4.3 coefficient
+ * matrix applied to held-out data): C' = U^T S', U n x kc (kc <= l), S'
+ * n x m_new.  U and C' are double for compute F64, float otherwise; S' has
+ * type s_dtype as for rpod_basis.  m_new may exceed the plan's m. */
+int rpod_project(const rpod_plan* plan, const void* U, int64_t ldu, int32_t kc,
+                 const void* S_new, int64_t lds, int64_t m_new, int32_t s_dtype,
+                 void* C, int64_t ldc, void* workspace, size_t workspace_bytes,
+                 void* stream);
+
+/* The plan's Gaussian sketch Lambda (Alg. 1, first step) alone: writes the
+ * m x l matrix (element type `dtype`, leading dimension ld >= m) to the device
+ * buffer Lam.  Same Philox counters as rpod_basis. */
+int rpod_sketch(const rpod_plan* plan, void* Lam, int64_t ld, int32_t dtype, void* stream);
+
+/* Pass profiling.  When enabled, rpod_basis records CUDA events on its stream
+ * around every pass over S (the products S Lambda, S^T Q, S Z and Q^T S).
+ * rpod_profile_read synchronises on the last recorded event and returns, for
+ * the last rpod_basis call, the number of passes, their summed device time in
+ * ms and the algorithmic bytes and flops of all passes (bytes of S read or
+ * written plus the skinny operands; 2 n m l flops per product). */
+int rpod_profile_enable(rpod_plan* plan, int enable);
+int rpod_profile_read(const rpod_plan* plan, int* passes, double* pass_ms, double* bytes,
+                      double* flops);
+
+/* Synchronises `stream`, reads and clears the workspace status word.  Returns
+ * the device-detected error (RPOD_OK if none) and stores warning bits in
+ * *flags_out when it is not NULL. */
+int rpod_status_sync(const rpod_plan* plan, void* workspace, void* stream,
+                     uint32_t* flags_out);
+
+void rpod_plan_destroy(rpod_plan* plan);
+
+/* Static string for a status code. */
+const char* rpod_strerror(int status);
+
+/* Number of kernels the last rpod_basis/rpod_project call on this plan
+ * enqueued (for launch accounting). */
+int rpod_last_launch_count(const rpod_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RPOD_H */

@@ -1,0 +1,82 @@
+// Internal declarations shared by the librpod translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/rpod.h"
+
+namespace rpod {
+
+// Device status word bits (first 32-bit word of the workspace).
+enum : unsigned {
+  ST_NONFINITE = 1u << 0,
+  ST_RANK_DEF = 1u << 1,
+  ST_NO_CONV = 1u << 2,
+  ST_TIMEOUT = 1u << 3,
+  ST_BREAKDOWN = 1u << 4,
+};
+
+constexpr int kMaxL = 128;  // one-block limit of the small dense kernels
+
+// Kernels enqueued by the calling host thread since the last reset (the
+// C ABI reports it per call).
+extern thread_local int g_launches;
+inline void note_launch() { ++g_launches; }
+
+// ---- generic SIMT GEMM --------------------------------------------------
+// C_z = sum_{k in split z} A(i, k) B(k, j) for i < M, j < N,
+//   A(i, k) = a_kcontig ? A[k + i*lda] : A[i + k*lda]
+//   B(k, j) = B[k + j*ldb]
+// Split z covers k in [z*kchunk, min(K, (z+1)*kchunk)) and is stored at
+// C + z*csplit + i*ci + j*cj.  TA/TB: stored types, TC: multiply-accumulate
+// type, TO: output type.  `check` flags non-finite A entries in *status.
+template <typename TA, typename TB, typename TC, typename TO>
+cudaError_t gemm(cudaStream_t st, bool a_kcontig, int64_t M, int64_t N, int64_t K,
+                 int nsplit, const TA* A, int64_t lda, const TB* B, int64_t ldb,
+                 TO* C, int64_t ci, int64_t cj, int64_t csplit,
+                 unsigned* status, bool check);
+
+// out[i*oi + j*oj] = sum_z part[z*M*N + i + j*M] (summed in double)
+template <typename TP, typename TO>
+cudaError_t reduce_splits(cudaStream_t st, int64_t M, int64_t N, int nsplit,
+                          const TP* part, TO* out, int64_t oi, int64_t oj);
+
+// Lambda (m x l) Philox sketch, stored at Lam[i + j*ld]; caller zeroes padding.
+template <typename T>
+cudaError_t sketch(cudaStream_t st, uint64_t seed, uint64_t stream_id, int64_t m,
+                   int l, T* Lam, int64_t ld);
+
+// One-block FP64 Cholesky of G (l x l, ld = l) with rank-revealing pivot
+// threshold; writes R (upper, l x l) and X with X R = I on the kept
+// directions (zero columns for dropped ones), in double and in TW.
+template <typename TW>
+cudaError_t cholesky(cudaStream_t st, int l, const double* G, double tol, double* R,
+                     double* X, TW* Xw, int ldxw, unsigned* status);
+
+// Symmetric eigen-decomposition of G (l x l, FP64): FP32 parallel two-sided
+// Jacobi, then FP64 Ogita-Aishima refinement.  Outputs eigenvalues
+// (descending, as sigma = sqrt(max(lambda, 0))) and eigenvectors Uhat (l x l).
+cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma,
+                    double* Uhat, double* work, unsigned* status, int refine_iters);
+size_t sym_eig_work_doubles(int l);
+
+// Column-sign convention: per column c < ncols of U (rows n, ld ldu) find the
+// largest |entry| (ties: lowest row) and multiply the column by its sign; the
+// same sign is applied to column c of Uhat (l rows, ld l).
+template <typename T>
+cudaError_t sign_fix(cudaStream_t st, int64_t n, int ncols, T* U, int64_t ldu,
+                     double* Uhat, int l, void* scratch, size_t scratch_bytes);
+size_t sign_fix_scratch_bytes(int64_t n, int ncols);
+
+template <typename TS, typename TD>
+cudaError_t convert_matrix(cudaStream_t st, int64_t rows, int64_t cols, const TS* src,
+                           int64_t lds, TD* dst, int64_t ldd);
+
+template <typename T>
+cudaError_t check_finite(cudaStream_t st, int64_t rows, int64_t cols, const T* S,
+                         int64_t lds, unsigned* status);
+
+}  // namespace rpod

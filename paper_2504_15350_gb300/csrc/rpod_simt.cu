@@ -1,0 +1,681 @@
+// SIMT kernels of librpod: the Philox sketch, the generic tall-skinny GEMM
+// used by the FP64/FP32 passes and by the small dense steps, split-K
+// reductions, the one-block Cholesky (CholeskyQR), the symmetric
+// eigensolver of the small SVD, and the column sign convention.
+#include <float.h>
+#include <math.h>
+
+#include "rpod_internal.cuh"
+
+namespace rpod {
+
+// ------------------------------------------------------------------------
+// conversions
+template <typename T> __device__ __forceinline__ T cvt(float x) { return T(x); }
+template <typename T> __device__ __forceinline__ T cvt(double x) { return T(x); }
+template <typename T> __device__ __forceinline__ T cvt(__nv_bfloat16 x) { return T(__bfloat162float(x)); }
+template <typename T> __device__ __forceinline__ T cvt(__half x) { return T(__half2float(x)); }
+template <> __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <> __device__ __forceinline__ __half cvt<__half>(float x) { return __float2half_rn(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(double x) { return __double2bfloat16(x); }
+template <> __device__ __forceinline__ __half cvt<__half>(double x) { return __double2half(x); }
+
+// ------------------------------------------------------------------------
+// Philox4x64-10 (Salmon et al., SC'11) and the Box-Muller sketch entries.
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += W0; k1 += W1; }
+    const uint64_t lo0 = M0 * c[0], hi0 = __umul64hi(M0, c[0]);
+    const uint64_t lo1 = M1 * c[2], hi1 = __umul64hi(M1, c[2]);
+    const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+  }
+}
+
+template <typename T>
+__global__ void k_sketch(uint64_t seed, uint64_t sid, int64_t m, int64_t total, T* Lam, int64_t ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t e0 = 2 * t;
+  if (e0 >= total) return;
+  uint64_t c[4] = {(uint64_t)t, sid, 0ull, 0ull};
+  philox4x64_10(c, seed, 0ull);
+  const double u1 = ((double)(c[0] >> 11) + 1.0) * 0x1p-53;
+  const double u2 = (double)(c[1] >> 11) * 0x1p-53;
+  const double r = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  Lam[(e0 % m) + (e0 / m) * ld] = cvt<T>(r * cs);
+  if (e0 + 1 < total) Lam[((e0 + 1) % m) + ((e0 + 1) / m) * ld] = cvt<T>(r * sn);
+}
+
+template <typename T>
+cudaError_t sketch(cudaStream_t st, uint64_t seed, uint64_t sid, int64_t m, int l, T* Lam, int64_t ld) {
+  const int64_t total = m * (int64_t)l;
+  const int64_t pairs = (total + 1) / 2;
+  k_sketch<T><<<(unsigned)((pairs + 255) / 256), 256, 0, st>>>(seed, sid, m, total, Lam, ld); note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t sketch<double>(cudaStream_t, uint64_t, uint64_t, int64_t, int, double*, int64_t);
+template cudaError_t sketch<float>(cudaStream_t, uint64_t, uint64_t, int64_t, int, float*, int64_t);
+template cudaError_t sketch<__nv_bfloat16>(cudaStream_t, uint64_t, uint64_t, int64_t, int, __nv_bfloat16*, int64_t);
+template cudaError_t sketch<__half>(cudaStream_t, uint64_t, uint64_t, int64_t, int, __half*, int64_t);
+
+// ------------------------------------------------------------------------
+// Generic SIMT GEMM.  16 x 16 threads; thread (ty, tx) owns rows ty + 16 r
+// and columns tx + 16 c of the BM x BN tile (ty varies fastest so that a
+// warp stores 16 consecutive rows of a column-major output).
+__device__ __forceinline__ bool finite_val(float v) { return isfinite(v); }
+__device__ __forceinline__ bool finite_val(double v) { return isfinite(v); }
+
+template <typename TA, typename TB, typename TC, typename TO, int BM, int BN, int BK, bool AKC>
+__global__ void __launch_bounds__(256)
+k_gemm(int64_t M, int64_t N, int64_t K, int64_t kchunk, const TA* __restrict__ A, int64_t lda,
+       const TB* __restrict__ B, int64_t ldb, TO* __restrict__ C, int64_t ci, int64_t cj,
+       int64_t csplit, unsigned* status, int check) {
+  constexpr int TM = BM / 16, TN = BN / 16;
+  __shared__ TC As[BK][BM + 1];
+  __shared__ TC Bs[BK][BN + 1];
+  const int tid = threadIdx.x, ty = tid & 15, tx = tid >> 4;
+  const int64_t i0 = (int64_t)blockIdx.x * BM, j0 = (int64_t)blockIdx.y * BN;
+  const int64_t kb = (int64_t)blockIdx.z * kchunk;
+  const int64_t ke = (K < kb + kchunk) ? K : kb + kchunk;
+  TC acc[TM][TN];
+#pragma unroll
+  for (int r = 0; r < TM; ++r)
+#pragma unroll
+    for (int c = 0; c < TN; ++c) acc[r][c] = TC(0);
+  bool bad = false;
+  for (int64_t k0 = kb; k0 < ke; k0 += BK) {
+    for (int idx = tid; idx < BM * BK; idx += 256) {
+      int kk, ii;
+      if (AKC) { kk = idx % BK; ii = idx / BK; } else { ii = idx % BM; kk = idx / BM; }
+      const int64_t gi = i0 + ii, gk = k0 + kk;
+      TC v = TC(0);
+      if (gi < M && gk < ke) {
+        v = cvt<TC>(AKC ? A[gk + gi * lda] : A[gi + gk * lda]);
+        if (check && !finite_val(v)) bad = true;
+      }
+      As[kk][ii] = v;
+    }
+    for (int idx = tid; idx < BN * BK; idx += 256) {
+      const int kk = idx % BK, jj = idx / BK;
+      const int64_t gj = j0 + jj, gk = k0 + kk;
+      Bs[kk][jj] = (gj < N && gk < ke) ? cvt<TC>(B[gk + gj * ldb]) : TC(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      TC a[TM], b[TN];
+#pragma unroll
+      for (int r = 0; r < TM; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < TN; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < TM; ++r)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+  if (check && bad) atomicOr(status, ST_NONFINITE);
+  TO* Cz = C + (int64_t)blockIdx.z * csplit;
+#pragma unroll
+  for (int r = 0; r < TM; ++r)
+#pragma unroll
+    for (int c = 0; c < TN; ++c) {
+      const int64_t gi = i0 + ty + 16 * r, gj = j0 + tx + 16 * c;
+      if (gi < M && gj < N) Cz[gi * ci + gj * cj] = cvt<TO>(acc[r][c]);
+    }
+}
+
+template <typename TA, typename TB, typename TC, typename TO, int BM, int BN, int BK>
+static cudaError_t launch_gemm(cudaStream_t st, bool akc, int64_t M, int64_t N, int64_t K,
+                               int nsplit, const TA* A, int64_t lda, const TB* B, int64_t ldb,
+                               TO* C, int64_t ci, int64_t cj, int64_t csplit, unsigned* status,
+                               bool check) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  int64_t kchunk = (K + nsplit - 1) / nsplit;
+  kchunk = ((kchunk + BK - 1) / BK) * BK;
+  if (kchunk <= 0) kchunk = BK;
+  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)nsplit);
+  if (akc)
+    k_gemm<TA, TB, TC, TO, BM, BN, BK, true><<<grid, 256, 0, st>>>(
+        M, N, K, kchunk, A, lda, B, ldb, C, ci, cj, csplit, status, check ? 1 : 0);
+  else
+    k_gemm<TA, TB, TC, TO, BM, BN, BK, false><<<grid, 256, 0, st>>>(
+        M, N, K, kchunk, A, lda, B, ldb, C, ci, cj, csplit, status, check ? 1 : 0);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename TA, typename TB, typename TC, typename TO>
+cudaError_t gemm(cudaStream_t st, bool akc, int64_t M, int64_t N, int64_t K, int nsplit,
+                 const TA* A, int64_t lda, const TB* B, int64_t ldb, TO* C, int64_t ci,
+                 int64_t cj, int64_t csplit, unsigned* status, bool check) {
+  if (nsplit < 1) nsplit = 1;
+  if (sizeof(TC) == 4) {
+    if (N <= 32) return launch_gemm<TA, TB, TC, TO, 128, 32, 16>(st, akc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
+    if (N <= 64) return launch_gemm<TA, TB, TC, TO, 128, 64, 16>(st, akc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
+    return launch_gemm<TA, TB, TC, TO, 128, 128, 16>(st, akc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
+  } else {
+    if (M <= 32 && N <= 32) return launch_gemm<TA, TB, TC, TO, 32, 32, 16>(st, akc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
+    if (N <= 32) return launch_gemm<TA, TB, TC, TO, 64, 32, 16>(st, akc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
+    return launch_gemm<TA, TB, TC, TO, 64, 64, 16>(st, akc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
+  }
+}
+
+#define INST_GEMM(TA, TB, TC, TO)                                                          \
+  template cudaError_t gemm<TA, TB, TC, TO>(cudaStream_t, bool, int64_t, int64_t, int64_t, \
+                                            int, const TA*, int64_t, const TB*, int64_t,  \
+                                            TO*, int64_t, int64_t, int64_t, unsigned*, bool);
+INST_GEMM(double, double, double, double)
+INST_GEMM(float, float, float, float)
+INST_GEMM(float, float, float, double)
+INST_GEMM(float, double, float, float)
+INST_GEMM(double, double, double, float)
+#undef INST_GEMM
+
+// ------------------------------------------------------------------------
+template <typename TP, typename TO>
+__global__ void k_reduce(int64_t M, int64_t N, int nsplit, const TP* __restrict__ part,
+                         TO* __restrict__ out, int64_t oi, int64_t oj) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t MN = M * N;
+  if (idx >= MN) return;
+  double s = 0.0;
+  for (int z = 0; z < nsplit; ++z) s += (double)part[z * MN + idx];
+  const int64_t i = idx % M, j = idx / M;
+  out[i * oi + j * oj] = (TO)s;
+}
+
+template <typename TP, typename TO>
+cudaError_t reduce_splits(cudaStream_t st, int64_t M, int64_t N, int nsplit, const TP* part,
+                          TO* out, int64_t oi, int64_t oj) {
+  const int64_t MN = M * N;
+  k_reduce<TP, TO><<<(unsigned)((MN + 255) / 256), 256, 0, st>>>(M, N, nsplit, part, out, oi, oj); note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t reduce_splits<double, double>(cudaStream_t, int64_t, int64_t, int, const double*, double*, int64_t, int64_t);
+template cudaError_t reduce_splits<float, float>(cudaStream_t, int64_t, int64_t, int, const float*, float*, int64_t, int64_t);
+template cudaError_t reduce_splits<double, float>(cudaStream_t, int64_t, int64_t, int, const double*, float*, int64_t, int64_t);
+
+// ------------------------------------------------------------------------
+// One-block FP64 Cholesky G = R^T R (right-looking, upper factor kept in
+// place), with a rank-revealing pivot test: column j is dropped when its
+// remaining pivot is <= tol * G_jj (or G_jj is negligible against the
+// largest diagonal), then the in-place inverse of the upper factor (column
+// by column, using the columns already inverted).  Dropped directions get
+// zero rows and columns in X, so Q = Y X has zero columns there.
+__device__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (lane < (int)(blockDim.x >> 5)) ? red[lane] : -DBL_MAX;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) red[0] = v;
+  }
+  __syncthreads();
+  v = red[0];
+  __syncthreads();
+  return v;
+}
+
+template <typename TW>
+__global__ void __launch_bounds__(256)
+k_cholesky(int l, const double* __restrict__ G, double tol, double* __restrict__ Xout,
+           TW* __restrict__ Xw, int ldxw, unsigned* status) {
+  extern __shared__ double sm[];
+  double* A = sm;               // l x l column-major
+  double* d0 = A + l * l;       // original diagonal
+  double* tmp = d0 + l;         // column buffer
+  __shared__ double red[32];
+  __shared__ double s_r;
+  __shared__ int s_keep[kMaxL];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < l * l; e += nt) A[e] = G[e];
+  __syncthreads();
+  double dm = 0.0;
+  for (int j = tid; j < l; j += nt) { d0[j] = A[j + j * l]; dm = fmax(dm, d0[j]); }
+  const double gmax = block_max(dm, red);
+  int ndropped = 0;
+  for (int j = 0; j < l; ++j) {
+    if (tid == 0) {
+      const double d = A[j + j * l];
+      const bool keep = (d0[j] > 1e-300) && (d0[j] > 1e-30 * gmax) && (d > tol * d0[j]);
+      s_keep[j] = keep ? 1 : 0;
+      s_r = keep ? sqrt(d) : 0.0;
+      A[j + j * l] = s_r;
+    }
+    __syncthreads();
+    const double r = s_r;
+    const bool keep = s_keep[j] != 0;
+    if (!keep) ++ndropped;
+    for (int c = j + 1 + tid; c < l; c += nt) A[j + c * l] = keep ? A[j + c * l] / r : 0.0;
+    __syncthreads();
+    // trailing update of the upper triangle
+    const int t = l - j - 1;
+    for (int e = tid; e < t * t; e += nt) {
+      const int a = j + 1 + e % t, b = j + 1 + e / t;
+      if (a <= b) A[a + b * l] -= A[j + a * l] * A[j + b * l];
+    }
+    __syncthreads();
+  }
+  // in-place inverse of the upper-triangular factor
+  for (int j = 0; j < l; ++j) {
+    const bool keep = s_keep[j] != 0;
+    for (int i = tid; i < j; i += nt) tmp[i] = keep ? A[i + j * l] : 0.0;
+    __syncthreads();
+    if (keep) {
+      const double ajj = 1.0 / A[j + j * l];
+      for (int i = tid; i < j; i += nt) {
+        double s = 0.0;
+        for (int t2 = i; t2 < j; ++t2) s += A[i + t2 * l] * tmp[t2];
+        A[i + j * l] = -ajj * s;
+      }
+      __syncthreads();
+      if (tid == 0) A[j + j * l] = ajj;
+    } else {
+      for (int i = tid; i <= j; i += nt) A[i + j * l] = 0.0;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < l * l; e += nt) {
+    const int i = e % l, j = e / l;
+    const double v = (i <= j) ? A[e] : 0.0;
+    Xout[e] = v;
+    Xw[i + (int64_t)j * ldxw] = (TW)v;
+  }
+  if (tid == 0 && ndropped > 0) atomicOr(status, ndropped == l ? (ST_RANK_DEF | ST_BREAKDOWN) : ST_RANK_DEF);
+}
+
+template <typename TW>
+cudaError_t cholesky(cudaStream_t st, int l, const double* G, double tol, double* R, double* X,
+                     TW* Xw, int ldxw, unsigned* status) {
+  (void)R;
+  const size_t sm = ((size_t)l * l + 2 * l) * sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_cholesky<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    attr_set = true;
+  }
+  k_cholesky<TW><<<1, 256, sm, st>>>(l, G, tol, X, Xw, ldxw, status); note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t cholesky<double>(cudaStream_t, int, const double*, double, double*, double*, double*, int, unsigned*);
+template cudaError_t cholesky<float>(cudaStream_t, int, const double*, double, double*, double*, float*, int, unsigned*);
+
+// ------------------------------------------------------------------------
+// Symmetric eigensolver for the small SVD.  T T^T = Uhat Sigma^2 Uhat^T, so
+// the left singular vectors and values of T come from the eigenpairs of its
+// l x l Gram matrix.
+//
+// Stage 1: parallel cyclic two-sided Jacobi in FP32 (round-robin pairing,
+// l/2 disjoint rotations per step: all row rotations, then all column
+// rotations).  Stage 2: FP64 iterative refinement of the eigenvectors
+// (Ogita & Aishima, "Iterative refinement for symmetric eigenvalue
+// decomposition", Japan J. Indust. Appl. Math. 35, 2018): with R = I - X^T X
+// and S = X^T A X, lambda_i = S_ii / (1 - R_ii), E_ij = (S_ij + lambda_j
+// R_ij) / (lambda_j - lambda_i) when |lambda_i - lambda_j| > delta, else
+// R_ij / 2, E_ii = R_ii / 2, X <- X + X E; each pass squares the error.
+__device__ __forceinline__ void rr_pair(int L, int s, int i, int& a, int& b) {
+  a = (i == 0) ? 0 : 1 + ((i - 1 + s) % (L - 1));
+  b = 1 + ((L - 2 - i + s) % (L - 1));
+}
+
+__global__ void __launch_bounds__(512)
+k_jacobi32(int l, const double* __restrict__ G, double* __restrict__ Vout, int max_sweeps,
+           unsigned* status) {
+  extern __shared__ float smf[];
+  const int L = l + (l & 1);
+  const int ld = L + 1;
+  float* A = smf;               // L x L, row stride ld
+  float* V = A + L * ld;        // L x L, row stride ld
+  float* cs = V + L * ld;       // L/2
+  float* sn = cs + L / 2;
+  int* pp = (int*)(sn + L / 2);
+  int* qq = pp + L / 2;
+  __shared__ double red[32];
+  __shared__ int s_rot;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double dm = 0.0;
+  for (int i = tid; i < l; i += nt) dm = fmax(dm, fabs(G[i + i * l]));
+  dm = block_max(dm, red);
+  const double scale = dm > 0.0 ? 1.0 / dm : 1.0;
+  for (int e = tid; e < L * L; e += nt) {
+    const int i = e % L, j = e / L;
+    A[i * ld + j] = (i < l && j < l) ? (float)(G[i + j * l] * scale) : 0.f;
+    V[i * ld + j] = (i == j) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  const float tol = 4e-7f;
+  bool converged = (L < 2);
+  for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int s = 0; s < L - 1; ++s) {
+      for (int pi = tid; pi < L / 2; pi += nt) {
+        int p, q;
+        rr_pair(L, s, pi, p, q);
+        if (p > q) { const int t = p; p = q; q = t; }
+        float c = 1.f, sv = 0.f;
+        if (q < l) {
+          const float apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
+          if (apq != 0.f && fabsf(apq) > tol * sqrtf(fabsf(app * aqq)) && fabsf(apq) > 1e-30f) {
+            const float tau = (aqq - app) / (2.f * apq);
+            const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            c = rsqrtf(1.f + t * t);
+            sv = t * c;
+            s_rot = 1;
+          }
+        }
+        cs[pi] = c; sn[pi] = sv; pp[pi] = p; qq[pi] = q;
+      }
+      __syncthreads();
+      // rows p, q <- J^T A
+      for (int e = tid; e < (L / 2) * L; e += nt) {
+        const int pi = e / L, x = e % L;
+        const float c = cs[pi], sv = sn[pi];
+        if (sv == 0.f) continue;
+        const int p = pp[pi], q = qq[pi];
+        const float ap = A[p * ld + x], aq = A[q * ld + x];
+        A[p * ld + x] = c * ap - sv * aq;
+        A[q * ld + x] = sv * ap + c * aq;
+      }
+      __syncthreads();
+      // columns p, q <- A J, V J
+      for (int e = tid; e < (L / 2) * L; e += nt) {
+        const int pi = e / L, x = e % L;
+        const float c = cs[pi], sv = sn[pi];
+        if (sv == 0.f) continue;
+        const int p = pp[pi], q = qq[pi];
+        const float ap = A[x * ld + p], aq = A[x * ld + q];
+        A[x * ld + p] = c * ap - sv * aq;
+        A[x * ld + q] = sv * ap + c * aq;
+        const float vp = V[x * ld + p], vq = V[x * ld + q];
+        V[x * ld + p] = c * vp - sv * vq;
+        V[x * ld + q] = sv * vp + c * vq;
+      }
+      __syncthreads();
+    }
+    converged = (s_rot == 0);
+    __syncthreads();
+  }
+  if (!converged && tid == 0) atomicOr(status, ST_NO_CONV);
+  for (int e = tid; e < l * l; e += nt) {
+    const int i = e % l, j = e / l;
+    Vout[e] = (double)V[i * ld + j];
+  }
+}
+
+__global__ void k_add_inplace(int64_t n, double* __restrict__ X, const double* __restrict__ D) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) X[i] += D[i];
+}
+
+__global__ void k_frob(int64_t n, const double* __restrict__ A, double* out) {
+  __shared__ double rs[32];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += A[i] * A[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) rs[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) a += rs[k];
+    *out = sqrt(a);
+  }
+}
+
+// Sort eigenpairs by descending eigenvalue (stable), sigma = sqrt(max(lambda, 0)).
+__global__ void k_sort_eig(int l, const double* __restrict__ lam, const double* __restrict__ X,
+                           double* __restrict__ sigma, double* __restrict__ U) {
+  __shared__ int rank[kMaxL];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < l; i += blockDim.x) {
+    int r = 0;
+    for (int j = 0; j < l; ++j) r += (lam[j] > lam[i]) || (lam[j] == lam[i] && j < i);
+    rank[i] = r;
+    sigma[r] = sqrt(fmax(lam[i], 0.0));
+  }
+  __syncthreads();
+  for (int e = tid; e < l * l; e += blockDim.x) {
+    const int i = e % l, j = e / l;
+    U[i + rank[j] * l] = X[e];
+  }
+}
+
+// Ogita-Aishima update: from XtX = X^T X and S = X^T A X (l x l) write the
+// eigenvalue estimates lambda and the correction E (FP64); ||A||_F is read
+// from the device.
+__global__ void __launch_bounds__(256)
+k_oa_update_dev(int l, const double* __restrict__ XtX, const double* __restrict__ S,
+                const double* __restrict__ normA, double* __restrict__ lam, double* __restrict__ E) {
+  extern __shared__ double sml[];
+  double* lm = sml;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < l; i += nt) lm[i] = S[i + i * l] / XtX[i + i * l];
+  __syncthreads();
+  double so = 0.0, sr = 0.0;
+  for (int e = tid; e < l * l; e += nt) {
+    const int i = e % l, j = e / l;
+    const double rij = (i == j ? 1.0 : 0.0) - XtX[e];
+    const double sij = S[e] - (i == j ? lm[i] : 0.0);
+    so += sij * sij;
+    sr += rij * rij;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    so += __shfl_xor_sync(0xffffffffu, so, o);
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+  }
+  __shared__ double rs[2][32];
+  __shared__ double s_delta;
+  const int w = tid >> 5, lane = tid & 31;
+  if (lane == 0) { rs[0][w] = so; rs[1][w] = sr; }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < (nt >> 5); ++k) { a += rs[0][k]; b += rs[1][k]; }
+    s_delta = 2.0 * (sqrt(a) + (*normA) * sqrt(b));
+  }
+  __syncthreads();
+  const double delta = s_delta;
+  for (int e = tid; e < l * l; e += nt) {
+    const int i = e % l, j = e / l;
+    const double rij = (i == j ? 1.0 : 0.0) - XtX[e];
+    double v;
+    if (i == j) v = 0.5 * rij;
+    else if (fabs(lm[i] - lm[j]) > delta) v = (S[e] + lm[j] * rij) / (lm[j] - lm[i]);
+    else v = 0.5 * rij;
+    E[e] = v;
+  }
+  for (int i = tid; i < l; i += nt) lam[i] = lm[i];
+}
+
+size_t sym_eig_work_doubles(int l) {
+  // V/X, XtX, AX, S, E, XE, lam, normA, split partials (8 splits of l*l)
+  return (size_t)l * l * (6 + 8) + 2 * (size_t)l + 8;
+}
+
+cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma, double* Uhat,
+                    double* work, unsigned* status, int refine_iters) {
+  const size_t ll = (size_t)l * l;
+  double* X = work;
+  double* XtX = X + ll;
+  double* AX = XtX + ll;
+  double* S = AX + ll;
+  double* E = S + ll;
+  double* XE = E + ll;
+  double* part = XE + ll;  // 8 * ll
+  double* lam = part + 8 * ll;
+  double* normA = lam + l;
+  const int L = l + (l & 1);
+  const size_t smj = (size_t)2 * L * (L + 1) * sizeof(float) + (size_t)L * (2 * sizeof(float) + 2 * sizeof(int));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_jacobi32<<<1, 512, smj, st>>>(l, G, X, 30, status); note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_frob<<<1, 256, 0, st>>>((int64_t)ll, G, normA); note_launch();
+  // normA is needed on the device only: pass through a tiny kernel chain
+  const int nsp = l > 64 ? 8 : 4;
+  for (int it = 0; it < refine_iters; ++it) {
+    // XtX = X^T X
+    if ((e = gemm<double, double, double, double>(st, true, l, l, l, nsp, X, l, X, l, part, 1, l, ll, status, false))) return e;
+    if ((e = reduce_splits<double, double>(st, l, l, nsp, part, XtX, 1, l))) return e;
+    // AX = G X
+    if ((e = gemm<double, double, double, double>(st, false, l, l, l, nsp, G, l, X, l, part, 1, l, ll, status, false))) return e;
+    if ((e = reduce_splits<double, double>(st, l, l, nsp, part, AX, 1, l))) return e;
+    // S = X^T AX
+    if ((e = gemm<double, double, double, double>(st, true, l, l, l, nsp, X, l, AX, l, part, 1, l, ll, status, false))) return e;
+    if ((e = reduce_splits<double, double>(st, l, l, nsp, part, S, 1, l))) return e;
+    k_oa_update_dev<<<1, 256, l * sizeof(double), st>>>(l, XtX, S, normA, lam, E); note_launch();
+    if ((e = cudaGetLastError())) return e;
+    // X <- X + X E
+    if ((e = gemm<double, double, double, double>(st, false, l, l, l, nsp, X, l, E, l, part, 1, l, ll, status, false))) return e;
+    if ((e = reduce_splits<double, double>(st, l, l, nsp, part, XE, 1, l))) return e;
+    k_add_inplace<<<(unsigned)((ll + 255) / 256), 256, 0, st>>>((int64_t)ll, X, XE); note_launch();
+    if ((e = cudaGetLastError())) return e;
+  }
+  if (refine_iters == 0) {
+    // eigenvalues from the Rayleigh quotients of the Jacobi vectors
+    if ((e = gemm<double, double, double, double>(st, false, l, l, l, nsp, G, l, X, l, part, 1, l, ll, status, false))) return e;
+    if ((e = reduce_splits<double, double>(st, l, l, nsp, part, AX, 1, l))) return e;
+    if ((e = gemm<double, double, double, double>(st, true, l, l, l, nsp, X, l, AX, l, part, 1, l, ll, status, false))) return e;
+    if ((e = reduce_splits<double, double>(st, l, l, nsp, part, S, 1, l))) return e;
+    if ((e = gemm<double, double, double, double>(st, true, l, l, l, nsp, X, l, X, l, part, 1, l, ll, status, false))) return e;
+    if ((e = reduce_splits<double, double>(st, l, l, nsp, part, XtX, 1, l))) return e;
+    k_oa_update_dev<<<1, 256, l * sizeof(double), st>>>(l, XtX, S, normA, lam, E); note_launch();
+  }
+  k_sort_eig<<<1, 128, 0, st>>>(l, lam, X, sigma, Uhat); note_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// Column sign convention.
+struct ArgMax { double v; long long i; };
+
+template <typename T>
+__global__ void k_colmax_partial(int64_t n, int64_t rows_per_blk, const T* __restrict__ U,
+                                 int64_t ldu, ArgMax* __restrict__ out, int nblk) {
+  const int c = blockIdx.y;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk;
+  const int64_t r1 = (r0 + rows_per_blk < n) ? r0 + rows_per_blk : n;
+  double bv = 0.0, ba = -1.0;
+  long long bi = LLONG_MAX;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    const double v = (double)U[r + c * ldu];
+    const double a = fabs(v);
+    if (a > ba) { ba = a; bv = v; bi = r; }
+  }
+  __shared__ double sa[256], sv[256];
+  __shared__ long long si[256];
+  sa[threadIdx.x] = ba; sv[threadIdx.x] = bv; si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      const int t = threadIdx.x + o;
+      if (sa[t] > sa[threadIdx.x] || (sa[t] == sa[threadIdx.x] && si[t] < si[threadIdx.x])) {
+        sa[threadIdx.x] = sa[t]; sv[threadIdx.x] = sv[t]; si[threadIdx.x] = si[t];
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c * nblk + blockIdx.x] = ArgMax{sa[0] < 0 ? 0.0 : sv[0], si[0]};
+}
+
+__global__ void k_colsign(int ncols, int nblk, const ArgMax* __restrict__ part, double* __restrict__ sgn,
+                          double* __restrict__ Uhat, int l) {
+  const int c = blockIdx.x;
+  __shared__ double s_s;
+  if (threadIdx.x == 0) {
+    double ba = -1.0, bv = 0.0;
+    long long bi = LLONG_MAX;
+    for (int b = 0; b < nblk; ++b) {
+      const ArgMax p = part[c * nblk + b];
+      const double a = fabs(p.v);
+      if (p.i != LLONG_MAX && (a > ba || (a == ba && p.i < bi))) { ba = a; bv = p.v; bi = p.i; }
+    }
+    s_s = (bv < 0.0) ? -1.0 : 1.0;
+    sgn[c] = s_s;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < l; i += blockDim.x) Uhat[i + c * l] *= s_s;
+}
+
+template <typename T>
+__global__ void k_scale_cols(int64_t n, int ncols, T* __restrict__ U, int64_t ldu, const double* __restrict__ sgn) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * ncols) return;
+  const int64_t r = idx % n;
+  const int c = (int)(idx / n);
+  if (sgn[c] < 0.0) U[r + c * ldu] = -U[r + c * ldu];
+}
+
+size_t sign_fix_scratch_bytes(int64_t n, int ncols) {
+  const int64_t nblk = (n + 8191) / 8192;
+  return (size_t)ncols * nblk * sizeof(ArgMax) + (size_t)ncols * sizeof(double) + 256;
+}
+
+template <typename T>
+cudaError_t sign_fix(cudaStream_t st, int64_t n, int ncols, T* U, int64_t ldu, double* Uhat, int l,
+                     void* scratch, size_t) {
+  const int64_t rpb = 8192;
+  const int nblk = (int)((n + rpb - 1) / rpb);
+  ArgMax* part = (ArgMax*)scratch;
+  double* sgn = (double*)((char*)scratch + (((size_t)ncols * nblk * sizeof(ArgMax) + 255) / 256) * 256);
+  k_colmax_partial<T><<<dim3(nblk, ncols), 256, 0, st>>>(n, rpb, U, ldu, part, nblk); note_launch();
+  k_colsign<<<ncols, 128, 0, st>>>(ncols, nblk, part, sgn, Uhat, l); note_launch();
+  const int64_t tot = n * ncols;
+  k_scale_cols<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, ncols, U, ldu, sgn); note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t sign_fix<double>(cudaStream_t, int64_t, int, double*, int64_t, double*, int, void*, size_t);
+template cudaError_t sign_fix<float>(cudaStream_t, int64_t, int, float*, int64_t, double*, int, void*, size_t);
+
+// ------------------------------------------------------------------------
+template <typename TS, typename TD>
+__global__ void k_convert(int64_t rows, int64_t cols, const TS* __restrict__ src, int64_t lds,
+                          TD* __restrict__ dst, int64_t ldd) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * cols) return;
+  const int64_t r = idx % rows, c = idx / rows;
+  dst[r + c * ldd] = cvt<TD>(src[r + c * lds]);
+}
+
+template <typename TS, typename TD>
+cudaError_t convert_matrix(cudaStream_t st, int64_t rows, int64_t cols, const TS* src, int64_t lds,
+                           TD* dst, int64_t ldd) {
+  const int64_t tot = rows * cols;
+  k_convert<TS, TD><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(rows, cols, src, lds, dst, ldd); note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t convert_matrix<double, float>(cudaStream_t, int64_t, int64_t, const double*, int64_t, float*, int64_t);
+template cudaError_t convert_matrix<double, double>(cudaStream_t, int64_t, int64_t, const double*, int64_t, double*, int64_t);
+
+template <typename T>
+__global__ void k_check_finite(int64_t rows, int64_t cols, const T* __restrict__ S, int64_t lds, unsigned* status) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * cols) return;
+  const float v = cvt<float>(S[idx % rows + (idx / rows) * lds]);
+  if (!isfinite(v)) atomicOr(status, ST_NONFINITE);
+}
+
+template <typename T>
+cudaError_t check_finite(cudaStream_t st, int64_t rows, int64_t cols, const T* S, int64_t lds, unsigned* status) {
+  const int64_t tot = rows * cols;
+  k_check_finite<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(rows, cols, S, lds, status); note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t check_finite<__nv_bfloat16>(cudaStream_t, int64_t, int64_t, const __nv_bfloat16*, int64_t, unsigned*);
+template cudaError_t check_finite<__half>(cudaStream_t, int64_t, int64_t, const __half*, int64_t, unsigned*);
+
+}  // namespace rpod

@@ -1,0 +1,250 @@
+"""ctypes binding of librpod's C ABI (include/rpod.h).
+
+Every function of the header is exposed under the same name with the same
+arguments (device pointers as Python ints, the stream as its integer
+handle).  `Plan` adds torch-tensor marshalling: it reads data pointers,
+leading dimensions and the current CUDA stream from tensors and allocates
+the outputs and the workspace with torch; all arithmetic runs in the
+library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "librpod.so")
+
+RPOD_F64, RPOD_F32, RPOD_BF16, RPOD_F16 = 0, 1, 2, 3
+RPOD_OK = 0
+RPOD_ERR_INVALID_ARG = 1
+RPOD_ERR_UNSUPPORTED = 2
+RPOD_ERR_NONFINITE = 3
+RPOD_ERR_BREAKDOWN = 4
+RPOD_ERR_NO_CONVERGENCE = 5
+RPOD_ERR_TIMEOUT = 6
+RPOD_ERR_CUDA = 7
+RPOD_ERR_WORKSPACE = 8
+RPOD_WARN_RANK_DEFICIENT = 1
+RPOD_FLAG_REFINE_FP32 = 1
+RPOD_FLAG_RETURN_ALL_L = 4
+
+_c_i64, _c_i32, _c_u64, _c_u32, _p = (ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                                      ctypes.c_uint32, ctypes.c_void_p)
+
+# name -> (restype, argtypes); mirrors include/rpod.h
+SIGNATURES = {
+    "rpod_plan_create": (ctypes.c_int, [ctypes.POINTER(_p), _c_i64, _c_i64, _c_i32, _c_i32, _c_i32,
+                                        _c_u64, _c_i32, _c_u32]),
+    "rpod_workspace_bytes": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "rpod_basis": (ctypes.c_int, [_p, _p, _c_i64, _c_i32, _p, _c_i64, _p, _c_i64, _p, _p, _c_i64,
+                                  _p, ctypes.c_size_t, _p]),
+    "rpod_project": (ctypes.c_int, [_p, _p, _c_i64, _c_i32, _p, _c_i64, _c_i64, _c_i32, _p, _c_i64,
+                                    _p, ctypes.c_size_t, _p]),
+    "rpod_status_sync": (ctypes.c_int, [_p, _p, _p, ctypes.POINTER(_c_u32)]),
+    "rpod_plan_destroy": (None, [_p]),
+    "rpod_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "rpod_last_launch_count": (ctypes.c_int, [_p]),
+    "rpod_sketch": (ctypes.c_int, [_p, _p, _c_i64, _c_i32, _p]),
+    "rpod_profile_enable": (ctypes.c_int, [_p, ctypes.c_int]),
+    "rpod_profile_read": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads librpod.so (built by paper_2504_15350_gb300.build) and declares
+    its signatures.  Raises if the library is missing: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"librpod.so not built ({path}); run paper_2504_15350_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class RpodError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = load().rpod_strerror(code).decode()
+        super().__init__(f"{what}: {msg} (status {code})" if what else f"{msg} (status {code})")
+
+
+def _check(code: int, what: str):
+    if code != RPOD_OK:
+        raise RpodError(code, what)
+
+
+# ---- same-name wrappers --------------------------------------------------
+def rpod_plan_create(n, m, k, p, q, seed, compute, flags=0) -> int:
+    h = _p()
+    _check(load().rpod_plan_create(ctypes.byref(h), n, m, k, p, q, seed, compute, flags),
+           "rpod_plan_create")
+    return h.value
+
+
+def rpod_workspace_bytes(plan) -> int:
+    b = ctypes.c_size_t()
+    _check(load().rpod_workspace_bytes(plan, ctypes.byref(b)), "rpod_workspace_bytes")
+    return b.value
+
+
+def rpod_basis(plan, S, lds, s_dtype, S_refine, ldr, U, ldu, sigma, C, ldc, ws, ws_bytes, stream):
+    return load().rpod_basis(plan, S, lds, s_dtype, S_refine, ldr, U, ldu, sigma, C, ldc, ws,
+                             ws_bytes, stream)
+
+
+def rpod_project(plan, U, ldu, kc, S_new, lds, m_new, s_dtype, C, ldc, ws, ws_bytes, stream):
+    return load().rpod_project(plan, U, ldu, kc, S_new, lds, m_new, s_dtype, C, ldc, ws, ws_bytes,
+                               stream)
+
+
+def rpod_status_sync(plan, ws, stream):
+    f = _c_u32()
+    rc = load().rpod_status_sync(plan, ws, stream, ctypes.byref(f))
+    return rc, f.value
+
+
+def rpod_plan_destroy(plan):
+    load().rpod_plan_destroy(plan)
+
+
+def rpod_strerror(code):
+    return load().rpod_strerror(code).decode()
+
+
+def rpod_last_launch_count(plan):
+    return load().rpod_last_launch_count(plan)
+
+
+def rpod_sketch(plan, Lam, ld, dtype, stream):
+    return load().rpod_sketch(plan, Lam, ld, dtype, stream)
+
+
+def rpod_profile_enable(plan, enable):
+    return load().rpod_profile_enable(plan, int(enable))
+
+
+def rpod_profile_read(plan):
+    n = ctypes.c_int(); ms = ctypes.c_double(); b = ctypes.c_double(); f = ctypes.c_double()
+    _check(load().rpod_profile_read(plan, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b),
+                                    ctypes.byref(f)), "rpod_profile_read")
+    return n.value, ms.value, b.value, f.value
+
+
+# ---- torch marshalling ------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def dtype_code(t) -> int:
+    torch = _torch()
+    return {torch.float64: RPOD_F64, torch.float32: RPOD_F32, torch.bfloat16: RPOD_BF16,
+            torch.float16: RPOD_F16}[t]
+
+
+def colmajor_ld(A) -> int:
+    """Leading dimension of a column-major 2-D view (stride (1, ld))."""
+    if A.dim() != 2 or A.stride(0) != 1:
+        raise ValueError("expected a column-major matrix view (stride(0) == 1); use X.t() of a "
+                         "row-major (m, n) tensor")
+    return max(A.stride(1), A.shape[0])
+
+
+def empty_colmajor(rows, cols, dtype, device):
+    torch = _torch()
+    return torch.empty((cols, rows), dtype=dtype, device=device).t()
+
+
+class Plan:
+    """An rPOD plan plus its workspace, for tensors on one CUDA device."""
+
+    def __init__(self, n, m, k, p, q, seed=0, compute="f32", flags=0, device="cuda"):
+        torch = _torch()
+        self.compute = {"f64": RPOD_F64, "f32": RPOD_F32, "bf16": RPOD_BF16,
+                        "f16": RPOD_F16}[compute] if isinstance(compute, str) else int(compute)
+        self.n, self.m, self.k, self.p, self.q, self.l = n, m, k, p, q, k + p
+        self.flags = flags
+        self.device = torch.device(device)
+        self.handle = rpod_plan_create(n, m, k, p, q, seed, self.compute, flags)
+        self.ws_bytes = rpod_workspace_bytes(self.handle)
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.ws.data_ptr()) % 256
+        self.ws_ptr = self.ws.data_ptr() + off
+        self.ws[off:off + 256].zero_()
+        self.out_dtype = torch.float64 if self.compute == RPOD_F64 else torch.float32
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                rpod_plan_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    def _stream(self):
+        return _torch().cuda.current_stream(self.device).cuda_stream
+
+    def basis(self, S, S_refine=None, out=None):
+        """Alg. 1 on the column-major n x m tensor S.  Returns (U, sigma, C):
+        U n x k (or n x l), sigma (l,) float64, C k x m (column-major views)."""
+        torch = _torch()
+        ku = self.l if (self.flags & RPOD_FLAG_RETURN_ALL_L) else self.k
+        if out is None:
+            U = empty_colmajor(self.n, ku, self.out_dtype, self.device)
+            sigma = torch.empty(self.l, dtype=torch.float64, device=self.device)
+            C = empty_colmajor(self.k, self.m, self.out_dtype, self.device)
+        else:
+            U, sigma, C = out
+        ref_ptr, ldr = (0, 0)
+        if S_refine is not None:
+            ref_ptr, ldr = S_refine.data_ptr(), colmajor_ld(S_refine)
+        rc = rpod_basis(self.handle, S.data_ptr(), colmajor_ld(S), dtype_code(S.dtype), ref_ptr or None,
+                        ldr, U.data_ptr(), colmajor_ld(U), sigma.data_ptr(), C.data_ptr(),
+                        colmajor_ld(C), self.ws_ptr, self.ws_bytes, self._stream())
+        _check(rc, "rpod_basis")
+        return U, sigma, C
+
+    def project(self, U, S_new, out=None):
+        """C' = U^T S' (kc x m_new, column-major)."""
+        kc = U.shape[1]
+        m_new = S_new.shape[1]
+        C = out if out is not None else empty_colmajor(kc, m_new, self.out_dtype, self.device)
+        rc = rpod_project(self.handle, U.data_ptr(), colmajor_ld(U), kc, S_new.data_ptr(),
+                          colmajor_ld(S_new), m_new, dtype_code(S_new.dtype), C.data_ptr(),
+                          colmajor_ld(C), self.ws_ptr, self.ws_bytes, self._stream())
+        _check(rc, "rpod_project")
+        return C
+
+    def status(self):
+        """(status code, warning flags) after synchronising the stream."""
+        return rpod_status_sync(self.handle, self.ws_ptr, self._stream())
+
+    def launches(self):
+        return rpod_last_launch_count(self.handle)
+
+    def sketch(self, dtype=None):
+        """The plan's Gaussian sketch Lambda (m x l, column-major)."""
+        torch = _torch()
+        dtype = dtype or self.out_dtype
+        Lam = empty_colmajor(self.m, self.l, dtype, self.device)
+        _check(rpod_sketch(self.handle, Lam.data_ptr(), colmajor_ld(Lam), dtype_code(dtype),
+                           self._stream()), "rpod_sketch")
+        return Lam
+
+    def profile(self, enable=True):
+        _check(rpod_profile_enable(self.handle, enable), "rpod_profile_enable")
+
+    def profile_read(self):
+        """(passes, summed pass ms, algorithmic bytes, flops) of the last basis call."""
+        return rpod_profile_read(self.handle)

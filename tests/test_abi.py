@@ -1,0 +1,79 @@
+"""CPU tests of the C ABI boundary: the library builds, loads and exports
+every function declared in include/*.h; host-side argument checks return
+their documented codes without touching a GPU."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import paper_2504_15350_gb300.rpod as R
+from paper_2504_15350_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z][a-z0-9_]*)\s*\(",
+                             src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return R.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "rpod_basis" in names and "rpod_plan_create" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    # the binding declares exactly the header's rpod_ functions
+    assert {n for n in names if n.startswith("rpod_")} <= set(R.SIGNATURES) | {
+        n for n in names if not n.startswith("rpod_")}
+
+
+def test_plan_argument_checks(lib):
+    h = ctypes.c_void_p()
+    bad = [(0, 10, 1, 0, 1), (10, 0, 1, 0, 1), (100, 50, 0, 5, 1), (100, 50, 5, -1, 1),
+           (100, 50, 5, 5, -1), (100, 50, 40, 20, 1), (1000, 1000, 100, 29, 1)]
+    for n, m, k, p, q in bad:
+        assert lib.rpod_plan_create(ctypes.byref(h), n, m, k, p, q, 0, R.RPOD_F32, 0) == R.RPOD_ERR_INVALID_ARG
+    assert lib.rpod_plan_create(ctypes.byref(h), 100, 50, 5, 5, 1, 0, 9, 0) == R.RPOD_ERR_INVALID_ARG
+    assert lib.rpod_plan_create(ctypes.byref(h), 100, 50, 5, 5, 1, 0, R.RPOD_F32, 1 << 9) == R.RPOD_ERR_INVALID_ARG
+    assert lib.rpod_plan_create(None, 100, 50, 5, 5, 1, 0, R.RPOD_F32, 0) == R.RPOD_ERR_INVALID_ARG
+    assert lib.rpod_plan_create(ctypes.byref(h), 100, 50, 100 - 28, 28, 1, 0, R.RPOD_F32, 0) == R.RPOD_ERR_INVALID_ARG
+
+
+def test_workspace_and_pointer_checks(lib):
+    plan = R.rpod_plan_create(4096, 500, 20, 10, 1, 0, R.RPOD_F64)
+    try:
+        ws = R.rpod_workspace_bytes(plan)
+        assert ws > 4096 * 30 * 8
+        fake = 1 << 20
+        # missing workspace, short workspace, misaligned workspace
+        assert R.rpod_basis(plan, fake, 4096, R.RPOD_F64, None, 0, fake, 4096, fake, fake, 20, None, ws, None) == R.RPOD_ERR_WORKSPACE
+        assert R.rpod_basis(plan, fake, 4096, R.RPOD_F64, None, 0, fake, 4096, fake, fake, 20, fake, ws - 1, None) == R.RPOD_ERR_WORKSPACE
+        assert R.rpod_basis(plan, fake, 4096, R.RPOD_F64, None, 0, fake, 4096, fake, fake, 20, fake + 8, ws, None) == R.RPOD_ERR_WORKSPACE
+        # leading dimensions and dtype
+        assert R.rpod_basis(plan, fake, 4095, R.RPOD_F64, None, 0, fake, 4096, fake, fake, 20, fake, ws, None) == R.RPOD_ERR_INVALID_ARG
+        assert R.rpod_basis(plan, fake, 4096, R.RPOD_F64, None, 0, fake, 4096, fake, fake, 19, fake, ws, None) == R.RPOD_ERR_INVALID_ARG
+        assert R.rpod_basis(plan, fake, 4096, R.RPOD_F32, None, 0, fake, 4096, fake, fake, 20, fake, ws, None) == R.RPOD_ERR_INVALID_ARG
+        assert R.rpod_basis(plan, None, 4096, R.RPOD_F64, None, 0, fake, 4096, fake, fake, 20, fake, ws, None) == R.RPOD_ERR_INVALID_ARG
+        assert R.rpod_project(plan, fake, 4096, 31, fake, 4096, 10, R.RPOD_F64, fake, 31, fake, ws, None) == R.RPOD_ERR_INVALID_ARG
+    finally:
+        R.rpod_plan_destroy(plan)
+
+
+def test_strerror_covers_codes(lib):
+    for c in range(9):
+        assert R.rpod_strerror(c) != "unknown status"
+    assert R.rpod_strerror(99) == "unknown status"

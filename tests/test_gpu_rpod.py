@@ -1,0 +1,201 @@
+"""GPU parity tests: librpod (through its C ABI) against the FP64 oracle on
+the same seeded inputs and the same Philox sketch.  Tolerances follow the
+rounding of each form: FP64 sigma within 1e-10 relative and the largest
+principal angle of span(U_k) within 1e-8; FP32 within 1e-5 and 1e-4."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2504_15350_gb300.rpod as R
+from oracle.philox import gaussian_sketch
+from oracle.rpod import project as oracle_project
+from oracle.rpod import rpod as oracle_rpod
+from synth import make_recipe, snapshot_matrix, time_matrix
+from tests.rpod_checks import max_angle, orth_err, sigma_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2504_15350_gb300.build import build
+    build()
+    R.load()
+
+
+def dev(S_cpu, dtype):
+    """Column-major device copy of a column-major host matrix."""
+    return S_cpu.t().contiguous().to(dtype).cuda().t()
+
+
+def lowrank(n, m, J, seed, decay=0.6, scale=10.0):
+    rng = np.random.default_rng(seed)
+    Uq, _ = np.linalg.qr(rng.standard_normal((n, J)))
+    Vq, _ = np.linalg.qr(rng.standard_normal((m, J)))
+    s = scale * decay ** np.arange(J)
+    return torch.from_numpy((Uq * s) @ Vq.T).t().contiguous().t(), Uq, s
+
+
+def run_gpu(S, k, p, q, seed, compute, flags=0):
+    n, m = S.shape
+    plan = R.Plan(n, m, k, p, q, seed=seed, compute=compute, flags=flags)
+    U, sig, C = plan.basis(S)
+    rc, warn = plan.status()
+    torch.cuda.synchronize()
+    return plan, U.double().cpu().numpy(), sig.cpu().numpy(), C.double().cpu().numpy(), rc, warn
+
+
+def check_signs(U):
+    idx = np.argmax(np.abs(U), axis=0)
+    return np.all(U[idx, np.arange(U.shape[1])] >= 0)
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("m,l,seed", [(501, 12, 3), (500, 30, 0), (7, 1, 9)])
+def test_sketch_matches_oracle(m, l, seed):
+    plan = R.Plan(max(m, 64), m, l, 0, 1, seed=seed, compute="f64")
+    lam = plan.sketch(torch.float64).cpu().numpy()
+    ref = gaussian_sketch(seed, m, l, 0)
+    assert np.abs(lam - ref).max() <= 1e-14
+    lam32 = plan.sketch(torch.float32).cpu().numpy()
+    assert np.abs(lam32 - ref).max() <= 4e-7
+
+
+def test_f64_config1_matches_oracle():
+    rec = make_recipe(64, 64, 500, 400, ("power", 1.5), seed=0, noise=1e-6)
+    S = snapshot_matrix(rec)
+    k, p, q = 20, 10, 1
+    o = oracle_rpod(S.numpy(), k, p, q, seed=0)
+    plan, U, sig, C, rc, warn = run_gpu(dev(S, torch.float64), k, p, q, 0, "f64")
+    assert rc == R.RPOD_OK and warn == 0
+    ok, er, ea = sigma_close(sig, o.sigma, 1e-10, 1e-12)
+    assert ok, (er, ea)
+    assert max_angle(o.U[:, :k], U) <= 1e-8
+    assert orth_err(U) <= 1e-12
+    assert check_signs(U)
+    # rows of C agree with the oracle's literal U_k^T S up to the row sign
+    for i in range(k):
+        d = min(np.abs(C[i] - o.C[i]).max(), np.abs(C[i] + o.C[i]).max())
+        assert d <= 1e-9 * o.sigma[0]
+    assert plan.launches() > 10
+
+
+@pytest.mark.parametrize("n,m,k,p,q", [
+    (1000, 333, 7, 5, 2),     # ragged tiles in every dimension
+    (50, 300, 10, 5, 1),      # wide matrix
+    (40, 24, 20, 4, 1),       # l = min(n, m): brute-force equality with the full SVD
+    (300, 200, 1, 0, 0),      # l = 1, q = 0
+    (257, 129, 60, 68, 3),    # l = 128, the one-block limit
+])
+def test_f64_shapes_match_oracle(n, m, k, p, q):
+    rng = np.random.default_rng(n + m)
+    S = torch.from_numpy(rng.standard_normal((n, m)) * np.logspace(0, -2, m)[None, :]).t().contiguous().t()
+    o = oracle_rpod(S.numpy(), k, p, q, seed=5)
+    _, U, sig, C, rc, _ = run_gpu(dev(S, torch.float64), k, p, q, 5, "f64")
+    assert rc == R.RPOD_OK
+    ok, er, ea = sigma_close(sig, o.sigma, 1e-10, 1e-12)
+    assert ok, (er, ea)
+    # compare subspaces only where the spectrum has a gap at k
+    if k < len(o.sigma) and o.sigma[k - 1] > o.sigma[k] * (1 + 1e-6):
+        gap = (o.sigma[k - 1] - o.sigma[k]) / o.sigma[0]
+        assert max_angle(o.U[:, :k], U) <= max(1e-8, 1e-13 / gap)
+    assert orth_err(U) <= 1e-12
+
+
+def test_f64_exact_rank_flags_and_recovers():
+    S, Uq, s = lowrank(600, 250, 5, seed=1)
+    _, U, sig, C, rc, warn = run_gpu(dev(S, torch.float64), 8, 4, 1, 2, "f64")
+    assert rc == R.RPOD_OK
+    assert warn & R.RPOD_WARN_RANK_DEFICIENT
+    assert np.allclose(sig[:5], s, rtol=1e-10)
+    assert np.all(sig[5:] <= 1e-7 * s[0])
+    assert max_angle(Uq, U[:, :5]) <= 1e-8
+
+
+def test_f32_config1_matches_oracle():
+    rec = make_recipe(64, 64, 500, 400, ("power", 1.5), seed=0, noise=1e-6)
+    S = snapshot_matrix(rec)
+    k, p, q = 20, 10, 1
+    o = oracle_rpod(S.float().double().numpy(), k, p, q, seed=0)
+    _, U, sig, C, rc, warn = run_gpu(dev(S, torch.float32), k, p, q, 0, "f32")
+    assert rc == R.RPOD_OK
+    ok, er, ea = sigma_close(sig[:k], o.sigma[:k], 1e-5, 1e-6)
+    assert ok, (er, ea)
+    assert max_angle(o.U[:, :k], U) <= 1e-4
+    assert orth_err(U) <= 1e-5
+    for i in range(k):
+        d = min(np.abs(C[i] - o.C[i]).max(), np.abs(C[i] + o.C[i]).max())
+        assert d <= 1e-5 * o.sigma[0]
+
+
+def test_project_matches_oracle():
+    rec = make_recipe(32, 64, 300, 100, ("power", 1.5), seed=3)
+    S = snapshot_matrix(rec)
+    plan = R.Plan(S.shape[0], S.shape[1], 10, 5, 1, seed=1, compute="f64")
+    Sd = dev(S, torch.float64)
+    U, sig, C = plan.basis(Sd)
+    rec2 = make_recipe(32, 64, 777, 100, ("power", 1.5), seed=4)
+    S2 = snapshot_matrix(rec2)
+    C2 = plan.project(U, dev(S2, torch.float64))
+    ref = oracle_project(U.cpu().numpy(), S2.numpy())
+    assert np.abs(C2.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    # projecting the training data reproduces the coefficients
+    C1 = plan.project(U, Sd)
+    assert np.abs(C1.cpu().numpy() - C.cpu().numpy()).max() <= 1e-10 * sig[0].item()
+
+
+def test_nonfinite_input_reported():
+    rng = np.random.default_rng(0)
+    S = torch.from_numpy(rng.standard_normal((200, 100))).t().contiguous().t()
+    S[17, 33] = float("nan")
+    plan = R.Plan(200, 100, 5, 5, 1, compute="f64")
+    plan.basis(dev(S, torch.float64))
+    rc, _ = plan.status()
+    assert rc == R.RPOD_ERR_NONFINITE
+    # the status word is cleared by the read
+    rng2 = np.random.default_rng(1)
+    plan.basis(dev(torch.from_numpy(rng2.standard_normal((200, 100))).t().contiguous().t(), torch.float64))
+    assert plan.status()[0] == R.RPOD_OK
+
+
+def test_bad_arguments_rejected():
+    plan = R.Plan(100, 50, 5, 5, 1, compute="f32")
+    S = torch.zeros((50, 100), device="cuda").t()
+    with pytest.raises(R.RpodError) as e:
+        plan.basis(S.double())        # dtype mismatch
+    assert e.value.code == R.RPOD_ERR_INVALID_ARG
+    U = torch.empty(1, device="cuda")
+    rc = R.rpod_basis(plan.handle, S.data_ptr(), 100, R.RPOD_F32, None, 0, U.data_ptr(), 100,
+                      U.data_ptr(), U.data_ptr(), 5, plan.ws_ptr, plan.ws_bytes - 256, 0)
+    assert rc == R.RPOD_ERR_WORKSPACE
+
+
+def test_config2_fp32_full_size_properties():
+    """n = 262144 (512 x 512 grid), m = 10000, 400 modes with exp(-j/40)
+    amplitudes, k = 100, p = 20, q = 2, FP32: properties that hold at any size
+    (the oracle cannot run here): Ritz values interlace the closed-form
+    spectrum from below and match it where rPOD has converged, U is
+    orthonormal, and sampled coefficient columns equal U_k^T S."""
+    rec = make_recipe(512, 512, 10000, 400, ("exp", 40.0), seed=0, noise=1e-6)
+    S = snapshot_matrix(rec, device="cuda", dtype=torch.float32)
+    closed = np.sqrt(rec.n) / 2 * np.linalg.svd((time_matrix(rec) * rec.amp[None, :]).T,
+                                                compute_uv=False)
+    k, p, q = 100, 20, 2
+    plan = R.Plan(rec.n, rec.m, k, p, q, seed=0, compute="f32")
+    U, sig, C = plan.basis(S)
+    rc, _ = plan.status()
+    assert rc == R.RPOD_OK
+    sig = sig.cpu().numpy()
+    fp32_floor = 1e-6 * closed[0] + 1e-6 * (np.sqrt(rec.n) + np.sqrt(rec.m))
+    assert np.all(sig[:k] <= closed[:k] + fp32_floor)          # interlacing
+    assert np.all(np.abs(sig[:50] - closed[:50]) <= 1e-5 * closed[:50] + fp32_floor)
+    Uh = U.double().cpu().numpy()
+    assert orth_err(Uh) <= 2e-5
+    cols = np.random.default_rng(0).choice(rec.m, 16, replace=False)
+    Scols = S[:, cols].double().cpu().numpy()
+    ref = oracle_project(Uh, Scols)
+    Cg = C[:, cols].double().cpu().numpy()
+    err = np.abs(Cg - ref).max(axis=0) / np.linalg.norm(Scols, axis=0)
+    assert np.all(err <= 2e-5)
+    del S
+    torch.cuda.empty_cache()
