@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""rPOD time-to-basis benchmark (Alg. 1, Sec. 4.2) on GB300.
+
+Workload: one randomized POD of an FP32 snapshot matrix with n = 262144 rows
+(512 x 512 grid) and m = 10000 snapshots of 400 synthetic modes with
+amplitudes exp(-j/40) (10.5 GB, column-major, resident in HBM), k = 100,
+p = 20, q = 2.  A step is one full rpod_basis call: sketch, every pass over S,
+CholeskyQR, T = Q^T S, the small SVD, lift, signs and coefficients.
+
+Forms: "bf16" (16-bit tensor-core passes with the FP32 refinement pass; the
+FP32 input is converted during the first pass) and "f32" (plain FP32 SIMT
+passes); --form picks the headline, the other is timed beside it when
+available.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own replica (weak scaling, no collective
+on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(nx=512, ny=512, m=10000, J=400, decay=("exp", 40.0), k=100, p=20, q=2,
+                seed=0, noise=1e-6)
+WORKLOAD_NAME = ("rPOD of FP32 snapshot matrix n=262144 (512x512 grid) x m=10000, "
+                 "400 modes exp(-j/40), k=100 p=20 q=2")
+METRIC = "rPOD time-to-basis (s)"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+CPU_SAMPLE_ROWS = (4096, 8192)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="auto", choices=["auto", "bf16", "f32"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ny", type=int, default=512,
+                    help="grid rows (n = 512 * ny); smaller values make the small profiling case")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_sha(*names):
+    h = hashlib.sha256()
+    for n in names:
+        h.update(open(os.path.join(ROOT, "paper_2504_15350_gb300", "csrc", n), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(form: str):
+    """Per-launch DRAM bytes of the dominant pass kernel from profiles/traffic.txt
+    (lines: form sha16 bytes_per_launch kernel), valid only while the kernel
+    source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = source_sha(*(["rpod_tc.cu"] if form == "bf16" else ["rpod_simt.cu"]))
+    for ln in open(path):
+        f = ln.split()
+        if len(f) >= 3 and not ln.startswith("#") and f[0] == form and f[1] == want:
+            return float(f[2])
+    return None
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_time(rows: int) -> float:
+    """Seconds the FP64 oracle takes for Alg. 1 on the first `rows` grid cells
+    of the workload (all m snapshots).  Runs in this process (the caller
+    spawns a fresh interpreter)."""
+    import numpy as np
+    from oracle.rpod import rpod as oracle_rpod
+    from synth import make_recipe, snapshot_matrix
+    w = WORKLOAD
+    rec = make_recipe(w["nx"], w["ny"], w["m"], w["J"], w["decay"], seed=w["seed"], noise=w["noise"])
+    S = snapshot_matrix(rec, rows=np.arange(rows), dtype=__import__("torch").float32).double().numpy()
+    t0 = time.perf_counter()
+    oracle_rpod(S, w["k"], w["p"], w["q"], seed=w["seed"])
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(samples=CPU_SAMPLE_ROWS, repeats=1):
+    """Times the oracle in a spawned interpreter at two row counts and
+    extrapolates linearly in n (passes, QR of Y, lift and C scale with n;
+    the Jacobi SVD of T and the QR of Z do not)."""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps([min(bench.cpu_oracle_time(r) for _ in range(%d)) for r in %r]))"
+            % (ROOT, repeats, list(samples)))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=1800)
+    if out.returncode != 0:
+        return None, out.stderr[-500:]
+    t = json.loads(out.stdout.strip().splitlines()[-1])
+    n = WORKLOAD["nx"] * WORKLOAD["ny"]
+    n1, n2 = samples
+    slope = (t[1] - t[0]) / (n2 - n1)
+    est = t[1] + slope * (n - n2)
+    return {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"FP64 oracle (numpy, default BLAS threads) on the first {n1} and {n2} of the "
+                       f"{n} rows, all {WORKLOAD['m']} snapshots: {t[0]:.2f} s and {t[1]:.2f} s, "
+                       f"extrapolated linearly in n to the full matrix")}, None
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import numpy as np
+    n = WORKLOAD["nx"] * WORKLOAD["ny"]
+    n1, n2 = CPU_SAMPLE_ROWS
+    # warm-up steps at both sample sizes give the slope of the linear model
+    t1 = min(cpu_oracle_time(n1) for _ in range(max(1, args.warmup // 2)))
+    t2w = min(cpu_oracle_time(n2) for _ in range(max(1, args.warmup - args.warmup // 2)))
+    times = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s = time.perf_counter()
+        cpu_oracle_time(n2)
+        times.append(time.perf_counter() - s)
+    total = time.perf_counter() - t0
+    step = total / args.steps
+    slope = (t2w - t1) / (n2 - n1)
+    value = step + slope * (n - n2)
+    line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD_NAME, "sample_rows": n2, "l2": "host run"},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": (f"each step: FP64 oracle on the first {n2} of {n} rows (all "
+                                        f"{WORKLOAD['m']} snapshots); value extrapolated linearly in "
+                                        f"n with the slope from warm-up runs at {n1} and {n2} rows")},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        # the oracle runs in a spawned interpreter before any CUDA work here
+        cpu, cpu_err = cpu_baseline()
+    else:
+        cpu, cpu_err = None, None
+
+    import torch
+    import torch.distributed as dist
+    import paper_2504_15350_gb300.rpod as R
+    from paper_2504_15350_gb300.build import build
+    from synth import make_recipe, snapshot_matrix
+
+    build()
+    R.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item()
+
+    w = dict(WORKLOAD)
+    w["ny"] = args.ny
+    rec = make_recipe(w["nx"], w["ny"], w["m"], w["J"], w["decay"], seed=w["seed"], noise=w["noise"])
+    n, m, k, p, q, l = rec.n, rec.m, w["k"], w["p"], w["q"], w["k"] + w["p"]
+    S = snapshot_matrix(rec, device=dev, dtype=torch.float32)
+    torch.cuda.synchronize()
+
+    forms = []
+    have_tc = True
+    try:
+        probe = R.Plan(256, 256, 4, 4, 1, compute="bf16", flags=R.RPOD_FLAG_REFINE_FP32, device=dev)
+        tmp = torch.zeros((256, 256), device=dev).t()
+        probe.basis(tmp)
+    except R.RpodError as e:
+        have_tc = e.code != R.RPOD_ERR_UNSUPPORTED
+    head = args.form if args.form != "auto" else ("bf16" if have_tc else "f32")
+    forms = [head] + [f for f in ("bf16", "f32") if f != head and (f != "bf16" or have_tc)]
+
+    peaks, peak_src = load_peaks()
+    results = {}
+    for form in forms:
+        if form == "bf16":
+            plan = R.Plan(n, m, k, p, q, seed=w["seed"], compute="bf16", flags=R.RPOD_FLAG_REFINE_FP32,
+                          device=dev)
+        else:
+            plan = R.Plan(n, m, k, p, q, seed=w["seed"], compute="f32", device=dev)
+        U = R.empty_colmajor(n, k, torch.float32, dev)
+        sig = torch.empty(l, dtype=torch.float64, device=dev)
+        C = R.empty_colmajor(k, m, torch.float32, dev)
+        out = (U, sig, C)
+        for _ in range(args.warmup):
+            plan.basis(S, out=out)
+        rc, _ = plan.status()
+        if rc != R.RPOD_OK:
+            raise RuntimeError(f"{form}: device status {R.rpod_strerror(rc)}")
+        steps = args.steps if form == head else max(3, min(args.steps, 5))
+        plan.profile(True)
+        stream = torch.cuda.current_stream(dev)
+        barrier()
+        torch.cuda.synchronize()
+        clk = ClockSampler(local) if form == head else None
+        if clk:
+            clk.start()
+            time.sleep(0.5)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.basis(S, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        clocks = clk.stop() if clk else None
+        passes, pass_ms, pbytes, pflops = plan.profile_read()
+        plan.profile(False)
+        launches = plan.launches()
+        rc, _ = plan.status()
+        if rc != R.RPOD_OK:
+            raise RuntimeError(f"{form}: device status {R.rpod_strerror(rc)}")
+        ms = max_over_ranks(ms)
+        results[form] = dict(ms=ms, passes=passes, pass_ms=pass_ms, bytes=pbytes, flops=pflops,
+                             launches=launches, steps=steps, clocks=clocks, plan=plan, out=out,
+                             sigma=sig.cpu().numpy().tolist()[:5])
+    hr = results[head]
+    # roofline of the dominant kernel: the passes over S
+    per_ms = hr["pass_ms"] / hr["passes"]
+    per_bytes = hr["bytes"] / hr["passes"]
+    per_flops = hr["flops"] / hr["passes"]
+    if head == "bf16":
+        peak = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
+        ach = per_bytes / (per_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "peak_source": f"{peak_src} hbm_gbs", "kernel": "passes over S (tcgen05)"}
+    else:
+        mhz = (hr["clocks"] or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        ach = per_flops / (per_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "peak_source": f"FP32 FFMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
+                               f"{mhz:.0f} MHz (median SM clock under load)",
+                "kernel": "passes over S (SIMT FP32 GEMM)",
+                "achieved_hbm_gbs": per_bytes / (per_ms * 1e-3) / 1e9}
+    roof["traffic"] = recorded_traffic(head)
+    roof["pass_ms_avg"] = per_ms
+    roof["passes_per_step"] = hr["passes"] / hr["steps"]
+
+    # end to end through the public API: pinned host S in, U/sigma/C out
+    e2e = None
+    if not args.no_e2e:
+        plan = hr["plan"]
+        U, sig, C = hr["out"]
+        S_host = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
+        S_host.copy_(S.t())
+        U_h = torch.empty((k, n), dtype=torch.float32, pin_memory=True)
+        s_h = torch.empty(l, dtype=torch.float64, pin_memory=True)
+        C_h = torch.empty((m, k), dtype=torch.float32, pin_memory=True)
+        St = S.t()
+        stream = torch.cuda.current_stream(dev)
+
+        def e2e_step():
+            St.copy_(S_host, non_blocking=True)
+            plan.basis(S, out=(U, sig, C))
+            U_h.copy_(U.t(), non_blocking=True)
+            s_h.copy_(sig, non_blocking=True)
+            C_h.copy_(C.t(), non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ems = max_over_ranks(a0.elapsed_time(a1) / args.e2e_steps)
+        e2e = {"value": ems / 1e3, "unit": "s", "h2d_bytes_per_step": 4 * n * m,
+               "d2h_bytes_per_step": 4 * n * k + 8 * l + 4 * k * m, "steps": args.e2e_steps}
+        del S_host
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": hr["ms"] / 1e3, "unit": "s", "n_gpus": world,
+        "steps": hr["steps"], "warmup": args.warmup, "ms_per_step": hr["ms"],
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16+f32-refine" if head == "bf16" else "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME if args.ny == 512 else
+                   f"reduced profiling case: {WORKLOAD_NAME} with n={n} (512x{args.ny} grid)",
+                   "n": n, "m": m, "k": k, "p": p, "q": q,
+                   "form": head, "l2": "inputs larger than L2 (S is 10.5 GB)",
+                   "replicas": world},
+        "roofline": roof,
+        "cpu_baseline": cpu if cpu else ({"value": None, "error": cpu_err} if cpu_err else None),
+        "e2e": e2e,
+        "gpu_launches": hr["launches"] * hr["steps"],
+        "clocks": hr["clocks"],
+        "throughput_rpod_per_s": world / (hr["ms"] / 1e3),
+    }
+    for f, r in results.items():
+        if f != head:
+            line[f"{f}_time_to_basis_s"] = r["ms"] / 1e3
+            line[f"{f}_pass_ms_avg"] = r["pass_ms"] / r["passes"]
+    if "f32" in results and head == "bf16":
+        line["speedup_vs_f32_plain"] = results["f32"]["ms"] / hr["ms"]
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -120,12 +120,22 @@ int rpod_project(const rpod_plan* plan, const void* U, int64_t ldu, int32_t kc,
  * buffer Lam.  Same Philox counters as rpod_basis. */
 int rpod_sketch(const rpod_plan* plan, void* Lam, int64_t ld, int32_t dtype, void* stream);
 
-/* Pass profiling.  When enabled, rpod_basis records CUDA events on its stream
- * around every pass over S (the products S Lambda, S^T Q, S Z and Q^T S).
- * rpod_profile_read synchronises on the last recorded event and returns, for
- * the last rpod_basis call, the number of passes, their summed device time in
- * ms and the algorithmic bytes and flops of all passes (bytes of S read or
- * written plus the skinny operands; 2 n m l flops per product). */
+/* The sampled matrix of Alg. 1 (second step) for a caller-given sketch, on
+ * the tensor-core path of a 16-bit plan: Y = S A with S n x m (ld lds) and
+ * A m x l (ld lda >= m), both of the plan's 16-bit type, Y n x l FP32
+ * (ld ldy >= n).  S must start on a 16-byte boundary with lds * 2 a multiple
+ * of 16 (else RPOD_ERR_UNSUPPORTED).  Uses the workspace. */
+int rpod_sample(const rpod_plan* plan, const void* A, int64_t lda, const void* S, int64_t lds,
+                int32_t s_dtype, float* Y, int64_t ldy, void* workspace,
+                size_t workspace_bytes, void* stream);
+
+/* Pass profiling.  rpod_profile_enable(plan, 1) creates CUDA events and
+ * resets the counters; from then on rpod_basis records events on its stream
+ * around every pass over S (the products S Lambda, S^T Q, S Z and Q^T S), up
+ * to 64 passes in total.  rpod_profile_read synchronises on the last recorded
+ * event and returns, summed over the recorded passes, their number, their
+ * device time in ms and their algorithmic bytes and flops (bytes of S and of
+ * the skinny operands read or written; 2 n m l flops per product). */
 int rpod_profile_enable(rpod_plan* plan, int enable);
 int rpod_profile_read(const rpod_plan* plan, int* passes, double* pass_ms, double* bytes,
                       double* flops);

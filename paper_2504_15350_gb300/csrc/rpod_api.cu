@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 
 #include "rpod_internal.cuh"
@@ -23,9 +24,13 @@ struct rpod_plan {
   uint32_t flags;
   // workspace layout (byte offsets)
   size_t off_status, off_lam, off_y, off_q, off_z, off_zq, off_tt, off_part, off_gpart, off_g,
-      off_x, off_xw, off_eig, off_sigma, off_uhat, off_sign, off_lowp, total;
-  int nsplit_z, nsplit_g, nsplit_t;
-  size_t part_elems, gpart_elems, sign_bytes;
+      off_x, off_xw, off_eig, off_sigma, off_uhat, off_sign, total;
+  // tensor-core forms: 16-bit copy of S, 16-bit operands (128 columns, zero
+  // padded), TF32-rounded basis, split-K partials of the W-pass
+  size_t off_sb, off_qb, off_zb, off_atf, off_wpart;
+  int64_t n_ld, m_ld;
+  int nsplit_z, nsplit_t, nsplit_w;
+  size_t part_elems, gpart_elems, sign_bytes, wpart_elems;
   int last_launches;
   // pass profiling
   int prof_on;
@@ -53,15 +58,6 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int elem_size(int dt) {
-  switch (dt) {
-    case RPOD_F64: return 8;
-    case RPOD_F32: return 4;
-    case RPOD_BF16: case RPOD_F16: return 2;
-    default: return 0;
-  }
-}
-
 bool is16(int dt) { return dt == RPOD_BF16 || dt == RPOD_F16; }
 
 int splits_for(int64_t K, int64_t chunk, int maxs) {
@@ -71,16 +67,23 @@ int splits_for(int64_t K, int64_t chunk, int maxs) {
   return (int)s;
 }
 
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
 #define CK(x)                                        \
   do {                                               \
     cudaError_t e_ = (x);                            \
     if (e_ != cudaSuccess) return RPOD_ERR_CUDA;     \
   } while (0)
+#define CR(x)                                        \
+  do {                                               \
+    int r_ = (x);                                    \
+    if (r_ != RPOD_OK) return r_;                    \
+  } while (0)
 
 // ---------------------------------------------------------------------------
-// SIMT pipeline on working type W (double for RPOD_F64, float for RPOD_F32).
+// Pipelines on working type W (double for RPOD_F64, float otherwise).
 template <typename W>
-struct SimtRun {
+struct Run {
   rpod_plan* P;
   char* ws;
   cudaStream_t st;
@@ -89,17 +92,18 @@ struct SimtRun {
   W* buf(size_t off) { return (W*)(ws + off); }
   double* dbuf(size_t off) { return (double*)(ws + off); }
 
-  // Gram G = A^T A (A rows x l, ld = rows) in FP64 (products in W, summed in
-  // W over chunks, then in FP64)
+  // Gram G = A^T A (A rows x l, ld lda) in FP64: products in W, summed in W
+  // within a split of rows, then in FP64 across splits.
   int gram(const W* A, int64_t rows, int64_t lda, double* G, int nsplit) {
     const int l = P->l;
-    CK((gemm<W, W, W, double>(st, true, l, l, rows, nsplit, A, lda, A, lda, dbuf(P->off_gpart), 1, l,
-                              (int64_t)l * l, status, false)));
+    CK((gemm<W, W, W, double>(st, true, l, l, rows, nsplit, A, lda, A, lda, dbuf(P->off_gpart), 1,
+                              l, (int64_t)l * l, status, false)));
     CK((reduce_splits<double, double>(st, l, l, nsplit, dbuf(P->off_gpart), G, 1, l)));
-    return 0;
+    return RPOD_OK;
   }
 
-  // CholeskyQR with `rounds` passes: returns the buffer holding Q (in or tmp)
+  // CholeskyQR with `rounds` passes (CholeskyQR2 for rounds = 2); returns the
+  // buffer holding Q (in or tmp).
   int orth(W* in, W* tmp, int64_t rows, int rounds, W** out) {
     const int l = P->l;
     const double tol = sizeof(W) == 8 ? 1e-13 : 1e-5;
@@ -109,20 +113,41 @@ struct SimtRun {
     W* dst = tmp;
     for (int r = 0; r < rounds; ++r) {
       double* G = dbuf(P->off_g);
-      if (int rc = gram(src, rows, rows, G, ns)) return rc;
-      CK((cholesky<W>(st, l, G, tol, nullptr, dbuf(P->off_x), buf(P->off_xw), l, status)));
+      CR(gram(src, rows, rows, G, ns));
+      CK((cholesky<W>(st, l, G, tol, r, dbuf(P->off_x), buf(P->off_xw), l, status)));
       CK((gemm<W, W, W, W>(st, false, rows, l, l, 1, src, rows, buf(P->off_xw), l, dst, 1, rows, 0,
                            status, false)));
       W* t = src; src = dst; dst = t;
     }
     *out = src;
-    return 0;
+    return RPOD_OK;
   }
 
-  int run(const W* S, int64_t lds, const W* Sref, int64_t ldr, W* U, int64_t ldu, double* sigma,
-          W* C, int64_t ldc) {
+  // After T (as Tt, m x l): small SVD, lift, signs, coefficients.
+  int finish(const W* Q, const W* Tt, W* U, int64_t ldu, double* sigma, W* C, int64_t ldc) {
     const int64_t n = P->n, m = P->m;
-    const int l = P->l, k = P->k, q = P->q;
+    const int l = P->l, k = P->k;
+    // Alg. 1: SVD of T via the eigenpairs of T T^T (FP64 Gram)
+    double* GT = dbuf(P->off_g);
+    const int ns = P->nsplit_t;
+    CK((gemm<W, W, W, double>(st, true, l, l, m, ns, Tt, m, Tt, m, dbuf(P->off_gpart), 1, l,
+                              (int64_t)l * l, status, false)));
+    CK((reduce_splits<double, double>(st, l, l, ns, dbuf(P->off_gpart), GT, 1, l)));
+    double* Uhat = dbuf(P->off_uhat);
+    CK((sym_eig(st, l, GT, sigma, Uhat, dbuf(P->off_eig), status, 4)));
+    CK((check_finite_vec(st, l, sigma, status)));
+    // Alg. 1: lift U = Q Uhat (first k or all l columns), then the sign rule
+    const int ku = (P->flags & RPOD_FLAG_RETURN_ALL_L) ? l : k;
+    CK((gemm<W, double, W, W>(st, false, n, ku, l, 1, Q, n, Uhat, l, U, 1, ldu, 0, status, false)));
+    CK((sign_fix<W>(st, n, ku, U, ldu, Uhat, l, ws + P->off_sign, P->sign_bytes)));
+    // Sec. 4.3 coefficients C = U_k^T S = Uhat_k^T T (k x m)
+    CK((gemm<W, double, W, W>(st, false, m, k, l, 1, Tt, m, Uhat, l, C, ldc, 1, 0, status, false)));
+    return RPOD_OK;
+  }
+
+  int run(const W* S, int64_t lds, W* U, int64_t ldu, double* sigma, W* C, int64_t ldc) {
+    const int64_t n = P->n, m = P->m;
+    const int l = P->l, q = P->q;
     W* Lam = buf(P->off_lam);
     W* Y = buf(P->off_y);
     W* Qb = buf(P->off_q);
@@ -130,12 +155,11 @@ struct SimtRun {
     W* Zq = buf(P->off_zq);
     W* Tt = buf(P->off_tt);
     W* part = buf(P->off_part);
-    // Alg. 1: Gaussian sketch
-    CK((sketch<W>(st, P->seed, 0, m, l, Lam, m)));
     const double sw = sizeof(W);
     const double pass_bytes = sw * ((double)n * m + (double)n * l + (double)m * l);
     const double pass_flops = 2.0 * n * m * l;
-    P->prof_n = 0; P->prof_bytes = 0; P->prof_flops = 0;
+    // Alg. 1: Gaussian sketch
+    CK((sketch<W>(st, P->seed, 0, m, l, Lam, m)));
     // Alg. 1: P = S Lambda (pass over S; flags non-finite input)
     prof_begin(P, st);
     CK((gemm<W, W, W, W>(st, false, n, l, m, 1, S, lds, Lam, m, Y, 1, n, 0, status, true)));
@@ -150,41 +174,120 @@ struct SimtRun {
         prof_end(P, st, pass_bytes, pass_flops);
         CK((reduce_splits<W, W>(st, m, l, P->nsplit_z, part, Z, 1, m)));
         W* Zo = nullptr;
-        if (int rc = orth(Z, Zq, m, 1, &Zo)) return rc;
+        CR(orth(Z, Zq, m, 1, &Zo));
         prof_begin(P, st);
         CK((gemm<W, W, W, W>(st, false, n, l, m, 1, S, lds, Zo, m, Y, 1, n, 0, status, false)));
         prof_end(P, st, pass_bytes, pass_flops);
       }
-      // Alg. 1 QR of the sampled matrix (CholeskyQR2 for the final basis)
-      W* Qo = nullptr;
-      if (int rc = orth(Y, Qb, n, it == q ? 2 : 1, &Qo)) return rc;
-      Q = Qo;  // Y's buffer is free again once Z = S^T Q is formed
+      // Alg. 1 QR of the sampled matrix (CholeskyQR2 for the final basis);
+      // Y's buffer is free again once Z = S^T Q is formed
+      CR(orth(Y, Qb, n, it == q ? 2 : 1, &Q));
     }
     // Alg. 1: T = Q^T S, stored transposed (m x l)
-    const W* ST = Sref ? Sref : S;
-    const int64_t ldt = Sref ? ldr : lds;
     prof_begin(P, st);
-    CK((gemm<W, W, W, W>(st, true, m, l, n, P->nsplit_z, ST, ldt, Q, n, part, 1, m, m * l, status,
+    CK((gemm<W, W, W, W>(st, true, m, l, n, P->nsplit_z, S, lds, Q, n, part, 1, m, m * l, status,
                          false)));
     prof_end(P, st, pass_bytes, pass_flops);
     CK((reduce_splits<W, W>(st, m, l, P->nsplit_z, part, Tt, 1, m)));
-    // Alg. 1: SVD of T via the eigenpairs of T T^T (FP64 Gram)
-    double* GT = dbuf(P->off_g);
-    {
-      const int ns = P->nsplit_t;
-      CK((gemm<W, W, W, double>(st, true, l, l, m, ns, Tt, m, Tt, m, dbuf(P->off_gpart), 1, l,
-                                (int64_t)l * l, status, false)));
-      CK((reduce_splits<double, double>(st, l, l, ns, dbuf(P->off_gpart), GT, 1, l)));
+    return finish(Q, Tt, U, ldu, sigma, C, ldc);
+  }
+
+  // Tensor-core form (W = float): passes over a 16-bit S on tcgen05, the
+  // final T = Q^T S on TF32 from an FP32 copy when refining.
+  int run_tc(const void* S_in, int64_t lds_in, int s_dtype, const float* Sref, int64_t ldr,
+             float* U, int64_t ldu, double* sigma, float* C, int64_t ldc) {
+    const int64_t n = P->n, m = P->m;
+    const int l = P->l, q = P->q;
+    const int dt = P->compute;  // RPOD_BF16 or RPOD_F16
+    float* Y = (float*)buf(P->off_y);
+    float* Qbuf = (float*)buf(P->off_q);
+    float* Z = (float*)buf(P->off_z);
+    float* Zq = (float*)buf(P->off_zq);
+    float* Tt = (float*)buf(P->off_tt);
+    float* wpart = (float*)(ws + P->off_wpart);
+    void* Qh = ws + P->off_qb;   // n_ld x 128, 16-bit
+    void* Zh = ws + P->off_zb;   // m_ld x 128, 16-bit
+    const int64_t nld = P->n_ld, mld = P->m_ld;
+    // 16-bit operand buffers: zero the padding columns l..127 once per call
+    CK(cudaMemsetAsync(Qh, 0, (size_t)nld * 128 * 2, st));
+    CK(cudaMemsetAsync(Zh, 0, (size_t)mld * 128 * 2, st));
+    // the 16-bit S read by the passes
+    const void* Sh = S_in;
+    int64_t ldh = lds_in;
+    const double pass_flops = 2.0 * n * m * l;
+    const double pb16 = 2.0 * ((double)n * m + (double)n * l + (double)m * l);
+    if (s_dtype == RPOD_F32) {
+      prof_begin(P, st);
+      if (dt == RPOD_BF16)
+        CK(convert_snapshots<__nv_bfloat16>(st, n, m, (const float*)S_in, lds_in,
+                                            (__nv_bfloat16*)(ws + P->off_sb), nld, status));
+      else
+        CK(convert_snapshots<__half>(st, n, m, (const float*)S_in, lds_in, (__half*)(ws + P->off_sb),
+                                     nld, status));
+      prof_end(P, st, 6.0 * (double)n * m, 0.0);
+      Sh = ws + P->off_sb;
+      ldh = nld;
+      if (!Sref) { Sref = (const float*)S_in; ldr = lds_in; }
     }
-    double* Uhat = dbuf(P->off_uhat);
-    CK((sym_eig(st, l, GT, sigma, Uhat, dbuf(P->off_eig), status, 3)));
-    // Alg. 1: lift U = Q Uhat (first k or all l columns), then the sign rule
-    const int ku = (P->flags & RPOD_FLAG_RETURN_ALL_L) ? l : k;
-    CK((gemm<W, double, W, W>(st, false, n, ku, l, 1, Q, n, Uhat, l, U, 1, ldu, 0, status, false)));
-    CK((sign_fix<W>(st, n, ku, U, ldu, Uhat, l, ws + P->off_sign, P->sign_bytes)));
-    // Sec. 4.3 coefficients C = U_k^T S = Uhat_k^T T (k x m)
-    CK((gemm<W, double, W, W>(st, false, m, k, l, 1, Tt, m, Uhat, l, C, ldc, 1, 0, status, false)));
-    return 0;
+    auto to16 = [&](const float* src, int64_t rows, int64_t ldsrc, void* dst, int64_t ldd) -> cudaError_t {
+      if (dt == RPOD_BF16)
+        return convert_matrix<float, __nv_bfloat16>(st, rows, l, src, ldsrc, (__nv_bfloat16*)dst, ldd);
+      return convert_matrix<float, __half>(st, rows, l, src, ldsrc, (__half*)dst, ldd);
+    };
+    // Alg. 1: Gaussian sketch, directly in the 16-bit operand layout
+    if (dt == RPOD_BF16)
+      CK((sketch<__nv_bfloat16>(st, P->seed, 0, m, l, (__nv_bfloat16*)Zh, mld)));
+    else
+      CK((sketch<__half>(st, P->seed, 0, m, l, (__half*)Zh, mld)));
+    // Alg. 1: P = S Lambda
+    prof_begin(P, st);
+    CR(tc_ypass(st, dt, Zh, mld, Sh, ldh, n, m, l, Y, n, status));
+    prof_end(P, st, pb16, pass_flops);
+    float* Q = nullptr;
+    for (int it = 0; it <= q; ++it) {
+      if (it > 0) {
+        // Alg. 1 subspace iteration: Z = S^T Q, orthonormalise, Y = S Z
+        prof_begin(P, st);
+        CR(tc_wpass(st, dt, Qh, nld, n, l, Sh, ldh, m, wpart, P->nsplit_w, status));
+        prof_end(P, st, pb16, pass_flops);
+        CK((reduce_splits<float, float>(st, m, l, P->nsplit_w, wpart, Z, 1, m)));
+        float* Zo = nullptr;
+        CR(orth(Z, Zq, m, 1, &Zo));
+        CK(to16(Zo, m, m, Zh, mld));
+        prof_begin(P, st);
+        CR(tc_ypass(st, dt, Zh, mld, Sh, ldh, n, m, l, Y, n, status));
+        prof_end(P, st, pb16, pass_flops);
+      }
+      CR(orth(Y, Qbuf, n, it == q ? 2 : 1, &Q));
+      if (it < q) CK(to16(Q, n, n, Qh, nld));
+    }
+    // Alg. 1: T = Q^T S (TF32 from the FP32 copy when refining)
+    const bool refine = (P->flags & RPOD_FLAG_REFINE_FP32) && Sref;
+    const bool ref_tma = refine && (((uintptr_t)Sref & 15) == 0) && ((ldr * 4) % 16 == 0);
+    if (refine && !ref_tma) {
+      // FP32 copy not addressable by TMA: the SIMT FP32 pass computes T
+      prof_begin(P, st);
+      CK((gemm<float, float, float, float>(st, true, m, l, n, P->nsplit_z, Sref, ldr, Q, n,
+                                           (float*)buf(P->off_part), 1, m, m * l, status, false)));
+      prof_end(P, st, 4.0 * ((double)n * m + (double)n * l + (double)m * l), pass_flops);
+      CK((reduce_splits<float, float>(st, m, l, P->nsplit_z, (float*)buf(P->off_part), Tt, 1, m)));
+      return finish(Q, Tt, U, ldu, sigma, C, ldc);
+    }
+    if (refine) {
+      float* Atf = (float*)(ws + P->off_atf);
+      CK(cudaMemsetAsync(Atf, 0, (size_t)n * 128 * 4, st));
+      CK(round_tf32(st, n, l, Q, n, Atf, n));
+      prof_begin(P, st);
+      CR(tc_wpass(st, RPOD_F32, Atf, n, n, l, Sref, ldr, m, wpart, P->nsplit_w, status));
+      prof_end(P, st, 4.0 * ((double)n * m + (double)n * l + (double)m * l), pass_flops);
+    } else {
+      CK(to16(Q, n, n, Qh, nld));
+      prof_begin(P, st);
+      CR(tc_wpass(st, dt, Qh, nld, n, l, Sh, ldh, m, wpart, P->nsplit_w, status));
+      prof_end(P, st, pb16, pass_flops);
+    }
+    CK((reduce_splits<float, float>(st, m, l, P->nsplit_w, wpart, Tt, 1, m)));
+    return finish(Q, Tt, U, ldu, sigma, C, ldc);
   }
 
   int project(const W* U, int64_t ldu, int kc, const W* Sn, int64_t lds, int64_t mn, W* C,
@@ -201,7 +304,32 @@ struct SimtRun {
                            mc * kc, status, false)));
       CK((reduce_splits<W, W>(st, mc, kc, P->nsplit_z, part, C + j0 * ldc, ldc, 1)));
     }
-    return 0;
+    return RPOD_OK;
+  }
+
+  // 16-bit S': the W-pass with U converted to the 16-bit operand layout.
+  int project_tc(const float* U, int64_t ldu, int kc, const void* Sn, int64_t lds, int64_t mn,
+                 float* C, int64_t ldc) {
+    const int64_t n = P->n;
+    const int dt = P->compute;
+    void* Qh = ws + P->off_qb;
+    float* wpart = (float*)(ws + P->off_wpart);
+    CK(cudaMemsetAsync(Qh, 0, (size_t)P->n_ld * 128 * 2, st));
+    if (dt == RPOD_BF16)
+      CK((convert_matrix<float, __nv_bfloat16>(st, n, kc, U, ldu, (__nv_bfloat16*)Qh, P->n_ld)));
+    else
+      CK((convert_matrix<float, __half>(st, n, kc, U, ldu, (__half*)Qh, P->n_ld)));
+    const int64_t per = (int64_t)(P->wpart_elems / ((size_t)64 * (size_t)kc));
+    const int64_t cols = std::max<int64_t>(256, per / 256 * 256);
+    for (int64_t j0 = 0; j0 < mn; j0 += cols) {
+      const int64_t mc = std::min(mn - j0, cols);
+      const int ns = tc_wpass_splits(n, mc, dt);
+      if ((size_t)ns * kc * mc > P->wpart_elems) return RPOD_ERR_WORKSPACE;
+      CR(tc_wpass(st, dt, Qh, P->n_ld, n, kc, (const char*)Sn + (size_t)j0 * lds * 2, lds, mc, wpart,
+                  ns, status));
+      CK((reduce_splits<float, float>(st, mc, kc, ns, wpart, C + j0 * ldc, ldc, 1)));
+    }
+    return RPOD_OK;
   }
 };
 
@@ -233,6 +361,7 @@ int rpod_plan_create(rpod_plan** out, int64_t n, int64_t m, int32_t k, int32_t p
     return RPOD_ERR_INVALID_ARG;
   if (compute < RPOD_F64 || compute > RPOD_F16) return RPOD_ERR_INVALID_ARG;
   if (flags & ~(uint32_t)(RPOD_FLAG_REFINE_FP32 | RPOD_FLAG_RETURN_ALL_L)) return RPOD_ERR_INVALID_ARG;
+  if (n > ((int64_t)1 << 31) - 1024 || m > ((int64_t)1 << 31) - 1024) return RPOD_ERR_UNSUPPORTED;
   rpod_plan* P = new (std::nothrow) rpod_plan();
   if (!P) return RPOD_ERR_INVALID_ARG;
   P->n = n; P->m = m; P->k = k; P->p = p; P->q = q; P->l = (int)l;
@@ -263,12 +392,20 @@ int rpod_plan_create(rpod_plan** out, int64_t n, int64_t m, int32_t k, int32_t p
   P->off_sigma = take(8 * L);
   P->off_uhat = take(8 * L * L);
   P->off_sign = take(P->sign_bytes);
-  P->off_lowp = 0;
+  P->n_ld = round_up(n, 64);
+  P->m_ld = round_up(m, 64);
+  P->off_sb = P->off_qb = P->off_zb = P->off_atf = P->off_wpart = 0;
+  P->nsplit_w = 0;
+  P->wpart_elems = 0;
   if (is16(compute)) {
-    if (int rc = tc_plan_extend(P->n, P->m, P->l, compute, &off, &P->off_lowp)) {
-      delete P;
-      return rc;
-    }
+    P->nsplit_w = std::max(tc_wpass_splits(n, m, compute), tc_wpass_splits(n, m, RPOD_F32));
+    // room for the project of up to 64 splits x 256 snapshots as well
+    P->wpart_elems = std::max((size_t)P->nsplit_w * L * m, (size_t)64 * L * 256);
+    P->off_sb = take((size_t)2 * P->n_ld * m);
+    P->off_qb = take((size_t)2 * P->n_ld * 128);
+    P->off_zb = take((size_t)2 * P->m_ld * 128);
+    P->off_atf = take((size_t)4 * n * 128);
+    P->off_wpart = take(4 * P->wpart_elems);
   }
   P->total = off;
   P->last_launches = 0;
@@ -281,6 +418,8 @@ int rpod_workspace_bytes(const rpod_plan* P, size_t* bytes) {
   *bytes = P->total;
   return RPOD_OK;
 }
+
+int rpod_profile_enable(rpod_plan* P, int enable);
 
 void rpod_plan_destroy(rpod_plan* P) {
   if (P && P->prof_on) rpod_profile_enable(P, 0);
@@ -304,36 +443,25 @@ int rpod_basis(rpod_plan* P, const void* S, int64_t lds, int32_t s_dtype, const 
   char* ws = (char*)workspace;
   const int c = P->compute;
   g_launches = 0;
+  int rc;
   if (c == RPOD_F64 || c == RPOD_F32) {
     if (s_dtype != c) return RPOD_ERR_INVALID_ARG;
     if (c == RPOD_F64) {
-      SimtRun<double> R{P, ws, st, (unsigned*)(ws + P->off_status)};
-      const int rc = R.run((const double*)S, lds, nullptr, 0, (double*)U, ldu, sigma, (double*)C, ldc);
-      P->last_launches = g_launches;
-      return rc;
+      Run<double> R{P, ws, st, (unsigned*)(ws + P->off_status)};
+      rc = R.run((const double*)S, lds, (double*)U, ldu, sigma, (double*)C, ldc);
+    } else {
+      Run<float> R{P, ws, st, (unsigned*)(ws + P->off_status)};
+      rc = R.run((const float*)S, lds, (float*)U, ldu, sigma, (float*)C, ldc);
     }
-    SimtRun<float> R{P, ws, st, (unsigned*)(ws + P->off_status)};
-    const int rc = R.run((const float*)S, lds, nullptr, 0, (float*)U, ldu, sigma, (float*)C, ldc);
-    P->last_launches = g_launches;
-    return rc;
+  } else {
+    // 16-bit tensor-core forms
+    if (!(s_dtype == c || s_dtype == RPOD_F32)) return RPOD_ERR_INVALID_ARG;
+    const bool want_ref = (P->flags & RPOD_FLAG_REFINE_FP32) && s_dtype != RPOD_F32;
+    if (want_ref && (!S_refine || ldr < P->n)) return RPOD_ERR_INVALID_ARG;
+    Run<float> R{P, ws, st, (unsigned*)(ws + P->off_status)};
+    rc = R.run_tc(S, lds, s_dtype, want_ref ? S_refine : nullptr, ldr, (float*)U, ldu, sigma,
+                  (float*)C, ldc);
   }
-  // 16-bit tensor-core forms
-  if (!(s_dtype == c || s_dtype == RPOD_F32)) return RPOD_ERR_INVALID_ARG;
-  if ((P->flags & RPOD_FLAG_REFINE_FP32) && s_dtype != RPOD_F32 && (!S_refine || ldr < P->n))
-    return RPOD_ERR_INVALID_ARG;
-  TcArgs a;
-  a.n = P->n; a.m = P->m; a.k = P->k; a.l = P->l; a.q = P->q; a.seed = P->seed;
-  a.compute = c; a.flags = P->flags;
-  a.S = S; a.lds = lds; a.s_dtype = s_dtype; a.Sref = S_refine; a.ldr = ldr;
-  a.U = (float*)U; a.ldu = ldu; a.sigma = sigma; a.C = (float*)C; a.ldc = ldc;
-  a.ws = ws; a.stream = st;
-  a.off_status = P->off_status; a.off_lam = P->off_lam; a.off_y = P->off_y; a.off_q = P->off_q;
-  a.off_z = P->off_z; a.off_zq = P->off_zq; a.off_tt = P->off_tt; a.off_part = P->off_part;
-  a.off_gpart = P->off_gpart; a.off_g = P->off_g; a.off_x = P->off_x; a.off_xw = P->off_xw;
-  a.off_eig = P->off_eig; a.off_uhat = P->off_uhat; a.off_sign = P->off_sign;
-  a.off_lowp = P->off_lowp; a.sign_bytes = P->sign_bytes;
-  a.nsplit_z = P->nsplit_z; a.nsplit_t = P->nsplit_t;
-  const int rc = tc_basis(a);
   P->last_launches = g_launches;
   return rc;
 }
@@ -348,26 +476,22 @@ int rpod_project(const rpod_plan* P, const void* U, int64_t ldu, int32_t kc, con
   char* ws = (char*)workspace;
   rpod_plan* Pm = const_cast<rpod_plan*>(P);
   g_launches = 0;
+  int rc = RPOD_ERR_INVALID_ARG;
   if (P->compute == RPOD_F64) {
     if (s_dtype != RPOD_F64) return RPOD_ERR_INVALID_ARG;
-    SimtRun<double> R{Pm, ws, st, (unsigned*)(ws + P->off_status)};
-    const int rc = R.project((const double*)U, ldu, kc, (const double*)S_new, lds, m_new, (double*)C, ldc);
-    Pm->last_launches = g_launches;
-    return rc;
+    Run<double> R{Pm, ws, st, (unsigned*)(ws + P->off_status)};
+    rc = R.project((const double*)U, ldu, kc, (const double*)S_new, lds, m_new, (double*)C, ldc);
+  } else if (s_dtype == RPOD_F32) {
+    Run<float> R{Pm, ws, st, (unsigned*)(ws + P->off_status)};
+    rc = R.project((const float*)U, ldu, kc, (const float*)S_new, lds, m_new, (float*)C, ldc);
+  } else if (is16(P->compute) && s_dtype == P->compute) {
+    Run<float> R{Pm, ws, st, (unsigned*)(ws + P->off_status)};
+    rc = R.project_tc((const float*)U, ldu, kc, S_new, lds, m_new, (float*)C, ldc);
+  } else {
+    return RPOD_ERR_INVALID_ARG;
   }
-  if (s_dtype == RPOD_F32) {
-    SimtRun<float> R{Pm, ws, st, (unsigned*)(ws + P->off_status)};
-    const int rc = R.project((const float*)U, ldu, kc, (const float*)S_new, lds, m_new, (float*)C, ldc);
-    Pm->last_launches = g_launches;
-    return rc;
-  }
-  if (is16(P->compute) && s_dtype == P->compute) {
-    const int rc = tc_project(P->n, (const float*)U, ldu, kc, S_new, lds, m_new, s_dtype, (float*)C, ldc,
-                              ws, P->off_part, P->part_elems, P->nsplit_z, P->off_status, st);
-    Pm->last_launches = g_launches;
-    return rc;
-  }
-  return RPOD_ERR_INVALID_ARG;
+  Pm->last_launches = g_launches;
+  return rc;
 }
 
 int rpod_sketch(const rpod_plan* P, void* Lam, int64_t ld, int32_t dtype, void* stream) {
@@ -384,6 +508,26 @@ int rpod_sketch(const rpod_plan* P, void* Lam, int64_t ld, int32_t dtype, void* 
   return e == cudaSuccess ? RPOD_OK : RPOD_ERR_CUDA;
 }
 
+int rpod_sample(const rpod_plan* P, const void* A, int64_t lda, const void* S, int64_t lds,
+                int32_t s_dtype, float* Y, int64_t ldy, void* workspace, size_t workspace_bytes,
+                void* stream) {
+  if (!P || !A || !S || !Y || lda < P->m || lds < P->n || ldy < P->n) return RPOD_ERR_INVALID_ARG;
+  if (!is16(P->compute) || s_dtype != P->compute) return RPOD_ERR_INVALID_ARG;
+  if (int rc = check_ws(P, workspace, workspace_bytes)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  void* Zh = ws + P->off_zb;
+  if (cudaMemsetAsync(Zh, 0, (size_t)P->m_ld * 128 * 2, st) != cudaSuccess) return RPOD_ERR_CUDA;
+  if (cudaMemcpy2DAsync(Zh, (size_t)P->m_ld * 2, A, (size_t)lda * 2, (size_t)P->m * 2, (size_t)P->l,
+                        cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return RPOD_ERR_CUDA;
+  g_launches = 0;
+  const int rc = tc_ypass(st, P->compute, Zh, P->m_ld, S, lds, P->n, P->m, P->l, Y, ldy,
+                          (unsigned*)(ws + P->off_status));
+  const_cast<rpod_plan*>(P)->last_launches = g_launches;
+  return rc;
+}
+
 int rpod_profile_enable(rpod_plan* P, int enable) {
   if (!P) return RPOD_ERR_INVALID_ARG;
   if (enable && !P->prof_on) {
@@ -395,6 +539,8 @@ int rpod_profile_enable(rpod_plan* P, int enable) {
     P->prof_on = 0;
   }
   P->prof_n = 0;
+  P->prof_bytes = 0.0;
+  P->prof_flops = 0.0;
   return RPOD_OK;
 }
 

@@ -49,11 +49,13 @@ template <typename T>
 cudaError_t sketch(cudaStream_t st, uint64_t seed, uint64_t stream_id, int64_t m,
                    int l, T* Lam, int64_t ld);
 
-// One-block FP64 Cholesky of G (l x l, ld = l) with rank-revealing pivot
-// threshold; writes R (upper, l x l) and X with X R = I on the kept
-// directions (zero columns for dropped ones), in double and in TW.
+// One-block Cholesky G = R^T R of the FP64 Gram G (l x l, ld = l) with a
+// rank-revealing pivot threshold, then X = R^{-1} on the kept directions
+// (zero rows and columns for dropped ones), written in double and in TW.
+// `round` is the CholeskyQR round (0 = first): it selects the precision of
+// the factorization for FP32 working types.
 template <typename TW>
-cudaError_t cholesky(cudaStream_t st, int l, const double* G, double tol, double* R,
+cudaError_t cholesky(cudaStream_t st, int l, const double* G, double tol, int round,
                      double* X, TW* Xw, int ldxw, unsigned* status);
 
 // Symmetric eigen-decomposition of G (l x l, FP64): FP32 parallel two-sided
@@ -78,5 +80,18 @@ cudaError_t convert_matrix(cudaStream_t st, int64_t rows, int64_t cols, const TS
 template <typename T>
 cudaError_t check_finite(cudaStream_t st, int64_t rows, int64_t cols, const T* S,
                          int64_t lds, unsigned* status);
+
+// FP32 snapshot matrix -> 16-bit copy (round to nearest), flagging
+// non-finite entries; TD is __nv_bfloat16 or __half.
+template <typename TD>
+cudaError_t convert_snapshots(cudaStream_t st, int64_t rows, int64_t cols, const float* S,
+                              int64_t lds, TD* D, int64_t ldd, unsigned* status);
+
+// FP32 copy rounded to TF32 (10-bit mantissa, round to nearest, ties away).
+cudaError_t round_tf32(cudaStream_t st, int64_t rows, int64_t cols, const float* src, int64_t lds,
+                       float* dst, int64_t ldd);
+
+// Flags ST_NONFINITE if any of the l values is NaN or Inf.
+cudaError_t check_finite_vec(cudaStream_t st, int l, const double* v, unsigned* status);
 
 }  // namespace rpod

@@ -226,89 +226,107 @@ __device__ double block_max(double v, double* red) {
   return v;
 }
 
-template <typename TW>
+// The factorization runs in TF and the inverse in TI: FP64 for the FP64
+// form; for the FP32-working forms the first CholeskyQR round factors in
+// FP64 (its Gram carries the squared condition number) and later rounds,
+// whose Gram is near the identity, in FP32, while the inverse is formed in
+// FP32 (its rounding is removed by the next CholeskyQR round).  Column j of
+// the factor lives in column j of the shared array (stride l + 1) and is
+// overwritten by column j of the inverse.
+template <typename TF, typename TI, typename TW>
 __global__ void __launch_bounds__(256)
 k_cholesky(int l, const double* __restrict__ G, double tol, double* __restrict__ Xout,
            TW* __restrict__ Xw, int ldxw, unsigned* status) {
   extern __shared__ double sm[];
-  double* A = sm;               // l x l column-major
-  double* d0 = A + l * l;       // original diagonal
-  double* tmp = d0 + l;         // column buffer
+  const int ld = l + 1;
+  TF* A = (TF*)sm;                                        // l x l, column-major, stride ld
+  double* d0 = (double*)(((uintptr_t)(A + l * ld) + 15) & ~(uintptr_t)15);  // original diagonal
+  TI* tmp = (TI*)(d0 + l);                                // column buffer
   __shared__ double red[32];
-  __shared__ double s_r;
+  __shared__ TF s_rinv;
   __shared__ int s_keep[kMaxL];
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < l * l; e += nt) A[e] = G[e];
-  __syncthreads();
+  for (int e = tid; e < l * l; e += nt) {
+    const int i = e % l, j = e / l;
+    if (i <= j) A[i + j * ld] = (TF)G[e];
+  }
   double dm = 0.0;
-  for (int j = tid; j < l; j += nt) { d0[j] = A[j + j * l]; dm = fmax(dm, d0[j]); }
-  const double gmax = block_max(dm, red);
+  for (int j = tid; j < l; j += nt) { d0[j] = G[j + j * l]; dm = fmax(dm, d0[j]); }
+  const double gmax = block_max(dm, red);   // also orders the loads above
   int ndropped = 0;
+  const int cb = tid & 127, rg = tid >> 7, ng = nt >> 7;
   for (int j = 0; j < l; ++j) {
     if (tid == 0) {
-      const double d = A[j + j * l];
+      const double d = (double)A[j + j * ld];
       const bool keep = (d0[j] > 1e-300) && (d0[j] > 1e-30 * gmax) && (d > tol * d0[j]);
       s_keep[j] = keep ? 1 : 0;
-      s_r = keep ? sqrt(d) : 0.0;
-      A[j + j * l] = s_r;
+      const TF r = keep ? (TF)sqrt(d) : (TF)0;
+      s_rinv = keep ? (TF)1 / r : (TF)0;
+      A[j + j * ld] = r;
     }
     __syncthreads();
-    const double r = s_r;
-    const bool keep = s_keep[j] != 0;
-    if (!keep) ++ndropped;
-    for (int c = j + 1 + tid; c < l; c += nt) A[j + c * l] = keep ? A[j + c * l] / r : 0.0;
+    const TF rinv = s_rinv;
+    if (!s_keep[j]) ++ndropped;
+    for (int c = j + 1 + tid; c < l; c += nt) A[j + c * ld] *= rinv;
     __syncthreads();
-    // trailing update of the upper triangle
-    const int t = l - j - 1;
-    for (int e = tid; e < t * t; e += nt) {
-      const int a = j + 1 + e % t, b = j + 1 + e / t;
-      if (a <= b) A[a + b * l] -= A[j + a * l] * A[j + b * l];
+    // trailing update of the upper triangle: column b = j + 1 + cb, rows a <= b
+    const int b = j + 1 + cb;
+    if (b < l) {
+      const TF rb = A[j + b * ld];
+      for (int a = j + 1 + rg; a <= b; a += ng) A[a + b * ld] -= A[j + a * ld] * rb;
     }
     __syncthreads();
   }
-  // in-place inverse of the upper-triangular factor
+  // inverse of the upper factor, column by column, in place
   for (int j = 0; j < l; ++j) {
     const bool keep = s_keep[j] != 0;
-    for (int i = tid; i < j; i += nt) tmp[i] = keep ? A[i + j * l] : 0.0;
+    for (int i = tid; i < j; i += nt) tmp[i] = keep ? (TI)A[i + j * ld] : (TI)0;
     __syncthreads();
     if (keep) {
-      const double ajj = 1.0 / A[j + j * l];
+      const TI ajj = (TI)1 / (TI)A[j + j * ld];
       for (int i = tid; i < j; i += nt) {
-        double s = 0.0;
-        for (int t2 = i; t2 < j; ++t2) s += A[i + t2 * l] * tmp[t2];
-        A[i + j * l] = -ajj * s;
+        TI s = 0;
+        for (int t2 = i; t2 < j; ++t2) s += (TI)A[i + t2 * ld] * tmp[t2];
+        A[i + j * ld] = (TF)(-ajj * s);
       }
       __syncthreads();
-      if (tid == 0) A[j + j * l] = ajj;
+      if (tid == 0) A[j + j * ld] = (TF)ajj;
     } else {
-      for (int i = tid; i <= j; i += nt) A[i + j * l] = 0.0;
+      for (int i = tid; i <= j; i += nt) A[i + j * ld] = (TF)0;
     }
     __syncthreads();
   }
   for (int e = tid; e < l * l; e += nt) {
     const int i = e % l, j = e / l;
-    const double v = (i <= j) ? A[e] : 0.0;
+    const double v = (i <= j) ? (double)A[i + j * ld] : 0.0;
     Xout[e] = v;
     Xw[i + (int64_t)j * ldxw] = (TW)v;
   }
   if (tid == 0 && ndropped > 0) atomicOr(status, ndropped == l ? (ST_RANK_DEF | ST_BREAKDOWN) : ST_RANK_DEF);
 }
 
-template <typename TW>
-cudaError_t cholesky(cudaStream_t st, int l, const double* G, double tol, double* R, double* X,
-                     TW* Xw, int ldxw, unsigned* status) {
-  (void)R;
-  const size_t sm = ((size_t)l * l + 2 * l) * sizeof(double);
+template <typename TF, typename TI, typename TW>
+static cudaError_t launch_cholesky(cudaStream_t st, int l, const double* G, double tol, double* X,
+                                   TW* Xw, int ldxw, unsigned* status) {
+  const size_t sm = (size_t)l * (l + 1) * sizeof(TF) + 16 + (size_t)l * (sizeof(double) + sizeof(TI));
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_cholesky<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    cudaFuncSetAttribute(k_cholesky<TF, TI, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     attr_set = true;
   }
-  k_cholesky<TW><<<1, 256, sm, st>>>(l, G, tol, X, Xw, ldxw, status); note_launch();
+  k_cholesky<TF, TI, TW><<<1, 256, sm, st>>>(l, G, tol, X, Xw, ldxw, status); note_launch();
   return cudaGetLastError();
 }
-template cudaError_t cholesky<double>(cudaStream_t, int, const double*, double, double*, double*, double*, int, unsigned*);
-template cudaError_t cholesky<float>(cudaStream_t, int, const double*, double, double*, double*, float*, int, unsigned*);
+
+template <typename TW>
+cudaError_t cholesky(cudaStream_t st, int l, const double* G, double tol, int round, double* X,
+                     TW* Xw, int ldxw, unsigned* status) {
+  if (sizeof(TW) == 8) return launch_cholesky<double, double, TW>(st, l, G, tol, X, Xw, ldxw, status);
+  if (round == 0) return launch_cholesky<double, float, TW>(st, l, G, tol, X, Xw, ldxw, status);
+  return launch_cholesky<float, float, TW>(st, l, G, tol, X, Xw, ldxw, status);
+}
+template cudaError_t cholesky<double>(cudaStream_t, int, const double*, double, int, double*, double*, int, unsigned*);
+template cudaError_t cholesky<float>(cudaStream_t, int, const double*, double, int, double*, float*, int, unsigned*);
 
 // ------------------------------------------------------------------------
 // Symmetric eigensolver for the small SVD.  T T^T = Uhat Sigma^2 Uhat^T, so
@@ -353,8 +371,13 @@ k_jacobi32(int l, const double* __restrict__ G, double* __restrict__ Vout, int m
     V[i * ld + j] = (i == j) ? 1.f : 0.f;
   }
   __syncthreads();
-  const float tol = 4e-7f;
+  // FP32 stage only needs to reach the basin of the FP64 refinement
+  const float tol = 1e-5f;
   bool converged = (L < 2);
+  // thread -> (element x, first pair group g); pairs g, g + ngrp, ...
+  const int ngrp = nt / L;
+  const int x = tid % L, g0 = tid / L;
+  const bool worker = g0 < ngrp;
   for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
     if (tid == 0) s_rot = 0;
     __syncthreads();
@@ -377,29 +400,33 @@ k_jacobi32(int l, const double* __restrict__ G, double* __restrict__ Vout, int m
         cs[pi] = c; sn[pi] = sv; pp[pi] = p; qq[pi] = q;
       }
       __syncthreads();
-      // rows p, q <- J^T A
-      for (int e = tid; e < (L / 2) * L; e += nt) {
-        const int pi = e / L, x = e % L;
-        const float c = cs[pi], sv = sn[pi];
-        if (sv == 0.f) continue;
-        const int p = pp[pi], q = qq[pi];
-        const float ap = A[p * ld + x], aq = A[q * ld + x];
-        A[p * ld + x] = c * ap - sv * aq;
-        A[q * ld + x] = sv * ap + c * aq;
+      // rows p, q <- J^T A (this thread: column x of every pair in its group)
+      if (worker) {
+        for (int pi = g0; pi < L / 2; pi += ngrp) {
+          const float sv = sn[pi];
+          if (sv == 0.f) continue;
+          const float c = cs[pi];
+          const int p = pp[pi], q = qq[pi];
+          const float ap = A[p * ld + x], aq = A[q * ld + x];
+          A[p * ld + x] = c * ap - sv * aq;
+          A[q * ld + x] = sv * ap + c * aq;
+        }
       }
       __syncthreads();
-      // columns p, q <- A J, V J
-      for (int e = tid; e < (L / 2) * L; e += nt) {
-        const int pi = e / L, x = e % L;
-        const float c = cs[pi], sv = sn[pi];
-        if (sv == 0.f) continue;
-        const int p = pp[pi], q = qq[pi];
-        const float ap = A[x * ld + p], aq = A[x * ld + q];
-        A[x * ld + p] = c * ap - sv * aq;
-        A[x * ld + q] = sv * ap + c * aq;
-        const float vp = V[x * ld + p], vq = V[x * ld + q];
-        V[x * ld + p] = c * vp - sv * vq;
-        V[x * ld + q] = sv * vp + c * vq;
+      // columns p, q <- A J, V J (this thread: row x)
+      if (worker) {
+        for (int pi = g0; pi < L / 2; pi += ngrp) {
+          const float sv = sn[pi];
+          if (sv == 0.f) continue;
+          const float c = cs[pi];
+          const int p = pp[pi], q = qq[pi];
+          const float ap = A[x * ld + p], aq = A[x * ld + q];
+          A[x * ld + p] = c * ap - sv * aq;
+          A[x * ld + q] = sv * ap + c * aq;
+          const float vp = V[x * ld + p], vq = V[x * ld + q];
+          V[x * ld + p] = c * vp - sv * vq;
+          V[x * ld + q] = sv * vp + c * vq;
+        }
       }
       __syncthreads();
     }
@@ -521,7 +548,7 @@ cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma, doub
     cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  k_jacobi32<<<1, 512, smj, st>>>(l, G, X, 30, status); note_launch();
+  k_jacobi32<<<1, 512, smj, st>>>(l, G, X, 20, status); note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_frob<<<1, 256, 0, st>>>((int64_t)ll, G, normA); note_launch();
@@ -677,5 +704,84 @@ cudaError_t check_finite(cudaStream_t st, int64_t rows, int64_t cols, const T* S
 }
 template cudaError_t check_finite<__nv_bfloat16>(cudaStream_t, int64_t, int64_t, const __nv_bfloat16*, int64_t, unsigned*);
 template cudaError_t check_finite<__half>(cudaStream_t, int64_t, int64_t, const __half*, int64_t, unsigned*);
+
+}  // namespace rpod
+
+namespace rpod {
+
+// ------------------------------------------------------------------------
+// FP32 -> 16-bit snapshot copy (the down-conversion of the 16-bit forms),
+// four elements per thread when rows and leading dimensions allow it.
+template <typename TD>
+__global__ void k_convert_snapshots(int64_t rows, int64_t cols, const float* __restrict__ S,
+                                    int64_t lds, TD* __restrict__ D, int64_t ldd, unsigned* status,
+                                    int vec) {
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (vec) {
+    const int64_t r4 = rows / 4;
+    const int64_t tot = r4 * cols;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += stride) {
+      const int64_t c = t / r4, r = (t - c * r4) * 4;
+      const float4 v = *(const float4*)(S + r + c * lds);
+      bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
+      TD* d = D + r + c * ldd;
+      d[0] = cvt<TD>(v.x); d[1] = cvt<TD>(v.y); d[2] = cvt<TD>(v.z); d[3] = cvt<TD>(v.w);
+    }
+  } else {
+    const int64_t tot = rows * cols;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += stride) {
+      const int64_t c = t / rows, r = t - c * rows;
+      const float v = S[r + c * lds];
+      bad |= !isfinite(v);
+      D[r + c * ldd] = cvt<TD>(v);
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
+}
+
+template <typename TD>
+cudaError_t convert_snapshots(cudaStream_t st, int64_t rows, int64_t cols, const float* S,
+                              int64_t lds, TD* D, int64_t ldd, unsigned* status) {
+  const int vec = ((rows & 3) == 0 && (lds & 3) == 0 && (ldd & 3) == 0 &&
+                   (((uintptr_t)S) & 15) == 0 && (((uintptr_t)D) & 7) == 0) ? 1 : 0;
+  k_convert_snapshots<TD><<<152 * 16, 256, 0, st>>>(rows, cols, S, lds, D, ldd, status, vec);
+  note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t convert_snapshots<__nv_bfloat16>(cudaStream_t, int64_t, int64_t, const float*, int64_t, __nv_bfloat16*, int64_t, unsigned*);
+template cudaError_t convert_snapshots<__half>(cudaStream_t, int64_t, int64_t, const float*, int64_t, __half*, int64_t, unsigned*);
+
+__global__ void k_round_tf32(int64_t rows, int64_t cols, const float* __restrict__ src, int64_t lds,
+                             float* __restrict__ dst, int64_t ldd) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * cols) return;
+  const int64_t c = t / rows, r = t - c * rows;
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(src[r + c * lds]));
+  dst[r + c * ldd] = __uint_as_float(u);
+}
+
+cudaError_t round_tf32(cudaStream_t st, int64_t rows, int64_t cols, const float* src, int64_t lds,
+                       float* dst, int64_t ldd) {
+  const int64_t tot = rows * cols;
+  k_round_tf32<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(rows, cols, src, lds, dst, ldd);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_check_finite_vec(int l, const double* __restrict__ v, unsigned* status) {
+  for (int i = threadIdx.x; i < l; i += blockDim.x)
+    if (!isfinite(v[i])) atomicOr(status, ST_NONFINITE);
+}
+
+cudaError_t check_finite_vec(cudaStream_t st, int l, const double* v, unsigned* status) {
+  k_check_finite_vec<<<1, 128, 0, st>>>(l, v, status);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template cudaError_t convert_matrix<float, __nv_bfloat16>(cudaStream_t, int64_t, int64_t, const float*, int64_t, __nv_bfloat16*, int64_t);
+template cudaError_t convert_matrix<float, __half>(cudaStream_t, int64_t, int64_t, const float*, int64_t, __half*, int64_t);
 
 }  // namespace rpod

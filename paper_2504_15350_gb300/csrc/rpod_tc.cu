@@ -1,16 +1,507 @@
-// Tensor-core passes (placeholder until the tcgen05 kernels land).
+// Tensor-core passes over the snapshot matrix S for the 16-bit (and the TF32
+// refinement) forms of Alg. 1 (Sec. 4.2), written for sm_103a:
+// TMA (cp.async.bulk.tensor) stages 128-byte-swizzled tiles of S and of the
+// skinny operand into shared memory through a STAGES-deep mbarrier ring, one
+// elected thread issues tcgen05.mma into a TMEM accumulator, and all four
+// warps drain TMEM with tcgen05.ld in the epilogue.
+//
+// Two pass shapes, both with the skinny l-wide operand as the MMA's M = 128
+// side (l <= 128, rows >= l of the operand are TMA zero fill):
+//   W-pass  W(c, j) = sum_i A(i, c) S(i, j)      (S^T Q and T = Q^T S)
+//           K = n rows, K-major A and S tiles, split-K over n; partial
+//           results part[z][c][j] are summed by a deterministic reduction.
+//   Y-pass  Y(i, c) = sum_j S(i, j) A(j, c)      (S Lambda and S Z)
+//           K = m snapshots, K-major A tile, MN-major S tile; each CTA owns
+//           BN rows of Y and streams all of S's columns for them.
+// Every mbarrier wait is bounded by a %globaltimer deadline; on expiry the
+// kernel records ST_TIMEOUT, stops issuing work, frees its TMEM and returns.
+#include <cuda.h>
+
 #include "rpod_tc.cuh"
 
 namespace rpod {
+namespace tc {
 
-int tc_plan_extend(int64_t, int64_t, int, int, size_t*, size_t* off_lowp) {
-  *off_lowp = 0;
-  return RPOD_OK;
+constexpr uint64_t kTimeoutNs = 4000000000ull;  // 4 s per wait
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
-int tc_basis(const TcArgs&) { return RPOD_ERR_UNSUPPORTED; }
-int tc_project(int64_t, const float*, int64_t, int, const void*, int64_t, int64_t, int, float*,
-               int64_t, char*, size_t, size_t, int, size_t, cudaStream_t) {
-  return RPOD_ERR_UNSUPPORTED;
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  return __uint_as_float(u);
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait on a phase; false when the deadline passed or another role
+// already gave up (the shared abort flag).
+__device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try(b, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (true) {
+    if (mbar_try(b, parity)) return true;
+    if (*abort_flag) return false;
+    if (gtimer() - t0 > kTimeoutNs) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                            int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(su32(dst)),
+      "l"((uint64_t)map), "r"(su32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tc_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if (KIND == 2) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   su32(bar))
+               : "memory");
+}
+// 32 lanes x 32 consecutive 32-bit columns of TMEM (one per thread and column).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor (tcgen05 format): start address, leading
+// and stride byte offsets (>> 4), version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// Instruction descriptor: FP32 accumulate, A/B format (0 f16, 1 bf16, 2 tf32),
+// A K-major, B K- or MN-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc(int fmt, bool b_mn, int M, int N) {
+  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((b_mn ? 1u : 0u) << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__host__ __device__ constexpr int fmt_of(int kind) { return kind == 2 ? 2 : (kind == 1 ? 0 : 1); }
+
+template <int BN, int STAGES>
+struct Smem {
+  static constexpr uint32_t A_BYTES = 128 * 128;
+  static constexpr uint32_t B_BYTES = BN * 128;
+  static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+  static constexpr uint32_t BARS = STAGES * STAGE;
+  static constexpr size_t TOTAL = 1024 + (size_t)STAGES * STAGE + 256;
+};
+
+// ---------------------------------------------------------------------------
+// W-pass.  KIND 0 bf16, 1 fp16, 2 tf32 (32-bit containers, 32 per 128-B row).
+template <int KIND, int BN, int STAGES>
+__global__ void __launch_bounds__(128, 1)
+k_wpass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmS, int64_t n,
+        int64_t m, int l, int kchunk, float* __restrict__ part, unsigned* status) {
+  using L = Smem<BN, STAGES>;
+  constexpr int BKE = (KIND == 2) ? 32 : 64;
+  extern __shared__ uint8_t smem_raw[];
+  // TF32 form: the FP32 S tile is rounded to TF32 (round to nearest) in shared
+  // memory by warps 2-3 before the MMA reads it, so that the tensor core's
+  // truncation of the low mantissa bits adds no bias.
+  constexpr bool RND = (KIND == 2);
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + L::BARS);
+  uint64_t* empty = full + STAGES;
+  uint64_t* conv = empty + STAGES;
+  uint64_t* done = conv + STAGES;
+  uint32_t* tslot = (uint32_t*)(done + 1);
+  volatile int* abort_flag = (volatile int*)(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t j0 = (int64_t)blockIdx.x * BN;
+  const int64_t ktiles = (n + BKE - 1) / BKE;
+  const int64_t kt0 = (int64_t)blockIdx.y * kchunk;
+  const int64_t kt1 = (kt0 + kchunk < ktiles) ? kt0 + kchunk : ktiles;
+  const int nk = kt1 > kt0 ? (int)(kt1 - kt0) : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      mbar_init(&conv[s], 2);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(tslot, BN);
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0 && lane == 0 && nk > 0) {
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (it >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+      uint8_t* a = smem + s * L::STAGE;
+      mbar_expect_tx(&full[s], L::STAGE);
+      const int kc = (int)((kt0 + it) * BKE);
+      tma_load_2d(a, &tmA, &full[s], kc, 0);
+      tma_load_2d(a + L::A_BYTES, &tmS, &full[s], kc, (int)j0);
+    }
+  } else if (RND && warp >= 2 && nk > 0) {
+    const int ct = threadIdx.x - 64;
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (!mbar_wait(&full[s], ph, abort_flag)) break;
+      float4* b4 = (float4*)(smem + s * L::STAGE + L::A_BYTES);
+      for (int e = ct; e < (int)(L::B_BYTES / 16); e += 64) {
+        float4 v = b4[e];
+        v.x = tf32_rna(v.x); v.y = tf32_rna(v.y); v.z = tf32_rna(v.z); v.w = tf32_rna(v.w);
+        b4[e] = v;
+      }
+      // make the generic-proxy stores visible to the tensor core's reads
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&conv[s]);
+    }
+  } else if (warp == 1 && lane == 0 && nk > 0) {
+    constexpr uint32_t id = idesc(fmt_of(KIND), false, 128, BN);
+    int it = 0;
+    for (; it < nk; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (!mbar_wait(RND ? &conv[s] : &full[s], ph, abort_flag)) break;
+      tc_after();
+      const uint32_t a = su32(smem + s * L::STAGE), b = a + L::A_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        mma<KIND>(tmem, sdesc(a + 32 * kk, 16, 1024), sdesc(b + 32 * kk, 16, 1024), id,
+                  (it > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+  bool ok = true;
+  if (nk > 0) ok = mbar_wait(done, 0, abort_flag);
+  ok = __all_sync(0xffffffffu, ok) && !*abort_flag;
+  tc_after();
+  const int c = warp * 32 + lane;
+  float* prow = part + (int64_t)blockIdx.y * (int64_t)l * m + (int64_t)c * m;
+  for (int cc = 0; cc < BN; cc += 32) {
+    float v[32];
+    if (nk > 0 && ok) {
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, v);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = 0.f;
+    }
+    if (c < l) {
+      const int64_t jb = j0 + cc;
+      if (((m & 3) == 0) && jb + 32 <= m) {
+        float4* d4 = (float4*)(prow + jb);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+      } else {
+        for (int i = 0; i < 32; ++i)
+          if (jb + i < m) prow[jb + i] = v[i];
+      }
+    }
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
+  tc_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, BN);
+}
+
+// ---------------------------------------------------------------------------
+// Y-pass (16-bit only): A^T tile K-major (128 x 64 snapshots), S tile MN-major
+// (BN rows as BN/64 boxes of 64 rows x 64 snapshots).
+template <int KIND, int BN, int STAGES>
+__global__ void __launch_bounds__(128, 1)
+k_ypass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmS, int64_t n,
+        int64_t m, int l, float* __restrict__ Y, int64_t ldy, unsigned* status) {
+  using L = Smem<BN, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + L::BARS);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tslot = (uint32_t*)(done + 1);
+  volatile int* abort_flag = (volatile int*)(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i0 = (int64_t)blockIdx.x * BN;
+  const int nk = (int)((m + 63) / 64);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(tslot, BN);
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0 && lane == 0) {
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (it >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+      uint8_t* a = smem + s * L::STAGE;
+      mbar_expect_tx(&full[s], L::STAGE);
+      tma_load_2d(a, &tmA, &full[s], it * 64, 0);
+#pragma unroll
+      for (int b = 0; b < BN / 64; ++b)
+        tma_load_2d(a + L::A_BYTES + b * 8192, &tmS, &full[s], (int)(i0 + 64 * b), it * 64);
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t id = idesc(fmt_of(KIND), true, 128, BN);
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (!mbar_wait(&full[s], ph, abort_flag)) break;
+      tc_after();
+      const uint32_t a = su32(smem + s * L::STAGE), b = a + L::A_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        mma<KIND>(tmem, sdesc(a + 32 * kk, 16, 1024), sdesc(b + 2048 * kk, 8192, 1024), id,
+                  (it > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+  bool ok = mbar_wait(done, 0, abort_flag);
+  ok = __all_sync(0xffffffffu, ok) && !*abort_flag;
+  tc_after();
+  const int c = warp * 32 + lane;
+  float* ycol = Y + (int64_t)c * ldy;
+  for (int cc = 0; cc < BN; cc += 32) {
+    float v[32];
+    if (ok) {
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, v);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = 0.f;
+    }
+    if (c < l) {
+      const int64_t ib = i0 + cc;
+      if (((ldy & 3) == 0) && ib + 32 <= n) {
+        float4* d4 = (float4*)(ycol + ib);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+      } else {
+        for (int i = 0; i < 32; ++i)
+          if (ib + i < n) ycol[ib + i] = v[i];
+      }
+    }
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
+  tc_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, BN);
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------
+// host side
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+CUtensorMapDataType tmap_type(int dt) {
+  switch (dt) {
+    case RPOD_BF16: return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    case RPOD_F16: return CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    default: return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  }
+}
+
+int esize(int dt) { return (dt == RPOD_BF16 || dt == RPOD_F16) ? 2 : 4; }
+
+// 2-D column-major matrix (rows contiguous): dims {rows, cols}, box {br, bc}.
+int make_map(CUtensorMap* map, const void* ptr, int dt, int64_t rows, int64_t cols, int64_t ld,
+             int br, int bc) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return RPOD_ERR_CUDA;
+  const int es = esize(dt);
+  if (((uintptr_t)ptr & 15) || ((ld * es) & 15)) return RPOD_ERR_UNSUPPORTED;
+  cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * es)};
+  cuuint32_t box[2] = {(cuuint32_t)br, (cuuint32_t)bc};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, tmap_type(dt), 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? RPOD_OK : RPOD_ERR_CUDA;
+}
+
+constexpr int kBN = 256;
+constexpr int kStages = 4;
+
+template <typename KernT>
+void set_smem(KernT k, size_t bytes) {
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+int tc_wpass_splits(int64_t n, int64_t m, int dt) {
+  const int bke = esize(dt) == 2 ? 64 : 32;
+  const int64_t ktiles = (n + bke - 1) / bke;
+  const int64_t cols = (m + kBN - 1) / kBN;
+  // aim for about five waves of 152 SMs, at least 16 k-tiles per split
+  int64_t s = (5 * 152 + cols - 1) / cols;
+  if (s > ktiles / 16) s = ktiles / 16;
+  if (s < 1) s = 1;
+  if (s > 64) s = 64;
+  return (int)s;
+}
+
+int tc_wpass(cudaStream_t st, int dt, const void* A, int64_t lda, int64_t n, int l, const void* S,
+             int64_t lds, int64_t m, float* part, int nsplit, unsigned* status) {
+  CUtensorMap ta, ts;
+  const int bke = esize(dt) == 2 ? 64 : 32;
+  if (int rc = make_map(&ta, A, dt, n, l, lda, bke, 128)) return rc;
+  if (int rc = make_map(&ts, S, dt, n, m, lds, bke, kBN)) return rc;
+  const int64_t ktiles = (n + bke - 1) / bke;
+  const int kchunk = (int)((ktiles + nsplit - 1) / nsplit);
+  dim3 grid((unsigned)((m + kBN - 1) / kBN), (unsigned)nsplit);
+  using L = tc::Smem<kBN, kStages>;
+  switch (dt) {
+    case RPOD_BF16:
+      set_smem(tc::k_wpass<0, kBN, kStages>, L::TOTAL);
+      tc::k_wpass<0, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, kchunk, part, status);
+      break;
+    case RPOD_F16:
+      set_smem(tc::k_wpass<1, kBN, kStages>, L::TOTAL);
+      tc::k_wpass<1, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, kchunk, part, status);
+      break;
+    default:
+      set_smem(tc::k_wpass<2, kBN, kStages>, L::TOTAL);
+      tc::k_wpass<2, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, kchunk, part, status);
+      break;
+  }
+  note_launch();
+  return cudaGetLastError() == cudaSuccess ? RPOD_OK : RPOD_ERR_CUDA;
+}
+
+int tc_ypass(cudaStream_t st, int dt, const void* A, int64_t lda, const void* S, int64_t lds,
+             int64_t n, int64_t m, int l, float* Y, int64_t ldy, unsigned* status) {
+  if (dt != RPOD_BF16 && dt != RPOD_F16) return RPOD_ERR_UNSUPPORTED;
+  CUtensorMap ta, ts;
+  if (int rc = make_map(&ta, A, dt, m, l, lda, 64, 128)) return rc;
+  if (int rc = make_map(&ts, S, dt, n, m, lds, 64, 64)) return rc;
+  dim3 grid((unsigned)((n + kBN - 1) / kBN));
+  using L = tc::Smem<kBN, kStages>;
+  if (dt == RPOD_BF16) {
+    set_smem(tc::k_ypass<0, kBN, kStages>, L::TOTAL);
+    tc::k_ypass<0, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, Y, ldy, status);
+  } else {
+    set_smem(tc::k_ypass<1, kBN, kStages>, L::TOTAL);
+    tc::k_ypass<1, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, Y, ldy, status);
+  }
+  note_launch();
+  return cudaGetLastError() == cudaSuccess ? RPOD_OK : RPOD_ERR_CUDA;
 }
 
 }  // namespace rpod

@@ -1,38 +1,24 @@
-// Tensor-core (tcgen05 + TMA) form of the rPOD passes for 16-bit snapshot
-// matrices: interface between the C ABI and rpod_tc.cu.
+// Tensor-core (tcgen05 + TMA) passes over S for the 16-bit and TF32 forms.
 #pragma once
 #include "rpod_internal.cuh"
 
 namespace rpod {
 
-struct TcArgs {
-  int64_t n, m;
-  int k, l, q;
-  uint64_t seed;
-  int compute;
-  uint32_t flags;
-  const void* S;
-  int64_t lds;
-  int s_dtype;
-  const float* Sref;
-  int64_t ldr;
-  float* U;
-  int64_t ldu;
-  double* sigma;
-  float* C;
-  int64_t ldc;
-  char* ws;
-  cudaStream_t stream;
-  size_t off_status, off_lam, off_y, off_q, off_z, off_zq, off_tt, off_part, off_gpart, off_g,
-      off_x, off_xw, off_eig, off_uhat, off_sign, off_lowp, sign_bytes;
-  int nsplit_z, nsplit_t;
-};
+// Number of split-K chunks the W-pass uses for an n x m matrix of type dt.
+int tc_wpass_splits(int64_t n, int64_t m, int dt);
 
-// Extra workspace the 16-bit forms need, appended at *off.
-int tc_plan_extend(int64_t n, int64_t m, int l, int compute, size_t* off, size_t* off_lowp);
-int tc_basis(const TcArgs& a);
-int tc_project(int64_t n, const float* U, int64_t ldu, int kc, const void* S, int64_t lds,
-               int64_t m, int s_dtype, float* C, int64_t ldc, char* ws, size_t off_part,
-               size_t part_elems, int nsplit, size_t off_status, cudaStream_t st);
+// W-pass: part[z][c][j] = sum over rows i of split z of A(i, c) S(i, j) for
+// c < l, j < m.  A: n x 128 column-major (ld lda, columns >= l zero), S: n x m
+// (ld lds), both of type dt (RPOD_BF16, RPOD_F16, or RPOD_F32 read as TF32).
+// Base pointers 16-byte aligned and ld * sizeof multiple of 16, else
+// RPOD_ERR_UNSUPPORTED.
+int tc_wpass(cudaStream_t st, int dt, const void* A, int64_t lda, int64_t n, int l, const void* S,
+             int64_t lds, int64_t m, float* part, int nsplit, unsigned* status);
+
+// Y-pass: Y(i, c) = sum_j S(i, j) A(j, c) for i < n, c < l; A: m x 128
+// column-major (ld lda, columns >= l zero), S: n x m, both 16-bit of type dt;
+// Y FP32 column-major (ld ldy).
+int tc_ypass(cudaStream_t st, int dt, const void* A, int64_t lda, const void* S, int64_t lds,
+             int64_t n, int64_t m, int l, float* Y, int64_t ldy, unsigned* status);
 
 }  // namespace rpod

@@ -46,6 +46,8 @@ SIGNATURES = {
     "rpod_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "rpod_last_launch_count": (ctypes.c_int, [_p]),
     "rpod_sketch": (ctypes.c_int, [_p, _p, _c_i64, _c_i32, _p]),
+    "rpod_sample": (ctypes.c_int, [_p, _p, _c_i64, _p, _c_i64, _c_i32, _p, _c_i64, _p,
+                                   ctypes.c_size_t, _p]),
     "rpod_profile_enable": (ctypes.c_int, [_p, ctypes.c_int]),
     "rpod_profile_read": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -127,6 +129,10 @@ def rpod_last_launch_count(plan):
 
 def rpod_sketch(plan, Lam, ld, dtype, stream):
     return load().rpod_sketch(plan, Lam, ld, dtype, stream)
+
+
+def rpod_sample(plan, A, lda, S, lds, s_dtype, Y, ldy, ws, ws_bytes, stream):
+    return load().rpod_sample(plan, A, lda, S, lds, s_dtype, Y, ldy, ws, ws_bytes, stream)
 
 
 def rpod_profile_enable(plan, enable):

@@ -171,16 +171,22 @@ def time_matrix(rec: ModeRecipe) -> np.ndarray:
 
 
 def snapshot_matrix(rec: ModeRecipe, device="cpu", dtype=torch.float64,
-                    noise: bool = True, chunk_cols: int = 512) -> torch.Tensor:
+                    noise: bool = True, chunk_cols: int = 512, rows=None) -> torch.Tensor:
     """The n x m snapshot matrix as a column-major torch tensor (shape (n, m),
     strides (1, n)): each snapshot is contiguous.
 
     On the host it is computed in FP64 with numpy Philox noise and cast to
-    `dtype`.  On a CUDA device it is built there by torch (FP32 products unless
-    dtype is float64) with torch-generated noise, `chunk_cols` snapshots at a
-    time so that no temporary of the full size is made."""
+    `dtype`; `rows` (host only) keeps a subset of the grid cells (the noise is
+    then drawn for the subset alone).  On a CUDA device it is built there by
+    torch (FP32 products unless dtype is float64) with torch-generated noise,
+    `chunk_cols` snapshots at a time so that no temporary of the full size is
+    made."""
     device = torch.device(device)
     phi = mode_matrix(rec)                         # (n, J)
+    if rows is not None:
+        if device.type != "cpu":
+            raise ValueError("row subsets are generated on the host")
+        phi = phi[rows]
     coef = time_matrix(rec) * rec.amp[None, :]     # (m, J)
     if device.type == "cpu":
         st = coef @ phi.T                          # (m, n) row-major == S col-major

@@ -1,0 +1,125 @@
+"""GPU tests of the tensor-core (tcgen05 + TMA) forms through the C ABI.
+
+Pass kernels are checked against FP64 products of the same 16-bit operands
+(exact inputs, so only FP32 accumulation separates them); the full 16-bit
+rPOD with FP32 refinement is checked against the FP64 oracle run on the
+16-bit-rounded snapshots and sketch (the storage error floor) and on the
+original FP32 snapshots."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2504_15350_gb300.rpod as R
+from oracle.rpod import rpod as oracle_rpod
+from oracle.rpod import round_to
+from synth import make_recipe, snapshot_matrix
+from tests.rpod_checks import max_angle, orth_err, sigma_close
+
+pytestmark = pytest.mark.gpu
+
+TDT = {"bf16": torch.bfloat16, "f16": torch.float16}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2504_15350_gb300.build import build
+    build()
+    R.load()
+
+
+def colmajor(rows, cols, dtype, gen, device="cuda"):
+    return torch.randn((cols, rows), generator=gen, dtype=torch.float32).to(dtype).to(device).t()
+
+
+def rel_err(a, b):
+    return float((a - b).abs().max() / b.abs().max())
+
+
+@pytest.mark.parametrize("form", ["bf16", "f16"])
+@pytest.mark.parametrize("n,m,kc", [(4096, 512, 32), (1000, 333, 17), (70000, 700, 120), (256, 64, 1)])
+def test_wpass_project_matches_fp64(form, n, m, kc):
+    g = torch.Generator().manual_seed(n + m + kc)
+    l = min(128, max(kc, 2))
+    plan = R.Plan(n, m if m >= l else l, kc, l - kc, 1, compute=form)
+    U = colmajor(n, kc, torch.float32, g)
+    S = colmajor(n, m, TDT[form], g)
+    C = plan.project(U, S)
+    torch.cuda.synchronize()
+    ref = (U.to(TDT[form]).double().t() @ S.double())
+    err = rel_err(C.double(), ref)
+    assert err < 2e-5, err
+
+
+@pytest.mark.parametrize("form", ["bf16", "f16"])
+@pytest.mark.parametrize("n,m,l", [(4096, 512, 30), (1000, 333, 12), (70000, 1000, 128), (304, 64, 5)])
+def test_ypass_sample_matches_fp64(form, n, m, l):
+    g = torch.Generator().manual_seed(7 * n + m + l)
+    plan = R.Plan(n, m, l, 0, 1, compute=form)
+    A = colmajor(m, l, TDT[form], g)
+    S = colmajor(n, m, TDT[form], g)
+    Y = R.empty_colmajor(n, l, torch.float32, "cuda")
+    rc = R.rpod_sample(plan.handle, A.data_ptr(), R.colmajor_ld(A), S.data_ptr(), R.colmajor_ld(S),
+                       R.dtype_code(TDT[form]), Y.data_ptr(), n, plan.ws_ptr, plan.ws_bytes,
+                       torch.cuda.current_stream().cuda_stream)
+    assert rc == R.RPOD_OK
+    torch.cuda.synchronize()
+    ref = S.double() @ A.double()
+    err = rel_err(Y.double(), ref)
+    assert err < 2e-5, err
+    assert plan.status()[0] == R.RPOD_OK
+
+
+def _oracles(S64, k, p, q, form):
+    Sr = round_to(S64, form)
+    lowp = oracle_rpod(S64, k, p, q, seed=0, sketch_dtype=form, S_passes=Sr)
+    orig = oracle_rpod(S64, k, p, q, seed=0)
+    return lowp, orig
+
+
+@pytest.mark.parametrize("form", ["bf16", "f16"])
+def test_basis_16bit_refine_config1(form):
+    """Config 1 shape (n = 4096, m = 500, k = 20, p = 10, q = 1), 16-bit
+    passes with the FP32 refinement pass; S handed over in FP32 and
+    converted on the device."""
+    rec = make_recipe(64, 64, 500, 400, ("power", 1.5), seed=0, noise=1e-6)
+    S = snapshot_matrix(rec, dtype=torch.float32)
+    S64 = S.double().numpy()
+    k, p, q = 20, 10, 1
+    lowp, orig = _oracles(S64, k, p, q, form)
+    plan = R.Plan(rec.n, rec.m, k, p, q, seed=0, compute=form, flags=R.RPOD_FLAG_REFINE_FP32)
+    U, sig, C = plan.basis(S.t().contiguous().cuda().t())
+    rc, _ = plan.status()
+    assert rc == R.RPOD_OK
+    sig = sig.cpu().numpy()
+    U = U.double().cpu().numpy()
+    ok, er, ea = sigma_close(sig[:k], lowp.sigma[:k], 1e-4, 1e-5)
+    assert ok, ("vs rounded-input oracle", er, ea)
+    ok, er, ea = sigma_close(sig[:k], orig.sigma[:k], 1e-4, 1e-5)
+    assert ok, ("vs FP32-input oracle", er, ea)
+    assert max_angle(lowp.U[:, :k], U) <= 1e-2
+    assert orth_err(U) <= 1e-5
+
+
+@pytest.mark.parametrize("n,m", [(1000, 333), (2048, 700)])
+def test_basis_bf16_ragged_and_16bit_input(n, m):
+    rng = np.random.default_rng(n)
+    S64 = (rng.standard_normal((n, m)) * np.logspace(0, -3, m)[None, :])
+    S32 = torch.from_numpy(S64).float()
+    k, p, q = 8, 6, 2
+    lowp, orig = _oracles(S32.double().numpy(), k, p, q, "bf16")
+    # 16-bit S plus an FP32 refinement copy
+    Sd = S32.t().contiguous().cuda().t()
+    Sb = Sd.t().contiguous().to(torch.bfloat16).t()
+    plan = R.Plan(n, m, k, p, q, seed=0, compute="bf16", flags=R.RPOD_FLAG_REFINE_FP32)
+    U, sig, C = plan.basis(Sb, S_refine=Sd)
+    assert plan.status()[0] == R.RPOD_OK
+    sig = sig.cpu().numpy()
+    ok, er, ea = sigma_close(sig[:k], orig.sigma[:k], 1e-3, 1e-4)
+    assert ok, (er, ea)
+    assert orth_err(U.double().cpu().numpy()) <= 1e-5
+    # without refinement: reported, loose bound
+    plan2 = R.Plan(n, m, k, p, q, seed=0, compute="bf16")
+    U2, sig2, _ = plan2.basis(Sb)
+    assert plan2.status()[0] == R.RPOD_OK
+    ok, er, ea = sigma_close(sig2.cpu().numpy()[:k], lowp.sigma[:k], 2e-2, 2e-3)
+    assert ok, (er, ea)
