@@ -140,6 +140,26 @@ int rpod_profile_enable(rpod_plan* plan, int enable);
 int rpod_profile_read(const rpod_plan* plan, int* passes, double* pass_ms, double* bytes,
                       double* flops);
 
+/* Allocation-free variant of rpod_project (the paper has no counterpart; this
+ * is a deployment convenience).  For callers that cannot call cudaMalloc or
+ * supply a workspace -- a host framework that owns all device memory through
+ * its own pool, a plugin whose execute callback may not allocate, a loop that
+ * must avoid the device synchronisation an allocation can cause.  The caller
+ * still passes U, S' and C' (same meaning, layout and types as rpod_project;
+ * compute F64 with double data, otherwise FP32 U, S' and C').  The split-K
+ * partial sums live in a 16 MiB array inside the library that every GPU which
+ * loads the library holds until the process exits; nothing is allocated.
+ * Limit: kc * m_new * sizeof(element) <= 16 MiB, else RPOD_ERR_UNSUPPORTED
+ * (project larger S' in column blocks).  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the array: calls whose kernels
+ * overlap on the GPU (several streams or host threads) race and must be
+ * serialised by the caller.  No part of the array needs clearing between
+ * calls.  Asynchronous on `stream`; argument errors are returned at once. */
+int rpod_project_static(const rpod_plan* plan, const void* U, int64_t ldu, int32_t kc,
+                        const void* S_new, int64_t lds, int64_t m_new, int32_t s_dtype,
+                        void* C, int64_t ldc, void* stream);
+
 /* Synchronises `stream`, reads and clears the workspace status word.  Returns
  * the device-detected error (RPOD_OK if none) and stores warning bits in
  * *flags_out when it is not NULL. */

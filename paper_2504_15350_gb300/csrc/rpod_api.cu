@@ -40,6 +40,15 @@ struct rpod_plan {
 };
 
 namespace rpod {
+// Read-only view of a plan for the allocation-free projection.
+__attribute__((visibility("hidden"))) void plan_shape(const rpod_plan* P, int64_t* n, int32_t* l,
+                                                      int32_t* compute, int32_t* nsplit) {
+  *n = P->n;
+  *l = P->l;
+  *compute = P->compute;
+  *nsplit = P->nsplit_z;
+}
+
 // Pass profiling hooks used by the pipelines.
 void prof_begin(rpod_plan* P, cudaStream_t st) {
   if (!P->prof_on || P->prof_n >= 64) return;

@@ -48,6 +48,8 @@ SIGNATURES = {
     "rpod_sketch": (ctypes.c_int, [_p, _p, _c_i64, _c_i32, _p]),
     "rpod_sample": (ctypes.c_int, [_p, _p, _c_i64, _p, _c_i64, _c_i32, _p, _c_i64, _p,
                                    ctypes.c_size_t, _p]),
+    "rpod_project_static": (ctypes.c_int, [_p, _p, _c_i64, _c_i32, _p, _c_i64, _c_i64, _c_i32, _p,
+                                           _c_i64, _p]),
     "rpod_profile_enable": (ctypes.c_int, [_p, ctypes.c_int]),
     "rpod_profile_read": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -133,6 +135,13 @@ def rpod_sketch(plan, Lam, ld, dtype, stream):
 
 def rpod_sample(plan, A, lda, S, lds, s_dtype, Y, ldy, ws, ws_bytes, stream):
     return load().rpod_sample(plan, A, lda, S, lds, s_dtype, Y, ldy, ws, ws_bytes, stream)
+
+
+def rpod_project_static(plan, U, ldu, kc, S_new, lds, m_new, s_dtype, C, ldc, stream):
+    """Allocation-free projection: same result as rpod_project, with the
+    split-K scratch in a fixed 16 MiB device array of the library (for
+    callers that cannot allocate device memory or hand out a workspace)."""
+    return load().rpod_project_static(plan, U, ldu, kc, S_new, lds, m_new, s_dtype, C, ldc, stream)
 
 
 def rpod_profile_enable(plan, enable):
