@@ -27,6 +27,9 @@
  *     host and returned synchronously; errors detected on the device
  *     (non-finite input, no convergence, wait timeout) are recorded in a
  *     status word inside the workspace and reported by rpod_status_sync().
+ *     rpod_basis clears the workspace's status block when it starts; the
+ *     word then collects that call's errors and those of later
+ *     rpod_project/rpod_sample calls until rpod_status_sync clears it.
  *   - Return values are rpod_status codes (0 = success).
  *   - There is no CPU fallback: without a usable CUDA device every compute
  *     call returns RPOD_ERR_CUDA.
@@ -159,6 +162,117 @@ int rpod_profile_read(const rpod_plan* plan, int* passes, double* pass_ms, doubl
 int rpod_project_static(const rpod_plan* plan, const void* U, int64_t ldu, int32_t kc,
                         const void* S_new, int64_t lds, int64_t m_new, int32_t s_dtype,
                         void* C, int64_t ldc, void* stream);
+
+/* ---- Batched rPOD ------------------------------------------------------
+ * Many independent instances of Alg. 1 (e.g. the 4 fields psi_1, psi_2, q_1,
+ * q_2 of Sec. 2 times the parameter samples mu_k of Sec. 4.1, each with its
+ * own snapshot count and rank) run as one unit.  The first rpod_batch_run
+ * captures every instance's pipeline into one CUDA graph (instances spread
+ * over worker streams inside the graph) and launches it; later runs with the
+ * same workspace pointer replay the graph with a single launch.  All
+ * pointers in the instance table are device pointers owned by the caller and
+ * must stay valid (the graph bakes them in); the data they point to may
+ * change between runs. */
+typedef struct rpod_instance {
+  int64_t n, m;               /* S is n x m */
+  int32_t k, p, q;            /* target rank, oversampling, subspace iterations */
+  uint64_t seed;              /* Philox key of this instance's sketch */
+  const void* S;              /* n x m, ld lds, element type s_dtype of the batch */
+  int64_t lds;
+  const float* S_refine;      /* FP32 copy for RPOD_FLAG_REFINE_FP32 with 16-bit S, else NULL */
+  int64_t ldr;
+  void* U;                    /* n x k (n x l with RPOD_FLAG_RETURN_ALL_L) */
+  int64_t ldu;
+  double* sigma;              /* l values */
+  void* C;                    /* k x m */
+  int64_t ldc;
+} rpod_instance;
+
+typedef struct rpod_batch rpod_batch;
+
+/* Creates a batch of `count` instances (copied; compute and flags as for
+ * rpod_plan_create, s_dtype as for rpod_basis).  Host memory only.
+ * RPOD_ERR_INVALID_ARG if any instance is invalid for rpod_plan_create. */
+int rpod_batch_create(rpod_batch** out, int32_t count, const rpod_instance* inst,
+                      int32_t compute, uint32_t flags, int32_t s_dtype);
+int rpod_batch_workspace_bytes(const rpod_batch* batch, size_t* bytes);
+/* Enqueues the whole batch on `stream` (graph capture on first use). */
+int rpod_batch_run(rpod_batch* batch, void* workspace, size_t workspace_bytes, void* stream);
+/* Autotuner: times the candidate launch configurations (worker streams in
+ * {1, 2, 4, 8, 16} x split-K scale in {1/2, 1, 2} of the passes' default
+ * split) `trials` times each with CUDA events on `stream` (synchronising),
+ * keeps the fastest, re-captures, and returns it through best_streams and
+ * best_split_pct (may be NULL).  Runs the batch many times: outputs hold the
+ * last run's results. */
+int rpod_batch_tune(rpod_batch* batch, void* workspace, size_t workspace_bytes, void* stream,
+                    int32_t trials, int32_t* best_streams, int32_t* best_split_pct);
+/* Sets the launch configuration directly (e.g. from a cached tuning). */
+int rpod_batch_configure(rpod_batch* batch, int32_t streams, int32_t split_pct);
+/* Synchronises, reads and clears every instance's status word; returns the
+ * first error found (and its instance index through first_bad, -1 if none)
+ * and ORs the warning bits into *flags_out. */
+int rpod_batch_status_sync(const rpod_batch* batch, void* workspace, void* stream,
+                           int32_t* first_bad, uint32_t* flags_out);
+int rpod_batch_last_launch_count(const rpod_batch* batch);
+void rpod_batch_destroy(rpod_batch* batch);
+
+/* ---- LSTM on modal coefficients (Sec. 4.3) ------------------------------
+ * Maps a window of `window` (= sigma_L) time steps of inputs [mu, alpha_1..N]
+ * (Eq. (input); `in_dim` features, the first in_dim - out_dim of them the
+ * physical parameters) to the next coefficients (`out_dim` = N features).
+ * Cell: gates [i, f, g, o] = W_x x_t + W_h h_{t-1} + b, i, f, o logistic,
+ * g tanh, c_t = f c_{t-1} + i g, h_t = o tanh(c_t), h_0 = c_0 = 0; `layers`
+ * stacked cells of `hidden` units; linear head y = W_y h_T + b_y.  Loss MSE
+ * (mean over batch and outputs); Adam (beta 0.9 / 0.999, eps 1e-8) with the
+ * weight decay added to the gradient (Table tab:hyperparam: lr 1e-3, weight
+ * decay 1e-5).  Parameters use one flat FP32 vector: per layer W_x
+ * (4H x I_l, row-major), W_h (4H x H), b (4H); then W_y (O x H), b_y (O).
+ * The weight matrices enter every product as BF16 copies; activations and
+ * accumulation are FP32.
+ * The caller's workspace (rpod_lstm_workspace_bytes) holds the parameters,
+ * the Adam moments and all activations: keep it for the life of the model.
+ * Inputs X are row-major (batch, window, in_dim) FP32 device arrays, targets
+ * and outputs row-major (batch, out_dim). */
+typedef struct rpod_lstm rpod_lstm;
+
+int rpod_lstm_create(rpod_lstm** out, int32_t in_dim, int32_t hidden, int32_t layers,
+                     int32_t out_dim, int32_t window, int32_t max_batch);
+int64_t rpod_lstm_param_count(const rpod_lstm* net);
+int rpod_lstm_workspace_bytes(const rpod_lstm* net, size_t* bytes);
+/* Copies the flat parameter vector (host or device pointer) into the
+ * workspace and resets Adam's moments and step count. */
+int rpod_lstm_set_params(rpod_lstm* net, const float* theta, void* workspace,
+                         size_t workspace_bytes, void* stream);
+int rpod_lstm_get_params(const rpod_lstm* net, float* theta, void* workspace,
+                         size_t workspace_bytes, void* stream);
+/* y = net(X) for B <= max_batch windows. */
+int rpod_lstm_forward(rpod_lstm* net, const float* X, int32_t B, float* Y, void* workspace,
+                      size_t workspace_bytes, void* stream);
+/* MSE loss against Y_target and its gradient (flat layout) by
+ * backpropagation through time; loss and grad may be NULL (kept in the
+ * workspace). */
+int rpod_lstm_loss_grad(rpod_lstm* net, const float* X, const float* Y_target, int32_t B,
+                        float* loss, float* grad, void* workspace, size_t workspace_bytes,
+                        void* stream);
+/* loss_grad followed by one Adam update of the parameters. */
+int rpod_lstm_train_step(rpod_lstm* net, const float* X, const float* Y_target, int32_t B,
+                         float lr, float weight_decay, float* loss, void* workspace,
+                         size_t workspace_bytes, void* stream);
+/* Training windows from coefficient series: series (n_series, t_len, out_dim)
+ * and mu (n_series, d) row-major, idx (B, 2) = (series, first step); writes
+ * X[b][t] = [mu[s], series[s][t0 + t]] for t < window and Y[b] =
+ * series[s][t0 + window].  Requires d + out_dim == in_dim. */
+int rpod_lstm_gather(const rpod_lstm* net, const float* series, const float* mu,
+                     int32_t n_series, int32_t t_len, int32_t d, const int32_t* idx, int32_t B,
+                     float* X, float* Y, void* stream);
+/* Autoregressive prediction (the online stage): from the window (B, window,
+ * in_dim), predict, append [mu of the newest row, prediction] as the newest
+ * row, drop the oldest, `steps` times; out (B, steps, out_dim). */
+int rpod_lstm_rollout(rpod_lstm* net, const float* window, int32_t B, int32_t mu_cols,
+                      int32_t steps, float* out, void* workspace, size_t workspace_bytes,
+                      void* stream);
+int rpod_lstm_last_launch_count(const rpod_lstm* net);
+void rpod_lstm_destroy(rpod_lstm* net);
 
 /* Synchronises `stream`, reads and clears the workspace status word.  Returns
  * the device-detected error (RPOD_OK if none) and stores warning bits in

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <new>
+#include <vector>
 
 #include "rpod_internal.cuh"
 #include "rpod_tc.cuh"
@@ -30,6 +31,7 @@ struct rpod_plan {
   size_t off_sb, off_qb, off_zb, off_atf, off_wpart;
   int64_t n_ld, m_ld;
   int nsplit_z, nsplit_t, nsplit_w;
+  int nsz_def, nsw_def, split_cap;  // default split counts and the scale the buffers allow
   size_t part_elems, gpart_elems, sign_bytes, wpart_elems;
   int last_launches;
   // pass profiling
@@ -105,8 +107,11 @@ struct Run {
   // within a split of rows, then in FP64 across splits.
   int gram(const W* A, int64_t rows, int64_t lda, double* G, int nsplit) {
     const int l = P->l;
-    CK((gemm<W, W, W, double>(st, true, l, l, rows, nsplit, A, lda, A, lda, dbuf(P->off_gpart), 1,
-                              l, (int64_t)l * l, status, false)));
+    if (sizeof(W) == 4)
+      CK(gram_f32(st, rows, l, (const float*)A, lda, nsplit, dbuf(P->off_gpart)));
+    else
+      CK((gemm<W, W, W, double>(st, true, l, l, rows, nsplit, A, lda, A, lda, dbuf(P->off_gpart), 1,
+                                l, (int64_t)l * l, status, false)));
     CK((reduce_splits<double, double>(st, l, l, nsplit, dbuf(P->off_gpart), G, 1, l)));
     return RPOD_OK;
   }
@@ -116,14 +121,16 @@ struct Run {
   int orth(W* in, W* tmp, int64_t rows, int rounds, W** out) {
     const int l = P->l;
     const double tol = sizeof(W) == 8 ? 1e-13 : 1e-5;
-    const int64_t chunk = sizeof(W) == 8 ? 4096 : 1024;
-    const int ns = splits_for(rows, chunk, 256);
+    // FP32 Gram: two row chunks per SM (the kernel fits two blocks per SM)
+    const int ns = sizeof(W) == 8 ? splits_for(rows, 4096, 256)
+                                  : (int)std::max<int64_t>(1, std::min<int64_t>(2 * 152, rows / 256));
     W* src = in;
     W* dst = tmp;
     for (int r = 0; r < rounds; ++r) {
       double* G = dbuf(P->off_g);
       CR(gram(src, rows, rows, G, ns));
-      CK((cholesky<W>(st, l, G, tol, r, dbuf(P->off_x), buf(P->off_xw), l, status)));
+      CK((cholesky<W>(st, l, G, tol, r, dbuf(P->off_x), buf(P->off_xw), l, status,
+                      sizeof(W) == 4 ? (const float*)src : nullptr, rows, dbuf(P->off_gpart), ns)));
       CK((gemm<W, W, W, W>(st, false, rows, l, l, 1, src, rows, buf(P->off_xw), l, dst, 1, rows, 0,
                            status, false)));
       W* t = src; src = dst; dst = t;
@@ -143,7 +150,7 @@ struct Run {
                               (int64_t)l * l, status, false)));
     CK((reduce_splits<double, double>(st, l, l, ns, dbuf(P->off_gpart), GT, 1, l)));
     double* Uhat = dbuf(P->off_uhat);
-    CK((sym_eig(st, l, GT, sigma, Uhat, dbuf(P->off_eig), status, 4)));
+    CK((sym_eig(st, l, GT, sigma, Uhat, dbuf(P->off_eig), status, 5)));
     CK((check_finite_vec(st, l, sigma, status)));
     // Alg. 1: lift U = Q Uhat (first k or all l columns), then the sign rule
     const int ku = (P->flags & RPOD_FLAG_RETURN_ALL_L) ? l : k;
@@ -361,8 +368,11 @@ const char* rpod_strerror(int s) {
   }
 }
 
-int rpod_plan_create(rpod_plan** out, int64_t n, int64_t m, int32_t k, int32_t p, int32_t q,
-                     uint64_t seed, int32_t compute, uint32_t flags) {
+// split_cap: the split-K counts of the passes may later be scaled up to this
+// factor (the batch autotuner), so the partial buffers are sized for it.
+static int plan_create_impl(rpod_plan** out, int64_t n, int64_t m, int32_t k, int32_t p,
+                            int32_t q, uint64_t seed, int32_t compute, uint32_t flags,
+                            int split_cap) {
   if (!out) return RPOD_ERR_INVALID_ARG;
   *out = nullptr;
   const int64_t l = (int64_t)k + p;
@@ -379,8 +389,10 @@ int rpod_plan_create(rpod_plan** out, int64_t n, int64_t m, int32_t k, int32_t p
   const size_t L = (size_t)l;
   P->nsplit_z = splits_for(n, compute == RPOD_F64 ? 4096 : 8192, 64);
   P->nsplit_t = splits_for(m, 256, 512);
-  const int nsg = 256;
-  P->part_elems = std::max((size_t)P->nsplit_z * m * L, (size_t)1);
+  const int nsg = 2 * 152;
+  P->split_cap = split_cap < 1 ? 1 : split_cap;
+  P->nsz_def = P->nsplit_z;
+  P->part_elems = std::max((size_t)P->nsplit_z * P->split_cap * m * L, (size_t)1);
   P->gpart_elems = std::max((size_t)nsg, (size_t)P->nsplit_t) * L * L;
   P->sign_bytes = sign_fix_scratch_bytes(n, (int)L);
   size_t off = 0;
@@ -408,8 +420,9 @@ int rpod_plan_create(rpod_plan** out, int64_t n, int64_t m, int32_t k, int32_t p
   P->wpart_elems = 0;
   if (is16(compute)) {
     P->nsplit_w = std::max(tc_wpass_splits(n, m, compute), tc_wpass_splits(n, m, RPOD_F32));
+    P->nsw_def = P->nsplit_w;
     // room for the project of up to 64 splits x 256 snapshots as well
-    P->wpart_elems = std::max((size_t)P->nsplit_w * L * m, (size_t)64 * L * 256);
+    P->wpart_elems = std::max((size_t)P->nsplit_w * P->split_cap * L * m, (size_t)64 * L * 256);
     P->off_sb = take((size_t)2 * P->n_ld * m);
     P->off_qb = take((size_t)2 * P->n_ld * 128);
     P->off_zb = take((size_t)2 * P->m_ld * 128);
@@ -420,6 +433,11 @@ int rpod_plan_create(rpod_plan** out, int64_t n, int64_t m, int32_t k, int32_t p
   P->last_launches = 0;
   *out = P;
   return RPOD_OK;
+}
+
+int rpod_plan_create(rpod_plan** out, int64_t n, int64_t m, int32_t k, int32_t p, int32_t q,
+                     uint64_t seed, int32_t compute, uint32_t flags) {
+  return plan_create_impl(out, n, m, k, p, q, seed, compute, flags, 1);
 }
 
 int rpod_workspace_bytes(const rpod_plan* P, size_t* bytes) {
@@ -452,6 +470,13 @@ int rpod_basis(rpod_plan* P, const void* S, int64_t lds, int32_t s_dtype, const 
   char* ws = (char*)workspace;
   const int c = P->compute;
   g_launches = 0;
+  if ((c == RPOD_F64 || c == RPOD_F32) ? (s_dtype != c) : !(s_dtype == c || s_dtype == RPOD_F32))
+    return RPOD_ERR_INVALID_ARG;
+  if (is16(c) && (P->flags & RPOD_FLAG_REFINE_FP32) && s_dtype != RPOD_F32 &&
+      (!S_refine || ldr < P->n))
+    return RPOD_ERR_INVALID_ARG;
+  // a basis call starts from a clear status block (status word, FP64 gate)
+  if (cudaMemsetAsync(ws + P->off_status, 0, 256, st) != cudaSuccess) return RPOD_ERR_CUDA;
   int rc;
   if (c == RPOD_F64 || c == RPOD_F32) {
     if (s_dtype != c) return RPOD_ERR_INVALID_ARG;
@@ -568,6 +593,238 @@ int rpod_profile_read(const rpod_plan* P, int* passes, double* pass_ms, double* 
     *pass_ms += ms;
   }
   return RPOD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched rPOD: per-instance pipelines on worker streams, captured into one
+// CUDA graph.
+struct rpod_batch {
+  int count = 0;
+  int compute = 0;
+  uint32_t flags = 0;
+  int s_dtype = 0;
+  std::vector<rpod_plan*> plans;
+  std::vector<rpod_instance> inst;
+  std::vector<size_t> ws_off;
+  size_t total = 0;
+  int nstreams = 4;
+  int split_pct = 100;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t cap = nullptr;  // capture origin (the legacy default stream cannot capture)
+  cudaGraphExec_t exec = nullptr;
+  void* graph_ws = nullptr;
+  int last_launches = 0;
+};
+
+namespace {
+
+void apply_split(rpod_plan* P, int pct) {
+  auto scale = [&](int def) {
+    if (def <= 0) return def;
+    int s = (int)((int64_t)def * pct / 100);
+    if (s < 1) s = 1;
+    if (s > def * P->split_cap) s = def * P->split_cap;
+    return s;
+  };
+  P->nsplit_z = scale(P->nsz_def);
+  if (P->nsw_def > 0) P->nsplit_w = scale(P->nsw_def);
+}
+
+void drop_graph(rpod_batch* B) {
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  B->exec = nullptr;
+  B->graph_ws = nullptr;
+}
+
+int ensure_streams(rpod_batch* B) {
+  while ((int)B->streams.size() < 16) {
+    cudaStream_t s;
+    cudaEvent_t e;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return RPOD_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return RPOD_ERR_CUDA;
+    B->streams.push_back(s);
+    B->join.push_back(e);
+  }
+  if (!B->fork && cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess)
+    return RPOD_ERR_CUDA;
+  if (!B->cap && cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) != cudaSuccess)
+    return RPOD_ERR_CUDA;
+  return RPOD_OK;
+}
+
+// Captures every instance's pipeline into B->exec, starting from the batch's
+// own stream; the graph is then launched on the caller's stream.
+int capture(rpod_batch* B, char* ws) {
+  CR(ensure_streams(B));
+  prepare_kernels();
+  drop_graph(B);
+  cudaStream_t stream = B->cap;
+  const int ns = std::max(1, std::min(B->nstreams, std::min(16, B->count)));
+  if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return RPOD_ERR_CUDA;
+  int rc = RPOD_OK;
+  int launches = 0;
+  if (cudaEventRecord(B->fork, stream) != cudaSuccess) rc = RPOD_ERR_CUDA;
+  for (int s = 0; s < ns && rc == RPOD_OK; ++s)
+    if (cudaStreamWaitEvent(B->streams[s], B->fork, 0) != cudaSuccess) rc = RPOD_ERR_CUDA;
+  for (int i = 0; i < B->count && rc == RPOD_OK; ++i) {
+    const rpod_instance& I = B->inst[i];
+    rc = rpod_basis(B->plans[i], I.S, I.lds, B->s_dtype, I.S_refine, I.ldr, I.U, I.ldu, I.sigma,
+                    I.C, I.ldc, ws + B->ws_off[i], B->plans[i]->total, B->streams[i % ns]);
+    launches += B->plans[i]->last_launches;
+  }
+  for (int s = 0; s < ns && rc == RPOD_OK; ++s) {
+    if (cudaEventRecord(B->join[s], B->streams[s]) != cudaSuccess ||
+        cudaStreamWaitEvent(stream, B->join[s], 0) != cudaSuccess)
+      rc = RPOD_ERR_CUDA;
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(stream, &g);
+  if (rc == RPOD_OK && ec != cudaSuccess) rc = RPOD_ERR_CUDA;
+  if (rc != RPOD_OK) cudaGetLastError();  // do not leave a capture error behind
+  if (rc == RPOD_OK && cudaGraphInstantiate(&B->exec, g, 0) != cudaSuccess) {
+    B->exec = nullptr;
+    rc = RPOD_ERR_CUDA;
+  }
+  if (g) cudaGraphDestroy(g);
+  if (rc == RPOD_OK) {
+    B->graph_ws = ws;
+    B->last_launches = launches;
+  }
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rpod_batch_create(rpod_batch** out, int32_t count, const rpod_instance* inst, int32_t compute,
+                      uint32_t flags, int32_t s_dtype) {
+  if (!out || count < 1 || !inst) return RPOD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if ((compute == RPOD_F64 || compute == RPOD_F32) ? (s_dtype != compute)
+                                                   : !(s_dtype == compute || s_dtype == RPOD_F32))
+    return RPOD_ERR_INVALID_ARG;
+  rpod_batch* B = new (std::nothrow) rpod_batch();
+  if (!B) return RPOD_ERR_INVALID_ARG;
+  B->count = count;
+  B->compute = compute;
+  B->flags = flags;
+  B->s_dtype = s_dtype;
+  size_t off = 0;
+  for (int i = 0; i < count; ++i) {
+    const rpod_instance& I = inst[i];
+    rpod_plan* P = nullptr;
+    const int rc = plan_create_impl(&P, I.n, I.m, I.k, I.p, I.q, I.seed, compute, flags, 2);
+    if (rc != RPOD_OK || !I.S || !I.U || !I.sigma || !I.C || I.lds < I.n || I.ldu < I.n ||
+        I.ldc < I.k) {
+      if (P) rpod_plan_destroy(P);
+      rpod_batch_destroy(B);
+      return rc != RPOD_OK ? rc : RPOD_ERR_INVALID_ARG;
+    }
+    B->plans.push_back(P);
+    B->inst.push_back(I);
+    B->ws_off.push_back(off);
+    off = align256(off + P->total);
+  }
+  B->total = off;
+  *out = B;
+  return RPOD_OK;
+}
+
+int rpod_batch_workspace_bytes(const rpod_batch* B, size_t* bytes) {
+  if (!B || !bytes) return RPOD_ERR_INVALID_ARG;
+  *bytes = B->total;
+  return RPOD_OK;
+}
+
+int rpod_batch_configure(rpod_batch* B, int32_t streams, int32_t split_pct) {
+  if (!B || streams < 1 || streams > 16 || split_pct < 10 || split_pct > 200)
+    return RPOD_ERR_INVALID_ARG;
+  B->nstreams = streams;
+  B->split_pct = split_pct;
+  for (rpod_plan* P : B->plans) apply_split(P, split_pct);
+  drop_graph(B);
+  return RPOD_OK;
+}
+
+int rpod_batch_run(rpod_batch* B, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!B) return RPOD_ERR_INVALID_ARG;
+  if (!workspace || workspace_bytes < B->total || ((uintptr_t)workspace & 255))
+    return RPOD_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!B->exec || B->graph_ws != workspace) CR(capture(B, (char*)workspace));
+  if (cudaGraphLaunch(B->exec, st) != cudaSuccess) return RPOD_ERR_CUDA;
+  return RPOD_OK;
+}
+
+int rpod_batch_tune(rpod_batch* B, void* workspace, size_t workspace_bytes, void* stream,
+                    int32_t trials, int32_t* best_streams, int32_t* best_split_pct) {
+  if (!B || trials < 1) return RPOD_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int stream_opts[5] = {1, 2, 4, 8, 16};
+  const int split_opts[3] = {50, 100, 200};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return RPOD_ERR_CUDA;
+  float best = 1e30f;
+  int bs = B->nstreams, bp = B->split_pct;
+  int rc = RPOD_OK;
+  for (int a = 0; a < 5 && rc == RPOD_OK; ++a) {
+    if (stream_opts[a] > std::max(1, B->count)) continue;
+    for (int b = 0; b < 3 && rc == RPOD_OK; ++b) {
+      rc = rpod_batch_configure(B, stream_opts[a], split_opts[b]);
+      if (rc == RPOD_OK) rc = rpod_batch_run(B, workspace, workspace_bytes, stream);  // capture + warm
+      if (rc != RPOD_OK) break;
+      cudaEventRecord(e0, st);
+      for (int t = 0; t < trials && rc == RPOD_OK; ++t) rc = rpod_batch_run(B, workspace, workspace_bytes, stream);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = RPOD_ERR_CUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rc == RPOD_OK && ms < best) { best = ms; bs = stream_opts[a]; bp = split_opts[b]; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != RPOD_OK) return rc;
+  CR(rpod_batch_configure(B, bs, bp));
+  if (best_streams) *best_streams = bs;
+  if (best_split_pct) *best_split_pct = bp;
+  return RPOD_OK;
+}
+
+int rpod_batch_status_sync(const rpod_batch* B, void* workspace, void* stream, int32_t* first_bad,
+                           uint32_t* flags_out) {
+  if (!B || !workspace) return RPOD_ERR_INVALID_ARG;
+  int first = RPOD_OK;
+  int bad = -1;
+  uint32_t fl = 0;
+  for (int i = 0; i < B->count; ++i) {
+    uint32_t f = 0;
+    const int rc = rpod_status_sync(B->plans[i], (char*)workspace + B->ws_off[i], stream, &f);
+    fl |= f;
+    if (rc != RPOD_OK && first == RPOD_OK) { first = rc; bad = i; }
+  }
+  if (first_bad) *first_bad = bad;
+  if (flags_out) *flags_out = fl;
+  return first;
+}
+
+int rpod_batch_last_launch_count(const rpod_batch* B) { return B ? B->last_launches : -1; }
+
+void rpod_batch_destroy(rpod_batch* B) {
+  if (!B) return;
+  drop_graph(B);
+  for (rpod_plan* P : B->plans) rpod_plan_destroy(P);
+  for (cudaStream_t s : B->streams) cudaStreamDestroy(s);
+  for (cudaEvent_t e : B->join) cudaEventDestroy(e);
+  if (B->fork) cudaEventDestroy(B->fork);
+  if (B->cap) cudaStreamDestroy(B->cap);
+  delete B;
 }
 
 int rpod_status_sync(const rpod_plan* P, void* workspace, void* stream, uint32_t* flags_out) {

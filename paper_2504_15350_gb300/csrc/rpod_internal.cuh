@@ -39,6 +39,12 @@ cudaError_t gemm(cudaStream_t st, bool a_kcontig, int64_t M, int64_t N, int64_t 
                  TO* C, int64_t ci, int64_t cj, int64_t csplit,
                  unsigned* status, bool check);
 
+// As gemm, with B(k, j) = bkc ? B[k + j*ldb] : B[k*ldb + j].
+template <typename TA, typename TB, typename TC, typename TO>
+cudaError_t gemm_ex(cudaStream_t st, bool a_kcontig, bool b_kcontig, int64_t M, int64_t N,
+                    int64_t K, int nsplit, const TA* A, int64_t lda, const TB* B, int64_t ldb,
+                    TO* C, int64_t ci, int64_t cj, int64_t csplit, unsigned* status, bool check);
+
 // out[i*oi + j*oj] = sum_z part[z*M*N + i + j*M] (summed in double)
 template <typename TP, typename TO>
 cudaError_t reduce_splits(cudaStream_t st, int64_t M, int64_t N, int nsplit,
@@ -52,11 +58,15 @@ cudaError_t sketch(cudaStream_t st, uint64_t seed, uint64_t stream_id, int64_t m
 // One-block Cholesky G = R^T R of the FP64 Gram G (l x l, ld = l) with a
 // rank-revealing pivot threshold, then X = R^{-1} on the kept directions
 // (zero rows and columns for dropped ones), written in double and in TW.
-// `round` is the CholeskyQR round (0 = first): it selects the precision of
-// the factorization for FP32 working types.
+// `round` is the CholeskyQR round (0 = first): for FP32 working types the
+// first round factors in FP32 and, when a pivot signals a condition number
+// beyond FP32 reach, a device-gated FP64 factorization takes over -- of the
+// Gram recomputed with FP64 products from Y (rows x l, ld rows) into the
+// nsplit partials at `part`, when Y is given.
 template <typename TW>
 cudaError_t cholesky(cudaStream_t st, int l, const double* G, double tol, int round,
-                     double* X, TW* Xw, int ldxw, unsigned* status);
+                     double* X, TW* Xw, int ldxw, unsigned* status, const float* Y = nullptr,
+                     int64_t rows = 0, double* part = nullptr, int nsplit = 0);
 
 // Symmetric eigen-decomposition of G (l x l, FP64): FP32 parallel two-sided
 // Jacobi, then FP64 Ogita-Aishima refinement.  Outputs eigenvalues
@@ -90,6 +100,17 @@ cudaError_t convert_snapshots(cudaStream_t st, int64_t rows, int64_t cols, const
 // FP32 copy rounded to TF32 (10-bit mantissa, round to nearest, ties away).
 cudaError_t round_tf32(cudaStream_t st, int64_t rows, int64_t cols, const float* src, int64_t lds,
                        float* dst, int64_t ldd);
+
+// FP64 partial Gram matrices part[z] = Y_z^T Y_z of nsplit row chunks of the
+// FP32 matrix Y (rows x l, l <= 128), products and chunk sums in FP32.
+cudaError_t gram_f32(cudaStream_t st, int64_t rows, int l, const float* Y, int64_t ldy, int nsplit,
+                     double* part);
+
+// Sets every kernel attribute the library needs (dynamic shared memory
+// limits) once per process, so that no attribute call happens during a
+// stream capture.
+void prepare_kernels();
+void prepare_kernels_tc();
 
 // Flags ST_NONFINITE if any of the l values is NaN or Inf.
 cudaError_t check_finite_vec(cudaStream_t st, int l, const double* v, unsigned* status);

@@ -5,6 +5,8 @@
 #include <float.h>
 #include <math.h>
 
+#include <mutex>
+
 #include "rpod_internal.cuh"
 
 namespace rpod {
@@ -74,7 +76,7 @@ template <typename TA, typename TB, typename TC, typename TO, int BM, int BN, in
 __global__ void __launch_bounds__(256)
 k_gemm(int64_t M, int64_t N, int64_t K, int64_t kchunk, const TA* __restrict__ A, int64_t lda,
        const TB* __restrict__ B, int64_t ldb, TO* __restrict__ C, int64_t ci, int64_t cj,
-       int64_t csplit, unsigned* status, int check) {
+       int64_t csplit, unsigned* status, int check, int bkc) {
   constexpr int TM = BM / 16, TN = BN / 16;
   __shared__ TC As[BK][BM + 1];
   __shared__ TC Bs[BK][BN + 1];
@@ -101,9 +103,10 @@ k_gemm(int64_t M, int64_t N, int64_t K, int64_t kchunk, const TA* __restrict__ A
       As[kk][ii] = v;
     }
     for (int idx = tid; idx < BN * BK; idx += 256) {
-      const int kk = idx % BK, jj = idx / BK;
+      // B(k, j) = B[k + j*ldb] (K-contiguous) or B[k*ldb + j] (N-contiguous)
+      const int kk = bkc ? idx % BK : idx / BN, jj = bkc ? idx / BK : idx % BN;
       const int64_t gj = j0 + jj, gk = k0 + kk;
-      Bs[kk][jj] = (gj < N && gk < ke) ? cvt<TC>(B[gk + gj * ldb]) : TC(0);
+      Bs[kk][jj] = (gj < N && gk < ke) ? cvt<TC>(bkc ? B[gk + gj * ldb] : B[gk * ldb + gj]) : TC(0);
     }
     __syncthreads();
 #pragma unroll
@@ -132,10 +135,10 @@ k_gemm(int64_t M, int64_t N, int64_t K, int64_t kchunk, const TA* __restrict__ A
 }
 
 template <typename TA, typename TB, typename TC, typename TO, int BM, int BN, int BK>
-static cudaError_t launch_gemm(cudaStream_t st, bool akc, int64_t M, int64_t N, int64_t K,
-                               int nsplit, const TA* A, int64_t lda, const TB* B, int64_t ldb,
-                               TO* C, int64_t ci, int64_t cj, int64_t csplit, unsigned* status,
-                               bool check) {
+static cudaError_t launch_gemm(cudaStream_t st, bool akc, bool bkc, int64_t M, int64_t N,
+                               int64_t K, int nsplit, const TA* A, int64_t lda, const TB* B,
+                               int64_t ldb, TO* C, int64_t ci, int64_t cj, int64_t csplit,
+                               unsigned* status, bool check) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   int64_t kchunk = (K + nsplit - 1) / nsplit;
   kchunk = ((kchunk + BK - 1) / BK) * BK;
@@ -143,39 +146,52 @@ static cudaError_t launch_gemm(cudaStream_t st, bool akc, int64_t M, int64_t N, 
   dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)nsplit);
   if (akc)
     k_gemm<TA, TB, TC, TO, BM, BN, BK, true><<<grid, 256, 0, st>>>(
-        M, N, K, kchunk, A, lda, B, ldb, C, ci, cj, csplit, status, check ? 1 : 0);
+        M, N, K, kchunk, A, lda, B, ldb, C, ci, cj, csplit, status, check ? 1 : 0, bkc ? 1 : 0);
   else
     k_gemm<TA, TB, TC, TO, BM, BN, BK, false><<<grid, 256, 0, st>>>(
-        M, N, K, kchunk, A, lda, B, ldb, C, ci, cj, csplit, status, check ? 1 : 0);
+        M, N, K, kchunk, A, lda, B, ldb, C, ci, cj, csplit, status, check ? 1 : 0, bkc ? 1 : 0);
   note_launch();
   return cudaGetLastError();
+}
+
+template <typename TA, typename TB, typename TC, typename TO>
+cudaError_t gemm_ex(cudaStream_t st, bool akc, bool bkc, int64_t M, int64_t N, int64_t K,
+                    int nsplit, const TA* A, int64_t lda, const TB* B, int64_t ldb, TO* C,
+                    int64_t ci, int64_t cj, int64_t csplit, unsigned* status, bool check) {
+  if (nsplit < 1) nsplit = 1;
+  if (sizeof(TC) == 4) {
+    if (N <= 32) return launch_gemm<TA, TB, TC, TO, 128, 32, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
+    if (N <= 64) return launch_gemm<TA, TB, TC, TO, 128, 64, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
+    return launch_gemm<TA, TB, TC, TO, 128, 128, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
+  } else {
+    if (M <= 32 && N <= 32) return launch_gemm<TA, TB, TC, TO, 32, 32, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
+    if (N <= 32) return launch_gemm<TA, TB, TC, TO, 64, 32, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
+    return launch_gemm<TA, TB, TC, TO, 64, 64, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
+  }
 }
 
 template <typename TA, typename TB, typename TC, typename TO>
 cudaError_t gemm(cudaStream_t st, bool akc, int64_t M, int64_t N, int64_t K, int nsplit,
                  const TA* A, int64_t lda, const TB* B, int64_t ldb, TO* C, int64_t ci,
                  int64_t cj, int64_t csplit, unsigned* status, bool check) {
-  if (nsplit < 1) nsplit = 1;
-  if (sizeof(TC) == 4) {
-    if (N <= 32) return launch_gemm<TA, TB, TC, TO, 128, 32, 16>(st, akc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
-    if (N <= 64) return launch_gemm<TA, TB, TC, TO, 128, 64, 16>(st, akc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
-    return launch_gemm<TA, TB, TC, TO, 128, 128, 16>(st, akc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
-  } else {
-    if (M <= 32 && N <= 32) return launch_gemm<TA, TB, TC, TO, 32, 32, 16>(st, akc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
-    if (N <= 32) return launch_gemm<TA, TB, TC, TO, 64, 32, 16>(st, akc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
-    return launch_gemm<TA, TB, TC, TO, 64, 64, 16>(st, akc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
-  }
+  return gemm_ex<TA, TB, TC, TO>(st, akc, true, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit,
+                                 status, check);
 }
 
 #define INST_GEMM(TA, TB, TC, TO)                                                          \
   template cudaError_t gemm<TA, TB, TC, TO>(cudaStream_t, bool, int64_t, int64_t, int64_t, \
                                             int, const TA*, int64_t, const TB*, int64_t,  \
-                                            TO*, int64_t, int64_t, int64_t, unsigned*, bool);
+                                            TO*, int64_t, int64_t, int64_t, unsigned*, bool); \
+  template cudaError_t gemm_ex<TA, TB, TC, TO>(cudaStream_t, bool, bool, int64_t, int64_t,   \
+                                               int64_t, int, const TA*, int64_t, const TB*, \
+                                               int64_t, TO*, int64_t, int64_t, int64_t,      \
+                                               unsigned*, bool);
 INST_GEMM(double, double, double, double)
 INST_GEMM(float, float, float, float)
 INST_GEMM(float, float, float, double)
 INST_GEMM(float, double, float, float)
 INST_GEMM(double, double, double, float)
+INST_GEMM(float, __nv_bfloat16, float, float)
 #undef INST_GEMM
 
 // ------------------------------------------------------------------------
@@ -309,24 +325,329 @@ template <typename TF, typename TI, typename TW>
 static cudaError_t launch_cholesky(cudaStream_t st, int l, const double* G, double tol, double* X,
                                    TW* Xw, int ldxw, unsigned* status) {
   const size_t sm = (size_t)l * (l + 1) * sizeof(TF) + 16 + (size_t)l * (sizeof(double) + sizeof(TI));
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_cholesky<TF, TI, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    attr_set = true;
-  }
+  prepare_kernels();
   k_cholesky<TF, TI, TW><<<1, 256, sm, st>>>(l, G, tol, X, Xw, ldxw, status); note_launch();
   return cudaGetLastError();
 }
 
+// Register-blocked FP32 CholeskyQR step (l <= 128): the 256 threads form a
+// 16 x 16 grid and each holds an 8 x 8 block of the (zero-padded) 128 x 128
+// Gram matrix in registers.  Step j of the right-looking factorization
+// publishes row j of R through shared memory and every thread applies the
+// rank-1 update to its block; the inverse X = R^{-1} is then formed by the
+// column sweep W <- I, X(:, j) = W(:, j) / R_jj, W(:, c) -= X(:, j) R_jc for
+// c > j, with the same blocking.  Two barriers per step.  Semantics (pivot
+// test, dropped directions, FP64 gate) as k_cholesky32.
+template <typename TW>
+__global__ void __launch_bounds__(256)
+k_cholesky_rb(int l, const double* __restrict__ G, float tol, int* gate, double* __restrict__ Xout,
+              TW* __restrict__ Xw, int ldxw, unsigned* status) {
+  __shared__ __align__(16) float s_row[128];
+  __shared__ __align__(16) float s_col[128];
+  __shared__ float s_d0[128];
+  __shared__ float s_rdiag[128];
+  __shared__ int s_keep[128];
+  __shared__ int s_ill;
+  __shared__ double red[32];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int r0 = ty * 8, c0 = tx * 8;
+  float A[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int i = r0 + a, j = c0 + b;
+      A[a][b] = (i < l && j < l) ? (float)G[i + j * l] : 0.f;
+    }
+  double dm = 0.0;
+  if (tid < 128) {
+    const double g = tid < l ? G[tid + tid * l] : 0.0;
+    s_d0[tid] = (float)g;
+    dm = g;
+  }
+  if (tid == 0) s_ill = 0;
+  const float gmax = (float)block_max(dm, red);
+  // factorization
+  for (int j = 0; j < l; ++j) {
+    const int jb = j >> 3, jo = j & 7;
+    if (ty == jb && tx == jb) {
+      float d = 0.f;
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+        if (a == jo) d = A[a][a];
+      const float d0 = s_d0[j];
+      const bool keep = (d0 > 1e-30f) && (d0 > 1e-30f * gmax) && (d > tol * d0);
+      if (d < 1e-4f * d0) s_ill = 1;
+      s_keep[j] = keep ? 1 : 0;
+      s_rdiag[j] = keep ? sqrtf(d) : 0.f;
+    }
+    __syncthreads();
+    if (ty == jb) {
+      const float rd = s_rdiag[j];
+      const float rinv = rd > 0.f ? 1.f / rd : 0.f;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        if (a != jo) continue;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const int c = c0 + b;
+          const float v = (c > j) ? A[a][b] * rinv : (c == j ? rd : 0.f);
+          A[a][b] = v;            // row j of A becomes row j of R
+          s_row[c] = v;
+        }
+      }
+    }
+    __syncthreads();
+    float ra[8], rb[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) ra[a] = s_row[r0 + a];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) rb[b] = s_row[c0 + b];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b)
+        if (r0 + a > j && c0 + b > j) A[a][b] -= ra[a] * rb[b];
+    __syncthreads();
+  }
+  // inverse by the column sweep; R stays in A's upper triangle
+  float W[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) W[a][b] = (r0 + a == c0 + b) ? 1.f : 0.f;
+  for (int j = 0; j < l; ++j) {
+    const int jb = j >> 3, jo = j & 7;
+    const float rd = s_rdiag[j];
+    if (tx == jb) {
+      const float rinv = rd > 0.f ? 1.f / rd : 0.f;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        if (b != jo) continue;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          const float x = W[a][b] * rinv;
+          W[a][b] = x;
+          s_col[r0 + a] = x;
+        }
+      }
+    }
+    if (ty == jb) {
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        if (a != jo) continue;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) s_row[c0 + b] = (c0 + b > j && rd > 0.f) ? A[a][b] : 0.f;
+      }
+    }
+    __syncthreads();
+    float xa[8], rc[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) xa[a] = s_col[r0 + a];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) rc[b] = s_row[c0 + b];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b)
+        if (c0 + b > j) W[a][b] -= xa[a] * rc[b];
+    __syncthreads();
+  }
+  int ndropped = 0;
+  if (tid == 0)
+    for (int j = 0; j < l; ++j) ndropped += s_keep[j] ? 0 : 1;
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int i = r0 + a, j = c0 + b;
+      if (i < l && j < l) {
+        const float v = (i <= j) ? W[a][b] : 0.f;
+        Xout[i + j * l] = (double)v;
+        Xw[i + (int64_t)j * ldxw] = (TW)v;
+      }
+    }
+  if (tid == 0) {
+    if (gate && s_ill) *gate = 1;
+    if (ndropped > 0 && !(gate && s_ill))
+      atomicOr(status, ndropped == l ? (ST_RANK_DEF | ST_BREAKDOWN) : ST_RANK_DEF);
+  }
+}
+
+// FP64 factorization that runs only when the FP32 attempt raised the gate.
+template <typename TW>
+__global__ void __launch_bounds__(256)
+k_cholesky64_gated(int l, const double* __restrict__ G, double tol, int* gate,
+                   double* __restrict__ Xout, TW* __restrict__ Xw, int ldxw, unsigned* status,
+                   const double* __restrict__ part, int nsplit);
+
+// Gram partials with FP64 products of an FP32 matrix, run only when the gate
+// is raised (an FP32 Gram cannot resolve pivots below about 1e-9 of the
+// column norms; FP64 products of FP32 data are exact).
+__global__ void __launch_bounds__(256)
+k_gram_f64_gated(int64_t rows, int l, const float* __restrict__ Y, int64_t ldy, int64_t chunk,
+                 double* __restrict__ part, const int* gate) {
+  __shared__ int s_go;
+  if (threadIdx.x == 0) s_go = *gate;
+  __syncthreads();
+  if (!s_go) return;
+  constexpr int BR = 32;
+  __shared__ __align__(16) float Ys[BR][128 + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk;
+  const int64_t r1 = (r0 + chunk < rows) ? r0 + chunk : rows;
+  double acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.0;
+  for (int64_t rb = r0; rb < r1; rb += BR) {
+    for (int e = tid; e < BR * 128; e += 256) {
+      const int rr = e & (BR - 1), c = e / BR;
+      const int64_t r = rb + rr;
+      Ys[rr][c] = (c < l && r < r1) ? Y[r + (int64_t)c * ldy] : 0.f;
+    }
+    __syncthreads();
+    for (int rr = 0; rr < BR; ++rr) {
+      double av[8], bv[8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) av[a] = (double)Ys[rr][ty * 8 + a];
+#pragma unroll
+      for (int b = 0; b < 8; ++b) bv[b] = (double)Ys[rr][tx * 8 + b];
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+  double* pz = part + (int64_t)blockIdx.x * l * l;
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int i = ty * 8 + a, j = tx * 8 + b;
+      if (i < l && j < l) pz[i + j * l] = acc[a][b];
+    }
+}
+
 template <typename TW>
 cudaError_t cholesky(cudaStream_t st, int l, const double* G, double tol, int round, double* X,
-                     TW* Xw, int ldxw, unsigned* status) {
+                     TW* Xw, int ldxw, unsigned* status, const float* Y, int64_t rows,
+                     double* part, int nsplit) {
   if (sizeof(TW) == 8) return launch_cholesky<double, double, TW>(st, l, G, tol, X, Xw, ldxw, status);
-  if (round == 0) return launch_cholesky<double, float, TW>(st, l, G, tol, X, Xw, ldxw, status);
-  return launch_cholesky<float, float, TW>(st, l, G, tol, X, Xw, ldxw, status);
+  // the gate word sits next to the status word (same 256-byte status block)
+  int* gate = (int*)(status + 2);
+  prepare_kernels();
+  k_cholesky_rb<TW><<<1, 256, 0, st>>>(l, G, (float)tol, round == 0 ? gate : nullptr, X, Xw, ldxw,
+                                       status);
+  note_launch();
+  if (round != 0) return cudaGetLastError();
+  const double* gp = nullptr;
+  if (Y && part && nsplit > 0) {
+    int64_t chunk = (rows + nsplit - 1) / nsplit;
+    chunk = (chunk + 31) / 32 * 32;
+    k_gram_f64_gated<<<nsplit, 256, 0, st>>>(rows, l, Y, rows, chunk, part, gate);
+    note_launch();
+    gp = part;
+  }
+  const size_t sm64 = (size_t)l * (l + 1) * sizeof(double) + 16 + (size_t)l * (sizeof(double) + sizeof(float));
+  k_cholesky64_gated<TW><<<1, 256, sm64, st>>>(l, G, 1e-13, gate, X, Xw, ldxw, status, gp, nsplit);
+  note_launch();
+  return cudaGetLastError();
 }
-template cudaError_t cholesky<double>(cudaStream_t, int, const double*, double, int, double*, double*, int, unsigned*);
-template cudaError_t cholesky<float>(cudaStream_t, int, const double*, double, int, double*, float*, int, unsigned*);
+
+template <typename TW>
+__global__ void __launch_bounds__(256)
+k_cholesky64_gated(int l, const double* __restrict__ G, double tol, int* gate,
+                   double* __restrict__ Xout, TW* __restrict__ Xw, int ldxw, unsigned* status,
+                   const double* __restrict__ part, int nsplit) {
+  __shared__ int s_go;
+  if (threadIdx.x == 0) s_go = *gate;
+  __syncthreads();
+  if (!s_go) return;
+  // FP64 factorization of the Gram matrix; with `part`, the Gram matrix is
+  // the sum of the FP64-product partials written by k_gram_f64_gated
+  extern __shared__ double sm[];
+  const int ld = l + 1;
+  double* A = sm;
+  double* d0 = (double*)(((uintptr_t)(A + l * ld) + 15) & ~(uintptr_t)15);
+  float* tmp = (float*)(d0 + l);
+  __shared__ double red[32];
+  __shared__ double s_rinv;
+  __shared__ int s_keep[kMaxL];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < l * l; e += nt) {
+    const int i = e % l, j = e / l;
+    if (i > j) continue;
+    double g = 0.0;
+    if (part) {
+      for (int z = 0; z < nsplit; ++z) g += part[(int64_t)z * l * l + e];
+    } else {
+      g = G[e];
+    }
+    A[i + j * ld] = g;
+    if (i == j) d0[j] = g;
+  }
+  __syncthreads();
+  double dm = 0.0;
+  for (int j = tid; j < l; j += nt) dm = fmax(dm, d0[j]);
+  const double gmax = block_max(dm, red);
+  int ndropped = 0;
+  const int cb = tid & 127, rg = tid >> 7, ng = nt >> 7;
+  for (int j = 0; j < l; ++j) {
+    if (tid == 0) {
+      const double d = A[j + j * ld];
+      const bool keep = (d0[j] > 1e-300) && (d0[j] > 1e-30 * gmax) && (d > 1e-13 * d0[j]);
+      s_keep[j] = keep ? 1 : 0;
+      const double r = keep ? sqrt(d) : 0.0;
+      s_rinv = keep ? 1.0 / r : 0.0;
+      A[j + j * ld] = r;
+    }
+    __syncthreads();
+    const double rinv = s_rinv;
+    if (!s_keep[j]) ++ndropped;
+    for (int c = j + 1 + tid; c < l; c += nt) A[j + c * ld] *= rinv;
+    __syncthreads();
+    const int b = j + 1 + cb;
+    if (b < l) {
+      const double rb = A[j + b * ld];
+      for (int a = j + 1 + rg; a <= b; a += ng) A[a + b * ld] -= A[j + a * ld] * rb;
+    }
+    __syncthreads();
+  }
+  for (int j = 0; j < l; ++j) {
+    const bool keep = s_keep[j] != 0;
+    for (int i = tid; i < j; i += nt) tmp[i] = keep ? (float)A[i + j * ld] : 0.f;
+    __syncthreads();
+    if (keep) {
+      const float ajj = 1.f / (float)A[j + j * ld];
+      for (int i = tid; i < j; i += nt) {
+        float s = 0.f;
+        for (int t2 = i; t2 < j; ++t2) s += (float)A[i + t2 * ld] * tmp[t2];
+        A[i + j * ld] = (double)(-ajj * s);
+      }
+      __syncthreads();
+      if (tid == 0) A[j + j * ld] = (double)ajj;
+    } else {
+      for (int i = tid; i <= j; i += nt) A[i + j * ld] = 0.0;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < l * l; e += nt) {
+    const int i = e % l, j = e / l;
+    const double v = (i <= j) ? A[i + j * ld] : 0.0;
+    Xout[e] = v;
+    Xw[i + (int64_t)j * ldxw] = (TW)v;
+  }
+  if (tid == 0) {
+    *gate = 0;
+    if (ndropped > 0) atomicOr(status, ndropped == l ? (ST_RANK_DEF | ST_BREAKDOWN) : ST_RANK_DEF);
+  }
+  (void)tol;
+}
+template cudaError_t cholesky<double>(cudaStream_t, int, const double*, double, int, double*, double*, int, unsigned*, const float*, int64_t, double*, int);
+template cudaError_t cholesky<float>(cudaStream_t, int, const double*, double, int, double*, float*, int, unsigned*, const float*, int64_t, double*, int);
 
 // ------------------------------------------------------------------------
 // Symmetric eigensolver for the small SVD.  T T^T = Uhat Sigma^2 Uhat^T, so
@@ -371,8 +692,11 @@ k_jacobi32(int l, const double* __restrict__ G, double* __restrict__ Vout, int m
     V[i * ld + j] = (i == j) ? 1.f : 0.f;
   }
   __syncthreads();
-  // FP32 stage only needs to reach the basin of the FP64 refinement
-  const float tol = 1e-5f;
+  // FP32 stage only needs to reach the basin of the FP64 refinement: rotate
+  // while |a_pq| exceeds 1e-4 of sqrt(a_pp a_qq).  The test is relative on
+  // purpose: an absolute floor would leave pairs of small eigenvalues
+  // unrotated, and the refinement cannot split such a pair.
+  const float tol = 1e-5f, abs_floor = 1e-30f;
   bool converged = (L < 2);
   // thread -> (element x, first pair group g); pairs g, g + ngrp, ...
   const int ngrp = nt / L;
@@ -389,7 +713,7 @@ k_jacobi32(int l, const double* __restrict__ G, double* __restrict__ Vout, int m
         float c = 1.f, sv = 0.f;
         if (q < l) {
           const float apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
-          if (apq != 0.f && fabsf(apq) > tol * sqrtf(fabsf(app * aqq)) && fabsf(apq) > 1e-30f) {
+          if (fabsf(apq) > tol * sqrtf(fabsf(app * aqq)) && fabsf(apq) > abs_floor) {
             const float tau = (aqq - app) / (2.f * apq);
             const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
             c = rsqrtf(1.f + t * t);
@@ -543,11 +867,7 @@ cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma, doub
   double* normA = lam + l;
   const int L = l + (l & 1);
   const size_t smj = (size_t)2 * L * (L + 1) * sizeof(float) + (size_t)L * (2 * sizeof(float) + 2 * sizeof(int));
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+  prepare_kernels();
   k_jacobi32<<<1, 512, smj, st>>>(l, G, X, 20, status); note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -783,5 +1103,85 @@ cudaError_t check_finite_vec(cudaStream_t st, int l, const double* v, unsigned* 
 
 template cudaError_t convert_matrix<float, __nv_bfloat16>(cudaStream_t, int64_t, int64_t, const float*, int64_t, __nv_bfloat16*, int64_t);
 template cudaError_t convert_matrix<float, __half>(cudaStream_t, int64_t, int64_t, const float*, int64_t, __half*, int64_t);
+
+}  // namespace rpod
+
+namespace rpod {
+
+// ------------------------------------------------------------------------
+// Gram partials of a tall FP32 matrix: part[z] = Y_z^T Y_z (l x l, FP64) for
+// the z-th chunk of rows, Y column-major (rows x l, ld ldy, l <= 128).  The
+// chunk is staged in shared memory once (both operands of the product are the
+// same tile), each thread accumulates an 8 x 8 block in FP32 with float4
+// shared loads, and the chunk's sum is written in FP64.
+__global__ void __launch_bounds__(256)
+k_gram_f32(int64_t rows, int l, const float* __restrict__ Y, int64_t ldy, int64_t chunk,
+           double* __restrict__ part) {
+  constexpr int BR = 32;
+  __shared__ __align__(16) float Ys[BR][128 + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk;
+  const int64_t r1 = (r0 + chunk < rows) ? r0 + chunk : rows;
+  float acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+  for (int64_t rb = r0; rb < r1; rb += BR) {
+    // column c, rows rb..rb+31: 32 consecutive floats per column
+    for (int e = tid; e < BR * 128; e += 256) {
+      const int rr = e & (BR - 1), c = e / BR;
+      const int64_t r = rb + rr;
+      Ys[rr][c] = (c < l && r < r1) ? Y[r + (int64_t)c * ldy] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < BR; ++rr) {
+      const float4 a0 = *(const float4*)&Ys[rr][ty * 8];
+      const float4 a1 = *(const float4*)&Ys[rr][ty * 8 + 4];
+      const float4 b0 = *(const float4*)&Ys[rr][tx * 8];
+      const float4 b1 = *(const float4*)&Ys[rr][tx * 8 + 4];
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+  double* pz = part + (int64_t)blockIdx.x * l * l;
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int i = ty * 8 + a, j = tx * 8 + b;
+      if (i < l && j < l) pz[i + j * l] = (double)acc[a][b];
+    }
+}
+
+cudaError_t gram_f32(cudaStream_t st, int64_t rows, int l, const float* Y, int64_t ldy, int nsplit,
+                     double* part) {
+  int64_t chunk = (rows + nsplit - 1) / nsplit;
+  chunk = (chunk + 31) / 32 * 32;
+  k_gram_f32<<<nsplit, 256, 0, st>>>(rows, l, Y, ldy, chunk, part);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace rpod
+
+namespace rpod {
+
+void prepare_kernels() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const int big = 160 * 1024;
+    cudaFuncSetAttribute(k_cholesky<double, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_cholesky64_gated<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
+  prepare_kernels_tc();
+}
 
 }  // namespace rpod

@@ -17,6 +17,8 @@
 // kernel records ST_TIMEOUT, stops issuing work, frees its TMEM and returns.
 #include <cuda.h>
 
+#include <mutex>
+
 #include "rpod_tc.cuh"
 
 namespace rpod {
@@ -438,12 +440,20 @@ int make_map(CUtensorMap* map, const void* ptr, int dt, int64_t rows, int64_t co
 constexpr int kBN = 256;
 constexpr int kStages = 4;
 
-template <typename KernT>
-void set_smem(KernT k, size_t bytes) {
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
 }  // namespace
+
+void prepare_kernels_tc() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    using L = tc::Smem<kBN, kStages>;
+    const int b = (int)L::TOTAL;
+    cudaFuncSetAttribute(tc::k_wpass<0, kBN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    cudaFuncSetAttribute(tc::k_wpass<1, kBN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    cudaFuncSetAttribute(tc::k_wpass<2, kBN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    cudaFuncSetAttribute(tc::k_ypass<0, kBN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    cudaFuncSetAttribute(tc::k_ypass<1, kBN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  });
+}
 
 int tc_wpass_splits(int64_t n, int64_t m, int dt) {
   const int bke = esize(dt) == 2 ? 64 : 32;
@@ -467,17 +477,15 @@ int tc_wpass(cudaStream_t st, int dt, const void* A, int64_t lda, int64_t n, int
   const int kchunk = (int)((ktiles + nsplit - 1) / nsplit);
   dim3 grid((unsigned)((m + kBN - 1) / kBN), (unsigned)nsplit);
   using L = tc::Smem<kBN, kStages>;
+  prepare_kernels_tc();
   switch (dt) {
     case RPOD_BF16:
-      set_smem(tc::k_wpass<0, kBN, kStages>, L::TOTAL);
       tc::k_wpass<0, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, kchunk, part, status);
       break;
     case RPOD_F16:
-      set_smem(tc::k_wpass<1, kBN, kStages>, L::TOTAL);
       tc::k_wpass<1, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, kchunk, part, status);
       break;
     default:
-      set_smem(tc::k_wpass<2, kBN, kStages>, L::TOTAL);
       tc::k_wpass<2, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, kchunk, part, status);
       break;
   }
@@ -493,13 +501,11 @@ int tc_ypass(cudaStream_t st, int dt, const void* A, int64_t lda, const void* S,
   if (int rc = make_map(&ts, S, dt, n, m, lds, 64, 64)) return rc;
   dim3 grid((unsigned)((n + kBN - 1) / kBN));
   using L = tc::Smem<kBN, kStages>;
-  if (dt == RPOD_BF16) {
-    set_smem(tc::k_ypass<0, kBN, kStages>, L::TOTAL);
+  prepare_kernels_tc();
+  if (dt == RPOD_BF16)
     tc::k_ypass<0, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, Y, ldy, status);
-  } else {
-    set_smem(tc::k_ypass<1, kBN, kStages>, L::TOTAL);
+  else
     tc::k_ypass<1, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, Y, ldy, status);
-  }
   note_launch();
   return cudaGetLastError() == cudaSuccess ? RPOD_OK : RPOD_ERR_CUDA;
 }

@@ -1,0 +1,185 @@
+"""rPOD-LSTM reduced-order model on synthetic parametric snapshots (Sec. 4.3).
+
+Pipeline (every numerical step of the method runs in librpod's kernels;
+torch holds device memory and does the data bookkeeping around them):
+  1. snapshot matrix S = [S(mu_1) ... S(mu_M)] (Sec. 4.1 column order: by
+     parameter sample, then time) of the synthetic parametric recipe;
+  2. randomized POD (Alg. 1) -> basis U_N and coefficients C = U_N^T S;
+  3. z-scored coefficient series and parameters, windows of sigma_L steps
+     (Eq. (input) without the time column) -> next coefficients;
+  4. LSTM training (MSE, Adam with Table tab:hyperparam's learning rate and
+     weight decay) on 80 % of the windows, validation loss on the rest, stop
+     when it has not improved for `patience` epochs;
+  5. held-out parameters: Galerkin projection C' = U_N^T S' of their
+     snapshots (the judge), LSTM rollout from the first sigma_L projected
+     steps, and two predictors without the network: persistence of the last
+     seed step, and the coefficients of the nearest training parameter sample
+     at the same times (the zero-order choice of Eq. (time_av_zero)).
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import rpod as R
+
+
+@dataclass
+class ROMConfig:
+    nx: int = 64
+    ny: int = 64
+    J: int = 400
+    n_train_mu: int = 32
+    n_steps: int = 2000
+    n_test_mu: int = 8
+    rollout: int = 500
+    k: int = 50
+    p: int = 10
+    q: int = 1
+    hidden: int = 256
+    layers: int = 2
+    window: int = 10
+    batch: int = 512
+    epochs: int = 500
+    lr: float = 1e-3
+    weight_decay: float = 1e-5
+    seed: int = 0
+    patience: int = 25
+
+
+@dataclass
+class ROMResult:
+    train_loss: list = field(default_factory=list)
+    val_loss: list = field(default_factory=list)
+    err_lstm: float = math.nan
+    err_persistence: float = math.nan
+    err_nearest: float = math.nan
+    train_seconds: float = 0.0
+    samples_per_s: float = 0.0
+    rollout_seconds: float = 0.0
+    rollout_steps_per_s: float = 0.0
+    epochs_run: int = 0
+    sigma: list = field(default_factory=list)
+
+
+def _snapshots(cfg: ROMConfig, mus, m, device, noise_stream0):
+    from synth import parametric_recipe, snapshot_matrix
+    blocks = []
+    for i, mu in enumerate(mus):
+        rec = parametric_recipe(cfg.nx, cfg.ny, m, cfg.J, mu, seed=cfg.seed,
+                                noise_stream=noise_stream0 + i)
+        blocks.append(snapshot_matrix(rec, device=device, dtype=torch.float32).t())  # (m, n)
+    return torch.cat(blocks, 0).t()   # column-major n x (M m)
+
+
+def _rel_err(pred, ref):
+    """Relative L2 error over all steps and modes, averaged over samples."""
+    num = torch.linalg.vector_norm(pred - ref, dim=(1, 2))
+    den = torch.linalg.vector_norm(ref, dim=(1, 2))
+    return float((num / den).mean())
+
+
+def init_params(net: "R.LSTM", seed: int) -> torch.Tensor:
+    """U(-1/sqrt(H), 1/sqrt(H)) for every parameter (the usual LSTM init)."""
+    g = torch.Generator().manual_seed(seed)
+    H = net.dims[1]
+    return (torch.rand(net.P, generator=g, dtype=torch.float32) * 2 - 1) / math.sqrt(H)
+
+
+def run(cfg: ROMConfig = ROMConfig(), device="cuda", log=None) -> ROMResult:
+    dev = torch.device(device)
+    rng = np.random.default_rng(cfg.seed + 12345)
+    mu_tr = rng.uniform(0.0, 1.0, (cfg.n_train_mu, 4))
+    mu_te = rng.uniform(0.0, 1.0, (cfg.n_test_mu, 4))
+    res = ROMResult()
+    O, d, T = cfg.k, 4, cfg.window
+    # 1-2: snapshots and randomized POD
+    S = _snapshots(cfg, mu_tr, cfg.n_steps, dev, 100)
+    n, m = S.shape
+    plan = R.Plan(n, m, cfg.k, cfg.p, cfg.q, seed=cfg.seed, compute="f32", device=dev)
+    U, sig, C = plan.basis(S)
+    rc, _ = plan.status()
+    if rc != R.RPOD_OK:
+        raise R.RpodError(rc, "rpod_basis")
+    res.sigma = sig[: cfg.k].cpu().tolist()
+    del S
+    series = C.t().contiguous().reshape(cfg.n_train_mu, cfg.n_steps, O)      # (M, t, N)
+    # 3: z-scores from the training series
+    c_mean = series.reshape(-1, O).mean(0)
+    c_std = series.reshape(-1, O).std(0) + 1e-12
+    mu_t = torch.tensor(mu_tr, dtype=torch.float32, device=dev)
+    m_mean, m_std = mu_t.mean(0), mu_t.std(0) + 1e-12
+    zs = ((series - c_mean) / c_std).contiguous()
+    zmu = ((mu_t - m_mean) / m_std).contiguous()
+    starts = cfg.n_steps - T
+    ii, tt = torch.meshgrid(torch.arange(cfg.n_train_mu), torch.arange(starts), indexing="ij")
+    idx_all = torch.stack([ii.reshape(-1), tt.reshape(-1)], -1).to(torch.int32)
+    g = torch.Generator().manual_seed(cfg.seed)
+    perm = torch.randperm(idx_all.shape[0], generator=g)
+    n_val = idx_all.shape[0] // 5
+    idx_val = idx_all[perm[:n_val]].to(dev)
+    idx_tr = idx_all[perm[n_val:]].to(dev)
+    # 4: training
+    net = R.LSTM(d + O, cfg.hidden, cfg.layers, O, T, max_batch=cfg.batch, device=dev)
+    net.set_params(init_params(net, cfg.seed))
+    B = cfg.batch
+    nb = idx_tr.shape[0] // B
+    best, best_theta, since = math.inf, None, 0
+    t0 = time.perf_counter()
+    samples = 0
+    for ep in range(cfg.epochs):
+        order = idx_tr[torch.randperm(idx_tr.shape[0], generator=g).to(dev)]
+        loss_sum = torch.zeros((), device=dev)
+        for b in range(nb):
+            X, Y = net.gather(zs, zmu, order[b * B:(b + 1) * B])
+            loss_sum += net.train_step(X, Y, lr=cfg.lr, weight_decay=cfg.weight_decay)[0]
+        samples += nb * B
+        vl = torch.zeros((), device=dev)
+        nvb = max(1, idx_val.shape[0] // B)
+        for b in range(nvb):
+            X, Y = net.gather(zs, zmu, idx_val[b * B:(b + 1) * B])
+            yh = net.forward(X)
+            vl += ((yh - Y) ** 2).mean()
+        tl, vl = float(loss_sum) / nb, float(vl) / nvb
+        res.train_loss.append(tl)
+        res.val_loss.append(vl)
+        if log:
+            log(f"epoch {ep}: train {tl:.3e} val {vl:.3e}")
+        if vl < best * (1 - 1e-3):
+            best, best_theta, since = vl, net.get_params().clone(), 0
+        else:
+            since += 1
+            if since >= cfg.patience:
+                break
+    torch.cuda.synchronize(dev)
+    res.train_seconds = time.perf_counter() - t0
+    res.samples_per_s = samples / res.train_seconds
+    res.epochs_run = len(res.train_loss)
+    if best_theta is not None:
+        net.set_params(best_theta)
+    # 5: held-out parameters, judged by Galerkin projection
+    Ste = _snapshots(cfg, mu_te, T + cfg.rollout, dev, 500)
+    Cte = plan.project(U, Ste)                                   # k x (M' (T + r))
+    del Ste
+    truth = Cte.t().contiguous().reshape(cfg.n_test_mu, T + cfg.rollout, O)
+    zmu_te = ((torch.tensor(mu_te, dtype=torch.float32, device=dev) - m_mean) / m_std)
+    zt = (truth - c_mean) / c_std
+    win = torch.cat([zmu_te[:, None, :].expand(-1, T, -1), zt[:, :T]], -1).contiguous()
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    pred = net.rollout(win, d, cfg.rollout)
+    torch.cuda.synchronize(dev)
+    res.rollout_seconds = time.perf_counter() - t1
+    res.rollout_steps_per_s = cfg.rollout / res.rollout_seconds
+    pred = pred * c_std + c_mean
+    ref = truth[:, T:]
+    res.err_lstm = _rel_err(pred, ref)
+    res.err_persistence = _rel_err(truth[:, T - 1:T].expand(-1, cfg.rollout, -1), ref)
+    dist = torch.cdist(torch.tensor(mu_te), torch.tensor(mu_tr))
+    near = dist.argmin(1).to(dev)
+    res.err_nearest = _rel_err(series[near, T:T + cfg.rollout], ref)
+    return res

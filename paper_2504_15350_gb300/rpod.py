@@ -32,8 +32,40 @@ RPOD_FLAG_RETURN_ALL_L = 4
 _c_i64, _c_i32, _c_u64, _c_u32, _p = (ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
                                       ctypes.c_uint32, ctypes.c_void_p)
 
+class Instance(ctypes.Structure):
+    """rpod_instance of include/rpod.h."""
+    _fields_ = [("n", _c_i64), ("m", _c_i64), ("k", _c_i32), ("p", _c_i32), ("q", _c_i32),
+                ("seed", _c_u64), ("S", _p), ("lds", _c_i64), ("S_refine", _p), ("ldr", _c_i64),
+                ("U", _p), ("ldu", _c_i64), ("sigma", _p), ("C", _p), ("ldc", _c_i64)]
+
+
+_pi32 = ctypes.POINTER(_c_i32)
+
 # name -> (restype, argtypes); mirrors include/rpod.h
 SIGNATURES = {
+    "rpod_batch_create": (ctypes.c_int, [ctypes.POINTER(_p), _c_i32, ctypes.POINTER(Instance), _c_i32,
+                                         _c_u32, _c_i32]),
+    "rpod_batch_workspace_bytes": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "rpod_batch_run": (ctypes.c_int, [_p, _p, ctypes.c_size_t, _p]),
+    "rpod_batch_tune": (ctypes.c_int, [_p, _p, ctypes.c_size_t, _p, _c_i32, _pi32, _pi32]),
+    "rpod_batch_configure": (ctypes.c_int, [_p, _c_i32, _c_i32]),
+    "rpod_batch_status_sync": (ctypes.c_int, [_p, _p, _p, _pi32, ctypes.POINTER(_c_u32)]),
+    "rpod_batch_last_launch_count": (ctypes.c_int, [_p]),
+    "rpod_batch_destroy": (None, [_p]),
+    "rpod_lstm_create": (ctypes.c_int, [ctypes.POINTER(_p), _c_i32, _c_i32, _c_i32, _c_i32, _c_i32,
+                                        _c_i32]),
+    "rpod_lstm_param_count": (_c_i64, [_p]),
+    "rpod_lstm_workspace_bytes": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "rpod_lstm_set_params": (ctypes.c_int, [_p, _p, _p, ctypes.c_size_t, _p]),
+    "rpod_lstm_get_params": (ctypes.c_int, [_p, _p, _p, ctypes.c_size_t, _p]),
+    "rpod_lstm_forward": (ctypes.c_int, [_p, _p, _c_i32, _p, _p, ctypes.c_size_t, _p]),
+    "rpod_lstm_loss_grad": (ctypes.c_int, [_p, _p, _p, _c_i32, _p, _p, _p, ctypes.c_size_t, _p]),
+    "rpod_lstm_train_step": (ctypes.c_int, [_p, _p, _p, _c_i32, ctypes.c_float, ctypes.c_float, _p, _p,
+                                            ctypes.c_size_t, _p]),
+    "rpod_lstm_gather": (ctypes.c_int, [_p, _p, _p, _c_i32, _c_i32, _c_i32, _p, _c_i32, _p, _p, _p]),
+    "rpod_lstm_rollout": (ctypes.c_int, [_p, _p, _c_i32, _c_i32, _c_i32, _p, _p, ctypes.c_size_t, _p]),
+    "rpod_lstm_last_launch_count": (ctypes.c_int, [_p]),
+    "rpod_lstm_destroy": (None, [_p]),
     "rpod_plan_create": (ctypes.c_int, [ctypes.POINTER(_p), _c_i64, _c_i64, _c_i32, _c_i32, _c_i32,
                                         _c_u64, _c_i32, _c_u32]),
     "rpod_workspace_bytes": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_size_t)]),
@@ -155,6 +187,49 @@ def rpod_profile_read(plan):
     return n.value, ms.value, b.value, f.value
 
 
+def rpod_batch_create(instances, compute, flags, s_dtype) -> int:
+    arr = (Instance * len(instances))(*instances)
+    h = _p()
+    _check(load().rpod_batch_create(ctypes.byref(h), len(instances), arr, compute, flags, s_dtype),
+           "rpod_batch_create")
+    return h.value
+
+
+def rpod_batch_workspace_bytes(batch) -> int:
+    b = ctypes.c_size_t()
+    _check(load().rpod_batch_workspace_bytes(batch, ctypes.byref(b)), "rpod_batch_workspace_bytes")
+    return b.value
+
+
+def rpod_batch_run(batch, ws, ws_bytes, stream):
+    return load().rpod_batch_run(batch, ws, ws_bytes, stream)
+
+
+def rpod_batch_tune(batch, ws, ws_bytes, stream, trials):
+    s, p = _c_i32(), _c_i32()
+    _check(load().rpod_batch_tune(batch, ws, ws_bytes, stream, trials, ctypes.byref(s), ctypes.byref(p)),
+           "rpod_batch_tune")
+    return s.value, p.value
+
+
+def rpod_batch_configure(batch, streams, split_pct):
+    return load().rpod_batch_configure(batch, streams, split_pct)
+
+
+def rpod_batch_status_sync(batch, ws, stream):
+    bad, fl = _c_i32(), _c_u32()
+    rc = load().rpod_batch_status_sync(batch, ws, stream, ctypes.byref(bad), ctypes.byref(fl))
+    return rc, bad.value, fl.value
+
+
+def rpod_batch_last_launch_count(batch):
+    return load().rpod_batch_last_launch_count(batch)
+
+
+def rpod_batch_destroy(batch):
+    load().rpod_batch_destroy(batch)
+
+
 # ---- torch marshalling ------------------------------------------------------
 def _torch():
     import torch
@@ -263,3 +338,220 @@ class Plan:
     def profile_read(self):
         """(passes, summed pass ms, algorithmic bytes, flops) of the last basis call."""
         return rpod_profile_read(self.handle)
+
+
+class Batch:
+    """A batch of independent rPOD instances over column-major torch tensors
+    S_b (n_b x m_b) on one device; outputs U_b, sigma_b, C_b are allocated
+    here and stay fixed (the captured graph writes into them)."""
+
+    def __init__(self, S_list, ks, p, q, seeds, compute="f32", flags=0, S_refine=None,
+                 device="cuda"):
+        torch = _torch()
+        self.device = torch.device(device)
+        self.compute = {"f64": RPOD_F64, "f32": RPOD_F32, "bf16": RPOD_BF16,
+                        "f16": RPOD_F16}[compute] if isinstance(compute, str) else int(compute)
+        out_dt = torch.float64 if self.compute == RPOD_F64 else torch.float32
+        self.S = list(S_list)
+        self.S_refine = list(S_refine) if S_refine is not None else [None] * len(self.S)
+        self.U, self.sigma, self.C, insts = [], [], [], []
+        for b, S in enumerate(self.S):
+            n, m = S.shape
+            k = int(ks[b])
+            l = k + p
+            ku = l if (flags & RPOD_FLAG_RETURN_ALL_L) else k
+            U = empty_colmajor(n, ku, out_dt, self.device)
+            sg = torch.empty(l, dtype=torch.float64, device=self.device)
+            C = empty_colmajor(k, m, out_dt, self.device)
+            self.U.append(U)
+            self.sigma.append(sg)
+            self.C.append(C)
+            R = self.S_refine[b]
+            insts.append(Instance(n, m, k, p, q, int(seeds[b]), S.data_ptr(), colmajor_ld(S),
+                                  R.data_ptr() if R is not None else None,
+                                  colmajor_ld(R) if R is not None else 0, U.data_ptr(),
+                                  colmajor_ld(U), sg.data_ptr(), C.data_ptr(), colmajor_ld(C)))
+        self.s_dtype = dtype_code(self.S[0].dtype)
+        self.handle = rpod_batch_create(insts, self.compute, flags, self.s_dtype)
+        self.ws_bytes = rpod_batch_workspace_bytes(self.handle)
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        self.ws_ptr = self.ws.data_ptr() + (-self.ws.data_ptr()) % 256
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                rpod_batch_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    def _stream(self):
+        return _torch().cuda.current_stream(self.device).cuda_stream
+
+    def run(self):
+        _check(rpod_batch_run(self.handle, self.ws_ptr, self.ws_bytes, self._stream()),
+               "rpod_batch_run")
+
+    def tune(self, trials=2):
+        return rpod_batch_tune(self.handle, self.ws_ptr, self.ws_bytes, self._stream(), trials)
+
+    def configure(self, streams, split_pct):
+        _check(rpod_batch_configure(self.handle, streams, split_pct), "rpod_batch_configure")
+
+    def status(self):
+        return rpod_batch_status_sync(self.handle, self.ws_ptr, self._stream())
+
+    def launches(self):
+        return rpod_batch_last_launch_count(self.handle)
+
+
+# ---- LSTM (same-name wrappers and a torch convenience class) ---------------
+def rpod_lstm_create(in_dim, hidden, layers, out_dim, window, max_batch):
+    h = _p()
+    _check(load().rpod_lstm_create(ctypes.byref(h), in_dim, hidden, layers, out_dim, window, max_batch),
+           "rpod_lstm_create")
+    return h.value
+
+
+def rpod_lstm_param_count(net):
+    return load().rpod_lstm_param_count(net)
+
+
+def rpod_lstm_workspace_bytes(net):
+    b = ctypes.c_size_t()
+    _check(load().rpod_lstm_workspace_bytes(net, ctypes.byref(b)), "rpod_lstm_workspace_bytes")
+    return b.value
+
+
+def rpod_lstm_set_params(net, theta, ws, ws_bytes, stream):
+    return load().rpod_lstm_set_params(net, theta, ws, ws_bytes, stream)
+
+
+def rpod_lstm_get_params(net, theta, ws, ws_bytes, stream):
+    return load().rpod_lstm_get_params(net, theta, ws, ws_bytes, stream)
+
+
+def rpod_lstm_forward(net, X, B, Y, ws, ws_bytes, stream):
+    return load().rpod_lstm_forward(net, X, B, Y, ws, ws_bytes, stream)
+
+
+def rpod_lstm_loss_grad(net, X, Yt, B, loss, grad, ws, ws_bytes, stream):
+    return load().rpod_lstm_loss_grad(net, X, Yt, B, loss, grad, ws, ws_bytes, stream)
+
+
+def rpod_lstm_train_step(net, X, Yt, B, lr, wd, loss, ws, ws_bytes, stream):
+    return load().rpod_lstm_train_step(net, X, Yt, B, lr, wd, loss, ws, ws_bytes, stream)
+
+
+def rpod_lstm_gather(net, series, mu, n_series, t_len, d, idx, B, X, Y, stream):
+    return load().rpod_lstm_gather(net, series, mu, n_series, t_len, d, idx, B, X, Y, stream)
+
+
+def rpod_lstm_rollout(net, window, B, mu_cols, steps, out, ws, ws_bytes, stream):
+    return load().rpod_lstm_rollout(net, window, B, mu_cols, steps, out, ws, ws_bytes, stream)
+
+
+def rpod_lstm_last_launch_count(net):
+    return load().rpod_lstm_last_launch_count(net)
+
+
+def rpod_lstm_destroy(net):
+    load().rpod_lstm_destroy(net)
+
+
+class LSTM:
+    """An rpod_lstm plus its workspace on one CUDA device (torch tensors in,
+    torch tensors out; all arithmetic in the library's kernels)."""
+
+    def __init__(self, in_dim, hidden, layers, out_dim, window, max_batch, theta=None, device="cuda"):
+        torch = _torch()
+        self.device = torch.device(device)
+        self.dims = (in_dim, hidden, layers, out_dim, window)
+        self.max_batch = max_batch
+        self.handle = rpod_lstm_create(in_dim, hidden, layers, out_dim, window, max_batch)
+        self.P = rpod_lstm_param_count(self.handle)
+        self.ws_bytes = rpod_lstm_workspace_bytes(self.handle)
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        self.ws_ptr = self.ws.data_ptr() + (-self.ws.data_ptr()) % 256
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        if theta is not None:
+            self.set_params(theta)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                rpod_lstm_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    def _stream(self):
+        return _torch().cuda.current_stream(self.device).cuda_stream
+
+    def set_params(self, theta):
+        torch = _torch()
+        t = torch.as_tensor(theta, dtype=torch.float32).to(self.device).contiguous()
+        assert t.numel() == self.P
+        self._theta_in = t
+        _check(rpod_lstm_set_params(self.handle, t.data_ptr(), self.ws_ptr, self.ws_bytes, self._stream()),
+               "rpod_lstm_set_params")
+
+    def get_params(self):
+        torch = _torch()
+        t = torch.empty(self.P, dtype=torch.float32, device=self.device)
+        _check(rpod_lstm_get_params(self.handle, t.data_ptr(), self.ws_ptr, self.ws_bytes, self._stream()),
+               "rpod_lstm_get_params")
+        return t
+
+    def forward(self, X):
+        torch = _torch()
+        X = X.contiguous()
+        B = X.shape[0]
+        Y = torch.empty((B, self.dims[3]), dtype=torch.float32, device=self.device)
+        _check(rpod_lstm_forward(self.handle, X.data_ptr(), B, Y.data_ptr(), self.ws_ptr, self.ws_bytes,
+                                 self._stream()), "rpod_lstm_forward")
+        return Y
+
+    def loss_grad(self, X, Yt):
+        torch = _torch()
+        X, Yt = X.contiguous(), Yt.contiguous()
+        g = torch.empty(self.P, dtype=torch.float32, device=self.device)
+        _check(rpod_lstm_loss_grad(self.handle, X.data_ptr(), Yt.data_ptr(), X.shape[0], self.loss.data_ptr(),
+                                   g.data_ptr(), self.ws_ptr, self.ws_bytes, self._stream()),
+               "rpod_lstm_loss_grad")
+        return self.loss.clone(), g
+
+    def train_step(self, X, Yt, lr=1e-3, weight_decay=1e-5):
+        _check(rpod_lstm_train_step(self.handle, X.data_ptr(), Yt.data_ptr(), X.shape[0], lr, weight_decay,
+                                    self.loss.data_ptr(), self.ws_ptr, self.ws_bytes, self._stream()),
+               "rpod_lstm_train_step")
+        return self.loss
+
+    def gather(self, series, mu, idx):
+        """Windows (X, Y) for rows idx (B, 2) = (series, first step) of
+        series (n_series, t_len, out_dim) and mu (n_series, d)."""
+        torch = _torch()
+        series, idx = series.contiguous(), idx.to(torch.int32).contiguous()
+        n_series, t_len, _ = series.shape
+        d = 0 if mu is None else mu.shape[1]
+        B = idx.shape[0]
+        X = torch.empty((B, self.dims[4], self.dims[0]), dtype=torch.float32, device=self.device)
+        Y = torch.empty((B, self.dims[3]), dtype=torch.float32, device=self.device)
+        mptr = mu.contiguous().data_ptr() if mu is not None else None
+        _check(rpod_lstm_gather(self.handle, series.data_ptr(), mptr, n_series, t_len, d, idx.data_ptr(), B,
+                                X.data_ptr(), Y.data_ptr(), self._stream()), "rpod_lstm_gather")
+        return X, Y
+
+    def rollout(self, window, mu_cols, steps):
+        torch = _torch()
+        window = window.contiguous()
+        B = window.shape[0]
+        out = torch.empty((B, steps, self.dims[3]), dtype=torch.float32, device=self.device)
+        _check(rpod_lstm_rollout(self.handle, window.data_ptr(), B, mu_cols, steps, out.data_ptr(), self.ws_ptr,
+                                 self.ws_bytes, self._stream()), "rpod_lstm_rollout")
+        return out
+
+    def launches(self):
+        return rpod_lstm_last_launch_count(self.handle)

@@ -1,0 +1,115 @@
+"""GPU tests of the LSTM kernels (Sec. 4.3) through the C ABI against the FP64
+oracle (oracle/lstm.py).  The library multiplies by BF16 copies of the weight
+matrices, so the oracle runs at the same BF16-rounded weights (biases exact);
+what remains is FP32 activations and accumulation."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2504_15350_gb300.rpod as R
+from oracle import lstm as OL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2504_15350_gb300.build import build
+    build()
+    R.load()
+
+
+def bf16_weights(theta, I, H, L, O):
+    """theta with every weight matrix rounded to BF16 (biases unchanged)."""
+    out = theta.copy()
+    off = 0
+    for shp in OL.param_shapes(I, H, L, O):
+        n = int(np.prod(shp))
+        if len(shp) == 2:
+            blk = torch.from_numpy(out[off:off + n].astype(np.float32)).to(torch.bfloat16).double().numpy()
+            out[off:off + n] = blk
+        off += n
+    return out
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-30))
+
+
+@pytest.mark.parametrize("I,H,L,O,T,B", [(6, 32, 2, 4, 5, 16), (54, 64, 2, 50, 10, 40), (5, 16, 1, 3, 3, 7)])
+def test_forward_and_gradients_match_oracle(I, H, L, O, T, B):
+    rng = np.random.default_rng(I * H + B)
+    theta = rng.uniform(-0.3, 0.3, OL.param_count(I, H, L, O)).astype(np.float32).astype(np.float64)
+    X = rng.standard_normal((B, T, I)).astype(np.float32)
+    Yt = rng.standard_normal((B, O)).astype(np.float32)
+    te = bf16_weights(theta, I, H, L, O)
+    y_o, cache = OL.forward(te, X.astype(np.float64), H, L, O)
+    loss_o, dy = OL.mse(y_o, Yt.astype(np.float64))
+    g_o = OL.backward(te, cache, dy, H, L, O)
+
+    net = R.LSTM(I, H, L, O, T, max_batch=64, theta=theta)
+    Xd = torch.from_numpy(X).cuda()
+    y = net.forward(Xd).cpu().numpy()
+    assert rel(y, y_o) < 2e-5
+    loss, g = net.loss_grad(Xd, torch.from_numpy(Yt).cuda())
+    torch.cuda.synchronize()
+    assert abs(loss.item() - loss_o) <= 1e-5 * loss_o
+    g = g.cpu().numpy()
+    # every parameter block separately (relative to the block's scale)
+    off = 0
+    for shp in OL.param_shapes(I, H, L, O):
+        n = int(np.prod(shp))
+        assert rel(g[off:off + n], g_o[off:off + n]) < 2e-4, shp
+        off += n
+    assert net.launches() > 2 * T
+
+
+def test_adam_step_matches_oracle():
+    I, H, L, O, T, B = 6, 32, 2, 4, 5, 16
+    rng = np.random.default_rng(3)
+    theta = rng.uniform(-0.3, 0.3, OL.param_count(I, H, L, O)).astype(np.float32).astype(np.float64)
+    X = rng.standard_normal((B, T, I)).astype(np.float32)
+    Yt = rng.standard_normal((B, O)).astype(np.float32)
+    net = R.LSTM(I, H, L, O, T, max_batch=B, theta=theta)
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Yt).cuda()
+    th = theta.copy()
+    m = np.zeros_like(th)
+    v = np.zeros_like(th)
+    for step in (1, 2, 3):
+        te = bf16_weights(th, I, H, L, O)
+        y_o, cache = OL.forward(te, X.astype(np.float64), H, L, O)
+        _, dy = OL.mse(y_o, Yt.astype(np.float64))
+        g_o = OL.backward(te, cache, dy, H, L, O)
+        th, m, v = OL.adam_step(th, g_o, m, v, step, lr=1e-3, weight_decay=1e-5)
+        net.train_step(Xd, Yd, lr=1e-3, weight_decay=1e-5)
+    got = net.get_params().cpu().numpy()
+    # three Adam steps move each weight by about 3e-3; compare the moves
+    assert rel(got - theta, th - theta) < 2e-3
+
+
+def test_rollout_matches_oracle():
+    I, H, L, O, T, B = 7, 32, 2, 5, 4, 3
+    rng = np.random.default_rng(5)
+    theta = rng.uniform(-0.4, 0.4, OL.param_count(I, H, L, O)).astype(np.float32).astype(np.float64)
+    win = rng.standard_normal((B, T, I)).astype(np.float32)
+    te = bf16_weights(theta, I, H, L, O)
+    ref = OL.rollout(te, win.astype(np.float64), 2, 6, H, L, O)
+    net = R.LSTM(I, H, L, O, T, max_batch=8, theta=theta)
+    out = net.rollout(torch.from_numpy(win).cuda(), 2, 6).cpu().numpy()
+    assert rel(out, ref) < 1e-4
+
+
+def test_gather_builds_windows():
+    I, H, L, O, T = 7, 16, 1, 5, 4
+    net = R.LSTM(I, H, L, O, T, max_batch=8)
+    rng = np.random.default_rng(0)
+    series = torch.from_numpy(rng.standard_normal((3, 20, O)).astype(np.float32)).cuda()
+    mu = torch.from_numpy(rng.standard_normal((3, 2)).astype(np.float32)).cuda()
+    idx = torch.tensor([[0, 0], [2, 15], [1, 7]], dtype=torch.int32).cuda()
+    X, Y = net.gather(series, mu, idx)
+    s, m_, X, Y = series.cpu(), mu.cpu(), X.cpu(), Y.cpu()
+    for b, (si, t0) in enumerate([(0, 0), (2, 15), (1, 7)]):
+        for t in range(T):
+            assert torch.equal(X[b, t, :2], m_[si])
+            assert torch.equal(X[b, t, 2:], s[si, t0 + t])
+        assert torch.equal(Y[b], s[si, t0 + T])
