@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="time only the headline form (skip the other precision form)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-instance batched leg")
+    ap.add_argument("--no-learned", action="store_true", help="skip the LSTM leg")
+    ap.add_argument("--learned-epochs", type=int, default=15)
     ap.add_argument("--ny", type=int, default=512,
                     help="grid rows (n = 512 * ny); smaller values make the small profiling case")
     return ap.parse_args()
@@ -214,6 +217,59 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+def run_batched(dev, max_over_ranks, barrier, rank=0, world=1, steps=5):
+    """64 independent instances (4 fields x 16 parameter samples) on a
+    128 x 256 grid, m_b ~ U{500..3000}, k_b in {10, 20, 30, 50}, p = 10,
+    q = 1, FP32, one captured CUDA graph per run; the launch configuration is
+    tuned first.  With N ranks the instances are split by cost across ranks
+    (no collective on the data path)."""
+    import torch
+    import paper_2504_15350_gb300.rpod as R
+    from paper_2504_15350_gb300.shard import instance_cost, shard
+    from synth import batched_recipes, snapshot_matrix
+    recs, ks = batched_recipes(count=64, nx=128, ny=256, J=200, seed=0)
+    mine = shard([instance_cost(r.n, r.m, k, 10, 1) for r, k in zip(recs, ks)], world)[rank]
+    recs, ks, seeds = [recs[b] for b in mine], [ks[b] for b in mine], [16 + b for b in mine]
+    S = [snapshot_matrix(r, device=dev, dtype=torch.float32) for r in recs]
+    B = R.Batch(S, ks, 10, 1, seeds, compute="f32", device=dev)
+    best = B.tune(trials=1)
+    B.run()
+    rc, bad, _ = B.status()
+    if rc != R.RPOD_OK:
+        raise RuntimeError(f"batched: instance {bad}: {R.rpod_strerror(rc)}")
+    stream = torch.cuda.current_stream(dev)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        B.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps)
+    nbytes = 4 * (2 * 1 + 2) * sum(r.n * r.m for r in recs)   # (2q + 2) passes over FP32 S
+    out = {"instances": 64, "instances_this_rank": len(recs), "n": recs[0].n,
+           "sum_m_this_rank": int(sum(r.m for r in recs)),
+           "ms_per_batch": ms, "pass_bytes_GB": nbytes / 1e9,
+           "effective_GBps": nbytes / (ms * 1e-3) / 1e9, "streams": best[0], "split_pct": best[1],
+           "gpu_launches_per_batch": B.launches(), "graph_launches_per_batch": 1}
+    del B, S
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_learned(dev, epochs):
+    """Short rPOD-LSTM run (Sec. 4.3): 2 layers x 256, window 10, batch 512,
+    coefficients of 32 parameter samples x 2000 steps; rollouts of 500 steps
+    for 8 held-out samples against Galerkin projection."""
+    from paper_2504_15350_gb300 import rom
+    r = rom.run(rom.ROMConfig(epochs=epochs, patience=max(4, epochs)), device=dev)
+    return {"epochs": r.epochs_run, "train_windows_per_s": r.samples_per_s,
+            "rollout_steps_per_s": r.rollout_steps_per_s, "rollout_seconds": r.rollout_seconds,
+            "rel_err_lstm": r.err_lstm, "rel_err_persistence": r.err_persistence,
+            "rel_err_nearest_mu": r.err_nearest, "final_val_loss": r.val_loss[-1]}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -377,6 +433,9 @@ def main():
                "d2h_bytes_per_step": 4 * n * k + 8 * l + 4 * k * m, "steps": args.e2e_steps}
         del S_host
 
+    batched = None if args.no_batched else run_batched(dev, max_over_ranks, barrier, rank, world)
+    learned = None if (args.no_learned or rank != 0) else run_learned(dev, args.learned_epochs)
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -397,6 +456,8 @@ def main():
         "gpu_launches": hr["launches"] * hr["steps"],
         "clocks": hr["clocks"],
         "throughput_rpod_per_s": world / (hr["ms"] / 1e3),
+        "batched": batched,
+        "learned": learned,
     }
     for f, r in results.items():
         if f != head:

@@ -106,6 +106,8 @@ def run(cfg: ROMConfig = ROMConfig(), device="cuda", log=None) -> ROMResult:
     if rc != R.RPOD_OK:
         raise R.RpodError(rc, "rpod_basis")
     res.sigma = sig[: cfg.k].cpu().tolist()
+    if log:
+        log(f"rPOD of {n} x {m} done: sigma_1 {res.sigma[0]:.4e}, sigma_k {res.sigma[-1]:.4e}")
     del S
     series = C.t().contiguous().reshape(cfg.n_train_mu, cfg.n_steps, O)      # (M, t, N)
     # 3: z-scores from the training series
@@ -182,4 +184,7 @@ def run(cfg: ROMConfig = ROMConfig(), device="cuda", log=None) -> ROMResult:
     dist = torch.cdist(torch.tensor(mu_te), torch.tensor(mu_tr))
     near = dist.argmin(1).to(dev)
     res.err_nearest = _rel_err(series[near, T:T + cfg.rollout], ref)
+    if log:
+        log(f"rollout {cfg.rollout} steps in {res.rollout_seconds:.3f} s; rel err LSTM {res.err_lstm:.4f}, "
+            f"persistence {res.err_persistence:.4f}, nearest mu {res.err_nearest:.4f}")
     return res

@@ -16,8 +16,10 @@ pytestmark = pytest.mark.gpu
 def test_lstm_rollout_beats_no_lstm_predictors():
     from paper_2504_15350_gb300.build import build
     build()
+    import time
+    t0 = time.time()
     cfg = rom.ROMConfig(epochs=40, patience=8)
-    res = rom.run(cfg)
+    res = rom.run(cfg, log=lambda s: print(f"[{time.time() - t0:7.1f}s] {s}", flush=True))
     print(f"\nLSTM {res.err_lstm:.4f}  persistence {res.err_persistence:.4f}  "
           f"nearest-mu {res.err_nearest:.4f}  epochs {res.epochs_run}  "
           f"train {res.samples_per_s:.0f} windows/s  rollout {res.rollout_steps_per_s:.0f} steps/s")
