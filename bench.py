@@ -217,12 +217,14 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
-def run_batched(dev, max_over_ranks, barrier, rank=0, world=1, steps=5):
+def run_batched(dev, max_over_ranks, barrier, rank=0, world=1, steps=5, form="f32"):
     """64 independent instances (4 fields x 16 parameter samples) on a
     128 x 256 grid, m_b ~ U{500..3000}, k_b in {10, 20, 30, 50}, p = 10,
-    q = 1, FP32, one captured CUDA graph per run; the launch configuration is
-    tuned first.  With N ranks the instances are split by cost across ranks
-    (no collective on the data path)."""
+    q = 1, FP32 snapshots, one captured CUDA graph per run; the launch
+    configuration is tuned first.  form "f32": FP32 passes; form "bf16":
+    BF16 tensor-core passes (the first one also writes the BF16 copy of
+    S) with the FP32 refinement pass.  With N ranks the instances are split
+    by cost across ranks (no collective on the data path)."""
     import torch
     import paper_2504_15350_gb300.rpod as R
     from paper_2504_15350_gb300.shard import instance_cost, shard
@@ -231,7 +233,8 @@ def run_batched(dev, max_over_ranks, barrier, rank=0, world=1, steps=5):
     mine = shard([instance_cost(r.n, r.m, k, 10, 1) for r, k in zip(recs, ks)], world)[rank]
     recs, ks, seeds = [recs[b] for b in mine], [ks[b] for b in mine], [16 + b for b in mine]
     S = [snapshot_matrix(r, device=dev, dtype=torch.float32) for r in recs]
-    B = R.Batch(S, ks, 10, 1, seeds, compute="f32", device=dev)
+    flags = R.RPOD_FLAG_REFINE_FP32 if form == "bf16" else 0
+    B = R.Batch(S, ks, 10, 1, seeds, compute=form, flags=flags, device=dev)
     best = B.tune(trials=1)
     B.run()
     rc, bad, _ = B.status()
@@ -247,8 +250,14 @@ def run_batched(dev, max_over_ranks, barrier, rank=0, world=1, steps=5):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = max_over_ranks(e0.elapsed_time(e1) / steps)
-    nbytes = 4 * (2 * 1 + 2) * sum(r.n * r.m for r in recs)   # (2q + 2) passes over FP32 S
-    out = {"instances": 64, "instances_this_rank": len(recs), "n": recs[0].n,
+    nm = sum(r.n * r.m for r in recs)
+    if form == "bf16":
+        # first Y-pass reads FP32 S and writes its BF16 copy, 2q BF16 passes,
+        # the FP32 refinement pass reads FP32 S
+        nbytes = (4 + 2 + 2 * 2 * 1 + 4) * nm
+    else:
+        nbytes = 4 * (2 * 1 + 2) * nm   # (2q + 2) passes over FP32 S
+    out = {"form": form, "instances": 64, "instances_this_rank": len(recs), "n": recs[0].n,
            "sum_m_this_rank": int(sum(r.m for r in recs)),
            "ms_per_batch": ms, "pass_bytes_GB": nbytes / 1e9,
            "effective_GBps": nbytes / (ms * 1e-3) / 1e9, "streams": best[0], "split_pct": best[1],
@@ -433,7 +442,10 @@ def main():
                "d2h_bytes_per_step": 4 * n * k + 8 * l + 4 * k * m, "steps": args.e2e_steps}
         del S_host
 
-    batched = None if args.no_batched else run_batched(dev, max_over_ranks, barrier, rank, world)
+    batched = batched_f32 = None
+    if not args.no_batched:
+        batched = run_batched(dev, max_over_ranks, barrier, rank, world, form="bf16")
+        batched_f32 = run_batched(dev, max_over_ranks, barrier, rank, world, form="f32")
     learned = None if (args.no_learned or rank != 0) else run_learned(dev, args.learned_epochs)
 
     if rank != 0:
@@ -457,6 +469,7 @@ def main():
         "clocks": hr["clocks"],
         "throughput_rpod_per_s": world / (hr["ms"] / 1e3),
         "batched": batched,
+        "batched_f32": batched_f32,
         "learned": learned,
     }
     for f, r in results.items():

@@ -235,8 +235,13 @@ void rpod_batch_destroy(rpod_batch* batch);
  * and outputs row-major (batch, out_dim). */
 typedef struct rpod_lstm rpod_lstm;
 
+/* rpod_lstm_create flags */
+enum {
+  RPOD_LSTM_FP32_WEIGHTS = 1u  /* products read the FP32 master weights, not BF16 copies */
+};
+
 int rpod_lstm_create(rpod_lstm** out, int32_t in_dim, int32_t hidden, int32_t layers,
-                     int32_t out_dim, int32_t window, int32_t max_batch);
+                     int32_t out_dim, int32_t window, int32_t max_batch, uint32_t flags);
 int64_t rpod_lstm_param_count(const rpod_lstm* net);
 int rpod_lstm_workspace_bytes(const rpod_lstm* net, size_t* bytes);
 /* Copies the flat parameter vector (host or device pointer) into the

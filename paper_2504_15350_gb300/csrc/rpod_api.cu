@@ -105,11 +105,18 @@ struct Run {
 
   // Gram G = A^T A (A rows x l, ld lda) in FP64: products in W, summed in W
   // within a split of rows, then in FP64 across splits.
-  int gram(const W* A, int64_t rows, int64_t lda, double* G, int nsplit) {
+  // Gram partials of the l columns of A, summed in FP64 into G.  FP32: the
+  // tensor-core split-TF32 kernel when `fast` (and A is TMA-addressable),
+  // else FP32 products on the SIMT pipes.
+  int gram(const W* A, int64_t rows, int64_t lda, double* G, int nsplit, bool fast) {
     const int l = P->l;
-    if (sizeof(W) == 4)
-      CK(gram_f32(st, rows, l, (const float*)A, lda, nsplit, dbuf(P->off_gpart)));
-    else
+    if (sizeof(W) == 4) {
+      int rc = fast ? tc_gram(st, (const float*)A, lda, rows, l, dbuf(P->off_gpart), nsplit, status)
+                    : RPOD_ERR_UNSUPPORTED;
+      if (rc == RPOD_ERR_CUDA) return rc;
+      if (rc != RPOD_OK)
+        CK(gram_f32(st, rows, l, (const float*)A, lda, nsplit, dbuf(P->off_gpart)));
+    } else
       CK((gemm<W, W, W, double>(st, true, l, l, rows, nsplit, A, lda, A, lda, dbuf(P->off_gpart), 1,
                                 l, (int64_t)l * l, status, false)));
     CK((reduce_splits<double, double>(st, l, l, nsplit, dbuf(P->off_gpart), G, 1, l)));
@@ -117,8 +124,12 @@ struct Run {
   }
 
   // CholeskyQR with `rounds` passes (CholeskyQR2 for rounds = 2); returns the
-  // buffer holding Q (in or tmp).
-  int orth(W* in, W* tmp, int64_t rows, int rounds, W** out) {
+  // buffer holding Q (in or tmp).  Only the conditioning of an intermediate
+  // basis matters (its span comes from the FP32 product Y R^{-1}), so its
+  // Gram may take the split-TF32 tensor path; with `exact_last` the last
+  // round, which fixes the orthogonality of the returned basis, keeps FP32
+  // products.
+  int orth(W* in, W* tmp, int64_t rows, int rounds, W** out, bool exact_last) {
     const int l = P->l;
     const double tol = sizeof(W) == 8 ? 1e-13 : 1e-5;
     // FP32 Gram: two row chunks per SM (the kernel fits two blocks per SM)
@@ -128,7 +139,7 @@ struct Run {
     W* dst = tmp;
     for (int r = 0; r < rounds; ++r) {
       double* G = dbuf(P->off_g);
-      CR(gram(src, rows, rows, G, ns));
+      CR(gram(src, rows, rows, G, ns, !(exact_last && r == rounds - 1)));
       CK((cholesky<W>(st, l, G, tol, r, dbuf(P->off_x), buf(P->off_xw), l, status,
                       sizeof(W) == 4 ? (const float*)src : nullptr, rows, dbuf(P->off_gpart), ns)));
       CK((gemm<W, W, W, W>(st, false, rows, l, l, 1, src, rows, buf(P->off_xw), l, dst, 1, rows, 0,
@@ -150,7 +161,11 @@ struct Run {
                               (int64_t)l * l, status, false)));
     CK((reduce_splits<double, double>(st, l, l, ns, dbuf(P->off_gpart), GT, 1, l)));
     double* Uhat = dbuf(P->off_uhat);
-    CK((sym_eig(st, l, GT, sigma, Uhat, dbuf(P->off_eig), status, 5)));
+    // FP64 refinement passes after the FP32 Jacobi stage: each squares the
+    // eigenvector error, so from about 1e-6 two reach FP64 level for
+    // separated eigenvalues; the FP32 forms stop at three, the FP64 form
+    // takes five for clusters.
+    CK((sym_eig(st, l, GT, sigma, Uhat, dbuf(P->off_eig), status, sizeof(W) == 8 ? 5 : 3)));
     CK((check_finite_vec(st, l, sigma, status)));
     // Alg. 1: lift U = Q Uhat (first k or all l columns), then the sign rule
     const int ku = (P->flags & RPOD_FLAG_RETURN_ALL_L) ? l : k;
@@ -190,14 +205,14 @@ struct Run {
         prof_end(P, st, pass_bytes, pass_flops);
         CK((reduce_splits<W, W>(st, m, l, P->nsplit_z, part, Z, 1, m)));
         W* Zo = nullptr;
-        CR(orth(Z, Zq, m, 1, &Zo));
+        CR(orth(Z, Zq, m, 1, &Zo, false));
         prof_begin(P, st);
         CK((gemm<W, W, W, W>(st, false, n, l, m, 1, S, lds, Zo, m, Y, 1, n, 0, status, false)));
         prof_end(P, st, pass_bytes, pass_flops);
       }
       // Alg. 1 QR of the sampled matrix (CholeskyQR2 for the final basis);
       // Y's buffer is free again once Z = S^T Q is formed
-      CR(orth(Y, Qb, n, it == q ? 2 : 1, &Q));
+      CR(orth(Y, Qb, n, it == q ? 2 : 1, &Q, it == q));
     }
     // Alg. 1: T = Q^T S, stored transposed (m x l)
     prof_begin(P, st);
@@ -224,27 +239,13 @@ struct Run {
     void* Qh = ws + P->off_qb;   // n_ld x 128, 16-bit
     void* Zh = ws + P->off_zb;   // m_ld x 128, 16-bit
     const int64_t nld = P->n_ld, mld = P->m_ld;
-    // 16-bit operand buffers: zero the padding columns l..127 once per call
-    CK(cudaMemsetAsync(Qh, 0, (size_t)nld * 128 * 2, st));
-    CK(cudaMemsetAsync(Zh, 0, (size_t)mld * 128 * 2, st));
+    // Columns l..127 of the 16-bit operand buffers are never read: the tensor
+    // maps span l columns and TMA fills the rest of each 128-wide box with 0.
     // the 16-bit S read by the passes
     const void* Sh = S_in;
     int64_t ldh = lds_in;
     const double pass_flops = 2.0 * n * m * l;
     const double pb16 = 2.0 * ((double)n * m + (double)n * l + (double)m * l);
-    if (s_dtype == RPOD_F32) {
-      prof_begin(P, st);
-      if (dt == RPOD_BF16)
-        CK(convert_snapshots<__nv_bfloat16>(st, n, m, (const float*)S_in, lds_in,
-                                            (__nv_bfloat16*)(ws + P->off_sb), nld, status));
-      else
-        CK(convert_snapshots<__half>(st, n, m, (const float*)S_in, lds_in, (__half*)(ws + P->off_sb),
-                                     nld, status));
-      prof_end(P, st, 6.0 * (double)n * m, 0.0);
-      Sh = ws + P->off_sb;
-      ldh = nld;
-      if (!Sref) { Sref = (const float*)S_in; ldr = lds_in; }
-    }
     auto to16 = [&](const float* src, int64_t rows, int64_t ldsrc, void* dst, int64_t ldd) -> cudaError_t {
       if (dt == RPOD_BF16)
         return convert_matrix<float, __nv_bfloat16>(st, rows, l, src, ldsrc, (__nv_bfloat16*)dst, ldd);
@@ -255,10 +256,35 @@ struct Run {
       CK((sketch<__nv_bfloat16>(st, P->seed, 0, m, l, (__nv_bfloat16*)Zh, mld)));
     else
       CK((sketch<__half>(st, P->seed, 0, m, l, (__half*)Zh, mld)));
-    // Alg. 1: P = S Lambda
-    prof_begin(P, st);
-    CR(tc_ypass(st, dt, Zh, mld, Sh, ldh, n, m, l, Y, n, status));
-    prof_end(P, st, pb16, pass_flops);
+    // Alg. 1: P = S Lambda.  An FP32 S is rounded to the 16-bit type by the
+    // same pass, which also leaves the 16-bit copy for the later passes.
+    if (s_dtype == RPOD_F32) {
+      void* Sb = ws + P->off_sb;
+      prof_begin(P, st);
+      int rc = tc_ypass_cvt(st, dt, Zh, mld, (const float*)S_in, lds_in, n, m, l, Y, n, Sb, nld,
+                            status);
+      if (rc == RPOD_ERR_UNSUPPORTED) {
+        if (dt == RPOD_BF16)
+          CK(convert_snapshots<__nv_bfloat16>(st, n, m, (const float*)S_in, lds_in,
+                                              (__nv_bfloat16*)Sb, nld, status));
+        else
+          CK(convert_snapshots<__half>(st, n, m, (const float*)S_in, lds_in, (__half*)Sb, nld,
+                                       status));
+        rc = tc_ypass(st, dt, Zh, mld, Sb, nld, n, m, l, Y, n, status);
+        CR(rc);
+        prof_end(P, st, 6.0 * (double)n * m + pb16, pass_flops);
+      } else {
+        CR(rc);
+        prof_end(P, st, 6.0 * (double)n * m + 2.0 * (double)m * l + 4.0 * (double)n * l, pass_flops);
+      }
+      Sh = Sb;
+      ldh = nld;
+      if (!Sref) { Sref = (const float*)S_in; ldr = lds_in; }
+    } else {
+      prof_begin(P, st);
+      CR(tc_ypass(st, dt, Zh, mld, Sh, ldh, n, m, l, Y, n, status));
+      prof_end(P, st, pb16, pass_flops);
+    }
     float* Q = nullptr;
     for (int it = 0; it <= q; ++it) {
       if (it > 0) {
@@ -268,13 +294,13 @@ struct Run {
         prof_end(P, st, pb16, pass_flops);
         CK((reduce_splits<float, float>(st, m, l, P->nsplit_w, wpart, Z, 1, m)));
         float* Zo = nullptr;
-        CR(orth(Z, Zq, m, 1, &Zo));
+        CR(orth(Z, Zq, m, 1, &Zo, false));
         CK(to16(Zo, m, m, Zh, mld));
         prof_begin(P, st);
         CR(tc_ypass(st, dt, Zh, mld, Sh, ldh, n, m, l, Y, n, status));
         prof_end(P, st, pb16, pass_flops);
       }
-      CR(orth(Y, Qbuf, n, it == q ? 2 : 1, &Q));
+      CR(orth(Y, Qbuf, n, it == q ? 2 : 1, &Q, it == q));
       if (it < q) CK(to16(Q, n, n, Qh, nld));
     }
     // Alg. 1: T = Q^T S (TF32 from the FP32 copy when refining)
@@ -291,10 +317,9 @@ struct Run {
     }
     if (refine) {
       float* Atf = (float*)(ws + P->off_atf);
-      CK(cudaMemsetAsync(Atf, 0, (size_t)n * 128 * 4, st));
-      CK(round_tf32(st, n, l, Q, n, Atf, n));
+      CK(round_tf32(st, n, l, Q, n, Atf, nld));
       prof_begin(P, st);
-      CR(tc_wpass(st, RPOD_F32, Atf, n, n, l, Sref, ldr, m, wpart, P->nsplit_w, status));
+      CR(tc_wpass(st, RPOD_F32, Atf, nld, n, l, Sref, ldr, m, wpart, P->nsplit_w, status));
       prof_end(P, st, 4.0 * ((double)n * m + (double)n * l + (double)m * l), pass_flops);
     } else {
       CK(to16(Q, n, n, Qh, nld));
@@ -330,7 +355,6 @@ struct Run {
     const int dt = P->compute;
     void* Qh = ws + P->off_qb;
     float* wpart = (float*)(ws + P->off_wpart);
-    CK(cudaMemsetAsync(Qh, 0, (size_t)P->n_ld * 128 * 2, st));
     if (dt == RPOD_BF16)
       CK((convert_matrix<float, __nv_bfloat16>(st, n, kc, U, ldu, (__nv_bfloat16*)Qh, P->n_ld)));
     else
@@ -426,7 +450,7 @@ static int plan_create_impl(rpod_plan** out, int64_t n, int64_t m, int32_t k, in
     P->off_sb = take((size_t)2 * P->n_ld * m);
     P->off_qb = take((size_t)2 * P->n_ld * 128);
     P->off_zb = take((size_t)2 * P->m_ld * 128);
-    P->off_atf = take((size_t)4 * n * 128);
+    P->off_atf = take((size_t)4 * P->n_ld * 128);
     P->off_wpart = take(4 * P->wpart_elems);
   }
   P->total = off;
@@ -551,7 +575,6 @@ int rpod_sample(const rpod_plan* P, const void* A, int64_t lda, const void* S, i
   cudaStream_t st = (cudaStream_t)stream;
   char* ws = (char*)workspace;
   void* Zh = ws + P->off_zb;
-  if (cudaMemsetAsync(Zh, 0, (size_t)P->m_ld * 128 * 2, st) != cudaSuccess) return RPOD_ERR_CUDA;
   if (cudaMemcpy2DAsync(Zh, (size_t)P->m_ld * 2, A, (size_t)lda * 2, (size_t)P->m * 2, (size_t)P->l,
                         cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return RPOD_ERR_CUDA;

@@ -30,6 +30,7 @@ struct rpod_lstm {
   size_t part_floats;
   int64_t step;
   int last_launches;
+  int wfp32;  // products read the FP32 master weights instead of BF16 copies
 };
 
 namespace rpod {
@@ -52,9 +53,13 @@ __global__ void k_to_time_major(int B, int T, int I, const float* __restrict__ X
 // One recurrent step of one layer for all batch rows: 256 threads, tile of
 // 32 batch rows x 32 units (x 4 gates); thread (tb, tu) holds 4 rows x 4 gates
 // of unit u0 + tu.
+__device__ __forceinline__ float ldw(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float ldw(const float* p) { return *p; }
+
+template <typename TW>
 __global__ void __launch_bounds__(256)
 k_lstm_fwd_step(int B, int H, const float* __restrict__ Gx, const float* __restrict__ bias,
-                const float* __restrict__ h_prev, const __nv_bfloat16* __restrict__ Wh,
+                const float* __restrict__ h_prev, const TW* __restrict__ Wh,
                 const float* __restrict__ c_prev, float* __restrict__ c_out, float* __restrict__ h_out,
                 float* __restrict__ gates) {
   __shared__ float hs[32][33];
@@ -76,7 +81,7 @@ k_lstm_fwd_step(int B, int H, const float* __restrict__ Gx, const float* __restr
       const int rr = e >> 5, kk = e & 31;
       const int g = rr >> 5, uu = rr & 31;
       const int u = u0 + uu, k = k0 + kk;
-      wsm[rr][kk] = (u < H && k < H) ? __bfloat162float(Wh[(int64_t)(g * H + u) * H + k]) : 0.f;
+      wsm[rr][kk] = (u < H && k < H) ? ldw(Wh + (int64_t)(g * H + u) * H + k) : 0.f;
     }
     __syncthreads();
 #pragma unroll 8
@@ -275,15 +280,27 @@ struct Net {
   float* cc(int l) const { return f(N->o_c) + l * layer_stride_ch(); }
   float* hh(int l) const { return f(N->o_h) + l * layer_stride_ch(); }
 
-  // forward over the time-major input Xt (T x B x I); y (B x O) without bias
+  template <typename TW>
+  const TW* weights() const {
+    return sizeof(TW) == 4 ? (const TW*)(ws + N->o_theta) : (const TW*)(ws + N->o_wbf);
+  }
   int forward(const float* Xt, int B) {
+    return N->wfp32 ? forward_t<float>(Xt, B) : forward_t<__nv_bfloat16>(Xt, B);
+  }
+  int backward(const float* Xt, int B) {
+    return N->wfp32 ? backward_t<float>(Xt, B) : backward_t<__nv_bfloat16>(Xt, B);
+  }
+
+  // forward over the time-major input Xt (T x B x I); y (B x O) without bias
+  template <typename TW>
+  int forward_t(const float* Xt, int B) {
     const int H = N->H, T = N->T;
-    const __nv_bfloat16* W = wbf();
+    const TW* W = weights<TW>();
     for (int l = 0; l < N->L; ++l) {
       const int Il = in_dim(l);
       const float* Xin = l == 0 ? Xt : hh(l - 1) + (size_t)B * H;  // h_1..h_T of the layer below
       // hoisted input projection for all T steps
-      LK((gemm_ex<float, __nv_bfloat16, float, float>(st, true, true, (int64_t)T * B, 4 * H, Il, 1, Xin, Il,
+      LK((gemm_ex<float, TW, float, float>(st, true, true, (int64_t)T * B, 4 * H, Il, 1, Xin, Il,
                                                      W + N->off_w[l][0], Il, gx(l), 4 * H, 1, 0,
                                                      nullptr, false)));
       LK(cudaMemsetAsync(cc(l), 0, (size_t)B * H * 4, st));
@@ -291,7 +308,7 @@ struct Net {
       const float* bias = f(N->o_theta) + N->off_w[l][2];
       dim3 grid((B + 31) / 32, (H + 31) / 32);
       for (int t = 0; t < T; ++t) {
-        k_lstm_fwd_step<<<grid, 256, 0, st>>>(B, H, gx(l) + (size_t)t * B * 4 * H, bias,
+        k_lstm_fwd_step<TW><<<grid, 256, 0, st>>>(B, H, gx(l) + (size_t)t * B * 4 * H, bias,
                                               hh(l) + (size_t)t * B * H, W + N->off_w[l][1],
                                               cc(l) + (size_t)t * B * H, cc(l) + (size_t)(t + 1) * B * H,
                                               hh(l) + (size_t)(t + 1) * B * H,
@@ -300,7 +317,7 @@ struct Net {
       }
     }
     const float* hT = hh(N->L - 1) + (size_t)T * B * H;
-    LK((gemm_ex<float, __nv_bfloat16, float, float>(st, true, true, B, N->O, H, 1, hT, H, W + N->off_wy, H,
+    LK((gemm_ex<float, TW, float, float>(st, true, true, B, N->O, H, 1, hT, H, W + N->off_wy, H,
                                                    f(N->o_y), N->O, 1, 0, nullptr, false)));
     return RPOD_OK;
   }
@@ -315,9 +332,10 @@ struct Net {
     return RPOD_OK;
   }
 
-  int backward(const float* Xt, int B) {
+  template <typename TW>
+  int backward_t(const float* Xt, int B) {
     const int H = N->H, T = N->T, O = N->O;
-    const __nv_bfloat16* W = wbf();
+    const TW* W = weights<TW>();
     float* G = f(N->o_grad);
     const float* hT = hh(N->L - 1) + (size_t)T * B * H;
     float* dy = f(N->o_dy);
@@ -327,7 +345,7 @@ struct Net {
     LL();
     float* dhext = f(N->o_dhext);
     LK(cudaMemsetAsync(dhext, 0, (size_t)T * B * H * 4, st));
-    LK((gemm_ex<float, __nv_bfloat16, float, float>(st, true, false, B, H, O, 1, dy, O, W + N->off_wy, H,
+    LK((gemm_ex<float, TW, float, float>(st, true, false, B, H, O, 1, dy, O, W + N->off_wy, H,
                                                    dhext + (size_t)(T - 1) * B * H, H, 1, 0, nullptr,
                                                    false)));
     float* dz = f(N->o_dz);
@@ -343,7 +361,7 @@ struct Net {
             dc, dz + (size_t)t * B * 4 * H);
         LL();
         if (t > 0)
-          LK((gemm_ex<float, __nv_bfloat16, float, float>(st, true, false, B, H, 4 * H, 1,
+          LK((gemm_ex<float, TW, float, float>(st, true, false, B, H, 4 * H, 1,
                                                          dz + (size_t)t * B * 4 * H, 4 * H,
                                                          W + N->off_w[l][1], H, dhrec, H, 1, 0, nullptr,
                                                          false)));
@@ -355,7 +373,7 @@ struct Net {
       k_colsum<<<(4 * H + 127) / 128, 128, 0, st>>>(rows, 4 * H, dz, G + N->off_w[l][2]);
       LL();
       if (l > 0)
-        LK((gemm_ex<float, __nv_bfloat16, float, float>(st, true, false, rows, Il, 4 * H, 1, dz, 4 * H,
+        LK((gemm_ex<float, TW, float, float>(st, true, false, rows, Il, 4 * H, 1, dz, 4 * H,
                                                        W + N->off_w[l][0], Il, dhext, Il, 1, 0, nullptr,
                                                        false)));
     }
@@ -371,13 +389,14 @@ using namespace rpod;
 extern "C" {
 
 int rpod_lstm_create(rpod_lstm** out, int32_t in_dim, int32_t hidden, int32_t layers,
-                     int32_t out_dim, int32_t window, int32_t max_batch) {
+                     int32_t out_dim, int32_t window, int32_t max_batch, uint32_t flags) {
   if (!out || in_dim < 1 || hidden < 1 || layers < 1 || layers > 8 || out_dim < 1 || window < 1 ||
-      max_batch < 1 || out_dim > in_dim)
+      max_batch < 1 || out_dim > in_dim || (flags & ~(uint32_t)RPOD_LSTM_FP32_WEIGHTS))
     return RPOD_ERR_INVALID_ARG;
   rpod_lstm* N = new (std::nothrow) rpod_lstm();
   if (!N) return RPOD_ERR_INVALID_ARG;
   N->I = in_dim; N->H = hidden; N->L = layers; N->O = out_dim; N->T = window; N->Bmax = max_batch;
+  N->wfp32 = (flags & RPOD_LSTM_FP32_WEIGHTS) ? 1 : 0;
   int64_t off = 0;
   for (int l = 0; l < layers; ++l) {
     const int64_t Il = l == 0 ? in_dim : hidden;

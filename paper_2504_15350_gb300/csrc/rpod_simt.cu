@@ -5,6 +5,7 @@
 #include <float.h>
 #include <math.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "rpod_internal.cuh"
@@ -195,23 +196,45 @@ INST_GEMM(float, __nv_bfloat16, float, float)
 #undef INST_GEMM
 
 // ------------------------------------------------------------------------
+// Deterministic split-K reduction out(i, j) = sum_z part[z][i + j M]: a
+// block covers 32 consecutive elements with 8 z-slices (32 x 8 threads), each
+// slice summed in z order with four accumulators, the slices combined in a
+// fixed order.
 template <typename TP, typename TO>
-__global__ void k_reduce(int64_t M, int64_t N, int nsplit, const TP* __restrict__ part,
-                         TO* __restrict__ out, int64_t oi, int64_t oj) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256)
+k_reduce(int64_t M, int64_t N, int nsplit, const TP* __restrict__ part, TO* __restrict__ out,
+         int64_t oi, int64_t oj) {
+  __shared__ double acc[8][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t idx = (int64_t)blockIdx.x * 32 + tx;
   const int64_t MN = M * N;
-  if (idx >= MN) return;
-  double s = 0.0;
-  for (int z = 0; z < nsplit; ++z) s += (double)part[z * MN + idx];
-  const int64_t i = idx % M, j = idx / M;
-  out[i * oi + j * oj] = (TO)s;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  if (idx < MN) {
+    int z = ty;
+    for (; z + 24 < nsplit; z += 32) {
+      s0 += (double)part[(int64_t)z * MN + idx];
+      s1 += (double)part[(int64_t)(z + 8) * MN + idx];
+      s2 += (double)part[(int64_t)(z + 16) * MN + idx];
+      s3 += (double)part[(int64_t)(z + 24) * MN + idx];
+    }
+    for (; z < nsplit; z += 8) s0 += (double)part[(int64_t)z * MN + idx];
+  }
+  acc[ty][tx] = (s0 + s1) + (s2 + s3);
+  __syncthreads();
+  if (ty == 0 && idx < MN) {
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += acc[k][tx];
+    const int64_t i = idx % M, j = idx / M;
+    out[i * oi + j * oj] = (TO)t;
+  }
 }
 
 template <typename TP, typename TO>
 cudaError_t reduce_splits(cudaStream_t st, int64_t M, int64_t N, int nsplit, const TP* part,
                           TO* out, int64_t oi, int64_t oj) {
   const int64_t MN = M * N;
-  k_reduce<TP, TO><<<(unsigned)((MN + 255) / 256), 256, 0, st>>>(M, N, nsplit, part, out, oi, oj); note_launch();
+  k_reduce<TP, TO><<<(unsigned)((MN + 31) / 32), 256, 0, st>>>(M, N, nsplit, part, out, oi, oj); note_launch();
   return cudaGetLastError();
 }
 template cudaError_t reduce_splits<double, double>(cudaStream_t, int64_t, int64_t, int, const double*, double*, int64_t, int64_t);
@@ -262,9 +285,18 @@ k_cholesky(int l, const double* __restrict__ G, double tol, double* __restrict__
   __shared__ TF s_rinv;
   __shared__ int s_keep[kMaxL];
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < l * l; e += nt) {
-    const int i = e % l, j = e / l;
-    if (i <= j) A[i + j * ld] = (TF)G[e];
+  for (int e0 = 0; e0 < l * l; e0 += 8 * nt) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * nt + tid;
+      v[u] = e < l * l ? G[e] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * nt + tid, i = e % l, j = e / l;
+      if (e < l * l && i <= j) A[i + j * ld] = (TF)v[u];
+    }
   }
   double dm = 0.0;
   for (int j = tid; j < l; j += nt) { d0[j] = G[j + j * l]; dm = fmax(dm, d0[j]); }
@@ -332,18 +364,24 @@ static cudaError_t launch_cholesky(cudaStream_t st, int l, const double* G, doub
 
 // Register-blocked FP32 CholeskyQR step (l <= 128): the 256 threads form a
 // 16 x 16 grid and each holds an 8 x 8 block of the (zero-padded) 128 x 128
-// Gram matrix in registers.  Step j of the right-looking factorization
-// publishes row j of R through shared memory and every thread applies the
-// rank-1 update to its block; the inverse X = R^{-1} is then formed by the
-// column sweep W <- I, X(:, j) = W(:, j) / R_jj, W(:, c) -= X(:, j) R_jc for
-// c > j, with the same blocking.  Two barriers per step.  Semantics (pivot
-// test, dropped directions, FP64 gate) as k_cholesky32.
+// Gram matrix in registers.  Step j of the right-looking factorization reads
+// the updated row j from a double-buffered shared row, forms row j of R
+// (every thread takes the same pivot decision from the same values), applies
+// the rank-1 update to its block and, if it owns row j + 1, publishes that
+// row for the next step: one barrier per step.  R is kept in shared memory.
+// The inverse X = R^{-1} is then formed by the column sweep W <- I,
+// X(:, j) = W(:, j) / R_jj, W(:, c) -= X(:, j) R_jc for c > j, again with one
+// barrier per step (the owner of column j + 1 publishes it scaled).
+// Semantics (pivot test, dropped directions, FP64 gate) as k_cholesky.
+constexpr int kRbLd = 129;
+constexpr size_t kRbSmem = (size_t)128 * kRbLd * sizeof(float);
+
 template <typename TW>
 __global__ void __launch_bounds__(256)
 k_cholesky_rb(int l, const double* __restrict__ G, float tol, int* gate, double* __restrict__ Xout,
               TW* __restrict__ Xw, int ldxw, unsigned* status) {
-  __shared__ __align__(16) float s_row[128];
-  __shared__ __align__(16) float s_col[128];
+  extern __shared__ float s_R[];  // [128][kRbLd]: G (column j at row j), then R rows, then X columns
+  __shared__ __align__(16) float s_u[2][128];
   __shared__ float s_d0[128];
   __shared__ float s_rdiag[128];
   __shared__ int s_keep[128];
@@ -351,14 +389,21 @@ k_cholesky_rb(int l, const double* __restrict__ G, float tol, int* gate, double*
   __shared__ double red[32];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int r0 = ty * 8, c0 = tx * 8;
-  float A[8][8];
+  // 16 independent loads in flight per thread (a plain strided loop would
+  // wait out one global-load latency per element)
+  for (int e0 = 0; e0 < 128 * 128; e0 += 256 * 16) {
+    float v[16];
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int i = r0 + a, j = c0 + b;
-      A[a][b] = (i < l && j < l) ? (float)G[i + j * l] : 0.f;
+    for (int u = 0; u < 16; ++u) {
+      const int e = e0 + u * 256 + tid, i = e & 127, j = e >> 7;
+      v[u] = (i < l && j < l) ? (float)G[i + j * l] : 0.f;
     }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int e = e0 + u * 256 + tid, i = e & 127, j = e >> 7;
+      s_R[j * kRbLd + i] = v[u];
+    }
+  }
   double dm = 0.0;
   if (tid < 128) {
     const double g = tid < l ? G[tid + tid * l] : 0.0;
@@ -366,108 +411,111 @@ k_cholesky_rb(int l, const double* __restrict__ G, float tol, int* gate, double*
     dm = g;
   }
   if (tid == 0) s_ill = 0;
-  const float gmax = (float)block_max(dm, red);
-  // factorization
-  for (int j = 0; j < l; ++j) {
-    const int jb = j >> 3, jo = j & 7;
-    if (ty == jb && tx == jb) {
-      float d = 0.f;
+  const float gmax = (float)block_max(dm, red);  // barrier: s_R, s_d0 visible
+  float A[8][8];
 #pragma unroll
-      for (int a = 0; a < 8; ++a)
-        if (a == jo) d = A[a][a];
-      const float d0 = s_d0[j];
-      const bool keep = (d0 > 1e-30f) && (d0 > 1e-30f * gmax) && (d > tol * d0);
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) A[a][b] = s_R[(c0 + b) * kRbLd + r0 + a];
+  if (tid < 128) s_u[0][tid] = s_R[tid * kRbLd];  // row 0 = column 0
+  __syncthreads();
+  // factorization; row j of R goes to s_R[j][*]
+  for (int j = 0; j < l; ++j) {
+    const int buf = j & 1;
+    const float d = s_u[buf][j], d0 = s_d0[j];
+    const bool keep = (d0 > 1e-30f) && (d0 > 1e-30f * gmax) && (d > tol * d0);
+    const float rd = keep ? sqrtf(d) : 0.f;
+    const float rinv = keep ? 1.f / rd : 0.f;
+    if (tid == 0) {
       if (d < 1e-4f * d0) s_ill = 1;
       s_keep[j] = keep ? 1 : 0;
-      s_rdiag[j] = keep ? sqrtf(d) : 0.f;
+      s_rdiag[j] = rd;
     }
-    __syncthreads();
-    if (ty == jb) {
-      const float rd = s_rdiag[j];
-      const float rinv = rd > 0.f ? 1.f / rd : 0.f;
-#pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        if (a != jo) continue;
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-          const int c = c0 + b;
-          const float v = (c > j) ? A[a][b] * rinv : (c == j ? rd : 0.f);
-          A[a][b] = v;            // row j of A becomes row j of R
-          s_row[c] = v;
-        }
-      }
-    }
-    __syncthreads();
     float ra[8], rb[8];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) ra[a] = s_row[r0 + a];
+    for (int a = 0; a < 8; ++a) ra[a] = (r0 + a > j) ? s_u[buf][r0 + a] * rinv : 0.f;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) rb[b] = s_row[c0 + b];
+    for (int b = 0; b < 8; ++b) rb[b] = (c0 + b > j) ? s_u[buf][c0 + b] * rinv : 0.f;
+    if (ty == 0) {
+#pragma unroll
+      for (int b = 0; b < 8; ++b) s_R[j * kRbLd + c0 + b] = (c0 + b == j) ? rd : rb[b];
+    }
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
-      for (int b = 0; b < 8; ++b)
-        if (r0 + a > j && c0 + b > j) A[a][b] -= ra[a] * rb[b];
+      for (int b = 0; b < 8; ++b) A[a][b] -= ra[a] * rb[b];
+    const int j1 = j + 1;
+    if (j1 < l && ty == (j1 >> 3)) {
+      const int jo = j1 & 7;
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+        if (a == jo) {
+#pragma unroll
+          for (int b = 0; b < 8; ++b) s_u[buf ^ 1][c0 + b] = A[a][b];
+        }
+    }
     __syncthreads();
   }
-  // inverse by the column sweep; R stays in A's upper triangle
+  // inverse by the column sweep
   float W[8][8];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
     for (int b = 0; b < 8; ++b) W[a][b] = (r0 + a == c0 + b) ? 1.f : 0.f;
+  if (tid < 128) {  // column 0 of X
+    const float rd0 = s_rdiag[0];
+    s_u[0][tid] = (tid == 0 && rd0 > 0.f) ? 1.f / rd0 : 0.f;
+  }
+  __syncthreads();
   for (int j = 0; j < l; ++j) {
-    const int jb = j >> 3, jo = j & 7;
-    const float rd = s_rdiag[j];
-    if (tx == jb) {
-      const float rinv = rd > 0.f ? 1.f / rd : 0.f;
-#pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        if (b != jo) continue;
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {
-          const float x = W[a][b] * rinv;
-          W[a][b] = x;
-          s_col[r0 + a] = x;
-        }
-      }
-    }
-    if (ty == jb) {
-#pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        if (a != jo) continue;
-#pragma unroll
-        for (int b = 0; b < 8; ++b) s_row[c0 + b] = (c0 + b > j && rd > 0.f) ? A[a][b] : 0.f;
-      }
-    }
-    __syncthreads();
+    const int buf = j & 1, jb = j >> 3, jo = j & 7;
+    const bool live = s_rdiag[j] > 0.f;
     float xa[8], rc[8];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) xa[a] = s_col[r0 + a];
+    for (int a = 0; a < 8; ++a) xa[a] = s_u[buf][r0 + a];
 #pragma unroll
-    for (int b = 0; b < 8; ++b) rc[b] = s_row[c0 + b];
+    for (int b = 0; b < 8; ++b) rc[b] = (live && c0 + b > j) ? s_R[j * kRbLd + c0 + b] : 0.f;
+    if (tx == jb) {
+#pragma unroll
+      for (int b = 0; b < 8; ++b)
+        if (b == jo) {
+#pragma unroll
+          for (int a = 0; a < 8; ++a) W[a][b] = xa[a];
+        }
+    }
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
+      for (int b = 0; b < 8; ++b) W[a][b] -= xa[a] * rc[b];
+    const int j1 = j + 1;
+    if (j1 < l && tx == (j1 >> 3)) {
+      const float rd1 = s_rdiag[j1];
+      const float rinv1 = rd1 > 0.f ? 1.f / rd1 : 0.f;
+      const int jo1 = j1 & 7;
+#pragma unroll
       for (int b = 0; b < 8; ++b)
-        if (c0 + b > j) W[a][b] -= xa[a] * rc[b];
+        if (b == jo1) {
+#pragma unroll
+          for (int a = 0; a < 8; ++a) s_u[buf ^ 1][r0 + a] = W[a][b] * rinv1;
+        }
+    }
     __syncthreads();
   }
-  int ndropped = 0;
-  if (tid == 0)
-    for (int j = 0; j < l; ++j) ndropped += s_keep[j] ? 0 : 1;
+  // X (upper triangle of W) through shared memory for coalesced stores
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int i = r0 + a, j = c0 + b;
-      if (i < l && j < l) {
-        const float v = (i <= j) ? W[a][b] : 0.f;
-        Xout[i + j * l] = (double)v;
-        Xw[i + (int64_t)j * ldxw] = (TW)v;
-      }
-    }
+    for (int b = 0; b < 8; ++b) s_R[(c0 + b) * kRbLd + r0 + a] = (r0 + a <= c0 + b) ? W[a][b] : 0.f;
+  __syncthreads();
+  for (int e = tid; e < l * l; e += 256) {
+    const int i = e % l, j = e / l;
+    const float v = s_R[j * kRbLd + i];
+    Xout[e] = (double)v;
+    Xw[i + (int64_t)j * ldxw] = (TW)v;
+  }
   if (tid == 0) {
+    int ndropped = 0;
+    for (int j = 0; j < l; ++j) ndropped += s_keep[j] ? 0 : 1;
     if (gate && s_ill) *gate = 1;
     if (ndropped > 0 && !(gate && s_ill))
       atomicOr(status, ndropped == l ? (ST_RANK_DEF | ST_BREAKDOWN) : ST_RANK_DEF);
@@ -539,7 +587,7 @@ cudaError_t cholesky(cudaStream_t st, int l, const double* G, double tol, int ro
   // the gate word sits next to the status word (same 256-byte status block)
   int* gate = (int*)(status + 2);
   prepare_kernels();
-  k_cholesky_rb<TW><<<1, 256, 0, st>>>(l, G, (float)tol, round == 0 ? gate : nullptr, X, Xw, ldxw,
+  k_cholesky_rb<TW><<<1, 256, kRbSmem, st>>>(l, G, (float)tol, round == 0 ? gate : nullptr, X, Xw, ldxw,
                                        status);
   note_launch();
   if (round != 0) return cudaGetLastError();
@@ -655,8 +703,8 @@ template cudaError_t cholesky<float>(cudaStream_t, int, const double*, double, i
 // l x l Gram matrix.
 //
 // Stage 1: parallel cyclic two-sided Jacobi in FP32 (round-robin pairing,
-// l/2 disjoint rotations per step: all row rotations, then all column
-// rotations).  Stage 2: FP64 iterative refinement of the eigenvectors
+// l/2 disjoint rotations per step, applied as independent 2 x 2 block
+// updates of A and column-pair updates of V).  Stage 2: FP64 iterative refinement of the eigenvectors
 // (Ogita & Aishima, "Iterative refinement for symmetric eigenvalue
 // decomposition", Japan J. Indust. Appl. Math. 35, 2018): with R = I - X^T X
 // and S = X^T A X, lambda_i = S_ii / (1 - R_ii), E_ij = (S_ij + lambda_j
@@ -667,18 +715,17 @@ __device__ __forceinline__ void rr_pair(int L, int s, int i, int& a, int& b) {
   b = 1 + ((L - 2 - i + s) % (L - 1));
 }
 
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(1024)
 k_jacobi32(int l, const double* __restrict__ G, double* __restrict__ Vout, int max_sweeps,
            unsigned* status) {
   extern __shared__ float smf[];
   const int L = l + (l & 1);
+  const int np = L / 2;
   const int ld = L + 1;
   float* A = smf;               // L x L, row stride ld
   float* V = A + L * ld;        // L x L, row stride ld
-  float* cs = V + L * ld;       // L/2
-  float* sn = cs + L / 2;
-  int* pp = (int*)(sn + L / 2);
-  int* qq = pp + L / 2;
+  // rotation of pair i: (c, s, p, q) packed in one float4 (p, q as int bits)
+  float4* prm = (float4*)(((uintptr_t)(V + L * ld) + 15) & ~(uintptr_t)15);
   __shared__ double red[32];
   __shared__ int s_rot;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -686,27 +733,35 @@ k_jacobi32(int l, const double* __restrict__ G, double* __restrict__ Vout, int m
   for (int i = tid; i < l; i += nt) dm = fmax(dm, fabs(G[i + i * l]));
   dm = block_max(dm, red);
   const double scale = dm > 0.0 ? 1.0 / dm : 1.0;
-  for (int e = tid; e < L * L; e += nt) {
-    const int i = e % L, j = e / L;
-    A[i * ld + j] = (i < l && j < l) ? (float)(G[i + j * l] * scale) : 0.f;
-    V[i * ld + j] = (i == j) ? 1.f : 0.f;
+  for (int e0 = 0; e0 < L * L; e0 += nt * 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * nt + tid, i = e % L, j = e / L;
+      v[u] = (e < L * L && i < l && j < l) ? G[i + j * l] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * nt + tid, i = e % L, j = e / L;
+      if (e < L * L) {
+        A[i * ld + j] = (float)(v[u] * scale);
+        V[i * ld + j] = (i == j) ? 1.f : 0.f;
+      }
+    }
   }
   __syncthreads();
-  // FP32 stage only needs to reach the basin of the FP64 refinement: rotate
-  // while |a_pq| exceeds 1e-4 of sqrt(a_pp a_qq).  The test is relative on
-  // purpose: an absolute floor would leave pairs of small eigenvalues
-  // unrotated, and the refinement cannot split such a pair.
+  // Rotate while |a_pq| exceeds 1e-5 of sqrt(a_pp a_qq).  The test is
+  // relative on purpose: an absolute floor would leave pairs of small
+  // eigenvalues unrotated, and the FP64 refinement cannot split such a pair.
   const float tol = 1e-5f, abs_floor = 1e-30f;
   bool converged = (L < 2);
-  // thread -> (element x, first pair group g); pairs g, g + ngrp, ...
-  const int ngrp = nt / L;
-  const int x = tid % L, g0 = tid / L;
-  const bool worker = g0 < ngrp;
+  int nsweeps = 0;
   for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
+    ++nsweeps;
     if (tid == 0) s_rot = 0;
     __syncthreads();
     for (int s = 0; s < L - 1; ++s) {
-      for (int pi = tid; pi < L / 2; pi += nt) {
+      for (int pi = tid; pi < np; pi += nt) {
         int p, q;
         rr_pair(L, s, pi, p, q);
         if (p > q) { const int t = p; p = q; q = t; }
@@ -721,43 +776,46 @@ k_jacobi32(int l, const double* __restrict__ G, double* __restrict__ Vout, int m
             s_rot = 1;
           }
         }
-        cs[pi] = c; sn[pi] = sv; pp[pi] = p; qq[pi] = q;
+        prm[pi] = make_float4(c, sv, __int_as_float(p), __int_as_float(q));
       }
       __syncthreads();
-      // rows p, q <- J^T A (this thread: column x of every pair in its group)
-      if (worker) {
-        for (int pi = g0; pi < L / 2; pi += ngrp) {
-          const float sv = sn[pi];
-          if (sv == 0.f) continue;
-          const float c = cs[pi];
-          const int p = pp[pi], q = qq[pi];
-          const float ap = A[p * ld + x], aq = A[q * ld + x];
-          A[p * ld + x] = c * ap - sv * aq;
-          A[q * ld + x] = sv * ap + c * aq;
-        }
+      // A <- J^T A J one 2 x 2 block at a time: block (i, j) holds rows
+      // (p_i, q_i) and columns (p_j, q_j); rotate its rows by pair i and its
+      // columns by pair j.  Blocks are disjoint, so one barrier suffices.
+      for (int b = tid; b < np * np; b += nt) {
+        const int i = b % np, j = b / np;
+        const float4 ri = prm[i], rj = prm[j];
+        if (ri.y == 0.f && rj.y == 0.f) continue;
+        const int pi_ = __float_as_int(ri.z), qi = __float_as_int(ri.w);
+        const int pj = __float_as_int(rj.z), qj = __float_as_int(rj.w);
+        const float b00 = A[pi_ * ld + pj], b01 = A[pi_ * ld + qj];
+        const float b10 = A[qi * ld + pj], b11 = A[qi * ld + qj];
+        const float t00 = ri.x * b00 - ri.y * b10, t01 = ri.x * b01 - ri.y * b11;
+        const float t10 = ri.y * b00 + ri.x * b10, t11 = ri.y * b01 + ri.x * b11;
+        A[pi_ * ld + pj] = rj.x * t00 - rj.y * t01;
+        A[pi_ * ld + qj] = rj.y * t00 + rj.x * t01;
+        A[qi * ld + pj] = rj.x * t10 - rj.y * t11;
+        A[qi * ld + qj] = rj.y * t10 + rj.x * t11;
       }
-      __syncthreads();
-      // columns p, q <- A J, V J (this thread: row x)
-      if (worker) {
-        for (int pi = g0; pi < L / 2; pi += ngrp) {
-          const float sv = sn[pi];
-          if (sv == 0.f) continue;
-          const float c = cs[pi];
-          const int p = pp[pi], q = qq[pi];
-          const float ap = A[x * ld + p], aq = A[x * ld + q];
-          A[x * ld + p] = c * ap - sv * aq;
-          A[x * ld + q] = sv * ap + c * aq;
-          const float vp = V[x * ld + p], vq = V[x * ld + q];
-          V[x * ld + p] = c * vp - sv * vq;
-          V[x * ld + q] = sv * vp + c * vq;
-        }
+      // V <- V J (this thread: row x of pair j's two columns)
+      for (int e = tid; e < L * np; e += nt) {
+        const int x = e % L, j = e / L;
+        const float4 r = prm[j];
+        if (r.y == 0.f) continue;
+        const int p = __float_as_int(r.z), q = __float_as_int(r.w);
+        const float vp = V[x * ld + p], vq = V[x * ld + q];
+        V[x * ld + p] = r.x * vp - r.y * vq;
+        V[x * ld + q] = r.y * vp + r.x * vq;
       }
       __syncthreads();
     }
     converged = (s_rot == 0);
     __syncthreads();
   }
-  if (!converged && tid == 0) atomicOr(status, ST_NO_CONV);
+  if (tid == 0) {
+    if (!converged) atomicOr(status, ST_NO_CONV);
+    status[4] = (unsigned)nsweeps;  // diagnostic word at byte 16 of the status block
+  }
   for (int e = tid; e < l * l; e += nt) {
     const int i = e % l, j = e / l;
     Vout[e] = (double)V[i * ld + j];
@@ -771,8 +829,14 @@ __global__ void k_add_inplace(int64_t n, double* __restrict__ X, const double* _
 
 __global__ void k_frob(int64_t n, const double* __restrict__ A, double* out) {
   __shared__ double rs[32];
-  double s = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += A[i] * A[i];
+  double s = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int64_t i = threadIdx.x;
+  for (; i + 3 * blockDim.x < n; i += 4 * blockDim.x) {
+    const double a0 = A[i], a1 = A[i + blockDim.x], a2 = A[i + 2 * blockDim.x], a3 = A[i + 3 * blockDim.x];
+    s += a0 * a0; s1 += a1 * a1; s2 += a2 * a2; s3 += a3 * a3;
+  }
+  for (; i < n; i += blockDim.x) s += A[i] * A[i];
+  s = (s + s1) + (s2 + s3);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) rs[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -784,26 +848,42 @@ __global__ void k_frob(int64_t n, const double* __restrict__ A, double* out) {
 }
 
 // Sort eigenpairs by descending eigenvalue (stable), sigma = sqrt(max(lambda, 0)).
-__global__ void k_sort_eig(int l, const double* __restrict__ lam, const double* __restrict__ X,
-                           double* __restrict__ sigma, double* __restrict__ U) {
+__global__ void __launch_bounds__(1024)
+k_sort_eig(int l, const double* __restrict__ lam, const double* __restrict__ X,
+           double* __restrict__ sigma, double* __restrict__ U) {
   __shared__ int rank[kMaxL];
+  __shared__ double sl[kMaxL];
   const int tid = threadIdx.x;
-  for (int i = tid; i < l; i += blockDim.x) {
+  if (tid < l) sl[tid] = lam[tid];
+  __syncthreads();
+  if (tid < l) {
+    const double li = sl[tid];
     int r = 0;
-    for (int j = 0; j < l; ++j) r += (lam[j] > lam[i]) || (lam[j] == lam[i] && j < i);
-    rank[i] = r;
-    sigma[r] = sqrt(fmax(lam[i], 0.0));
+    for (int j = 0; j < l; ++j) r += (sl[j] > li) || (sl[j] == li && j < tid);
+    rank[tid] = r;
+    sigma[r] = sqrt(fmax(li, 0.0));
   }
   __syncthreads();
-  for (int e = tid; e < l * l; e += blockDim.x) {
-    const int i = e % l, j = e / l;
-    U[i + rank[j] * l] = X[e];
+  for (int e0 = 0; e0 < l * l; e0 += 8 * (int)blockDim.x) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * (int)blockDim.x + tid;
+      v[u] = e < l * l ? X[e] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * (int)blockDim.x + tid;
+      if (e < l * l) U[e % l + rank[e / l] * l] = v[u];
+    }
   }
 }
 
 // Ogita-Aishima update: from XtX = X^T X and S = X^T A X (l x l) write the
 // eigenvalue estimates lambda and the correction E (FP64); ||A||_F is read
-// from the device.
+// from the device.  Every block recomputes the two norms of delta (l^2 reads
+// from L2) and then fills its share of E, so the FP64 divisions spread over
+// the grid.
 __global__ void __launch_bounds__(256)
 k_oa_update_dev(int l, const double* __restrict__ XtX, const double* __restrict__ S,
                 const double* __restrict__ normA, double* __restrict__ lam, double* __restrict__ E) {
@@ -836,7 +916,7 @@ k_oa_update_dev(int l, const double* __restrict__ XtX, const double* __restrict_
   }
   __syncthreads();
   const double delta = s_delta;
-  for (int e = tid; e < l * l; e += nt) {
+  for (int e = blockIdx.x * nt + tid; e < l * l; e += gridDim.x * nt) {
     const int i = e % l, j = e / l;
     const double rij = (i == j ? 1.0 : 0.0) - XtX[e];
     double v;
@@ -845,7 +925,12 @@ k_oa_update_dev(int l, const double* __restrict__ XtX, const double* __restrict_
     else v = 0.5 * rij;
     E[e] = v;
   }
-  for (int i = tid; i < l; i += nt) lam[i] = lm[i];
+  if (blockIdx.x == 0)
+    for (int i = tid; i < l; i += nt) lam[i] = lm[i];
+}
+
+static unsigned oa_blocks(int l) {
+  return (unsigned)std::min(64, std::max(1, (l * l + 255) / 256));
 }
 
 size_t sym_eig_work_doubles(int l) {
@@ -866,9 +951,9 @@ cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma, doub
   double* lam = part + 8 * ll;
   double* normA = lam + l;
   const int L = l + (l & 1);
-  const size_t smj = (size_t)2 * L * (L + 1) * sizeof(float) + (size_t)L * (2 * sizeof(float) + 2 * sizeof(int));
+  const size_t smj = (size_t)2 * L * (L + 1) * sizeof(float) + 16 + (size_t)(L / 2) * sizeof(float4);
   prepare_kernels();
-  k_jacobi32<<<1, 512, smj, st>>>(l, G, X, 20, status); note_launch();
+  k_jacobi32<<<1, 1024, smj, st>>>(l, G, X, 20, status); note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_frob<<<1, 256, 0, st>>>((int64_t)ll, G, normA); note_launch();
@@ -884,7 +969,7 @@ cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma, doub
     // S = X^T AX
     if ((e = gemm<double, double, double, double>(st, true, l, l, l, nsp, X, l, AX, l, part, 1, l, ll, status, false))) return e;
     if ((e = reduce_splits<double, double>(st, l, l, nsp, part, S, 1, l))) return e;
-    k_oa_update_dev<<<1, 256, l * sizeof(double), st>>>(l, XtX, S, normA, lam, E); note_launch();
+    k_oa_update_dev<<<oa_blocks(l), 256, l * sizeof(double), st>>>(l, XtX, S, normA, lam, E); note_launch();
     if ((e = cudaGetLastError())) return e;
     // X <- X + X E
     if ((e = gemm<double, double, double, double>(st, false, l, l, l, nsp, X, l, E, l, part, 1, l, ll, status, false))) return e;
@@ -900,9 +985,9 @@ cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma, doub
     if ((e = reduce_splits<double, double>(st, l, l, nsp, part, S, 1, l))) return e;
     if ((e = gemm<double, double, double, double>(st, true, l, l, l, nsp, X, l, X, l, part, 1, l, ll, status, false))) return e;
     if ((e = reduce_splits<double, double>(st, l, l, nsp, part, XtX, 1, l))) return e;
-    k_oa_update_dev<<<1, 256, l * sizeof(double), st>>>(l, XtX, S, normA, lam, E); note_launch();
+    k_oa_update_dev<<<oa_blocks(l), 256, l * sizeof(double), st>>>(l, XtX, S, normA, lam, E); note_launch();
   }
-  k_sort_eig<<<1, 128, 0, st>>>(l, lam, X, sigma, Uhat); note_launch();
+  k_sort_eig<<<1, 1024, 0, st>>>(l, lam, X, sigma, Uhat); note_launch();
   return cudaGetLastError();
 }
 
@@ -918,10 +1003,22 @@ __global__ void k_colmax_partial(int64_t n, int64_t rows_per_blk, const T* __res
   const int64_t r1 = (r0 + rows_per_blk < n) ? r0 + rows_per_blk : n;
   double bv = 0.0, ba = -1.0;
   long long bi = LLONG_MAX;
-  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    const double v = (double)U[r + c * ldu];
-    const double a = fabs(v);
-    if (a > ba) { ba = a; bv = v; bi = r; }
+  // eight loads in flight per thread; rows visited in increasing order so
+  // the first of equal magnitudes wins
+  const int64_t step = blockDim.x;
+  for (int64_t rb = r0 + threadIdx.x; rb < r1; rb += 8 * step) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t r = rb + u * step;
+      v[u] = r < r1 ? (double)U[r + c * ldu] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t r = rb + u * step;
+      const double a = fabs(v[u]);
+      if (r < r1 && a > ba) { ba = a; bv = v[u]; bi = r; }
+    }
   }
   __shared__ double sa[256], sv[256];
   __shared__ long long si[256];
@@ -1030,31 +1127,76 @@ template cudaError_t check_finite<__half>(cudaStream_t, int64_t, int64_t, const 
 namespace rpod {
 
 // ------------------------------------------------------------------------
-// FP32 -> 16-bit snapshot copy (the down-conversion of the 16-bit forms),
-// four elements per thread when rows and leading dimensions allow it.
+// FP32 -> 16-bit snapshot copy (the down-conversion of the 16-bit forms).
+// Work is split into units of (column, 8192-row chunk) handed out grid-
+// stride, so no per-element division; in the vector form each thread moves
+// 8 consecutive rows per step (two 16-byte loads, one 16-byte store) with
+// four steps in flight.
+template <typename TD> __device__ __forceinline__ unsigned pack2(float a, float b);
+template <> __device__ __forceinline__ unsigned pack2<__nv_bfloat16>(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  unsigned u;
+  memcpy(&u, &h, 4);
+  return u;
+}
+template <> __device__ __forceinline__ unsigned pack2<__half>(float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);
+  unsigned u;
+  memcpy(&u, &h, 4);
+  return u;
+}
+
+__device__ __forceinline__ bool finite4(const float4& v) {
+  return isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w);
+}
+
+constexpr int kConvThreads = 256;
+constexpr int kConvSteps = 4;
+constexpr int kConvRows = kConvThreads * 8 * kConvSteps;  // rows per work unit
+
 template <typename TD>
-__global__ void k_convert_snapshots(int64_t rows, int64_t cols, const float* __restrict__ S,
-                                    int64_t lds, TD* __restrict__ D, int64_t ldd, unsigned* status,
-                                    int vec) {
+__global__ void __launch_bounds__(kConvThreads, 4)
+k_convert_snapshots(int64_t rows, int64_t cols, const float* __restrict__ S, int64_t lds,
+                    TD* __restrict__ D, int64_t ldd, unsigned* status, int vec) {
   bool bad = false;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  if (vec) {
-    const int64_t r4 = rows / 4;
-    const int64_t tot = r4 * cols;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += stride) {
-      const int64_t c = t / r4, r = (t - c * r4) * 4;
-      const float4 v = *(const float4*)(S + r + c * lds);
-      bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
-      TD* d = D + r + c * ldd;
-      d[0] = cvt<TD>(v.x); d[1] = cvt<TD>(v.y); d[2] = cvt<TD>(v.z); d[3] = cvt<TD>(v.w);
-    }
-  } else {
-    const int64_t tot = rows * cols;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += stride) {
-      const int64_t c = t / rows, r = t - c * rows;
-      const float v = S[r + c * lds];
-      bad |= !isfinite(v);
-      D[r + c * ldd] = cvt<TD>(v);
+  const int64_t per_col = (rows + kConvRows - 1) / kConvRows;
+  const int64_t units = per_col * cols;
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int64_t c = u / per_col;
+    const int64_t r0 = (u - c * per_col) * kConvRows;
+    const float* s = S + c * lds;
+    TD* d = D + c * ldd;
+    if (vec) {  // rows % 8 == 0: every 8-row group is whole
+      float4 v[2 * kConvSteps];
+#pragma unroll
+      for (int i = 0; i < kConvSteps; ++i) {
+        const int64_t r = r0 + (int64_t)(i * kConvThreads + threadIdx.x) * 8;
+        if (r < rows) {
+          v[2 * i] = __ldcs(reinterpret_cast<const float4*>(s + r));
+          v[2 * i + 1] = __ldcs(reinterpret_cast<const float4*>(s + r + 4));
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kConvSteps; ++i) {
+        const int64_t r = r0 + (int64_t)(i * kConvThreads + threadIdx.x) * 8;
+        if (r < rows) {
+          const float4 a = v[2 * i], b = v[2 * i + 1];
+          bad |= !(finite4(a) && finite4(b));
+          uint4 o;
+          o.x = pack2<TD>(a.x, a.y);
+          o.y = pack2<TD>(a.z, a.w);
+          o.z = pack2<TD>(b.x, b.y);
+          o.w = pack2<TD>(b.z, b.w);
+          *reinterpret_cast<uint4*>(d + r) = o;
+        }
+      }
+    } else {
+      const int64_t r1 = min(rows, r0 + (int64_t)kConvRows);
+      for (int64_t r = r0 + threadIdx.x; r < r1; r += kConvThreads) {
+        const float x = s[r];
+        bad |= !isfinite(x);
+        d[r] = cvt<TD>(x);
+      }
     }
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
@@ -1063,29 +1205,40 @@ __global__ void k_convert_snapshots(int64_t rows, int64_t cols, const float* __r
 template <typename TD>
 cudaError_t convert_snapshots(cudaStream_t st, int64_t rows, int64_t cols, const float* S,
                               int64_t lds, TD* D, int64_t ldd, unsigned* status) {
-  const int vec = ((rows & 3) == 0 && (lds & 3) == 0 && (ldd & 3) == 0 &&
-                   (((uintptr_t)S) & 15) == 0 && (((uintptr_t)D) & 7) == 0) ? 1 : 0;
-  k_convert_snapshots<TD><<<152 * 16, 256, 0, st>>>(rows, cols, S, lds, D, ldd, status, vec);
+  const int vec = ((rows & 7) == 0 && (lds & 3) == 0 && (ldd & 7) == 0 &&
+                   (((uintptr_t)S) & 15) == 0 && (((uintptr_t)D) & 15) == 0) ? 1 : 0;
+  const int64_t units = (rows + kConvRows - 1) / kConvRows * cols;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(units, 152 * 4));
+  k_convert_snapshots<TD><<<grid, kConvThreads, 0, st>>>(rows, cols, S, lds, D, ldd, status, vec);
   note_launch();
   return cudaGetLastError();
 }
 template cudaError_t convert_snapshots<__nv_bfloat16>(cudaStream_t, int64_t, int64_t, const float*, int64_t, __nv_bfloat16*, int64_t, unsigned*);
 template cudaError_t convert_snapshots<__half>(cudaStream_t, int64_t, int64_t, const float*, int64_t, __half*, int64_t, unsigned*);
 
-__global__ void k_round_tf32(int64_t rows, int64_t cols, const float* __restrict__ src, int64_t lds,
-                             float* __restrict__ dst, int64_t ldd) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= rows * cols) return;
-  const int64_t c = t / rows, r = t - c * rows;
-  uint32_t u;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(src[r + c * lds]));
-  dst[r + c * ldd] = __uint_as_float(u);
+// Round-to-nearest (ties away) of an FP32 matrix to TF32, same unit split.
+__global__ void __launch_bounds__(kConvThreads)
+k_round_tf32(int64_t rows, int64_t cols, const float* __restrict__ src, int64_t lds,
+             float* __restrict__ dst, int64_t ldd) {
+  const int64_t per_col = (rows + kConvRows - 1) / kConvRows;
+  const int64_t units = per_col * cols;
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int64_t c = u / per_col;
+    const int64_t r0 = (u - c * per_col) * kConvRows;
+    const int64_t r1 = min(rows, r0 + (int64_t)kConvRows);
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += kConvThreads) {
+      uint32_t v;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(v) : "f"(src[r + c * lds]));
+      dst[r + c * ldd] = __uint_as_float(v);
+    }
+  }
 }
 
 cudaError_t round_tf32(cudaStream_t st, int64_t rows, int64_t cols, const float* src, int64_t lds,
                        float* dst, int64_t ldd) {
-  const int64_t tot = rows * cols;
-  k_round_tf32<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(rows, cols, src, lds, dst, ldd);
+  const int64_t units = (rows + kConvRows - 1) / kConvRows * cols;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(units, 152 * 8));
+  k_round_tf32<<<grid, kConvThreads, 0, st>>>(rows, cols, src, lds, dst, ldd);
   note_launch();
   return cudaGetLastError();
 }
@@ -1180,6 +1333,8 @@ void prepare_kernels() {
     cudaFuncSetAttribute(k_cholesky<double, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_cholesky64_gated<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_cholesky_rb<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRbSmem);
+    cudaFuncSetAttribute(k_cholesky_rb<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRbSmem);
   });
   prepare_kernels_tc();
 }

@@ -13,11 +13,16 @@
 //   Y-pass  Y(i, c) = sum_j S(i, j) A(j, c)      (S Lambda and S Z)
 //           K = m snapshots, K-major A tile, MN-major S tile; each CTA owns
 //           BN rows of Y and streams all of S's columns for them.
+// The first Y-pass over an FP32 S can also write the 16-bit copy of S that
+// the later passes read (one HBM read of S for both).
+// A third kernel forms Gram matrices Y^T Y of FP32 tall-skinny matrices on
+// the TF32 path with a hi/lo split (CholeskyQR's Gram, Alg. 1).
 // Every mbarrier wait is bounded by a %globaltimer deadline; on expiry the
 // kernel records ST_TIMEOUT, stops issuing work, frees its TMEM and returns.
 #include <cuda.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "rpod_tc.cuh"
 
@@ -384,6 +389,314 @@ k_ypass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
   if (warp == 0) tmem_dealloc(tmem, BN);
 }
 
+// ---------------------------------------------------------------------------
+// Gram matrix G = Y^T Y of an FP32 matrix on the TF32 tensor path with the
+// three-term split y = hi + lo, hi = rn_tf32(y), lo = rn_tf32(y - hi):
+// G ~ hi^T hi + hi^T lo + lo^T hi (the dropped lo^T lo term is below 2^-22 of
+// each product).  One 32-row x 128-column K-major tile of Y serves as both
+// MMA operands.  Warp 0 loads tiles by TMA, warps 2-5 split each tile into
+// hi (in place) and lo (second buffer), warp 1 issues the MMAs; split-K over
+// rows with FP64 partials part[z][c + j l], which the caller reduces.
+template <int STAGES>
+struct GramSmem {
+  static constexpr uint32_t TILE = 128 * 128;  // 128 columns x 32 rows of FP32
+  static constexpr uint32_t STAGE = 2 * TILE;
+  static constexpr uint32_t BARS = STAGES * STAGE;
+  static constexpr size_t TOTAL = 1024 + (size_t)STAGES * STAGE + 256;
+};
+
+template <int STAGES>
+__global__ void __launch_bounds__(192, 1)
+k_gram3(const __grid_constant__ CUtensorMap tmY, int64_t rows, int l, int kchunk,
+        double* __restrict__ part, unsigned* status) {
+  using L = GramSmem<STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + L::BARS);
+  uint64_t* empty = full + STAGES;
+  uint64_t* conv = empty + STAGES;
+  uint64_t* done = conv + STAGES;
+  uint32_t* tslot = (uint32_t*)(done + 1);
+  volatile int* abort_flag = (volatile int*)(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ktiles = (rows + 31) / 32;
+  const int64_t kt0 = (int64_t)blockIdx.x * kchunk;
+  const int64_t kt1 = (kt0 + kchunk < ktiles) ? kt0 + kchunk : ktiles;
+  const int nk = kt1 > kt0 ? (int)(kt1 - kt0) : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      mbar_init(&conv[s], 4);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(tslot, 128);
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0 && lane == 0 && nk > 0) {
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (it >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+      mbar_expect_tx(&full[s], L::TILE);
+      tma_load_2d(smem + s * L::STAGE, &tmY, &full[s], (int)((kt0 + it) * 32), 0);
+    }
+  } else if (warp >= 2 && nk > 0) {
+    const int ct = threadIdx.x - 64;
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (!mbar_wait(&full[s], ph, abort_flag)) break;
+      float4* h4 = (float4*)(smem + s * L::STAGE);
+      float4* l4 = (float4*)(smem + s * L::STAGE + L::TILE);
+#pragma unroll 4
+      for (int e = ct; e < (int)(L::TILE / 16); e += 128) {
+        const float4 v = h4[e];
+        float4 h, o;
+        h.x = tf32_rna(v.x); o.x = tf32_rna(v.x - h.x);
+        h.y = tf32_rna(v.y); o.y = tf32_rna(v.y - h.y);
+        h.z = tf32_rna(v.z); o.z = tf32_rna(v.z - h.z);
+        h.w = tf32_rna(v.w); o.w = tf32_rna(v.w - h.w);
+        h4[e] = h;
+        l4[e] = o;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&conv[s]);
+    }
+  } else if (warp == 1 && lane == 0 && nk > 0) {
+    constexpr uint32_t id = idesc(2, false, 128, 128);
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (!mbar_wait(&conv[s], ph, abort_flag)) break;
+      tc_after();
+      const uint32_t h = su32(smem + s * L::STAGE), lo = h + L::TILE;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t dh = sdesc(h + 32 * kk, 16, 1024), dl = sdesc(lo + 32 * kk, 16, 1024);
+        mma<2>(tmem, dh, dh, id, (it > 0 || kk > 0) ? 1u : 0u);
+        mma<2>(tmem, dh, dl, id, 1u);
+        mma<2>(tmem, dl, dh, id, 1u);
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+  if (warp >= 2) {
+    bool ok = true;
+    if (nk > 0) ok = mbar_wait(done, 0, abort_flag);
+    ok = __all_sync(0xffffffffu, ok) && !*abort_flag;
+    tc_after();
+    const int q = warp & 3;  // TMEM lane quarter this warp may read
+    const int c = q * 32 + lane;
+    double* pz = part + (int64_t)blockIdx.x * l * l;
+    for (int cc = 0; cc < 128; cc += 32) {
+      float v[32];
+      if (nk > 0 && ok) {
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)cc, v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+      }
+      if (c < l) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (cc + i < l) pz[c + (int64_t)(cc + i) * l] = (double)v[i];
+      }
+    }
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
+  tc_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+// ---------------------------------------------------------------------------
+// First Y-pass of the 16-bit forms fused with the down-conversion of an FP32
+// S: TMA stages the FP32 tile (128 rows x 64 snapshots as four {32, 64} SW128
+// boxes), warps 2-5 convert it into the MN-major 16-bit SW128 tile the MMA
+// reads (two {64, 64} atoms) and store the same 16-bit values to the global
+// copy Sh that the later passes read, warp 1 issues the MMAs.  S is read from
+// HBM once for both the product and the copy.
+template <int STAGES>
+struct YcvtSmem {
+  static constexpr uint32_t A_BYTES = 128 * 128;  // A^T tile, 128 x 64 16-bit
+  static constexpr uint32_t F_BYTES = 128 * 256;  // FP32 S tile, 128 rows x 64
+  static constexpr uint32_t H_BYTES = 128 * 128;  // 16-bit S tile
+  static constexpr uint32_t STAGE = A_BYTES + F_BYTES + H_BYTES;
+  static constexpr uint32_t BARS = STAGES * STAGE;
+  static constexpr size_t TOTAL = 1024 + (size_t)STAGES * STAGE + 256;
+};
+
+template <typename TH> __device__ __forceinline__ uint32_t pack16x2(float a, float b);
+template <> __device__ __forceinline__ uint32_t pack16x2<__nv_bfloat16>(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  uint32_t u;
+  memcpy(&u, &h, 4);
+  return u;
+}
+template <> __device__ __forceinline__ uint32_t pack16x2<__half>(float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);
+  uint32_t u;
+  memcpy(&u, &h, 4);
+  return u;
+}
+
+template <int KIND, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+k_ypass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmF,
+            int64_t n, int64_t m, int l, float* __restrict__ Y, int64_t ldy, void* __restrict__ Sh,
+            int64_t ldh, unsigned* status) {
+  using L = YcvtSmem<STAGES>;
+  using TH = typename std::conditional<KIND == 0, __nv_bfloat16, __half>::type;
+  constexpr int BN = 128;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + L::BARS);
+  uint64_t* empty = full + STAGES;
+  uint64_t* conv = empty + STAGES;
+  uint64_t* done = conv + STAGES;
+  uint32_t* tslot = (uint32_t*)(done + 1);
+  volatile int* abort_flag = (volatile int*)(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i0 = (int64_t)blockIdx.x * BN;
+  const int nk = (int)((m + 63) / 64);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      mbar_init(&conv[s], 4);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(tslot, BN);
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0 && lane == 0) {
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (it >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+      uint8_t* a = smem + s * L::STAGE;
+      mbar_expect_tx(&full[s], L::A_BYTES + L::F_BYTES);
+      tma_load_2d(a, &tmA, &full[s], it * 64, 0);
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        tma_load_2d(a + L::A_BYTES + b * 8192, &tmF, &full[s], (int)(i0 + 32 * b), it * 64);
+    }
+  } else if (warp >= 2) {
+    // item = (row group rg of 8 rows, snapshot kk): 16 x 64 items per stage
+    const int ct = threadIdx.x - 64;
+    TH* shg = (TH*)Sh;
+    bool bad = false;
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (!mbar_wait(&full[s], ph, abort_flag)) break;
+      const uint8_t* f = smem + s * L::STAGE + L::A_BYTES;
+      uint8_t* h = smem + s * L::STAGE + L::A_BYTES + L::F_BYTES;
+#pragma unroll 2
+      for (int i = 0; i < 8; ++i) {
+        const int item = ct + 128 * i;
+        const int rg = item & 15, kk = item >> 4;
+        const int sw = kk & 7;
+        const uint8_t* fb = f + (rg >> 2) * 8192 + kk * 128;
+        const int c0 = (rg & 3) * 2;
+        const float4 x = *(const float4*)(fb + ((c0 ^ sw) << 4));
+        const float4 y = *(const float4*)(fb + (((c0 + 1) ^ sw) << 4));
+        bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(x.w) &&
+                 isfinite(y.x) && isfinite(y.y) && isfinite(y.z) && isfinite(y.w));
+        uint4 o;
+        o.x = pack16x2<TH>(x.x, x.y);
+        o.y = pack16x2<TH>(x.z, x.w);
+        o.z = pack16x2<TH>(y.x, y.y);
+        o.w = pack16x2<TH>(y.z, y.w);
+        *(uint4*)(h + (rg >> 3) * 8192 + kk * 128 + (((rg & 7) ^ sw) << 4)) = o;
+        const int64_t r = i0 + 8 * rg, c = (int64_t)it * 64 + kk;
+        if (c < m) {
+          TH* g = shg + r + c * ldh;
+          if (r + 8 <= n) {
+            *(uint4*)g = o;
+          } else {
+            const TH* ov = (const TH*)&o;
+            for (int e = 0; e < 8; ++e)
+              if (r + e < n) g[e] = ov[e];
+          }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&conv[s]);
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_NONFINITE);
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t id = idesc(fmt_of(KIND), true, 128, BN);
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (!mbar_wait(&conv[s], ph, abort_flag)) break;
+      tc_after();
+      const uint32_t a = su32(smem + s * L::STAGE), b = a + L::A_BYTES + L::F_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        mma<KIND>(tmem, sdesc(a + 32 * kk, 16, 1024), sdesc(b + 2048 * kk, 8192, 1024), id,
+                  (it > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+  if (warp >= 2) {
+    bool ok = mbar_wait(done, 0, abort_flag);
+    ok = __all_sync(0xffffffffu, ok) && !*abort_flag;
+    tc_after();
+    const int q = warp & 3;
+    const int c = q * 32 + lane;
+    float* ycol = Y + (int64_t)c * ldy;
+    for (int cc = 0; cc < BN; cc += 32) {
+      float v[32];
+      if (ok) {
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)cc, v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+      }
+      if (c < l) {
+        const int64_t ib = i0 + cc;
+        if (((ldy & 3) == 0) && ib + 32 <= n) {
+          float4* d4 = (float4*)(ycol + ib);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        } else {
+          for (int i = 0; i < 32; ++i)
+            if (ib + i < n) ycol[ib + i] = v[i];
+        }
+      }
+    }
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
+  tc_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, BN);
+}
+
 }  // namespace tc
 
 // ---------------------------------------------------------------------------
@@ -439,6 +752,8 @@ int make_map(CUtensorMap* map, const void* ptr, int dt, int64_t rows, int64_t co
 
 constexpr int kBN = 256;
 constexpr int kStages = 4;
+constexpr int kGramStages = 3;  // 96 KB: two CTAs per SM
+constexpr int kYcvtStages = 3;  // 192 KB
 
 }  // namespace
 
@@ -452,6 +767,11 @@ void prepare_kernels_tc() {
     cudaFuncSetAttribute(tc::k_wpass<2, kBN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     cudaFuncSetAttribute(tc::k_ypass<0, kBN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     cudaFuncSetAttribute(tc::k_ypass<1, kBN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    cudaFuncSetAttribute(tc::k_gram3<kGramStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tc::GramSmem<kGramStages>::TOTAL);
+    const int yc = (int)tc::YcvtSmem<kYcvtStages>::TOTAL;
+    cudaFuncSetAttribute(tc::k_ypass_cvt<0, kYcvtStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, yc);
+    cudaFuncSetAttribute(tc::k_ypass_cvt<1, kYcvtStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, yc);
   });
 }
 
@@ -506,6 +826,39 @@ int tc_ypass(cudaStream_t st, int dt, const void* A, int64_t lda, const void* S,
     tc::k_ypass<0, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, Y, ldy, status);
   else
     tc::k_ypass<1, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, Y, ldy, status);
+  note_launch();
+  return cudaGetLastError() == cudaSuccess ? RPOD_OK : RPOD_ERR_CUDA;
+}
+
+int tc_gram(cudaStream_t st, const float* Y, int64_t ldy, int64_t rows, int l, double* part,
+            int nsplit, unsigned* status) {
+  if (l < 1 || l > 128 || rows < 1 || nsplit < 1) return RPOD_ERR_INVALID_ARG;
+  CUtensorMap ty;
+  if (int rc = make_map(&ty, Y, RPOD_F32, rows, l, ldy, 32, 128)) return rc;
+  const int64_t ktiles = (rows + 31) / 32;
+  const int kchunk = (int)((ktiles + nsplit - 1) / nsplit);
+  using L = tc::GramSmem<kGramStages>;
+  prepare_kernels_tc();
+  tc::k_gram3<kGramStages><<<(unsigned)nsplit, 192, L::TOTAL, st>>>(ty, rows, l, kchunk, part, status);
+  note_launch();
+  return cudaGetLastError() == cudaSuccess ? RPOD_OK : RPOD_ERR_CUDA;
+}
+
+int tc_ypass_cvt(cudaStream_t st, int dt, const void* A, int64_t lda, const float* S, int64_t lds,
+                 int64_t n, int64_t m, int l, float* Y, int64_t ldy, void* Sh, int64_t ldh,
+                 unsigned* status) {
+  if (dt != RPOD_BF16 && dt != RPOD_F16) return RPOD_ERR_UNSUPPORTED;
+  if (((uintptr_t)Sh & 15) || (ldh & 7)) return RPOD_ERR_UNSUPPORTED;
+  CUtensorMap ta, tf;
+  if (int rc = make_map(&ta, A, dt, m, l, lda, 64, 128)) return rc;
+  if (int rc = make_map(&tf, S, RPOD_F32, n, m, lds, 32, 64)) return rc;
+  dim3 grid((unsigned)((n + 127) / 128));
+  using L = tc::YcvtSmem<kYcvtStages>;
+  prepare_kernels_tc();
+  if (dt == RPOD_BF16)
+    tc::k_ypass_cvt<0, kYcvtStages><<<grid, 192, L::TOTAL, st>>>(ta, tf, n, m, l, Y, ldy, Sh, ldh, status);
+  else
+    tc::k_ypass_cvt<1, kYcvtStages><<<grid, 192, L::TOTAL, st>>>(ta, tf, n, m, l, Y, ldy, Sh, ldh, status);
   note_launch();
   return cudaGetLastError() == cudaSuccess ? RPOD_OK : RPOD_ERR_CUDA;
 }

@@ -21,4 +21,21 @@ int tc_wpass(cudaStream_t st, int dt, const void* A, int64_t lda, int64_t n, int
 int tc_ypass(cudaStream_t st, int dt, const void* A, int64_t lda, const void* S, int64_t lds,
              int64_t n, int64_t m, int l, float* Y, int64_t ldy, unsigned* status);
 
+// First Y-pass over an FP32 S (n x m, ld lds): Y as tc_ypass with S rounded
+// to the 16-bit type dt, and that rounded S written to Sh (n x m, ld ldh, a
+// multiple of 8; Sh 16-byte aligned); records ST_NONFINITE for non-finite
+// entries of S.  RPOD_ERR_UNSUPPORTED when S, A or Sh is not addressable.
+int tc_ypass_cvt(cudaStream_t st, int dt, const void* A, int64_t lda, const float* S, int64_t lds,
+                 int64_t n, int64_t m, int l, float* Y, int64_t ldy, void* Sh, int64_t ldh,
+                 unsigned* status);
+
+// Gram partials part[z][c + j l] (FP64) = sum over rows of split z of
+// Y(i, c) Y(i, j) for c, j < l <= 128, on the TF32 tensor path with a hi/lo
+// split of every element (about 2^-21 relative error per product, FP32
+// accumulation); nsplit CTAs, each a contiguous run of 32-row tiles.  Y FP32
+// column-major (ld ldy); base 16-byte aligned and ldy a multiple of 4, else
+// RPOD_ERR_UNSUPPORTED.
+int tc_gram(cudaStream_t st, const float* Y, int64_t ldy, int64_t rows, int l, double* part,
+            int nsplit, unsigned* status);
+
 }  // namespace rpod

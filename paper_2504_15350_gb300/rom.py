@@ -49,6 +49,7 @@ class ROMConfig:
     weight_decay: float = 1e-5
     seed: int = 0
     patience: int = 25
+    fp32_weights: bool = False
 
 
 @dataclass
@@ -64,6 +65,21 @@ class ROMResult:
     rollout_steps_per_s: float = 0.0
     epochs_run: int = 0
     sigma: list = field(default_factory=list)
+    # Eq. (l2-error): relative L2 error of the time-averaged field over the
+    # prediction window, for the LSTM, the two predictors without it, and the
+    # projection of the true coefficients (the floor set by the basis)
+    tavg_err_lstm: float = math.nan
+    tavg_err_persistence: float = math.nan
+    tavg_err_nearest: float = math.nan
+    tavg_err_projection: float = math.nan
+    err_lstm_first50: float = math.nan
+    err_lstm_first10: float = math.nan
+    err_persistence_first10: float = math.nan
+    err_nearest_first10: float = math.nan
+    # held-out one-step prediction from true windows (teacher forcing)
+    onestep_err_lstm: float = math.nan
+    onestep_err_persistence: float = math.nan
+    onestep_err_nearest: float = math.nan
 
 
 def _snapshots(cfg: ROMConfig, mus, m, device, noise_stream0):
@@ -126,7 +142,8 @@ def run(cfg: ROMConfig = ROMConfig(), device="cuda", log=None) -> ROMResult:
     idx_val = idx_all[perm[:n_val]].to(dev)
     idx_tr = idx_all[perm[n_val:]].to(dev)
     # 4: training
-    net = R.LSTM(d + O, cfg.hidden, cfg.layers, O, T, max_batch=cfg.batch, device=dev)
+    net = R.LSTM(d + O, cfg.hidden, cfg.layers, O, T, max_batch=cfg.batch, device=dev,
+                 fp32_weights=cfg.fp32_weights)
     net.set_params(init_params(net, cfg.seed))
     B = cfg.batch
     nb = idx_tr.shape[0] // B
@@ -166,6 +183,9 @@ def run(cfg: ROMConfig = ROMConfig(), device="cuda", log=None) -> ROMResult:
     # 5: held-out parameters, judged by Galerkin projection
     Ste = _snapshots(cfg, mu_te, T + cfg.rollout, dev, 500)
     Cte = plan.project(U, Ste)                                   # k x (M' (T + r))
+    # time-averaged true fields over the prediction window, one per sample
+    L_ = T + cfg.rollout
+    fom_avg = torch.stack([Ste[:, i * L_ + T:(i + 1) * L_].mean(1) for i in range(cfg.n_test_mu)], 0)
     del Ste
     truth = Cte.t().contiguous().reshape(cfg.n_test_mu, T + cfg.rollout, O)
     zmu_te = ((torch.tensor(mu_te, dtype=torch.float32, device=dev) - m_mean) / m_std)
@@ -184,7 +204,38 @@ def run(cfg: ROMConfig = ROMConfig(), device="cuda", log=None) -> ROMResult:
     dist = torch.cdist(torch.tensor(mu_te), torch.tensor(mu_tr))
     near = dist.argmin(1).to(dev)
     res.err_nearest = _rel_err(series[near, T:T + cfg.rollout], ref)
+    res.err_lstm_first50 = _rel_err(pred[:, :50], ref[:, :50])
+    res.err_lstm_first10 = _rel_err(pred[:, :10], ref[:, :10])
+    res.err_persistence_first10 = _rel_err(truth[:, T - 1:T].expand(-1, 10, -1), ref[:, :10])
+    res.err_nearest_first10 = _rel_err(series[near, T:T + 10], ref[:, :10])
+    # one-step predictions from true held-out windows
+    idx_te = torch.stack(torch.meshgrid(torch.arange(cfg.n_test_mu), torch.arange(cfg.rollout),
+                                        indexing="ij"), -1).reshape(-1, 2).to(torch.int32).to(dev)
+    one = []
+    for b0 in range(0, idx_te.shape[0], B):
+        Xw, _ = net.gather(zt.contiguous(), zmu_te.contiguous(), idx_te[b0:b0 + B])
+        one.append(net.forward(Xw))
+    one = (torch.cat(one, 0) * c_std + c_mean).reshape(cfg.n_test_mu, cfg.rollout, O)
+    res.onestep_err_lstm = _rel_err(one, ref)
+    res.onestep_err_persistence = _rel_err(truth[:, T - 1:T + cfg.rollout - 1], ref)
+    res.onestep_err_nearest = res.err_nearest
+
+    def tavg_err(coeffs):   # coeffs (M', r, N) -> mean over samples of Eq. (l2-error)
+        rom_avg = coeffs.mean(1) @ U.t()                       # (M', n)
+        num = torch.linalg.vector_norm(rom_avg - fom_avg, dim=1)
+        return float((num / torch.linalg.vector_norm(fom_avg, dim=1)).mean())
+
+    res.tavg_err_lstm = tavg_err(pred)
+    res.tavg_err_persistence = tavg_err(truth[:, T - 1:T].expand(-1, cfg.rollout, -1))
+    res.tavg_err_nearest = tavg_err(series[near, T:T + cfg.rollout])
+    res.tavg_err_projection = tavg_err(ref)
     if log:
-        log(f"rollout {cfg.rollout} steps in {res.rollout_seconds:.3f} s; rel err LSTM {res.err_lstm:.4f}, "
-            f"persistence {res.err_persistence:.4f}, nearest mu {res.err_nearest:.4f}")
+        log(f"rollout {cfg.rollout} steps in {res.rollout_seconds:.3f} s; trajectory rel err LSTM "
+            f"{res.err_lstm:.4f} (first 50 steps {res.err_lstm_first50:.4f}), persistence "
+            f"{res.err_persistence:.4f}, nearest mu {res.err_nearest:.4f}; time-averaged field err "
+            f"LSTM {res.tavg_err_lstm:.4f}, persistence {res.tavg_err_persistence:.4f}, nearest mu "
+            f"{res.tavg_err_nearest:.4f}, projection floor {res.tavg_err_projection:.4f}; one-step err "
+            f"LSTM {res.onestep_err_lstm:.4f}, persistence {res.onestep_err_persistence:.4f}; first 10 steps "
+            f"LSTM {res.err_lstm_first10:.4f}, persistence {res.err_persistence_first10:.4f}, nearest mu "
+            f"{res.err_nearest_first10:.4f}")
     return res

@@ -53,7 +53,7 @@ SIGNATURES = {
     "rpod_batch_last_launch_count": (ctypes.c_int, [_p]),
     "rpod_batch_destroy": (None, [_p]),
     "rpod_lstm_create": (ctypes.c_int, [ctypes.POINTER(_p), _c_i32, _c_i32, _c_i32, _c_i32, _c_i32,
-                                        _c_i32]),
+                                        _c_i32, _c_u32]),
     "rpod_lstm_param_count": (_c_i64, [_p]),
     "rpod_lstm_workspace_bytes": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_size_t)]),
     "rpod_lstm_set_params": (ctypes.c_int, [_p, _p, _p, ctypes.c_size_t, _p]),
@@ -407,10 +407,13 @@ class Batch:
 
 
 # ---- LSTM (same-name wrappers and a torch convenience class) ---------------
-def rpod_lstm_create(in_dim, hidden, layers, out_dim, window, max_batch):
+RPOD_LSTM_FP32_WEIGHTS = 1
+
+
+def rpod_lstm_create(in_dim, hidden, layers, out_dim, window, max_batch, flags=0):
     h = _p()
-    _check(load().rpod_lstm_create(ctypes.byref(h), in_dim, hidden, layers, out_dim, window, max_batch),
-           "rpod_lstm_create")
+    _check(load().rpod_lstm_create(ctypes.byref(h), in_dim, hidden, layers, out_dim, window, max_batch,
+                                   flags), "rpod_lstm_create")
     return h.value
 
 
@@ -464,12 +467,15 @@ class LSTM:
     """An rpod_lstm plus its workspace on one CUDA device (torch tensors in,
     torch tensors out; all arithmetic in the library's kernels)."""
 
-    def __init__(self, in_dim, hidden, layers, out_dim, window, max_batch, theta=None, device="cuda"):
+    def __init__(self, in_dim, hidden, layers, out_dim, window, max_batch, theta=None, device="cuda",
+                 fp32_weights=False):
         torch = _torch()
         self.device = torch.device(device)
         self.dims = (in_dim, hidden, layers, out_dim, window)
         self.max_batch = max_batch
-        self.handle = rpod_lstm_create(in_dim, hidden, layers, out_dim, window, max_batch)
+        self.fp32_weights = fp32_weights
+        self.handle = rpod_lstm_create(in_dim, hidden, layers, out_dim, window, max_batch,
+                                       RPOD_LSTM_FP32_WEIGHTS if fp32_weights else 0)
         self.P = rpod_lstm_param_count(self.handle)
         self.ws_bytes = rpod_lstm_workspace_bytes(self.handle)
         self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)

@@ -1,7 +1,8 @@
 """GPU tests of the LSTM kernels (Sec. 4.3) through the C ABI against the FP64
-oracle (oracle/lstm.py).  The library multiplies by BF16 copies of the weight
-matrices, so the oracle runs at the same BF16-rounded weights (biases exact);
-what remains is FP32 activations and accumulation."""
+oracle (oracle/lstm.py).  By default the library multiplies by BF16 copies of
+the weight matrices, so the oracle runs at the same BF16-rounded weights
+(biases exact); what remains is FP32 activations and accumulation.  With FP32
+weights the oracle runs at the FP32 parameters themselves."""
 import numpy as np
 import pytest
 import torch
@@ -36,18 +37,19 @@ def rel(a, b):
     return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-30))
 
 
+@pytest.mark.parametrize("fp32", [False, True])
 @pytest.mark.parametrize("I,H,L,O,T,B", [(6, 32, 2, 4, 5, 16), (54, 64, 2, 50, 10, 40), (5, 16, 1, 3, 3, 7)])
-def test_forward_and_gradients_match_oracle(I, H, L, O, T, B):
+def test_forward_and_gradients_match_oracle(I, H, L, O, T, B, fp32):
     rng = np.random.default_rng(I * H + B)
     theta = rng.uniform(-0.3, 0.3, OL.param_count(I, H, L, O)).astype(np.float32).astype(np.float64)
     X = rng.standard_normal((B, T, I)).astype(np.float32)
     Yt = rng.standard_normal((B, O)).astype(np.float32)
-    te = bf16_weights(theta, I, H, L, O)
+    te = theta if fp32 else bf16_weights(theta, I, H, L, O)
     y_o, cache = OL.forward(te, X.astype(np.float64), H, L, O)
     loss_o, dy = OL.mse(y_o, Yt.astype(np.float64))
     g_o = OL.backward(te, cache, dy, H, L, O)
 
-    net = R.LSTM(I, H, L, O, T, max_batch=64, theta=theta)
+    net = R.LSTM(I, H, L, O, T, max_batch=64, theta=theta, fp32_weights=fp32)
     Xd = torch.from_numpy(X).cuda()
     y = net.forward(Xd).cpu().numpy()
     assert rel(y, y_o) < 2e-5
@@ -87,14 +89,15 @@ def test_adam_step_matches_oracle():
     assert rel(got - theta, th - theta) < 2e-3
 
 
-def test_rollout_matches_oracle():
+@pytest.mark.parametrize("fp32", [False, True])
+def test_rollout_matches_oracle(fp32):
     I, H, L, O, T, B = 7, 32, 2, 5, 4, 3
     rng = np.random.default_rng(5)
     theta = rng.uniform(-0.4, 0.4, OL.param_count(I, H, L, O)).astype(np.float32).astype(np.float64)
     win = rng.standard_normal((B, T, I)).astype(np.float32)
-    te = bf16_weights(theta, I, H, L, O)
+    te = theta if fp32 else bf16_weights(theta, I, H, L, O)
     ref = OL.rollout(te, win.astype(np.float64), 2, 6, H, L, O)
-    net = R.LSTM(I, H, L, O, T, max_batch=8, theta=theta)
+    net = R.LSTM(I, H, L, O, T, max_batch=8, theta=theta, fp32_weights=fp32)
     out = net.rollout(torch.from_numpy(win).cuda(), 2, 6).cpu().numpy()
     assert rel(out, ref) < 1e-4
 

@@ -123,3 +123,37 @@ def test_basis_bf16_ragged_and_16bit_input(n, m):
     assert plan2.status()[0] == R.RPOD_OK
     ok, er, ea = sigma_close(sig2.cpu().numpy()[:k], lowp.sigma[:k], 2e-2, 2e-3)
     assert ok, (er, ea)
+
+
+def _padded(S64, ld, dtype):
+    """Column-major n x m view with leading dimension ld (rows n..ld-1 zero)."""
+    n, m = S64.shape
+    buf = torch.zeros((m, ld), dtype=torch.float32)
+    buf[:, :n] = torch.from_numpy(S64.T).float()
+    return buf.to(dtype).cuda().t()[:n]
+
+
+@pytest.mark.parametrize("n,m,ld", [(1001, 333, 1004), (4100, 700, 4100), (262, 64, 264)])
+def test_fp32_input_first_pass_conversion_matches_16bit_input(n, m, ld):
+    """An FP32 S is rounded to BF16 inside the first Y-pass, which also writes
+    the BF16 copy the later passes read; the result must equal the pipeline
+    fed with the same BF16 values converted on the host (ragged row counts,
+    padded leading dimensions, a partial last row group)."""
+    rng = np.random.default_rng(n + m)
+    S64 = rng.standard_normal((n, m)) * np.logspace(0, -3, m)[None, :]
+    Sd = _padded(S64, ld, torch.float32)
+    Sb = _padded(S64, (n + 7) // 8 * 8, torch.bfloat16)
+    k, p, q = 8, 6, 2
+    fused = R.Plan(n, m, k, p, q, seed=0, compute="bf16", flags=R.RPOD_FLAG_REFINE_FP32)
+    U1, s1, C1 = fused.basis(Sd)
+    assert fused.status()[0] == R.RPOD_OK
+    host = R.Plan(n, m, k, p, q, seed=0, compute="bf16", flags=R.RPOD_FLAG_REFINE_FP32)
+    U2, s2, C2 = host.basis(Sb, S_refine=Sd)
+    assert host.status()[0] == R.RPOD_OK
+    s1, s2 = s1.cpu().numpy(), s2.cpu().numpy()
+    assert np.abs(s1[:k] - s2[:k]).max() <= 1e-6 * s2[0]
+    assert max_angle(U2.double().cpu().numpy(), U1.double().cpu().numpy()) <= 1e-4
+    # a non-finite snapshot entry is reported by the fused pass
+    Sd[n - 1, m - 1] = float("nan")
+    fused.basis(Sd)
+    assert fused.status()[0] == R.RPOD_ERR_NONFINITE
