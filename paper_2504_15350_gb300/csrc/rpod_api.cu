@@ -25,7 +25,7 @@ struct rpod_plan {
   uint32_t flags;
   // workspace layout (byte offsets)
   size_t off_status, off_lam, off_y, off_q, off_z, off_zq, off_tt, off_part, off_gpart, off_g,
-      off_x, off_xw, off_eig, off_sigma, off_uhat, off_sign, total;
+      off_x, off_xw, off_xu, off_eig, off_sigma, off_uhat, off_sign, total;
   // tensor-core forms: 16-bit copy of S, 16-bit operands (128 columns, zero
   // padded), TF32-rounded basis, split-K partials of the W-pass
   size_t off_sb, off_qb, off_zb, off_atf, off_wpart;
@@ -129,7 +129,12 @@ struct Run {
   // Gram may take the split-TF32 tensor path; with `exact_last` the last
   // round, which fixes the orthogonality of the returned basis, keeps FP32
   // products.
-  int orth(W* in, W* tmp, int64_t rows, int rounds, W** out, bool exact_last) {
+  // With `defer` the last round stops after its Cholesky factor: the
+  // returned buffer holds the previous round's basis Q1 and the final basis
+  // is Q1 X with X = R^{-1} left in off_x (FP64) and off_xw (W); the caller
+  // folds X into the small matrices (T = X^T Q1^T S, U = Q1 (X Uhat)), which
+  // saves one n x l x l product.
+  int orth(W* in, W* tmp, int64_t rows, int rounds, W** out, bool exact_last, bool defer = false) {
     const int l = P->l;
     const double tol = sizeof(W) == 8 ? 1e-13 : 1e-5;
     // FP32 Gram: two row chunks per SM (the kernel fits two blocks per SM)
@@ -142,6 +147,7 @@ struct Run {
       CR(gram(src, rows, rows, G, ns, !(exact_last && r == rounds - 1)));
       CK((cholesky<W>(st, l, G, tol, r, dbuf(P->off_x), buf(P->off_xw), l, status,
                       sizeof(W) == 4 ? (const float*)src : nullptr, rows, dbuf(P->off_gpart), ns)));
+      if (defer && r == rounds - 1) break;
       CK((gemm<W, W, W, W>(st, false, rows, l, l, 1, src, rows, buf(P->off_xw), l, dst, 1, rows, 0,
                            status, false)));
       W* t = src; src = dst; dst = t;
@@ -150,8 +156,21 @@ struct Run {
     return RPOD_OK;
   }
 
-  // After T (as Tt, m x l): small SVD, lift, signs, coefficients.
-  int finish(const W* Q, const W* Tt, W* U, int64_t ldu, double* sigma, W* C, int64_t ldc) {
+  // Fold a deferred last CholeskyQR factor into T: Tt (m x l) = Tt1 X,
+  // written to `out` (m x l).
+  int fold_t(const W* Tt1, W* out) {
+    const int64_t m = P->m;
+    const int l = P->l;
+    CK((gemm<W, W, W, W>(st, false, m, l, l, 1, Tt1, m, buf(P->off_xw), l, out, 1, m, 0, status,
+                         false)));
+    return RPOD_OK;
+  }
+
+  // After T (as Tt, m x l): small SVD, lift, signs, coefficients.  With
+  // `deferred` the basis is Q X (X from the deferred last CholeskyQR round)
+  // and the lift uses X Uhat.
+  int finish(const W* Q, const W* Tt, W* U, int64_t ldu, double* sigma, W* C, int64_t ldc,
+             bool deferred = false) {
     const int64_t n = P->n, m = P->m;
     const int l = P->l, k = P->k;
     // Alg. 1: SVD of T via the eigenpairs of T T^T (FP64 Gram)
@@ -169,10 +188,23 @@ struct Run {
     CK((check_finite_vec(st, l, sigma, status)));
     // Alg. 1: lift U = Q Uhat (first k or all l columns), then the sign rule
     const int ku = (P->flags & RPOD_FLAG_RETURN_ALL_L) ? l : k;
-    CK((gemm<W, double, W, W>(st, false, n, ku, l, 1, Q, n, Uhat, l, U, 1, ldu, 0, status, false)));
+    const double* Ul = Uhat;
+    if (deferred) {
+      double* XU = dbuf(P->off_xu);
+      CK((gemm<double, double, double, double>(st, false, l, ku, l, 1, dbuf(P->off_x), l, Uhat, l, XU,
+                                               1, l, 0, status, false)));
+      Ul = XU;
+    }
+    // The small factor enters the n- and m-sized products in W: converted
+    // once here rather than per tile load (FP64 conversions are slow on
+    // GB300).  off_xw (l x l in W) is free after fold_t.
+    W* Uw = buf(P->off_xw);
+    CK((convert_matrix<double, W>(st, l, ku, Ul, l, Uw, l)));
+    CK((gemm<W, W, W, W>(st, false, n, ku, l, 1, Q, n, Uw, l, U, 1, ldu, 0, status, false)));
     CK((sign_fix<W>(st, n, ku, U, ldu, Uhat, l, ws + P->off_sign, P->sign_bytes)));
-    // Sec. 4.3 coefficients C = U_k^T S = Uhat_k^T T (k x m)
-    CK((gemm<W, double, W, W>(st, false, m, k, l, 1, Tt, m, Uhat, l, C, ldc, 1, 0, status, false)));
+    // Sec. 4.3 coefficients C = U_k^T S = Uhat_k^T T (k x m), Uhat with the signs
+    CK((convert_matrix<double, W>(st, l, k, Uhat, l, Uw, l)));
+    CK((gemm<W, W, W, W>(st, false, m, k, l, 1, Tt, m, Uw, l, C, ldc, 1, 0, status, false)));
     return RPOD_OK;
   }
 
@@ -212,15 +244,17 @@ struct Run {
       }
       // Alg. 1 QR of the sampled matrix (CholeskyQR2 for the final basis);
       // Y's buffer is free again once Z = S^T Q is formed
-      CR(orth(Y, Qb, n, it == q ? 2 : 1, &Q, it == q));
+      CR(orth(Y, Qb, n, it == q ? 2 : 1, &Q, it == q, it == q));
     }
-    // Alg. 1: T = Q^T S, stored transposed (m x l)
+    // Alg. 1: T = Q^T S, stored transposed (m x l), with the deferred last
+    // CholeskyQR factor folded in afterwards
     prof_begin(P, st);
     CK((gemm<W, W, W, W>(st, true, m, l, n, P->nsplit_z, S, lds, Q, n, part, 1, m, m * l, status,
                          false)));
     prof_end(P, st, pass_bytes, pass_flops);
-    CK((reduce_splits<W, W>(st, m, l, P->nsplit_z, part, Tt, 1, m)));
-    return finish(Q, Tt, U, ldu, sigma, C, ldc);
+    CK((reduce_splits<W, W>(st, m, l, P->nsplit_z, part, Zq, 1, m)));
+    CR(fold_t(Zq, Tt));
+    return finish(Q, Tt, U, ldu, sigma, C, ldc, true);
   }
 
   // Tensor-core form (W = float): passes over a 16-bit S on tcgen05, the
@@ -300,7 +334,7 @@ struct Run {
         CR(tc_ypass(st, dt, Zh, mld, Sh, ldh, n, m, l, Y, n, status));
         prof_end(P, st, pb16, pass_flops);
       }
-      CR(orth(Y, Qbuf, n, it == q ? 2 : 1, &Q, it == q));
+      CR(orth(Y, Qbuf, n, it == q ? 2 : 1, &Q, it == q, it == q));
       if (it < q) CK(to16(Q, n, n, Qh, nld));
     }
     // Alg. 1: T = Q^T S (TF32 from the FP32 copy when refining)
@@ -312,8 +346,9 @@ struct Run {
       CK((gemm<float, float, float, float>(st, true, m, l, n, P->nsplit_z, Sref, ldr, Q, n,
                                            (float*)buf(P->off_part), 1, m, m * l, status, false)));
       prof_end(P, st, 4.0 * ((double)n * m + (double)n * l + (double)m * l), pass_flops);
-      CK((reduce_splits<float, float>(st, m, l, P->nsplit_z, (float*)buf(P->off_part), Tt, 1, m)));
-      return finish(Q, Tt, U, ldu, sigma, C, ldc);
+      CK((reduce_splits<float, float>(st, m, l, P->nsplit_z, (float*)buf(P->off_part), Zq, 1, m)));
+      CR(fold_t(Zq, Tt));
+      return finish(Q, Tt, U, ldu, sigma, C, ldc, true);
     }
     if (refine) {
       float* Atf = (float*)(ws + P->off_atf);
@@ -327,8 +362,9 @@ struct Run {
       CR(tc_wpass(st, dt, Qh, nld, n, l, Sh, ldh, m, wpart, P->nsplit_w, status));
       prof_end(P, st, pb16, pass_flops);
     }
-    CK((reduce_splits<float, float>(st, m, l, P->nsplit_w, wpart, Tt, 1, m)));
-    return finish(Q, Tt, U, ldu, sigma, C, ldc);
+    CK((reduce_splits<float, float>(st, m, l, P->nsplit_w, wpart, Zq, 1, m)));
+    CR(fold_t(Zq, Tt));
+    return finish(Q, Tt, U, ldu, sigma, C, ldc, true);
   }
 
   int project(const W* U, int64_t ldu, int kc, const W* Sn, int64_t lds, int64_t mn, W* C,
@@ -433,6 +469,7 @@ static int plan_create_impl(rpod_plan** out, int64_t n, int64_t m, int32_t k, in
   P->off_g = take(8 * L * L);
   P->off_x = take(8 * L * L);
   P->off_xw = take(w * L * L);
+  P->off_xu = take(8 * L * L);
   P->off_eig = take(8 * sym_eig_work_doubles((int)L));
   P->off_sigma = take(8 * L);
   P->off_uhat = take(8 * L * L);

@@ -69,18 +69,51 @@ template cudaError_t sketch<__half>(cudaStream_t, uint64_t, uint64_t, int64_t, i
 // ------------------------------------------------------------------------
 // Generic SIMT GEMM.  16 x 16 threads; thread (ty, tx) owns rows ty + 16 r
 // and columns tx + 16 c of the BM x BN tile (ty varies fastest so that a
-// warp stores 16 consecutive rows of a column-major output).
+// warp stores 16 consecutive rows of a column-major output).  The shared
+// tiles hold each thread's TM rows (TN columns) contiguously, so the inner
+// product step reads them with 16-byte loads: the unpermuted layout needed
+// one shared-memory wavefront per FMA pair and capped the kernel near half
+// the FP32 rate.
 __device__ __forceinline__ bool finite_val(float v) { return isfinite(v); }
 __device__ __forceinline__ bool finite_val(double v) { return isfinite(v); }
 
+template <int NV>
+__device__ __forceinline__ void lds_vec(const float* p, float* v) {
+  if constexpr (NV % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < NV / 4; ++i) {
+      const float4 q = reinterpret_cast<const float4*>(p)[i];
+      v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = p[i];
+  }
+}
+template <int NV>
+__device__ __forceinline__ void lds_vec(const double* p, double* v) {
+  if constexpr (NV % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < NV / 2; ++i) {
+      const double2 q = reinterpret_cast<const double2*>(p)[i];
+      v[2 * i] = q.x; v[2 * i + 1] = q.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = p[i];
+  }
+}
+
 template <typename TA, typename TB, typename TC, typename TO, int BM, int BN, int BK, bool AKC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (sizeof(TC) == 4 && BM * BN >= 128 * 128) ? 2 : 1)
 k_gemm(int64_t M, int64_t N, int64_t K, int64_t kchunk, const TA* __restrict__ A, int64_t lda,
        const TB* __restrict__ B, int64_t ldb, TO* __restrict__ C, int64_t ci, int64_t cj,
        int64_t csplit, unsigned* status, int check, int bkc) {
   constexpr int TM = BM / 16, TN = BN / 16;
-  __shared__ TC As[BK][BM + 1];
-  __shared__ TC Bs[BK][BN + 1];
+  constexpr int NA = BM * BK / 256, NB = BN * BK / 256;
+  constexpr int PAD = 16 / (int)sizeof(TC);  // keeps every row 16-byte aligned
+  __shared__ __align__(16) TC As[BK][BM + PAD];
+  __shared__ __align__(16) TC Bs[BK][BN + PAD];
   const int tid = threadIdx.x, ty = tid & 15, tx = tid >> 4;
   const int64_t i0 = (int64_t)blockIdx.x * BM, j0 = (int64_t)blockIdx.y * BN;
   const int64_t kb = (int64_t)blockIdx.z * kchunk;
@@ -91,32 +124,51 @@ k_gemm(int64_t M, int64_t N, int64_t K, int64_t kchunk, const TA* __restrict__ A
 #pragma unroll
     for (int c = 0; c < TN; ++c) acc[r][c] = TC(0);
   bool bad = false;
-  for (int64_t k0 = kb; k0 < ke; k0 += BK) {
-    for (int idx = tid; idx < BM * BK; idx += 256) {
+  // The next k-tile is loaded into registers while the current one is
+  // multiplied, so each tile costs one global-load latency, not one per
+  // element.
+  TC ra[NA], rb[NB];
+  auto load_tiles = [&](int64_t k0) {
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+      const int idx = tid + u * 256;
       int kk, ii;
       if (AKC) { kk = idx % BK; ii = idx / BK; } else { ii = idx % BM; kk = idx / BM; }
       const int64_t gi = i0 + ii, gk = k0 + kk;
-      TC v = TC(0);
-      if (gi < M && gk < ke) {
-        v = cvt<TC>(AKC ? A[gk + gi * lda] : A[gi + gk * lda]);
-        if (check && !finite_val(v)) bad = true;
-      }
-      As[kk][ii] = v;
+      ra[u] = (gi < M && gk < ke) ? cvt<TC>(AKC ? A[gk + gi * lda] : A[gi + gk * lda]) : TC(0);
     }
-    for (int idx = tid; idx < BN * BK; idx += 256) {
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
       // B(k, j) = B[k + j*ldb] (K-contiguous) or B[k*ldb + j] (N-contiguous)
+      const int idx = tid + u * 256;
       const int kk = bkc ? idx % BK : idx / BN, jj = bkc ? idx / BK : idx % BN;
       const int64_t gj = j0 + jj, gk = k0 + kk;
-      Bs[kk][jj] = (gj < N && gk < ke) ? cvt<TC>(bkc ? B[gk + gj * ldb] : B[gk * ldb + gj]) : TC(0);
+      rb[u] = (gj < N && gk < ke) ? cvt<TC>(bkc ? B[gk + gj * ldb] : B[gk * ldb + gj]) : TC(0);
+    }
+  };
+  if (kb < ke) load_tiles(kb);
+  for (int64_t k0 = kb; k0 < ke; k0 += BK) {
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+      const int idx = tid + u * 256;
+      int kk, ii;
+      if (AKC) { kk = idx % BK; ii = idx / BK; } else { ii = idx % BM; kk = idx / BM; }
+      if (check && !finite_val(ra[u])) bad = true;
+      As[kk][(ii & 15) * TM + (ii >> 4)] = ra[u];  // row ty + 16 r at ty * TM + r
+    }
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int idx = tid + u * 256;
+      const int kk = bkc ? idx % BK : idx / BN, jj = bkc ? idx / BK : idx % BN;
+      Bs[kk][(jj & 15) * TN + (jj >> 4)] = rb[u];
     }
     __syncthreads();
+    if (k0 + BK < ke) load_tiles(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       TC a[TM], b[TN];
-#pragma unroll
-      for (int r = 0; r < TM; ++r) a[r] = As[kk][ty + 16 * r];
-#pragma unroll
-      for (int c = 0; c < TN; ++c) b[c] = Bs[kk][tx + 16 * c];
+      lds_vec<TM>(&As[kk][ty * TM], a);
+      lds_vec<TN>(&Bs[kk][tx * TN], b);
 #pragma unroll
       for (int r = 0; r < TM; ++r)
 #pragma unroll
@@ -200,33 +252,82 @@ INST_GEMM(float, __nv_bfloat16, float, float)
 // block covers 32 consecutive elements with 8 z-slices (32 x 8 threads), each
 // slice summed in z order with four accumulators, the slices combined in a
 // fixed order.
+// Partials are summed in their own precision: FP64 partials (Grams, the
+// FP64 form) in FP64, FP32 partials in FP32 (GB300 issues FP64 adds at
+// 1/64 of the FP32 rate, which made an FP64-accumulating FP32 reduction
+// arithmetic-bound).
 template <typename TP, typename TO>
 __global__ void __launch_bounds__(256)
 k_reduce(int64_t M, int64_t N, int nsplit, const TP* __restrict__ part, TO* __restrict__ out,
          int64_t oi, int64_t oj) {
-  __shared__ double acc[8][33];
+  __shared__ TP acc[8][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t idx = (int64_t)blockIdx.x * 32 + tx;
   const int64_t MN = M * N;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  TP s0 = TP(0), s1 = TP(0), s2 = TP(0), s3 = TP(0);
   if (idx < MN) {
     int z = ty;
     for (; z + 24 < nsplit; z += 32) {
-      s0 += (double)part[(int64_t)z * MN + idx];
-      s1 += (double)part[(int64_t)(z + 8) * MN + idx];
-      s2 += (double)part[(int64_t)(z + 16) * MN + idx];
-      s3 += (double)part[(int64_t)(z + 24) * MN + idx];
+      s0 += part[(int64_t)z * MN + idx];
+      s1 += part[(int64_t)(z + 8) * MN + idx];
+      s2 += part[(int64_t)(z + 16) * MN + idx];
+      s3 += part[(int64_t)(z + 24) * MN + idx];
     }
-    for (; z < nsplit; z += 8) s0 += (double)part[(int64_t)z * MN + idx];
+    for (; z < nsplit; z += 8) s0 += part[(int64_t)z * MN + idx];
   }
   acc[ty][tx] = (s0 + s1) + (s2 + s3);
   __syncthreads();
   if (ty == 0 && idx < MN) {
-    double t = 0.0;
+    TP t = TP(0);
 #pragma unroll
     for (int k = 0; k < 8; ++k) t += acc[k][tx];
-    const int64_t i = idx % M, j = idx / M;
+    const int64_t j = idx / M, i = idx - j * M;
     out[i * oi + j * oj] = (TO)t;
+  }
+}
+
+// Up to 32 splits (the W-pass partials): each thread sums four consecutive
+// elements over z in order (16-byte loads of FP32 partials when aligned),
+// with eight splits in flight.
+template <typename TP, typename TO>
+__global__ void __launch_bounds__(256)
+k_reduce_flat(int64_t M, int64_t N, int nsplit, const TP* __restrict__ part, TO* __restrict__ out,
+              int64_t oi, int64_t oj, int vec) {
+  const int64_t idx0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  const int64_t MN = M * N;
+  if (idx0 >= MN) return;
+  TP s[4] = {TP(0), TP(0), TP(0), TP(0)};
+  if (vec && idx0 + 4 <= MN) {
+    const float* pf = reinterpret_cast<const float*>(part);
+    float f[4] = {0.f, 0.f, 0.f, 0.f};
+    int z = 0;
+    for (; z + 8 <= nsplit; z += 8) {
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = *(const float4*)(pf + (int64_t)(z + u) * MN + idx0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        f[0] += v[u].x; f[1] += v[u].y; f[2] += v[u].z; f[3] += v[u].w;
+      }
+    }
+    for (; z < nsplit; ++z) {
+      const float4 v = *(const float4*)(pf + (int64_t)z * MN + idx0);
+      f[0] += v.x; f[1] += v.y; f[2] += v.z; f[3] += v.w;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) s[e] = (TP)f[e];
+  } else {
+    for (int z = 0; z < nsplit; ++z)
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (idx0 + e < MN) s[e] += part[(int64_t)z * MN + idx0 + e];
+  }
+  // one division per thread; the four elements advance (i, j) in order
+  int64_t j = idx0 / M, i = idx0 - j * M;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if (idx0 + e < MN) out[i * oi + j * oj] = (TO)s[e];
+    if (++i == M) { i = 0; ++j; }
   }
 }
 
@@ -234,7 +335,14 @@ template <typename TP, typename TO>
 cudaError_t reduce_splits(cudaStream_t st, int64_t M, int64_t N, int nsplit, const TP* part,
                           TO* out, int64_t oi, int64_t oj) {
   const int64_t MN = M * N;
-  k_reduce<TP, TO><<<(unsigned)((MN + 31) / 32), 256, 0, st>>>(M, N, nsplit, part, out, oi, oj); note_launch();
+  if (nsplit <= 32) {
+    const int vec = (sizeof(TP) == 4 && (MN & 3) == 0 && ((uintptr_t)part & 15) == 0) ? 1 : 0;
+    k_reduce_flat<TP, TO><<<(unsigned)((MN + 1023) / 1024), 256, 0, st>>>(M, N, nsplit, part, out, oi,
+                                                                          oj, vec);
+  }
+  else
+    k_reduce<TP, TO><<<(unsigned)((MN + 31) / 32), 256, 0, st>>>(M, N, nsplit, part, out, oi, oj);
+  note_launch();
   return cudaGetLastError();
 }
 template cudaError_t reduce_splits<double, double>(cudaStream_t, int64_t, int64_t, int, const double*, double*, int64_t, int64_t);
@@ -362,35 +470,34 @@ static cudaError_t launch_cholesky(cudaStream_t st, int l, const double* G, doub
   return cudaGetLastError();
 }
 
-// Register-blocked FP32 CholeskyQR step (l <= 128): the 256 threads form a
-// 16 x 16 grid and each holds an 8 x 8 block of the (zero-padded) 128 x 128
-// Gram matrix in registers.  Step j of the right-looking factorization reads
-// the updated row j from a double-buffered shared row, forms row j of R
-// (every thread takes the same pivot decision from the same values), applies
-// the rank-1 update to its block and, if it owns row j + 1, publishes that
-// row for the next step: one barrier per step.  R is kept in shared memory.
-// The inverse X = R^{-1} is then formed by the column sweep W <- I,
-// X(:, j) = W(:, j) / R_jj, W(:, c) -= X(:, j) R_jc for c > j, again with one
-// barrier per step (the owner of column j + 1 publishes it scaled).
-// Semantics (pivot test, dropped directions, FP64 gate) as k_cholesky.
-constexpr int kRbLd = 129;
-constexpr size_t kRbSmem = (size_t)128 * kRbLd * sizeof(float);
+// Blocked FP32 CholeskyQR step (l <= 128): A = R^T R with R upper, in 8 x 8
+// blocks.  The 256 threads form a 16 x 16 grid; thread (ty, tx) holds block
+// (ty, tx) of the zero-padded Gram matrix in registers.  Block step k: the
+// owner of diagonal block (k, k) factors it (pivot test per column), the
+// owners of row block k solve R_kj = R_kk^{-T} A_kj, and the owners of the
+// upper trailing blocks apply A_ij -= R_ki^T R_kj: two barriers per block step
+// instead of per column.  The inverse X = R^{-1} follows by the blocked
+// column sweep X(:, k) = W(:, k) R_kk^{-1}, W(:, c) -= X(:, k) R_kc.  Pivot
+// semantics as k_cholesky: a column whose pivot falls to tol times its
+// original diagonal is dropped (zero row of R, zero column of X); in round 0
+// a pivot below 1e-4 of it raises the FP64 gate.
+constexpr int kBlkLd = 132;  // row stride of the shared R (16-byte aligned rows)
+constexpr size_t kBlkSmem = (size_t)(128 * kBlkLd + 128 * 8) * sizeof(float);
 
 template <typename TW>
 __global__ void __launch_bounds__(256)
-k_cholesky_rb(int l, const double* __restrict__ G, float tol, int* gate, double* __restrict__ Xout,
-              TW* __restrict__ Xw, int ldxw, unsigned* status) {
-  extern __shared__ float s_R[];  // [128][kRbLd]: G (column j at row j), then R rows, then X columns
-  __shared__ __align__(16) float s_u[2][128];
+k_cholesky_blk(int l, const double* __restrict__ G, float tol, int* gate, double* __restrict__ Xout,
+               TW* __restrict__ Xw, int ldxw, unsigned* status) {
+  extern __shared__ __align__(16) float s_R[];  // [128][kBlkLd]: G, then R rows, then X
+  float* s_X = s_R + 128 * kBlkLd;              // [128][8]: one block column of X
   __shared__ float s_d0[128];
-  __shared__ float s_rdiag[128];
+  __shared__ float s_rd[128];
   __shared__ int s_keep[128];
   __shared__ int s_ill;
   __shared__ double red[32];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int r0 = ty * 8, c0 = tx * 8;
-  // 16 independent loads in flight per thread (a plain strided loop would
-  // wait out one global-load latency per element)
+  const int nb = (l + 7) >> 3;
   for (int e0 = 0; e0 < 128 * 128; e0 += 256 * 16) {
     float v[16];
 #pragma unroll
@@ -401,13 +508,15 @@ k_cholesky_rb(int l, const double* __restrict__ G, float tol, int* gate, double*
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       const int e = e0 + u * 256 + tid, i = e & 127, j = e >> 7;
-      s_R[j * kRbLd + i] = v[u];
+      s_R[j * kBlkLd + i] = v[u];  // G is symmetric: row j = column j
     }
   }
   double dm = 0.0;
   if (tid < 128) {
     const double g = tid < l ? G[tid + tid * l] : 0.0;
     s_d0[tid] = (float)g;
+    s_rd[tid] = 0.f;
+    s_keep[tid] = 0;
     dm = g;
   }
   if (tid == 0) s_ill = 0;
@@ -416,100 +525,135 @@ k_cholesky_rb(int l, const double* __restrict__ G, float tol, int* gate, double*
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int b = 0; b < 8; ++b) A[a][b] = s_R[(c0 + b) * kRbLd + r0 + a];
-  if (tid < 128) s_u[0][tid] = s_R[tid * kRbLd];  // row 0 = column 0
+    for (int b = 0; b < 8; ++b) A[a][b] = s_R[(r0 + a) * kBlkLd + c0 + b];
   __syncthreads();
-  // factorization; row j of R goes to s_R[j][*]
-  for (int j = 0; j < l; ++j) {
-    const int buf = j & 1;
-    const float d = s_u[buf][j], d0 = s_d0[j];
-    const bool keep = (d0 > 1e-30f) && (d0 > 1e-30f * gmax) && (d > tol * d0);
-    const float rd = keep ? sqrtf(d) : 0.f;
-    const float rinv = keep ? 1.f / rd : 0.f;
-    if (tid == 0) {
-      if (d < 1e-4f * d0) s_ill = 1;
-      s_keep[j] = keep ? 1 : 0;
-      s_rdiag[j] = rd;
-    }
-    float ra[8], rb[8];
+  for (int k = 0; k < nb; ++k) {
+    const int k0 = 8 * k;
+    if (ty == k && tx == k) {
+      // diagonal block: unblocked right-looking factorization in registers
+      int ill = 0;
 #pragma unroll
-    for (int a = 0; a < 8; ++a) ra[a] = (r0 + a > j) ? s_u[buf][r0 + a] * rinv : 0.f;
+      for (int t = 0; t < 8; ++t) {
+        const int j = k0 + t;
+        const float d = A[t][t], d0 = s_d0[j];
+        const bool keep = (j < l) && (d0 > 1e-30f) && (d0 > 1e-30f * gmax) && (d > tol * d0);
+        if (j < l && d < 1e-4f * d0) ill = 1;
+        const float rd = keep ? sqrtf(d) : 0.f;
+        const float rinv = keep ? 1.f / rd : 0.f;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) rb[b] = (c0 + b > j) ? s_u[buf][c0 + b] * rinv : 0.f;
-    if (ty == 0) {
+        for (int b = 0; b < 8; ++b) A[t][b] = (b > t) ? A[t][b] * rinv : (b == t ? rd : 0.f);
 #pragma unroll
-      for (int b = 0; b < 8; ++b) s_R[j * kRbLd + c0 + b] = (c0 + b == j) ? rd : rb[b];
-    }
+        for (int a = t + 1; a < 8; ++a)
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-      for (int b = 0; b < 8; ++b) A[a][b] -= ra[a] * rb[b];
-    const int j1 = j + 1;
-    if (j1 < l && ty == (j1 >> 3)) {
-      const int jo = j1 & 7;
+          for (int b = t + 1; b < 8; ++b) A[a][b] -= A[t][a] * A[t][b];
+        s_keep[j] = keep ? 1 : 0;
+        s_rd[j] = rd;
+      }
+      if (ill) s_ill = 1;
 #pragma unroll
       for (int a = 0; a < 8; ++a)
-        if (a == jo) {
 #pragma unroll
-          for (int b = 0; b < 8; ++b) s_u[buf ^ 1][c0 + b] = A[a][b];
-        }
+        for (int b = 0; b < 8; ++b) s_R[(k0 + a) * kBlkLd + k0 + b] = (b >= a) ? A[a][b] : 0.f;
     }
     __syncthreads();
+    if (ty == k && tx > k && tx < nb) {
+      // row block k: R_kj = R_kk^{-T} A_kj, forward substitution over rows t
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const float rd = s_rd[k0 + t];
+        const float rinv = rd > 0.f ? 1.f / rd : 0.f;
+#pragma unroll
+        for (int s = 0; s < t; ++s) {
+          const float rst = s_R[(k0 + s) * kBlkLd + k0 + t];
+#pragma unroll
+          for (int b = 0; b < 8; ++b) A[t][b] -= rst * A[s][b];
+        }
+#pragma unroll
+        for (int b = 0; b < 8; ++b) A[t][b] *= rinv;
+      }
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        float4* dst = (float4*)&s_R[(k0 + a) * kBlkLd + c0];
+        dst[0] = make_float4(A[a][0], A[a][1], A[a][2], A[a][3]);
+        dst[1] = make_float4(A[a][4], A[a][5], A[a][6], A[a][7]);
+      }
+    }
+    __syncthreads();
+    if (ty > k && tx >= ty && tx < nb) {
+      // upper trailing blocks: A_ij -= R_ki^T R_kj
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const float4* ri4 = (const float4*)&s_R[(k0 + s) * kBlkLd + r0];
+        const float4* rj4 = (const float4*)&s_R[(k0 + s) * kBlkLd + c0];
+        const float4 i0 = ri4[0], i1 = ri4[1], j0 = rj4[0], j1 = rj4[1];
+        const float ri[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
+        const float rj[8] = {j0.x, j0.y, j0.z, j0.w, j1.x, j1.y, j1.z, j1.w};
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) A[a][b] -= ri[a] * rj[b];
+      }
+    }
+    // block step k + 1 writes rows k0 + 8.. only; no barrier needed here
   }
-  // inverse by the column sweep
+  __syncthreads();
+  // inverse: W = I; for each block column k, X(:, k) = W(:, k) R_kk^{-1}
+  // (rows 0..k0+7), then W(:, c) -= X(:, k) R_kc for c > k
   float W[8][8];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
     for (int b = 0; b < 8; ++b) W[a][b] = (r0 + a == c0 + b) ? 1.f : 0.f;
-  if (tid < 128) {  // column 0 of X
-    const float rd0 = s_rdiag[0];
-    s_u[0][tid] = (tid == 0 && rd0 > 0.f) ? 1.f / rd0 : 0.f;
-  }
-  __syncthreads();
-  for (int j = 0; j < l; ++j) {
-    const int buf = j & 1, jb = j >> 3, jo = j & 7;
-    const bool live = s_rdiag[j] > 0.f;
-    float xa[8], rc[8];
+  for (int k = 0; k < nb; ++k) {
+    const int k0 = 8 * k;
+    if (tx == k && ty <= k) {
 #pragma unroll
-    for (int a = 0; a < 8; ++a) xa[a] = s_u[buf][r0 + a];
+      for (int b = 0; b < 8; ++b) {
+        const float rd = s_rd[k0 + b];
+        const float rinv = rd > 0.f ? 1.f / rd : 0.f;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) rc[b] = (live && c0 + b > j) ? s_R[j * kRbLd + c0 + b] : 0.f;
-    if (tx == jb) {
+        for (int s = 0; s < b; ++s) {
+          const float rsb = s_R[(k0 + s) * kBlkLd + k0 + b];
 #pragma unroll
-      for (int b = 0; b < 8; ++b)
-        if (b == jo) {
-#pragma unroll
-          for (int a = 0; a < 8; ++a) W[a][b] = xa[a];
+          for (int a = 0; a < 8; ++a) W[a][b] -= W[a][s] * rsb;
         }
+#pragma unroll
+        for (int a = 0; a < 8; ++a) W[a][b] *= rinv;
+      }
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        float4* dst = (float4*)&s_X[(r0 + a) * 8];
+        dst[0] = make_float4(W[a][0], W[a][1], W[a][2], W[a][3]);
+        dst[1] = make_float4(W[a][4], W[a][5], W[a][6], W[a][7]);
+      }
     }
+    __syncthreads();
+    if (tx > k && tx < nb && ty <= k) {
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+      for (int s = 0; s < 8; ++s) {
+        const float4* rk4 = (const float4*)&s_R[(k0 + s) * kBlkLd + c0];
+        const float4 q0 = rk4[0], q1 = rk4[1];
+        const float rk[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+        float xs[8];
 #pragma unroll
-      for (int b = 0; b < 8; ++b) W[a][b] -= xa[a] * rc[b];
-    const int j1 = j + 1;
-    if (j1 < l && tx == (j1 >> 3)) {
-      const float rd1 = s_rdiag[j1];
-      const float rinv1 = rd1 > 0.f ? 1.f / rd1 : 0.f;
-      const int jo1 = j1 & 7;
+        for (int a = 0; a < 8; ++a) xs[a] = s_X[(r0 + a) * 8 + s];
 #pragma unroll
-      for (int b = 0; b < 8; ++b)
-        if (b == jo1) {
+        for (int a = 0; a < 8; ++a)
 #pragma unroll
-          for (int a = 0; a < 8; ++a) s_u[buf ^ 1][r0 + a] = W[a][b] * rinv1;
-        }
+          for (int b = 0; b < 8; ++b) W[a][b] -= xs[a] * rk[b];
+      }
     }
     __syncthreads();
   }
-  // X (upper triangle of W) through shared memory for coalesced stores
+  // X (upper block triangle of W) through shared memory for coalesced stores
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int b = 0; b < 8; ++b) s_R[(c0 + b) * kRbLd + r0 + a] = (r0 + a <= c0 + b) ? W[a][b] : 0.f;
+    for (int b = 0; b < 8; ++b) s_R[(c0 + b) * kBlkLd + r0 + a] = (r0 + a <= c0 + b) ? W[a][b] : 0.f;
   __syncthreads();
   for (int e = tid; e < l * l; e += 256) {
     const int i = e % l, j = e / l;
-    const float v = s_R[j * kRbLd + i];
+    const float v = s_R[j * kBlkLd + i];
     Xout[e] = (double)v;
     Xw[i + (int64_t)j * ldxw] = (TW)v;
   }
@@ -587,7 +731,7 @@ cudaError_t cholesky(cudaStream_t st, int l, const double* G, double tol, int ro
   // the gate word sits next to the status word (same 256-byte status block)
   int* gate = (int*)(status + 2);
   prepare_kernels();
-  k_cholesky_rb<TW><<<1, 256, kRbSmem, st>>>(l, G, (float)tol, round == 0 ? gate : nullptr, X, Xw, ldxw,
+  k_cholesky_blk<TW><<<1, 256, kBlkSmem, st>>>(l, G, (float)tol, round == 0 ? gate : nullptr, X, Xw, ldxw,
                                        status);
   note_launch();
   if (round != 0) return cudaGetLastError();
@@ -710,10 +854,6 @@ template cudaError_t cholesky<float>(cudaStream_t, int, const double*, double, i
 // and S = X^T A X, lambda_i = S_ii / (1 - R_ii), E_ij = (S_ij + lambda_j
 // R_ij) / (lambda_j - lambda_i) when |lambda_i - lambda_j| > delta, else
 // R_ij / 2, E_ii = R_ii / 2, X <- X + X E; each pass squares the error.
-__device__ __forceinline__ void rr_pair(int L, int s, int i, int& a, int& b) {
-  a = (i == 0) ? 0 : 1 + ((i - 1 + s) % (L - 1));
-  b = 1 + ((L - 2 - i + s) % (L - 1));
-}
 
 __global__ void __launch_bounds__(1024)
 k_jacobi32(int l, const double* __restrict__ G, double* __restrict__ Vout, int max_sweeps,
@@ -756,56 +896,69 @@ k_jacobi32(int l, const double* __restrict__ G, double* __restrict__ Vout, int m
   const float tol = 1e-5f, abs_floor = 1e-30f;
   bool converged = (L < 2);
   int nsweeps = 0;
+  // Fixed work assignment (no index division inside the rounds): blocks
+  // (bi, j) for j = bg, bg + ngb, ...; V entries (vx, pair j) for j = vg,
+  // vg + ngv, ...; thread pi < np owns the round-robin pair slot pi, whose
+  // two indices advance cyclically through 1..L-1 (slot 0 keeps index 0).
+  const int bi = tid % np, bg = tid / np, ngb = nt / np;
+  const int vx = tid % L, vg = tid / L, ngv = nt / L;
+  int ia = tid == 0 ? 0 : tid, ib = L - 1 - tid;
   for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
     ++nsweeps;
     if (tid == 0) s_rot = 0;
     __syncthreads();
     for (int s = 0; s < L - 1; ++s) {
-      for (int pi = tid; pi < np; pi += nt) {
-        int p, q;
-        rr_pair(L, s, pi, p, q);
-        if (p > q) { const int t = p; p = q; q = t; }
+      if (tid < np) {
+        const int p = min(ia, ib), q = max(ia, ib);
         float c = 1.f, sv = 0.f;
         if (q < l) {
           const float apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
           if (fabsf(apq) > tol * sqrtf(fabsf(app * aqq)) && fabsf(apq) > abs_floor) {
-            const float tau = (aqq - app) / (2.f * apq);
-            const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-            c = rsqrtf(1.f + t * t);
+            // t = sign(tau) / (|tau| + sqrt(1 + tau^2)), tau = (a_qq - a_pp) / (2 a_pq)
+            const float tau = __fdividef(aqq - app, 2.f * apq);
+            const float at = fabsf(tau);
+            const float den = at < 1e18f ? at + sqrtf(fmaf(at, at, 1.f)) : 2.f * at;
+            const float t = copysignf(__frcp_rn(den), tau);
+            c = rsqrtf(fmaf(t, t, 1.f));
             sv = t * c;
             s_rot = 1;
           }
         }
-        prm[pi] = make_float4(c, sv, __int_as_float(p), __int_as_float(q));
+        prm[tid] = make_float4(c, sv, __int_as_float(p), __int_as_float(q));
+        if (tid > 0) ia = (ia == L - 1) ? 1 : ia + 1;
+        ib = (ib == L - 1) ? 1 : ib + 1;
       }
       __syncthreads();
       // A <- J^T A J one 2 x 2 block at a time: block (i, j) holds rows
       // (p_i, q_i) and columns (p_j, q_j); rotate its rows by pair i and its
       // columns by pair j.  Blocks are disjoint, so one barrier suffices.
-      for (int b = tid; b < np * np; b += nt) {
-        const int i = b % np, j = b / np;
-        const float4 ri = prm[i], rj = prm[j];
-        if (ri.y == 0.f && rj.y == 0.f) continue;
+      if (bg < ngb) {
+        const float4 ri = prm[bi];
         const int pi_ = __float_as_int(ri.z), qi = __float_as_int(ri.w);
-        const int pj = __float_as_int(rj.z), qj = __float_as_int(rj.w);
-        const float b00 = A[pi_ * ld + pj], b01 = A[pi_ * ld + qj];
-        const float b10 = A[qi * ld + pj], b11 = A[qi * ld + qj];
-        const float t00 = ri.x * b00 - ri.y * b10, t01 = ri.x * b01 - ri.y * b11;
-        const float t10 = ri.y * b00 + ri.x * b10, t11 = ri.y * b01 + ri.x * b11;
-        A[pi_ * ld + pj] = rj.x * t00 - rj.y * t01;
-        A[pi_ * ld + qj] = rj.y * t00 + rj.x * t01;
-        A[qi * ld + pj] = rj.x * t10 - rj.y * t11;
-        A[qi * ld + qj] = rj.y * t10 + rj.x * t11;
+        for (int j = bg; j < np; j += ngb) {
+          const float4 rj = prm[j];
+          if (ri.y == 0.f && rj.y == 0.f) continue;
+          const int pj = __float_as_int(rj.z), qj = __float_as_int(rj.w);
+          const float b00 = A[pi_ * ld + pj], b01 = A[pi_ * ld + qj];
+          const float b10 = A[qi * ld + pj], b11 = A[qi * ld + qj];
+          const float t00 = ri.x * b00 - ri.y * b10, t01 = ri.x * b01 - ri.y * b11;
+          const float t10 = ri.y * b00 + ri.x * b10, t11 = ri.y * b01 + ri.x * b11;
+          A[pi_ * ld + pj] = rj.x * t00 - rj.y * t01;
+          A[pi_ * ld + qj] = rj.y * t00 + rj.x * t01;
+          A[qi * ld + pj] = rj.x * t10 - rj.y * t11;
+          A[qi * ld + qj] = rj.y * t10 + rj.x * t11;
+        }
       }
-      // V <- V J (this thread: row x of pair j's two columns)
-      for (int e = tid; e < L * np; e += nt) {
-        const int x = e % L, j = e / L;
-        const float4 r = prm[j];
-        if (r.y == 0.f) continue;
-        const int p = __float_as_int(r.z), q = __float_as_int(r.w);
-        const float vp = V[x * ld + p], vq = V[x * ld + q];
-        V[x * ld + p] = r.x * vp - r.y * vq;
-        V[x * ld + q] = r.y * vp + r.x * vq;
+      // V <- V J (this thread: row vx of the column pairs j)
+      if (vg < ngv) {
+        for (int j = vg; j < np; j += ngv) {
+          const float4 r = prm[j];
+          if (r.y == 0.f) continue;
+          const int p = __float_as_int(r.z), q = __float_as_int(r.w);
+          const float vp = V[vx * ld + p], vq = V[vx * ld + q];
+          V[vx * ld + p] = r.x * vp - r.y * vq;
+          V[vx * ld + q] = r.y * vp + r.x * vq;
+        }
       }
       __syncthreads();
     }
@@ -995,45 +1148,58 @@ cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma, doub
 // Column sign convention.
 struct ArgMax { double v; long long i; };
 
+// Per column and 8192-row block: the entry of largest magnitude (first row
+// on ties).  Eight loads in flight per thread, then warp shuffles and one
+// pass over the eight warp results.
 template <typename T>
-__global__ void k_colmax_partial(int64_t n, int64_t rows_per_blk, const T* __restrict__ U,
-                                 int64_t ldu, ArgMax* __restrict__ out, int nblk) {
+__device__ __forceinline__ void argmax_merge(T& ba, T& bv, long long& bi, T a, T v, long long i) {
+  if (a > ba || (a == ba && i < bi)) { ba = a; bv = v; bi = i; }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_colmax_partial(int64_t n, int64_t rows_per_blk, const T* __restrict__ U, int64_t ldu,
+                 ArgMax* __restrict__ out, int nblk) {
   const int c = blockIdx.y;
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk;
   const int64_t r1 = (r0 + rows_per_blk < n) ? r0 + rows_per_blk : n;
-  double bv = 0.0, ba = -1.0;
+  const T* u = U + (int64_t)c * ldu;
+  // compared in the matrix's own type (FP64 compares of FP32 data would run
+  // on GB300's narrow FP64 pipe)
+  T bv = T(0), ba = T(-1);
   long long bi = LLONG_MAX;
-  // eight loads in flight per thread; rows visited in increasing order so
-  // the first of equal magnitudes wins
+  // rows visited in increasing order so the first of equal magnitudes wins
   const int64_t step = blockDim.x;
   for (int64_t rb = r0 + threadIdx.x; rb < r1; rb += 8 * step) {
-    double v[8];
+    T v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int64_t r = rb + u * step;
-      v[u] = r < r1 ? (double)U[r + c * ldu] : 0.0;
+    for (int k = 0; k < 8; ++k) {
+      const int64_t r = rb + k * step;
+      v[k] = r < r1 ? u[r] : T(0);
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int64_t r = rb + u * step;
-      const double a = fabs(v[u]);
-      if (r < r1 && a > ba) { ba = a; bv = v[u]; bi = r; }
+    for (int k = 0; k < 8; ++k) {
+      const int64_t r = rb + k * step;
+      const T a = fabs(v[k]);
+      if (r < r1 && a > ba) { ba = a; bv = v[k]; bi = r; }
     }
   }
-  __shared__ double sa[256], sv[256];
-  __shared__ long long si[256];
-  sa[threadIdx.x] = ba; sv[threadIdx.x] = bv; si[threadIdx.x] = bi;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T oa = __shfl_xor_sync(0xffffffffu, ba, o);
+    const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    argmax_merge(ba, bv, bi, oa, ov, oi);
+  }
+  __shared__ T sa[8], sv[8];
+  __shared__ long long si[8];
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { sa[w] = ba; sv[w] = bv; si[w] = bi; }
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) {
-      const int t = threadIdx.x + o;
-      if (sa[t] > sa[threadIdx.x] || (sa[t] == sa[threadIdx.x] && si[t] < si[threadIdx.x])) {
-        sa[threadIdx.x] = sa[t]; sv[threadIdx.x] = sv[t]; si[threadIdx.x] = si[t];
-      }
-    }
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) argmax_merge(ba, bv, bi, sa[k], sv[k], si[k]);
+    out[c * nblk + blockIdx.x] = ArgMax{ba < T(0) ? 0.0 : (double)bv, bi};
   }
-  if (threadIdx.x == 0) out[c * nblk + blockIdx.x] = ArgMax{sa[0] < 0 ? 0.0 : sv[0], si[0]};
 }
 
 __global__ void k_colsign(int ncols, int nblk, const ArgMax* __restrict__ part, double* __restrict__ sgn,
@@ -1055,13 +1221,27 @@ __global__ void k_colsign(int ncols, int nblk, const ArgMax* __restrict__ part, 
   for (int i = threadIdx.x; i < l; i += blockDim.x) Uhat[i + c * l] *= s_s;
 }
 
+// grid: x = column, y = chunks of 1024 rows (grid-stride); a column whose
+// sign is + is left untouched.
 template <typename T>
-__global__ void k_scale_cols(int64_t n, int ncols, T* __restrict__ U, int64_t ldu, const double* __restrict__ sgn) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n * ncols) return;
-  const int64_t r = idx % n;
-  const int c = (int)(idx / n);
-  if (sgn[c] < 0.0) U[r + c * ldu] = -U[r + c * ldu];
+__global__ void __launch_bounds__(256)
+k_scale_cols(int64_t n, int ncols, T* __restrict__ U, int64_t ldu, const double* __restrict__ sgn) {
+  const int c = blockIdx.x;
+  if (!(sgn[c] < 0.0)) return;
+  T* u = U + (int64_t)c * ldu;
+  for (int64_t r0 = (int64_t)blockIdx.y * 1024 + threadIdx.x; r0 < n; r0 += (int64_t)gridDim.y * 1024) {
+    T v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = (r0 + 256 * k < n) ? u[r0 + 256 * k] : T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (r0 + 256 * k < n) u[r0 + 256 * k] = -v[k];
+  }
+}
+
+static dim3 col_grid(int64_t rows, int64_t cols) {
+  const int64_t chunks = (rows + 1023) / 1024;
+  return dim3((unsigned)cols, (unsigned)std::max<int64_t>(1, std::min<int64_t>(chunks, 65535)));
 }
 
 size_t sign_fix_scratch_bytes(int64_t n, int ncols) {
@@ -1078,45 +1258,61 @@ cudaError_t sign_fix(cudaStream_t st, int64_t n, int ncols, T* U, int64_t ldu, d
   double* sgn = (double*)((char*)scratch + (((size_t)ncols * nblk * sizeof(ArgMax) + 255) / 256) * 256);
   k_colmax_partial<T><<<dim3(nblk, ncols), 256, 0, st>>>(n, rpb, U, ldu, part, nblk); note_launch();
   k_colsign<<<ncols, 128, 0, st>>>(ncols, nblk, part, sgn, Uhat, l); note_launch();
-  const int64_t tot = n * ncols;
-  k_scale_cols<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, ncols, U, ldu, sgn); note_launch();
+  k_scale_cols<T><<<col_grid(n, ncols), 256, 0, st>>>(n, ncols, U, ldu, sgn); note_launch();
   return cudaGetLastError();
 }
 template cudaError_t sign_fix<double>(cudaStream_t, int64_t, int, double*, int64_t, double*, int, void*, size_t);
 template cudaError_t sign_fix<float>(cudaStream_t, int64_t, int, float*, int64_t, double*, int, void*, size_t);
 
 // ------------------------------------------------------------------------
+// grid: x = column, y = chunks of 1024 rows (grid-stride), four loads in
+// flight per thread.
 template <typename TS, typename TD>
-__global__ void k_convert(int64_t rows, int64_t cols, const TS* __restrict__ src, int64_t lds,
-                          TD* __restrict__ dst, int64_t ldd) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= rows * cols) return;
-  const int64_t r = idx % rows, c = idx / rows;
-  dst[r + c * ldd] = cvt<TD>(src[r + c * lds]);
+__global__ void __launch_bounds__(256)
+k_convert(int64_t rows, int64_t cols, const TS* __restrict__ src, int64_t lds,
+          TD* __restrict__ dst, int64_t ldd) {
+  const int64_t c = blockIdx.x;
+  const TS* sc = src + c * lds;
+  TD* dc = dst + c * ldd;
+  for (int64_t r0 = (int64_t)blockIdx.y * 1024 + threadIdx.x; r0 < rows; r0 += (int64_t)gridDim.y * 1024) {
+    TS v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = (r0 + 256 * k < rows) ? sc[r0 + 256 * k] : TS(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (r0 + 256 * k < rows) dc[r0 + 256 * k] = cvt<TD>(v[k]);
+  }
 }
 
 template <typename TS, typename TD>
 cudaError_t convert_matrix(cudaStream_t st, int64_t rows, int64_t cols, const TS* src, int64_t lds,
                            TD* dst, int64_t ldd) {
-  const int64_t tot = rows * cols;
-  k_convert<TS, TD><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(rows, cols, src, lds, dst, ldd); note_launch();
+  if (rows < 1 || cols < 1) return cudaSuccess;
+  k_convert<TS, TD><<<col_grid(rows, cols), 256, 0, st>>>(rows, cols, src, lds, dst, ldd); note_launch();
   return cudaGetLastError();
 }
 template cudaError_t convert_matrix<double, float>(cudaStream_t, int64_t, int64_t, const double*, int64_t, float*, int64_t);
 template cudaError_t convert_matrix<double, double>(cudaStream_t, int64_t, int64_t, const double*, int64_t, double*, int64_t);
 
 template <typename T>
-__global__ void k_check_finite(int64_t rows, int64_t cols, const T* __restrict__ S, int64_t lds, unsigned* status) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= rows * cols) return;
-  const float v = cvt<float>(S[idx % rows + (idx / rows) * lds]);
-  if (!isfinite(v)) atomicOr(status, ST_NONFINITE);
+__global__ void __launch_bounds__(256)
+k_check_finite(int64_t rows, int64_t cols, const T* __restrict__ S, int64_t lds, unsigned* status) {
+  const T* sc = S + (int64_t)blockIdx.x * lds;
+  bool bad = false;
+  for (int64_t r0 = (int64_t)blockIdx.y * 1024 + threadIdx.x; r0 < rows; r0 += (int64_t)gridDim.y * 1024) {
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = (r0 + 256 * k < rows) ? cvt<float>(sc[r0 + 256 * k]) : 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) bad |= !isfinite(v[k]);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
 }
 
 template <typename T>
 cudaError_t check_finite(cudaStream_t st, int64_t rows, int64_t cols, const T* S, int64_t lds, unsigned* status) {
-  const int64_t tot = rows * cols;
-  k_check_finite<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(rows, cols, S, lds, status); note_launch();
+  if (rows < 1 || cols < 1) return cudaSuccess;
+  k_check_finite<T><<<col_grid(rows, cols), 256, 0, st>>>(rows, cols, S, lds, status); note_launch();
   return cudaGetLastError();
 }
 template cudaError_t check_finite<__nv_bfloat16>(cudaStream_t, int64_t, int64_t, const __nv_bfloat16*, int64_t, unsigned*);
@@ -1333,8 +1529,8 @@ void prepare_kernels() {
     cudaFuncSetAttribute(k_cholesky<double, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_cholesky64_gated<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_cholesky_rb<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRbSmem);
-    cudaFuncSetAttribute(k_cholesky_rb<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRbSmem);
+    cudaFuncSetAttribute(k_cholesky_blk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlkSmem);
+    cudaFuncSetAttribute(k_cholesky_blk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlkSmem);
   });
   prepare_kernels_tc();
 }
