@@ -168,7 +168,8 @@ int rpod_project_static(const rpod_plan* plan, const void* U, int64_t ldu, int32
  * q_2 of Sec. 2 times the parameter samples mu_k of Sec. 4.1, each with its
  * own snapshot count and rank) run as one unit.  The first rpod_batch_run
  * captures every instance's pipeline into one CUDA graph (instances spread
- * over worker streams inside the graph) and launches it; later runs with the
+ * over worker streams inside the graph, costliest first, each to the least
+ * loaded stream) and launches it; later runs with the
  * same workspace pointer replay the graph with a single launch.  All
  * pointers in the instance table are device pointers owned by the caller and
  * must stay valid (the graph bakes them in); the data they point to may
@@ -199,14 +200,15 @@ int rpod_batch_workspace_bytes(const rpod_batch* batch, size_t* bytes);
 /* Enqueues the whole batch on `stream` (graph capture on first use). */
 int rpod_batch_run(rpod_batch* batch, void* workspace, size_t workspace_bytes, void* stream);
 /* Autotuner: times the candidate launch configurations (worker streams in
- * {1, 2, 4, 8, 16} x split-K scale in {1/2, 1, 2} of the passes' default
+ * {1, 2, 4, 8, 16, 32, 64} x split-K scale in {1/2, 1, 2} of the passes' default
  * split) `trials` times each with CUDA events on `stream` (synchronising),
  * keeps the fastest, re-captures, and returns it through best_streams and
  * best_split_pct (may be NULL).  Runs the batch many times: outputs hold the
  * last run's results. */
 int rpod_batch_tune(rpod_batch* batch, void* workspace, size_t workspace_bytes, void* stream,
                     int32_t trials, int32_t* best_streams, int32_t* best_split_pct);
-/* Sets the launch configuration directly (e.g. from a cached tuning). */
+/* Sets the launch configuration directly (e.g. from a cached tuning):
+ * 1..64 worker streams, split_pct in 10..200. */
 int rpod_batch_configure(rpod_batch* batch, int32_t streams, int32_t split_pct);
 /* Synchronises, reads and clears every instance's status word; returns the
  * first error found (and its instance index through first_bad, -1 if none)

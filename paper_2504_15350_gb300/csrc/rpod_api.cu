@@ -180,11 +180,13 @@ struct Run {
                               (int64_t)l * l, status, false)));
     CK((reduce_splits<double, double>(st, l, l, ns, dbuf(P->off_gpart), GT, 1, l)));
     double* Uhat = dbuf(P->off_uhat);
-    // FP64 refinement passes after the FP32 Jacobi stage: each squares the
-    // eigenvector error, so from about 1e-6 two reach FP64 level for
-    // separated eigenvalues; the FP32 forms stop at three, the FP64 form
-    // takes five for clusters.
-    CK((sym_eig(st, l, GT, sigma, Uhat, dbuf(P->off_eig), status, sizeof(W) == 8 ? 5 : 3)));
+    // FP32 Jacobi down to rotations below 1e-5 of sqrt(a_pp a_qq), then FP64
+    // refinement passes, each of which squares the eigenvector error outside
+    // clusters; the cluster threshold of a pass scales with the norm of all
+    // remaining off-diagonal terms, so eigenvalues closer than that are
+    // separated only by a later pass: three passes for the FP32 forms, five
+    // for the FP64 form.
+    CK((sym_eig(st, l, GT, sigma, Uhat, dbuf(P->off_eig), status, sizeof(W) == 8 ? 5 : 3, 1e-5f)));
     CK((check_finite_vec(st, l, sigma, status)));
     // Alg. 1: lift U = Q Uhat (first k or all l columns), then the sign rule
     const int ku = (P->flags & RPOD_FLAG_RETURN_ALL_L) ? l : k;
@@ -700,8 +702,10 @@ void drop_graph(rpod_batch* B) {
   B->graph_ws = nullptr;
 }
 
+constexpr int kMaxBatchStreams = 64;
+
 int ensure_streams(rpod_batch* B) {
-  while ((int)B->streams.size() < 16) {
+  while ((int)B->streams.size() < kMaxBatchStreams) {
     cudaStream_t s;
     cudaEvent_t e;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return RPOD_ERR_CUDA;
@@ -723,7 +727,27 @@ int capture(rpod_batch* B, char* ws) {
   prepare_kernels();
   drop_graph(B);
   cudaStream_t stream = B->cap;
-  const int ns = std::max(1, std::min(B->nstreams, std::min(16, B->count)));
+  const int ns = std::max(1, std::min(B->nstreams, std::min(kMaxBatchStreams, B->count)));
+  // Longest-processing-time assignment of instances to worker streams: the
+  // costliest instances first, each to the stream with the least work so
+  // far.  Cost = pass bytes (2q + 2 passes over n x m) plus a fixed share for
+  // the latency-bound small-matrix steps, which scale with l.
+  std::vector<int> order(B->count), where(B->count);
+  std::vector<double> cost(B->count), load(ns, 0.0);
+  for (int i = 0; i < B->count; ++i) {
+    const rpod_instance& I = B->inst[i];
+    const double l = (double)(I.k + I.p);
+    cost[i] = (2.0 * I.q + 2.0) * (double)I.n * (double)I.m + 4.0e6 * l;
+    order[i] = i;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  for (int i : order) {
+    int best = 0;
+    for (int s2 = 1; s2 < ns; ++s2)
+      if (load[s2] < load[best]) best = s2;
+    where[i] = best;
+    load[best] += cost[i];
+  }
   if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return RPOD_ERR_CUDA;
   int rc = RPOD_OK;
@@ -731,10 +755,11 @@ int capture(rpod_batch* B, char* ws) {
   if (cudaEventRecord(B->fork, stream) != cudaSuccess) rc = RPOD_ERR_CUDA;
   for (int s = 0; s < ns && rc == RPOD_OK; ++s)
     if (cudaStreamWaitEvent(B->streams[s], B->fork, 0) != cudaSuccess) rc = RPOD_ERR_CUDA;
-  for (int i = 0; i < B->count && rc == RPOD_OK; ++i) {
+  for (int oi = 0; oi < B->count && rc == RPOD_OK; ++oi) {
+    const int i = order[oi];
     const rpod_instance& I = B->inst[i];
     rc = rpod_basis(B->plans[i], I.S, I.lds, B->s_dtype, I.S_refine, I.ldr, I.U, I.ldu, I.sigma,
-                    I.C, I.ldc, ws + B->ws_off[i], B->plans[i]->total, B->streams[i % ns]);
+                    I.C, I.ldc, ws + B->ws_off[i], B->plans[i]->total, B->streams[where[i]]);
     launches += B->plans[i]->last_launches;
   }
   for (int s = 0; s < ns && rc == RPOD_OK; ++s) {
@@ -803,7 +828,7 @@ int rpod_batch_workspace_bytes(const rpod_batch* B, size_t* bytes) {
 }
 
 int rpod_batch_configure(rpod_batch* B, int32_t streams, int32_t split_pct) {
-  if (!B || streams < 1 || streams > 16 || split_pct < 10 || split_pct > 200)
+  if (!B || streams < 1 || streams > kMaxBatchStreams || split_pct < 10 || split_pct > 200)
     return RPOD_ERR_INVALID_ARG;
   B->nstreams = streams;
   B->split_pct = split_pct;
@@ -826,14 +851,14 @@ int rpod_batch_tune(rpod_batch* B, void* workspace, size_t workspace_bytes, void
                     int32_t trials, int32_t* best_streams, int32_t* best_split_pct) {
   if (!B || trials < 1) return RPOD_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  const int stream_opts[5] = {1, 2, 4, 8, 16};
+  const int stream_opts[7] = {1, 2, 4, 8, 16, 32, 64};
   const int split_opts[3] = {50, 100, 200};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return RPOD_ERR_CUDA;
   float best = 1e30f;
   int bs = B->nstreams, bp = B->split_pct;
   int rc = RPOD_OK;
-  for (int a = 0; a < 5 && rc == RPOD_OK; ++a) {
+  for (int a = 0; a < 7 && rc == RPOD_OK; ++a) {
     if (stream_opts[a] > std::max(1, B->count)) continue;
     for (int b = 0; b < 3 && rc == RPOD_OK; ++b) {
       rc = rpod_batch_configure(B, stream_opts[a], split_opts[b]);

@@ -72,7 +72,8 @@ cudaError_t cholesky(cudaStream_t st, int l, const double* G, double tol, int ro
 // Jacobi, then FP64 Ogita-Aishima refinement.  Outputs eigenvalues
 // (descending, as sigma = sqrt(max(lambda, 0))) and eigenvectors Uhat (l x l).
 cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma,
-                    double* Uhat, double* work, unsigned* status, int refine_iters);
+                    double* Uhat, double* work, unsigned* status, int refine_iters,
+                    float jacobi_tol);
 size_t sym_eig_work_doubles(int l);
 
 // Column-sign convention: per column c < ncols of U (rows n, ld ldu) find the

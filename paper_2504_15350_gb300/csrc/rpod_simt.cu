@@ -38,6 +38,59 @@ __device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64
   }
 }
 
+// Entry e = i + j m of Lambda is z0 (e even) or z1 (e odd) of the
+// Box-Muller pair of Philox block e / 2: u1 = (w0 >> 11 + 1) 2^-53,
+// u2 = (w1 >> 11) 2^-53, z0 = sqrt(-2 ln u1) cos(2 pi u2), z1 = ... sin.
+// FP64 and FP32 sketches evaluate it in FP64.  A sketch stored in a 16-bit
+// type keeps 8 or 11 mantissa bits, so it is evaluated in FP32 (GB300's FP64
+// transcendental throughput made the FP64 form of this kernel 90 us for
+// m l = 1.2e6): the integer words and uniforms are the same, ln u1 is taken
+// as log1p(-(1 - u1)) for u1 >= 1/2 so that u1 near 1 keeps its relative
+// accuracy, and the result differs from the FP64 value by a few FP32 ulps,
+// which changes the 16-bit rounding only for values within that distance
+// of a rounding boundary (the angle is reduced to within a quarter turn in
+// integer arithmetic, so values near the zeros of sin and cos keep their
+// relative accuracy).
+template <typename T>
+__device__ __forceinline__ void box_muller_store(uint64_t w0, uint64_t w1, T* a, T* b) {
+  const uint64_t x0 = w0 >> 11, x1 = w1 >> 11;
+  if constexpr (sizeof(T) == 2) {
+    float lnu;
+    if (x0 >= (1ull << 52)) {
+      // 1 - u1 = (2^53 - 1 - x0) 2^-53, exact in FP64, accurate in FP32
+      const float d = (float)((double)((1ull << 53) - 1ull - x0) * 0x1p-53);
+      lnu = log1pf(-d);
+    } else {
+      lnu = logf((float)(((double)x0 + 1.0) * 0x1p-53));
+    }
+    const float r = sqrtf(-2.f * lnu);
+    // angle pi t with t = x1 2^-52 in [0, 2): split t = q/2 + f exactly in
+    // integers (|f| <= 1/4) so that sin and cos keep their relative accuracy
+    // near their zeros, then rotate by the quarter turns q
+    const int64_t q = (int64_t)((x1 + (1ull << 50)) >> 51);
+    const float f = (float)((double)((int64_t)x1 - q * (int64_t)(1ull << 51)) * 0x1p-52);
+    float s0, c0;
+    sincospif(f, &s0, &c0);
+    float sn, cs;
+    switch (q & 3) {
+      case 0: sn = s0; cs = c0; break;
+      case 1: sn = c0; cs = -s0; break;
+      case 2: sn = -s0; cs = -c0; break;
+      default: sn = -c0; cs = s0; break;
+    }
+    *a = cvt<T>(r * cs);
+    if (b) *b = cvt<T>(r * sn);
+  } else {
+    const double u1 = ((double)x0 + 1.0) * 0x1p-53;
+    const double u2 = (double)x1 * 0x1p-53;
+    const double r = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    *a = cvt<T>(r * cs);
+    if (b) *b = cvt<T>(r * sn);
+  }
+}
+
 template <typename T>
 __global__ void k_sketch(uint64_t seed, uint64_t sid, int64_t m, int64_t total, T* Lam, int64_t ld) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -45,13 +98,9 @@ __global__ void k_sketch(uint64_t seed, uint64_t sid, int64_t m, int64_t total, 
   if (e0 >= total) return;
   uint64_t c[4] = {(uint64_t)t, sid, 0ull, 0ull};
   philox4x64_10(c, seed, 0ull);
-  const double u1 = ((double)(c[0] >> 11) + 1.0) * 0x1p-53;
-  const double u2 = (double)(c[1] >> 11) * 0x1p-53;
-  const double r = sqrt(-2.0 * log(u1));
-  double sn, cs;
-  sincospi(2.0 * u2, &sn, &cs);
-  Lam[(e0 % m) + (e0 / m) * ld] = cvt<T>(r * cs);
-  if (e0 + 1 < total) Lam[((e0 + 1) % m) + ((e0 + 1) / m) * ld] = cvt<T>(r * sn);
+  const int64_t j0 = e0 / m, i0 = e0 - j0 * m;
+  const int64_t i1 = (i0 + 1 == m) ? 0 : i0 + 1, j1 = (i0 + 1 == m) ? j0 + 1 : j0;
+  box_muller_store<T>(c[0], c[1], Lam + i0 + j0 * ld, e0 + 1 < total ? Lam + i1 + j1 * ld : nullptr);
 }
 
 template <typename T>
@@ -387,7 +436,9 @@ k_cholesky(int l, const double* __restrict__ G, double tol, double* __restrict__
   extern __shared__ double sm[];
   const int ld = l + 1;
   TF* A = (TF*)sm;                                        // l x l, column-major, stride ld
-  double* d0 = (double*)(((uintptr_t)(A + l * ld) + 15) & ~(uintptr_t)15);  // original diagonal
+  // offsets in elements of the shared array (an integer round trip of the
+  // pointer would turn its accesses into generic ones)
+  double* d0 = sm + (((size_t)l * ld * sizeof(TF) + 15) / 16) * 2;  // original diagonal
   TI* tmp = (TI*)(d0 + l);                                // column buffer
   __shared__ double red[32];
   __shared__ TF s_rinv;
@@ -673,53 +724,91 @@ k_cholesky64_gated(int l, const double* __restrict__ G, double tol, int* gate,
                    double* __restrict__ Xout, TW* __restrict__ Xw, int ldxw, unsigned* status,
                    const double* __restrict__ part, int nsplit);
 
-// Gram partials with FP64 products of an FP32 matrix, run only when the gate
-// is raised (an FP32 Gram cannot resolve pivots below about 1e-9 of the
-// column norms; FP64 products of FP32 data are exact).
+// Gram partials of an FP32 matrix with exact products, run only when the
+// gate is raised (an FP32 Gram cannot resolve pivots below about 1e-9 of the
+// column norms).  GB300 issues FP64 arithmetic at 1/64 of the FP32 rate, so
+// the exact sums are kept as unevaluated FP32 pairs (double-float): each
+// product a*b is split exactly into p = fl(a*b) and e = fma(a, b, -p), p is
+// added to the high word with Knuth's TwoSum and the rounding error plus e
+// go to the low word (Dekker, Numer. Math. 18, 1971), relative error of
+// order rows * 2^-46.  Only blocks on or above the diagonal are formed (the
+// factorization reads the upper triangle): thread t < 136 owns upper block
+// (bi, bj) of a 16 x 16 grid of B x B blocks, 16 B >= l.
+template <int B>
 __global__ void __launch_bounds__(256)
-k_gram_f64_gated(int64_t rows, int l, const float* __restrict__ Y, int64_t ldy, int64_t chunk,
-                 double* __restrict__ part, const int* gate) {
+k_gram_df_gated(int64_t rows, int l, const float* __restrict__ Y, int64_t ldy, int64_t chunk,
+                double* __restrict__ part, const int* gate) {
   __shared__ int s_go;
   if (threadIdx.x == 0) s_go = *gate;
   __syncthreads();
   if (!s_go) return;
-  constexpr int BR = 32;
-  __shared__ __align__(16) float Ys[BR][128 + 4];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  constexpr int BR = 32, W = 16 * B;
+  __shared__ __align__(16) float Ys[BR][W + 4];
+  const int tid = threadIdx.x;
   const int64_t r0 = (int64_t)blockIdx.x * chunk;
   const int64_t r1 = (r0 + chunk < rows) ? r0 + chunk : rows;
-  double acc[8][8];
+  int bi = 0, bj = 0;
+  const bool active = tid < 136;
+  if (active) {
+    int rem = tid;
+    while (rem >= 16 - bi) { rem -= 16 - bi; ++bi; }
+    bj = bi + rem;
+  }
+  const bool work = active && bi * B < l && bj * B < l;
+  float sh[B][B], sl[B][B];
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
+  for (int a = 0; a < B; ++a)
 #pragma unroll
-    for (int b = 0; b < 8; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < B; ++b) { sh[a][b] = 0.f; sl[a][b] = 0.f; }
   for (int64_t rb = r0; rb < r1; rb += BR) {
-    for (int e = tid; e < BR * 128; e += 256) {
-      const int rr = e & (BR - 1), c = e / BR;
-      const int64_t r = rb + rr;
-      Ys[rr][c] = (c < l && r < r1) ? Y[r + (int64_t)c * ldy] : 0.f;
+    constexpr int NL = BR * W / 256;  // loads per thread, in batches of 8 in flight
+#pragma unroll
+    for (int u0 = 0; u0 < NL; u0 += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = tid + (u0 + u) * 256, rr = e % BR, c = e / BR;
+        const int64_t r = rb + rr;
+        v[u] = (u0 + u < NL && c < l && r < r1) ? Y[r + (int64_t)c * ldy] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = tid + (u0 + u) * 256;
+        if (u0 + u < NL) Ys[e % BR][e / BR] = v[u];
+      }
     }
     __syncthreads();
-    for (int rr = 0; rr < BR; ++rr) {
-      double av[8], bv[8];
+    if (work) {
+      for (int rr = 0; rr < BR; ++rr) {
+        float av[B], bv[B];
 #pragma unroll
-      for (int a = 0; a < 8; ++a) av[a] = (double)Ys[rr][ty * 8 + a];
+        for (int a = 0; a < B; ++a) av[a] = Ys[rr][bi * B + a];
 #pragma unroll
-      for (int b = 0; b < 8; ++b) bv[b] = (double)Ys[rr][tx * 8 + b];
+        for (int b = 0; b < B; ++b) bv[b] = Ys[rr][bj * B + b];
 #pragma unroll
-      for (int a = 0; a < 8; ++a)
+        for (int a = 0; a < B; ++a)
 #pragma unroll
-        for (int b = 0; b < 8; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+          for (int b = 0; b < B; ++b) {
+            const float p = av[a] * bv[b];
+            const float e = fmaf(av[a], bv[b], -p);
+            const float t = sh[a][b] + p;
+            const float bp = t - sh[a][b];
+            const float err = (sh[a][b] - (t - bp)) + (p - bp);
+            sh[a][b] = t;
+            sl[a][b] += err + e;
+          }
+      }
     }
     __syncthreads();
   }
+  if (!work) return;
   double* pz = part + (int64_t)blockIdx.x * l * l;
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
+  for (int a = 0; a < B; ++a)
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int i = ty * 8 + a, j = tx * 8 + b;
-      if (i < l && j < l) pz[i + j * l] = acc[a][b];
+    for (int b = 0; b < B; ++b) {
+      const int i = bi * B + a, j = bj * B + b;
+      if (i < l && j < l) pz[i + j * l] = (double)sh[a][b] + (double)sl[a][b];
     }
 }
 
@@ -739,7 +828,10 @@ cudaError_t cholesky(cudaStream_t st, int l, const double* G, double tol, int ro
   if (Y && part && nsplit > 0) {
     int64_t chunk = (rows + nsplit - 1) / nsplit;
     chunk = (chunk + 31) / 32 * 32;
-    k_gram_f64_gated<<<nsplit, 256, 0, st>>>(rows, l, Y, rows, chunk, part, gate);
+    if (l <= 64)
+      k_gram_df_gated<4><<<nsplit, 256, 0, st>>>(rows, l, Y, rows, chunk, part, gate);
+    else
+      k_gram_df_gated<8><<<nsplit, 256, 0, st>>>(rows, l, Y, rows, chunk, part, gate);
     note_launch();
     gp = part;
   }
@@ -759,11 +851,11 @@ k_cholesky64_gated(int l, const double* __restrict__ G, double tol, int* gate,
   __syncthreads();
   if (!s_go) return;
   // FP64 factorization of the Gram matrix; with `part`, the Gram matrix is
-  // the sum of the FP64-product partials written by k_gram_f64_gated
+  // the sum of the exact-product partials written by k_gram_df_gated
   extern __shared__ double sm[];
   const int ld = l + 1;
   double* A = sm;
-  double* d0 = (double*)(((uintptr_t)(A + l * ld) + 15) & ~(uintptr_t)15);
+  double* d0 = sm + (((size_t)l * ld + 1) / 2) * 2;
   float* tmp = (float*)(d0 + l);
   __shared__ double red[32];
   __shared__ double s_rinv;
@@ -857,15 +949,18 @@ template cudaError_t cholesky<float>(cudaStream_t, int, const double*, double, i
 
 __global__ void __launch_bounds__(1024)
 k_jacobi32(int l, const double* __restrict__ G, double* __restrict__ Vout, int max_sweeps,
-           unsigned* status) {
-  extern __shared__ float smf[];
+           float tol, unsigned* status) {
+  extern __shared__ float4 smf4[];
+  float* smf = reinterpret_cast<float*>(smf4);
   const int L = l + (l & 1);
   const int np = L / 2;
   const int ld = L + 1;
   float* A = smf;               // L x L, row stride ld
   float* V = A + L * ld;        // L x L, row stride ld
-  // rotation of pair i: (c, s, p, q) packed in one float4 (p, q as int bits)
-  float4* prm = (float4*)(((uintptr_t)(V + L * ld) + 15) & ~(uintptr_t)15);
+  // rotation of pair i: (c, s, p, q) packed in one float4 (p, q as int
+  // bits), placed by element offset so that its accesses stay shared-memory
+  // accesses
+  float4* prm = smf4 + (2 * L * ld + 3) / 4;
   __shared__ double red[32];
   __shared__ int s_rot;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -890,10 +985,10 @@ k_jacobi32(int l, const double* __restrict__ G, double* __restrict__ Vout, int m
     }
   }
   __syncthreads();
-  // Rotate while |a_pq| exceeds 1e-5 of sqrt(a_pp a_qq).  The test is
+  // Rotate while |a_pq| exceeds tol * sqrt(a_pp a_qq).  The test is
   // relative on purpose: an absolute floor would leave pairs of small
   // eigenvalues unrotated, and the FP64 refinement cannot split such a pair.
-  const float tol = 1e-5f, abs_floor = 1e-30f;
+  const float abs_floor = 1e-30f;
   bool converged = (L < 2);
   int nsweeps = 0;
   // Fixed work assignment (no index division inside the rounds): blocks
@@ -1092,7 +1187,7 @@ size_t sym_eig_work_doubles(int l) {
 }
 
 cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma, double* Uhat,
-                    double* work, unsigned* status, int refine_iters) {
+                    double* work, unsigned* status, int refine_iters, float jacobi_tol) {
   const size_t ll = (size_t)l * l;
   double* X = work;
   double* XtX = X + ll;
@@ -1106,7 +1201,7 @@ cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma, doub
   const int L = l + (l & 1);
   const size_t smj = (size_t)2 * L * (L + 1) * sizeof(float) + 16 + (size_t)(L / 2) * sizeof(float4);
   prepare_kernels();
-  k_jacobi32<<<1, 1024, smj, st>>>(l, G, X, 20, status); note_launch();
+  k_jacobi32<<<1, 1024, smj, st>>>(l, G, X, 20, jacobi_tol, status); note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_frob<<<1, 256, 0, st>>>((int64_t)ll, G, normA); note_launch();

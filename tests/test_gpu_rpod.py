@@ -61,6 +61,24 @@ def test_sketch_matches_oracle(m, l, seed):
     assert np.abs(lam32 - ref).max() <= 4e-7
 
 
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+def test_16bit_sketch_is_the_rounded_oracle_sketch(dtype):
+    """16-bit sketches are evaluated in FP32: every entry is the oracle's FP64
+    value rounded to the 16-bit type, except entries within a few FP32 ulps of
+    a rounding boundary, which may land on the neighbouring 16-bit value."""
+    m, l, seed = 3001, 120, 11
+    plan = R.Plan(4096, m, l, 0, 1, seed=seed, compute="bf16")
+    got = plan.sketch(dtype).float().cpu().numpy().astype(np.float64)
+    ref64 = gaussian_sketch(seed, m, l, 0)
+    ref = torch.from_numpy(ref64).to(dtype).double().numpy()
+    diff = got != ref
+    assert diff.mean() <= 2e-3, diff.mean()
+    ulp = np.abs(ref) * (2.0 ** -7 if dtype == torch.bfloat16 else 2.0 ** -10)
+    assert np.all(np.abs(got - ref)[diff] <= 1.01 * ulp[diff] + 2.0 ** -24)
+    # and the shared mantissa bits agree with the FP64 value to FP32 accuracy
+    assert np.abs(got - ref64).max() <= 2.0 ** -7 * np.abs(ref64).max()
+
+
 def test_f64_config1_matches_oracle():
     rec = make_recipe(64, 64, 500, 400, ("power", 1.5), seed=0, noise=1e-6)
     S = snapshot_matrix(rec)
