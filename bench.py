@@ -59,6 +59,11 @@ def parse():
     ap.add_argument("--learned-epochs", type=int, default=15)
     ap.add_argument("--ny", type=int, default=512,
                     help="grid rows (n = 512 * ny); smaller values make the small profiling case")
+    ap.add_argument("--only-batched", choices=["bf16", "f32"], default=None,
+                    help="profiling aid: run only the batched leg in this form and print its "
+                         "JSON object")
+    ap.add_argument("--batched-config", default=None,
+                    help="STREAMS,SPLIT_PCT: skip the tuner and use this launch configuration")
     return ap.parse_args()
 
 
@@ -217,7 +222,7 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
-def run_batched(dev, max_over_ranks, barrier, rank=0, world=1, steps=5, form="f32"):
+def run_batched(dev, max_over_ranks, barrier, rank=0, world=1, steps=5, form="f32", config=None):
     """64 independent instances (4 fields x 16 parameter samples) on a
     128 x 256 grid, m_b ~ U{500..3000}, k_b in {10, 20, 30, 50}, p = 10,
     q = 1, FP32 snapshots, one captured CUDA graph per run; the launch
@@ -235,7 +240,11 @@ def run_batched(dev, max_over_ranks, barrier, rank=0, world=1, steps=5, form="f3
     S = [snapshot_matrix(r, device=dev, dtype=torch.float32) for r in recs]
     flags = R.RPOD_FLAG_REFINE_FP32 if form == "bf16" else 0
     B = R.Batch(S, ks, 10, 1, seeds, compute=form, flags=flags, device=dev)
-    best = B.tune(trials=1)
+    if config:
+        best = tuple(int(v) for v in config.split(","))
+        B.configure(*best)
+    else:
+        best = B.tune(trials=1)
     B.run()
     rc, bad, _ = B.status()
     if rc != R.RPOD_OK:
@@ -316,6 +325,15 @@ def main():
         t = torch.tensor([x], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return t.item()
+
+    if args.only_batched:
+        out = run_batched(dev, max_over_ranks, barrier, rank, world, steps=args.steps,
+                          form=args.only_batched, config=args.batched_config)
+        if rank == 0:
+            print(json.dumps({"batched": out}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     w = dict(WORKLOAD)
     w["ny"] = args.ny
@@ -402,7 +420,8 @@ def main():
                                f"{mhz:.0f} MHz (median SM clock under load)",
                 "kernel": "passes over S (SIMT FP32 GEMM)",
                 "achieved_hbm_gbs": per_bytes / (per_ms * 1e-3) / 1e9}
-    roof["traffic"] = recorded_traffic(head)
+    # recorded for the full bench workload only
+    roof["traffic"] = recorded_traffic(head) if args.ny == 512 else None
     roof["pass_ms_avg"] = per_ms
     roof["passes_per_step"] = hr["passes"] / hr["steps"]
 

@@ -1027,32 +1027,65 @@ k_jacobi32(int l, const double* __restrict__ G, double* __restrict__ Vout, int m
       // A <- J^T A J one 2 x 2 block at a time: block (i, j) holds rows
       // (p_i, q_i) and columns (p_j, q_j); rotate its rows by pair i and its
       // columns by pair j.  Blocks are disjoint, so one barrier suffices.
+      // (np <= 64 and nt = 1024, so a thread owns at most 4 blocks and 8 V
+      // pairs; all their loads are issued before any store)
       if (bg < ngb) {
         const float4 ri = prm[bi];
         const int pi_ = __float_as_int(ri.z), qi = __float_as_int(ri.w);
-        for (int j = bg; j < np; j += ngb) {
-          const float4 rj = prm[j];
-          if (ri.y == 0.f && rj.y == 0.f) continue;
-          const int pj = __float_as_int(rj.z), qj = __float_as_int(rj.w);
-          const float b00 = A[pi_ * ld + pj], b01 = A[pi_ * ld + qj];
-          const float b10 = A[qi * ld + pj], b11 = A[qi * ld + qj];
-          const float t00 = ri.x * b00 - ri.y * b10, t01 = ri.x * b01 - ri.y * b11;
-          const float t10 = ri.y * b00 + ri.x * b10, t11 = ri.y * b01 + ri.x * b11;
-          A[pi_ * ld + pj] = rj.x * t00 - rj.y * t01;
-          A[pi_ * ld + qj] = rj.y * t00 + rj.x * t01;
-          A[qi * ld + pj] = rj.x * t10 - rj.y * t11;
-          A[qi * ld + qj] = rj.y * t10 + rj.x * t11;
+        float4 rj[4];
+        float b[4][4];
+        bool act[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = bg + u * ngb;
+          act[u] = j < np;
+          rj[u] = act[u] ? prm[j] : make_float4(1.f, 0.f, 0.f, 0.f);
+          act[u] = act[u] && (ri.y != 0.f || rj[u].y != 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (!act[u]) continue;
+          const int pj = __float_as_int(rj[u].z), qj = __float_as_int(rj[u].w);
+          b[u][0] = A[pi_ * ld + pj];
+          b[u][1] = A[pi_ * ld + qj];
+          b[u][2] = A[qi * ld + pj];
+          b[u][3] = A[qi * ld + qj];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (!act[u]) continue;
+          const int pj = __float_as_int(rj[u].z), qj = __float_as_int(rj[u].w);
+          const float t00 = ri.x * b[u][0] - ri.y * b[u][2], t01 = ri.x * b[u][1] - ri.y * b[u][3];
+          const float t10 = ri.y * b[u][0] + ri.x * b[u][2], t11 = ri.y * b[u][1] + ri.x * b[u][3];
+          A[pi_ * ld + pj] = rj[u].x * t00 - rj[u].y * t01;
+          A[pi_ * ld + qj] = rj[u].y * t00 + rj[u].x * t01;
+          A[qi * ld + pj] = rj[u].x * t10 - rj[u].y * t11;
+          A[qi * ld + qj] = rj[u].y * t10 + rj[u].x * t11;
         }
       }
       // V <- V J (this thread: row vx of the column pairs j)
       if (vg < ngv) {
-        for (int j = vg; j < np; j += ngv) {
-          const float4 r = prm[j];
-          if (r.y == 0.f) continue;
-          const int p = __float_as_int(r.z), q = __float_as_int(r.w);
-          const float vp = V[vx * ld + p], vq = V[vx * ld + q];
-          V[vx * ld + p] = r.x * vp - r.y * vq;
-          V[vx * ld + q] = r.y * vp + r.x * vq;
+#pragma unroll
+        for (int u0 = 0; u0 < 8; u0 += 4) {
+          float4 r[4];
+          float vp[4], vq[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = vg + (u0 + u) * ngv;
+            r[u] = j < np ? prm[j] : make_float4(1.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (r[u].y == 0.f) continue;
+            vp[u] = V[vx * ld + __float_as_int(r[u].z)];
+            vq[u] = V[vx * ld + __float_as_int(r[u].w)];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (r[u].y == 0.f) continue;
+            V[vx * ld + __float_as_int(r[u].z)] = r[u].x * vp[u] - r[u].y * vq[u];
+            V[vx * ld + __float_as_int(r[u].w)] = r[u].y * vp[u] + r[u].x * vq[u];
+          }
         }
       }
       __syncthreads();
