@@ -180,13 +180,13 @@ struct Run {
                               (int64_t)l * l, status, false)));
     CK((reduce_splits<double, double>(st, l, l, ns, dbuf(P->off_gpart), GT, 1, l)));
     double* Uhat = dbuf(P->off_uhat);
-    // FP32 Jacobi down to rotations below 1e-5 of sqrt(a_pp a_qq), then FP64
-    // refinement passes, each of which squares the eigenvector error outside
-    // clusters; the cluster threshold of a pass scales with the norm of all
-    // remaining off-diagonal terms, so eigenvalues closer than that are
-    // separated only by a later pass: three passes for the FP32 forms, five
-    // for the FP64 form.
-    CK((sym_eig(st, l, GT, sigma, Uhat, dbuf(P->off_eig), status, sizeof(W) == 8 ? 5 : 3, 1e-5f)));
+    // FP32 start from the tridiagonal reduction, then FP64 refinement
+    // passes, each of which squares the eigenvector error outside clusters;
+    // the cluster threshold of a pass scales with the norm of all remaining
+    // off-diagonal terms, so eigenvalues closer than that are separated only
+    // by a later pass: three passes for the FP32 forms, five for the FP64
+    // form.
+    CK((sym_eig(st, l, GT, sigma, Uhat, dbuf(P->off_eig), status, sizeof(W) == 8 ? 5 : 3)));
     CK((check_finite_vec(st, l, sigma, status)));
     // Alg. 1: lift U = Q Uhat (first k or all l columns), then the sign rule
     const int ku = (P->flags & RPOD_FLAG_RETURN_ALL_L) ? l : k;

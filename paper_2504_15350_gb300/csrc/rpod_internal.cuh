@@ -68,12 +68,19 @@ cudaError_t cholesky(cudaStream_t st, int l, const double* G, double tol, int ro
                      double* X, TW* Xw, int ldxw, unsigned* status, const float* Y = nullptr,
                      int64_t rows = 0, double* part = nullptr, int nsplit = 0);
 
-// Symmetric eigen-decomposition of G (l x l, FP64): FP32 parallel two-sided
-// Jacobi, then FP64 Ogita-Aishima refinement.  Outputs eigenvalues
-// (descending, as sigma = sqrt(max(lambda, 0))) and eigenvectors Uhat (l x l).
+// Symmetric eigen-decomposition of G (l x l, FP64): an FP32 start from the
+// tridiagonal reduction, then FP64 Ogita-Aishima refinement.  Outputs
+// eigenvalues (descending, as sigma = sqrt(max(lambda, 0))) and eigenvectors
+// Uhat (l x l).
 cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma,
-                    double* Uhat, double* work, unsigned* status, int refine_iters,
-                    float jacobi_tol);
+                    double* Uhat, double* work, unsigned* status, int refine_iters);
+
+// FP32 starting eigenvectors X (l x l, FP64, column-major, ascending
+// eigenvalues) of the symmetric G (l x l, FP64, lower triangle read) from
+// one CTA: Householder tridiagonalization, multisection, twisted
+// factorizations.  Writes the number of replaced vectors of multiple
+// eigenvalues to status[4] (diagnostic).
+cudaError_t tridiag_eig32(cudaStream_t st, int l, const double* G, double* X, unsigned* status);
 size_t sym_eig_work_doubles(int l);
 
 // Column-sign convention: per column c < ncols of U (rows n, ld ldu) find the
@@ -112,6 +119,7 @@ cudaError_t gram_f32(cudaStream_t st, int64_t rows, int l, const float* Y, int64
 // stream capture.
 void prepare_kernels();
 void prepare_kernels_tc();
+void prepare_eig_kernels();
 
 // Flags ST_NONFINITE if any of the l values is NaN or Inf.
 cudaError_t check_finite_vec(cudaStream_t st, int l, const double* v, unsigned* status);

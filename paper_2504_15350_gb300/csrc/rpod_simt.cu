@@ -938,170 +938,14 @@ template cudaError_t cholesky<float>(cudaStream_t, int, const double*, double, i
 // the left singular vectors and values of T come from the eigenpairs of its
 // l x l Gram matrix.
 //
-// Stage 1: parallel cyclic two-sided Jacobi in FP32 (round-robin pairing,
-// l/2 disjoint rotations per step, applied as independent 2 x 2 block
-// updates of A and column-pair updates of V).  Stage 2: FP64 iterative refinement of the eigenvectors
-// (Ogita & Aishima, "Iterative refinement for symmetric eigenvalue
-// decomposition", Japan J. Indust. Appl. Math. 35, 2018): with R = I - X^T X
-// and S = X^T A X, lambda_i = S_ii / (1 - R_ii), E_ij = (S_ij + lambda_j
-// R_ij) / (lambda_j - lambda_i) when |lambda_i - lambda_j| > delta, else
-// R_ij / 2, E_ii = R_ii / 2, X <- X + X E; each pass squares the error.
-
-__global__ void __launch_bounds__(1024)
-k_jacobi32(int l, const double* __restrict__ G, double* __restrict__ Vout, int max_sweeps,
-           float tol, unsigned* status) {
-  extern __shared__ float4 smf4[];
-  float* smf = reinterpret_cast<float*>(smf4);
-  const int L = l + (l & 1);
-  const int np = L / 2;
-  const int ld = L + 1;
-  float* A = smf;               // L x L, row stride ld
-  float* V = A + L * ld;        // L x L, row stride ld
-  // rotation of pair i: (c, s, p, q) packed in one float4 (p, q as int
-  // bits), placed by element offset so that its accesses stay shared-memory
-  // accesses
-  float4* prm = smf4 + (2 * L * ld + 3) / 4;
-  __shared__ double red[32];
-  __shared__ int s_rot;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  double dm = 0.0;
-  for (int i = tid; i < l; i += nt) dm = fmax(dm, fabs(G[i + i * l]));
-  dm = block_max(dm, red);
-  const double scale = dm > 0.0 ? 1.0 / dm : 1.0;
-  for (int e0 = 0; e0 < L * L; e0 += nt * 8) {
-    double v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * nt + tid, i = e % L, j = e / L;
-      v[u] = (e < L * L && i < l && j < l) ? G[i + j * l] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * nt + tid, i = e % L, j = e / L;
-      if (e < L * L) {
-        A[i * ld + j] = (float)(v[u] * scale);
-        V[i * ld + j] = (i == j) ? 1.f : 0.f;
-      }
-    }
-  }
-  __syncthreads();
-  // Rotate while |a_pq| exceeds tol * sqrt(a_pp a_qq).  The test is
-  // relative on purpose: an absolute floor would leave pairs of small
-  // eigenvalues unrotated, and the FP64 refinement cannot split such a pair.
-  const float abs_floor = 1e-30f;
-  bool converged = (L < 2);
-  int nsweeps = 0;
-  // Fixed work assignment (no index division inside the rounds): blocks
-  // (bi, j) for j = bg, bg + ngb, ...; V entries (vx, pair j) for j = vg,
-  // vg + ngv, ...; thread pi < np owns the round-robin pair slot pi, whose
-  // two indices advance cyclically through 1..L-1 (slot 0 keeps index 0).
-  const int bi = tid % np, bg = tid / np, ngb = nt / np;
-  const int vx = tid % L, vg = tid / L, ngv = nt / L;
-  int ia = tid == 0 ? 0 : tid, ib = L - 1 - tid;
-  for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
-    ++nsweeps;
-    if (tid == 0) s_rot = 0;
-    __syncthreads();
-    for (int s = 0; s < L - 1; ++s) {
-      if (tid < np) {
-        const int p = min(ia, ib), q = max(ia, ib);
-        float c = 1.f, sv = 0.f;
-        if (q < l) {
-          const float apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
-          if (fabsf(apq) > tol * sqrtf(fabsf(app * aqq)) && fabsf(apq) > abs_floor) {
-            // t = sign(tau) / (|tau| + sqrt(1 + tau^2)), tau = (a_qq - a_pp) / (2 a_pq)
-            const float tau = __fdividef(aqq - app, 2.f * apq);
-            const float at = fabsf(tau);
-            const float den = at < 1e18f ? at + sqrtf(fmaf(at, at, 1.f)) : 2.f * at;
-            const float t = copysignf(__frcp_rn(den), tau);
-            c = rsqrtf(fmaf(t, t, 1.f));
-            sv = t * c;
-            s_rot = 1;
-          }
-        }
-        prm[tid] = make_float4(c, sv, __int_as_float(p), __int_as_float(q));
-        if (tid > 0) ia = (ia == L - 1) ? 1 : ia + 1;
-        ib = (ib == L - 1) ? 1 : ib + 1;
-      }
-      __syncthreads();
-      // A <- J^T A J one 2 x 2 block at a time: block (i, j) holds rows
-      // (p_i, q_i) and columns (p_j, q_j); rotate its rows by pair i and its
-      // columns by pair j.  Blocks are disjoint, so one barrier suffices.
-      // (np <= 64 and nt = 1024, so a thread owns at most 4 blocks and 8 V
-      // pairs; all their loads are issued before any store)
-      if (bg < ngb) {
-        const float4 ri = prm[bi];
-        const int pi_ = __float_as_int(ri.z), qi = __float_as_int(ri.w);
-        float4 rj[4];
-        float b[4][4];
-        bool act[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int j = bg + u * ngb;
-          act[u] = j < np;
-          rj[u] = act[u] ? prm[j] : make_float4(1.f, 0.f, 0.f, 0.f);
-          act[u] = act[u] && (ri.y != 0.f || rj[u].y != 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (!act[u]) continue;
-          const int pj = __float_as_int(rj[u].z), qj = __float_as_int(rj[u].w);
-          b[u][0] = A[pi_ * ld + pj];
-          b[u][1] = A[pi_ * ld + qj];
-          b[u][2] = A[qi * ld + pj];
-          b[u][3] = A[qi * ld + qj];
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (!act[u]) continue;
-          const int pj = __float_as_int(rj[u].z), qj = __float_as_int(rj[u].w);
-          const float t00 = ri.x * b[u][0] - ri.y * b[u][2], t01 = ri.x * b[u][1] - ri.y * b[u][3];
-          const float t10 = ri.y * b[u][0] + ri.x * b[u][2], t11 = ri.y * b[u][1] + ri.x * b[u][3];
-          A[pi_ * ld + pj] = rj[u].x * t00 - rj[u].y * t01;
-          A[pi_ * ld + qj] = rj[u].y * t00 + rj[u].x * t01;
-          A[qi * ld + pj] = rj[u].x * t10 - rj[u].y * t11;
-          A[qi * ld + qj] = rj[u].y * t10 + rj[u].x * t11;
-        }
-      }
-      // V <- V J (this thread: row vx of the column pairs j)
-      if (vg < ngv) {
-#pragma unroll
-        for (int u0 = 0; u0 < 8; u0 += 4) {
-          float4 r[4];
-          float vp[4], vq[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int j = vg + (u0 + u) * ngv;
-            r[u] = j < np ? prm[j] : make_float4(1.f, 0.f, 0.f, 0.f);
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (r[u].y == 0.f) continue;
-            vp[u] = V[vx * ld + __float_as_int(r[u].z)];
-            vq[u] = V[vx * ld + __float_as_int(r[u].w)];
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (r[u].y == 0.f) continue;
-            V[vx * ld + __float_as_int(r[u].z)] = r[u].x * vp[u] - r[u].y * vq[u];
-            V[vx * ld + __float_as_int(r[u].w)] = r[u].y * vp[u] + r[u].x * vq[u];
-          }
-        }
-      }
-      __syncthreads();
-    }
-    converged = (s_rot == 0);
-    __syncthreads();
-  }
-  if (tid == 0) {
-    if (!converged) atomicOr(status, ST_NO_CONV);
-    status[4] = (unsigned)nsweeps;  // diagnostic word at byte 16 of the status block
-  }
-  for (int e = tid; e < l * l; e += nt) {
-    const int i = e % l, j = e / l;
-    Vout[e] = (double)V[i * ld + j];
-  }
-}
+// Stage 1: an FP32 starting basis from the tridiagonal reduction of the
+// Gram matrix (tridiag_eig32, rpod_eig.cu).  Stage 2: FP64 iterative
+// refinement of the eigenvectors (Ogita & Aishima, "Iterative refinement
+// for symmetric eigenvalue decomposition", Japan J. Indust. Appl. Math. 35,
+// 2018): with R = I - X^T X and S = X^T A X, lambda_i = S_ii / (1 - R_ii),
+// E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i) when
+// |lambda_i - lambda_j| > delta, else R_ij / 2, E_ii = R_ii / 2,
+// X <- X + X E; each pass squares the error.
 
 __global__ void k_add_inplace(int64_t n, double* __restrict__ X, const double* __restrict__ D) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1220,7 +1064,7 @@ size_t sym_eig_work_doubles(int l) {
 }
 
 cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma, double* Uhat,
-                    double* work, unsigned* status, int refine_iters, float jacobi_tol) {
+                    double* work, unsigned* status, int refine_iters) {
   const size_t ll = (size_t)l * l;
   double* X = work;
   double* XtX = X + ll;
@@ -1231,11 +1075,8 @@ cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma, doub
   double* part = XE + ll;  // 8 * ll
   double* lam = part + 8 * ll;
   double* normA = lam + l;
-  const int L = l + (l & 1);
-  const size_t smj = (size_t)2 * L * (L + 1) * sizeof(float) + 16 + (size_t)(L / 2) * sizeof(float4);
   prepare_kernels();
-  k_jacobi32<<<1, 1024, smj, st>>>(l, G, X, 20, jacobi_tol, status); note_launch();
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = tridiag_eig32(st, l, G, X, status);
   if (e != cudaSuccess) return e;
   k_frob<<<1, 256, 0, st>>>((int64_t)ll, G, normA); note_launch();
   // normA is needed on the device only: pass through a tiny kernel chain
@@ -1656,7 +1497,7 @@ void prepare_kernels() {
     const int big = 160 * 1024;
     cudaFuncSetAttribute(k_cholesky<double, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_cholesky64_gated<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    prepare_eig_kernels();
     cudaFuncSetAttribute(k_cholesky_blk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlkSmem);
     cudaFuncSetAttribute(k_cholesky_blk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlkSmem);
   });
