@@ -11,22 +11,33 @@
 //   2. Eigenvalues of the tridiagonal T by multisection on Sturm counts
 //      (the number of negative pivots of the LDL^T factorization of T - x I
 //      is the number of eigenvalues below x), 8 points per step and per
-//      eigenvalue, stopped at a relative width of two ulps.
+//      eigenvalue, stopped at a relative width of two ulps.  The counts use
+//      IEEE infinities in place of a pivot threshold (a zero pivot gives an
+//      infinite next pivot, counted by its sign bit), with e_k^2 kept at or
+//      above the smallest normal number so that no 0/0 arises.
 //   3. Eigenvectors of T from twisted factorizations (Dhillon and Parlett,
 //      "Multiple representations to compute orthogonal eigenvectors of
 //      symmetric tridiagonal matrices", Lin. Alg. Appl. 387, 2004): with the
 //      forward pivots D+ and backward pivots D- of T - lambda I, the twist
 //      index r minimising |gamma_r|, gamma_r = D+_r - e_r^2 / D-_{r+1},
-//      gives the vector with x_r = 1 by two one-term recurrences; one
-//      Rayleigh-quotient correction lambda += gamma_r / ||x||^2 and a second
-//      factorization follow.
-//   4. Vectors of eigenvalues closer than 1e-4 ||T|| are orthogonalised
-//      against each other (modified Gram-Schmidt in ascending order); a
+//      gives the vector with x_r = 1 by two one-term recurrences.  Two
+//      threads per eigenvalue: one runs the forward recurrences, one the
+//      backward ones.
+//   4. Vectors of eigenvalues closer than 1e-5 ||T|| are orthogonalised
+//      against each other (Gram-Schmidt in ascending order); a
 //      vector that loses more than half its norm there (a multiple
 //      eigenvalue) is replaced by a pseudo-random vector orthogonalised
-//      against all others.
+//      against all others.  Vectors of eigenvalues further apart come out
+//      of step 3 orthogonal to a few 1e-5 at most, which the refinement
+//      removes.
 //   5. Back-transformation X = H Z, column by column, each column held in
 //      the registers of 8 threads.
+//
+// Step 1 keeps the rows of A as float4 (four consecutive rows per warp, the
+// reduced rows replaced by the full reflector vectors, zeros included), so
+// that the matrix-vector product, the rank-2 update and the
+// back-transformation run on 16-byte shared-memory accesses without
+// per-element bounds tests.
 //
 // The FP64 refinement that follows squares the error of this start per
 // pass; its accuracy, not this one's, sets the final result.
@@ -39,16 +50,16 @@ namespace rpod {
 namespace {
 
 constexpr int kEigThreads = 1024;
-constexpr int kGrp = 8;                    // threads per eigenvalue / per column
-constexpr int kRowsPerThread = kMaxL / kGrp;
+constexpr int kGrp = 8;  // threads per eigenvalue (multisection) and per column (back-transform)
 
-__host__ __device__ inline int eig_lda(int l) { return (l & 1) ? l : l + 1; }
-// Smallest leading dimension >= l that is 4 mod 32: the back-transform's
-// 8 rows x 4 columns per warp then fall in 32 distinct banks.
-__host__ __device__ inline int eig_ldx(int l) { return ((l + 27) / 32) * 32 + 4; }
+// Rows of A start on 16-byte boundaries; Xs/Ws use a leading dimension of
+// 1 mod 32, so that a column, a row and the back-transform's 4 columns x 8
+// row groups each fall in distinct banks.
+__host__ __device__ inline int eig_lda(int l) { return (l + 3) & ~3; }
+__host__ __device__ inline int eig_ldx(int l) { return ((l + 31) & ~31) + 1; }
 
 size_t eig_smem_bytes(int l) {
-  return sizeof(float) * ((size_t)l * eig_lda(l) + 2 * (size_t)l * eig_ldx(l) + 8 * (size_t)kMaxL);
+  return sizeof(float) * ((size_t)l * eig_lda(l) + 12 * (size_t)kMaxL + 2 * (size_t)l * eig_ldx(l));
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -57,32 +68,83 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+__device__ __forceinline__ float pick(const float4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+__device__ __forceinline__ float dot4(const float4& a, const float4& b) {
+  return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+}
+
 __device__ __forceinline__ uint32_t mix32(uint32_t x) {
   x ^= x >> 16; x *= 0x7feb352du; x ^= x >> 15; x *= 0x846ca68bu; x ^= x >> 16;
   return x;
+}
+
+// Householder reflector of step j from row j (x: this lane's columns
+// 4 lane .. 4 lane + 3), called by all 32 lanes of one warp.  Writes the full
+// vector v (zeros up to column j, 1 at j + 1) to row j of A and to vbuf,
+// tau_j, d_j and e_j, and clears the two entries of the step's p buffer
+// that the step before last left behind.
+__device__ __forceinline__ void reflector(int j, int lda, const float4& x, int lane, float* rowj,
+                                          float* vbuf, float* pbuf, float* tau, float* dd,
+                                          float* ee) {
+  const int c0 = 4 * lane;
+  float s2 = 0.f;
+  s2 = c0 + 0 > j + 1 ? fmaf(x.x, x.x, s2) : s2;
+  s2 = c0 + 1 > j + 1 ? fmaf(x.y, x.y, s2) : s2;
+  s2 = c0 + 2 > j + 1 ? fmaf(x.z, x.z, s2) : s2;
+  s2 = c0 + 3 > j + 1 ? fmaf(x.w, x.w, s2) : s2;
+  s2 = warp_sum(s2);
+  const float alpha = __shfl_sync(0xffffffffu, pick(x, (j + 1) & 3), (j + 1) >> 2);
+  const float djj = __shfl_sync(0xffffffffu, pick(x, j & 3), j >> 2);
+  float t = 0.f, scv = 0.f, beta = alpha;
+  if (s2 > 0.f) {
+    beta = -copysignf(sqrtf(fmaf(alpha, alpha, s2)), alpha);
+    t = (beta - alpha) / beta;
+    scv = 1.f / (alpha - beta);
+  }
+  float4 v;
+  v.x = c0 + 0 == j + 1 ? 1.f : (c0 + 0 > j + 1 ? x.x * scv : 0.f);
+  v.y = c0 + 1 == j + 1 ? 1.f : (c0 + 1 > j + 1 ? x.y * scv : 0.f);
+  v.z = c0 + 2 == j + 1 ? 1.f : (c0 + 2 > j + 1 ? x.z * scv : 0.f);
+  v.w = c0 + 3 == j + 1 ? 1.f : (c0 + 3 > j + 1 ? x.w * scv : 0.f);
+  if (c0 < lda) {
+    *reinterpret_cast<float4*>(rowj + c0) = v;
+    *reinterpret_cast<float4*>(vbuf + c0) = v;
+  }
+  if (lane == 0) {
+    tau[j] = t;
+    dd[j] = djj;
+    ee[j] = beta;
+    pbuf[j] = 0.f;
+    if (j > 0) pbuf[j - 1] = 0.f;
+  }
 }
 
 __global__ void __launch_bounds__(kEigThreads)
 k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
                 unsigned* __restrict__ status) {
   extern __shared__ float4 sm4[];
-  float* const A = reinterpret_cast<float*>(sm4);
   const int lda = eig_lda(l), ldx = eig_ldx(l);
-  float* const Xs = A + (size_t)l * lda;   // eigenvectors of T, row r at r*ldx
-  float* const Ws = Xs + (size_t)l * ldx;  // per-eigenvalue forward pivots
-  float* const vs = Ws + (size_t)l * ldx;  // Householder vector, double-buffered
-  float* const ps = vs + 2 * kMaxL;
-  float* const dd = ps + kMaxL;            // diagonal of T
-  float* const ee = dd + kMaxL;            // off-diagonal of T
-  float* const e2 = ee + kMaxL;
-  float* const tau = e2 + kMaxL;
+  float* const A = reinterpret_cast<float*>(sm4);  // l x lda
+  float* const vs = A + (size_t)l * lda;           // [2][kMaxL] reflector vectors
+  float* const psb = vs + 2 * kMaxL;               // [2][kMaxL] p = tau A22 v
+  float2* const de = reinterpret_cast<float2*>(psb + 2 * kMaxL);  // (d_k, e_{k-1}^2)
+  float* const dd = psb + 4 * kMaxL;               // diagonal of T
+  float* const ee = dd + kMaxL;                    // off-diagonal of T
+  float* const tau = ee + kMaxL;
   float* const lam = tau + kMaxL;
+  float* const Xs = lam + kMaxL;                   // eigenvectors of T: row r at r*ldx
+  float* const Ws = Xs + (size_t)l * ldx;          // forward pivots per eigenvalue
   __shared__ double s_red[32];
   __shared__ float s_bnd[3];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
   const float pivmin = 1e-30f;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
 
-  // ---- 1. A = G / max_i G_ii (FP32, both triangles from G's lower one)
+  // ---- 1. A = G / max_i G_ii (FP32, zero padding columns); p buffers
+  // cleared
   double dm = 0.0;
   for (int i = tid; i < l; i += nt) dm = fmax(dm, fabs(G[i + (size_t)i * l]));
 #pragma unroll
@@ -97,91 +159,118 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
   }
   __syncthreads();
   dm = s_red[0];
-  const double sc = dm > 0.0 ? 1.0 / dm : 1.0;
-  for (int e = tid; e < l * l; e += nt) {
-    const int i = e / l, j = e - i * l;
-    const int a = max(i, j), b = min(i, j);
-    A[i * lda + j] = (float)(G[a + (size_t)b * l] * sc);
+  // entries of a Gram matrix are bounded by its largest diagonal entry;
+  // when that is above 1e-30 the FP32 conversion before scaling loses nothing
+  const bool f32scale = dm > 1e-30;
+  const double scd = dm > 0.0 ? 1.0 / dm : 1.0;
+  const float scf = (float)scd;
+  // row i of A from column i of the symmetric G (coalesced); warp w holds
+  // rows w + 32u, eight loads of a thread in flight before their stores
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    double g[8];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = warp + 32 * (2 * h + u), j = lane + 32 * q;
+        g[4 * u + q] = (i < l && j < l) ? G[j + (size_t)i * l] : 0.0;
+      }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = warp + 32 * (2 * h + u), j = lane + 32 * q;
+        if (i < l && j < lda)
+          A[i * lda + j] = f32scale ? (float)g[4 * u + q] * scf : (float)(g[4 * u + q] * scd);
+      }
   }
+  for (int e = tid; e < 2 * kMaxL; e += nt) psb[e] = 0.f;
   __syncthreads();
 
-  // ---- 2. Householder tridiagonalization.  Row r of the trailing matrix
-  // belongs to warp r % 32 (matrix-vector product and rank-2 update);
-  // step j's reflector comes from row j (= column j) and is kept in row j,
-  // columns j+2..l-1 (v_j(j+1) = 1 is implicit).
+  // ---- 2. Householder tridiagonalization.  Warp w owns rows 4w..4w+3 of
+  // the trailing matrix; lane q holds columns 4q..4q+3 of a row.  Step j:
+  // p = tau A22 v on the owned rows, then A22 -= v w^T + w v^T with
+  // w = p - (tau/2)(p.v) v; the owner of row j+1 forms the next reflector
+  // from the updated row while it is still in registers.  Columns up to j
+  // of v and p are zero, so whole rows are processed.
+  const int c0 = 4 * lane;
+  const bool lact = c0 < lda;
+  if (l >= 2 && warp == 0) {
+    const float4 x = lact ? *reinterpret_cast<const float4*>(A + c0) : z4;
+    reflector(0, lda, x, lane, A, vs, psb, tau, dd, ee);
+  }
   for (int j = 0; j + 1 < l; ++j) {
-    const int m = l - 1 - j;
-    float* const v = vs + (j & 1) * kMaxL;
-    float* const Aj = A + j * lda + j + 1;
-    if (warp == (j & 31)) {
-      float s2 = 0.f;
-      for (int k = 1 + lane; k < m; k += 32) s2 = fmaf(Aj[k], Aj[k], s2);
-      s2 = warp_sum(s2);
-      const float alpha = Aj[0];
-      float t = 0.f, scv = 0.f, beta = alpha;
-      if (s2 > 0.f) {
-        beta = -copysignf(sqrtf(fmaf(alpha, alpha, s2)), alpha);
-        t = (beta - alpha) / beta;
-        scv = 1.f / (alpha - beta);
-      }
-      for (int k = lane; k < m; k += 32) {
-        const float vk = k == 0 ? 1.f : Aj[k] * scv;
-        v[k] = vk;
-        if (k) Aj[k] = vk;
-      }
-      if (lane == 0) {
-        tau[j] = t;
-        dd[j] = A[j * lda + j];
-        ee[j] = beta;
-      }
-    }
     __syncthreads();
     const float t = tau[j];
-    if (t == 0.f) continue;
-    const int r0 = j + 1 + ((warp - (j + 1)) & 31);  // first row of this warp
-    float s[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int r = r0 + 32 * u;
-      s[u] = 0.f;
-      if (r < l) {
-        const float* Ar = A + r * lda + j + 1;
-        for (int k = lane; k < m; k += 32) s[u] = fmaf(Ar[k], v[k], s[u]);
+    const int nxt = j + 1;
+    const bool mk_next = nxt + 1 < l && warp == (nxt >> 2);
+    if (t == 0.f) {
+      if (mk_next) {
+        const float4 x = lact ? *reinterpret_cast<const float4*>(A + nxt * lda + c0) : z4;
+        reflector(nxt, lda, x, lane, A + nxt * lda, vs + (nxt & 1) * kMaxL,
+                  psb + (nxt & 1) * kMaxL, tau, dd, ee);
       }
+      continue;
     }
+    const float* const v = vs + (j & 1) * kMaxL;
+    float* const ps = psb + (j & 1) * kMaxL;
+    const int rb = 4 * warp;
+    const bool owns = rb + 3 >= j + 1 && rb < l;
+    float4 v4 = z4, rw[4];
+    if (owns) {
+      v4 = lact ? *reinterpret_cast<const float4*>(v + c0) : z4;
+      float s[4];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int u = 0; u < 4; ++u) s[u] += __shfl_xor_sync(0xffffffffu, s[u], o);
-    if (lane == 0) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (r0 + 32 * u < l) ps[r0 + 32 * u - j - 1] = t * s[u];
+      for (int u = 0; u < 4; ++u) {
+        const int r = rb + u;
+        rw[u] = (r >= j + 1 && r < l && lact) ? *reinterpret_cast<const float4*>(A + r * lda + c0) : z4;
+        s[u] = dot4(rw[u], v4);
+      }
+      // four row sums at once: lanes 8u..8u+7 end with the sum of row rb+u
+      const bool hi16 = lane & 16, hi8 = lane & 8;
+      float k0 = hi16 ? s[2] : s[0], k1 = hi16 ? s[3] : s[1];
+      k0 += __shfl_xor_sync(0xffffffffu, hi16 ? s[0] : s[2], 16);
+      k1 += __shfl_xor_sync(0xffffffffu, hi16 ? s[1] : s[3], 16);
+      float k = hi8 ? k1 : k0;
+      k += __shfl_xor_sync(0xffffffffu, hi8 ? k0 : k1, 8);
+      k += __shfl_xor_sync(0xffffffffu, k, 4);
+      k += __shfl_xor_sync(0xffffffffu, k, 2);
+      k += __shfl_xor_sync(0xffffffffu, k, 1);
+      const int r = rb + (lane >> 3);
+      if ((lane & 7) == 0 && r >= j + 1 && r < l) ps[r] = t * k;
     }
     __syncthreads();
-    // w = p - (t/2)(p.v) v; A22 -= v w^T + w v^T on this warp's rows
-    float pv = 0.f;
-    for (int k = lane; k < m; k += 32) pv = fmaf(ps[k], v[k], pv);
-    const float K = -0.5f * t * warp_sum(pv);
+    if (owns) {
+      const float4 p4 = lact ? *reinterpret_cast<const float4*>(ps + c0) : z4;
+      const float K = -0.5f * t * warp_sum(dot4(p4, v4));
+      float4 w4;
+      w4.x = fmaf(K, v4.x, p4.x); w4.y = fmaf(K, v4.y, p4.y);
+      w4.z = fmaf(K, v4.z, p4.z); w4.w = fmaf(K, v4.w, p4.w);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int r = r0 + 32 * u;
-      if (r >= l) break;
-      const int i = r - j - 1;
-      const float vi = v[i], wi = fmaf(K, vi, ps[i]);
-      float* Ar = A + r * lda + j + 1;
-      for (int k = lane; k < m; k += 32) {
-        const float vk = v[k];
-        const float wk = fmaf(K, vk, ps[k]);
-        Ar[k] = fmaf(-wi, vk, fmaf(-vi, wk, Ar[k]));
+      for (int u = 0; u < 4; ++u) {
+        const int r = rb + u;
+        if (r < j + 1 || r >= l) continue;
+        const float vr = v[r], wr = fmaf(K, vr, ps[r]);
+        float4 a = rw[u];
+        a.x = fmaf(-wr, v4.x, fmaf(-vr, w4.x, a.x));
+        a.y = fmaf(-wr, v4.y, fmaf(-vr, w4.y, a.y));
+        a.z = fmaf(-wr, v4.z, fmaf(-vr, w4.z, a.z));
+        a.w = fmaf(-wr, v4.w, fmaf(-vr, w4.w, a.w));
+        if (lact) *reinterpret_cast<float4*>(A + r * lda + c0) = a;
+        if (r == nxt && mk_next)
+          reflector(nxt, lda, a, lane, A + nxt * lda, vs + (nxt & 1) * kMaxL,
+                    psb + (nxt & 1) * kMaxL, tau, dd, ee);
       }
     }
   }
+  __syncthreads();
   if (tid == 0) dd[l - 1] = A[(l - 1) * lda + l - 1];
   __syncthreads();
 
   // ---- 3. eigenvalues of T (ascending) by multisection
-  for (int k = tid; k + 1 < l; k += nt) e2[k] = ee[k] * ee[k];
+  for (int k = tid; k < l; k += nt)
+    de[k] = make_float2(dd[k], k > 0 ? fmaxf(ee[k - 1] * ee[k - 1], FLT_MIN) : 0.f);
   if (warp == 0) {
     float lo = FLT_MAX, hi = -FLT_MAX;
     for (int k = lane; k < l; k += 32) {
@@ -195,7 +284,8 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
       hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
     const float bn = fmaxf(fabsf(lo), fabsf(hi));
-    const float pad = 4.f * FLT_EPSILON * bn * (float)l + pivmin;
+    // (the e_k^2 floor moves eigenvalues by less than 1e-18)
+    const float pad = 4.f * FLT_EPSILON * bn * (float)l + 1e-18f;
     if (lane == 0) { s_bnd[0] = lo - pad; s_bnd[1] = hi + pad; s_bnd[2] = bn; }
   }
   __syncthreads();
@@ -209,15 +299,16 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
         if (hi - lo <= fmaf(2.4e-7f, fmaxf(fabsf(lo), fabsf(hi)), atol)) break;
         const float h = (hi - lo) * (1.f / 9.f);
         const float x = fmaf(h, (float)(t8 + 1), lo);
-        float q = dd[0] - x;
-        if (fabsf(q) < pivmin) q = -pivmin;
-        int c = q < 0.f;
+        // number of negative pivots of T - x I = eigenvalues below x
+        float q = de[0].x - x;
+        unsigned c = __float_as_uint(q) >> 31;
+#pragma unroll 4
         for (int k = 1; k < l; ++k) {
-          q = (dd[k] - x) - __fdividef(e2[k - 1], q);
-          if (fabsf(q) < pivmin) q = -pivmin;
-          c += q < 0.f;
+          const float2 p = de[k];
+          q = fmaf(-p.y, __fdividef(1.f, q), p.x - x);
+          c += __float_as_uint(q) >> 31;
         }
-        const unsigned bits = (__ballot_sync(gmask, c > g) >> (lane & 24)) & 0xFFu;
+        const unsigned bits = (__ballot_sync(gmask, c > (unsigned)g) >> (lane & 24)) & 0xFFu;
         const int tt = bits ? __ffs(bits) - 1 : kGrp;
         const float nlo = tt == 0 ? lo : fmaf(h, (float)tt, lo);
         const float nhi = tt == kGrp ? hi : fmaf(h, (float)(tt + 1), lo);
@@ -229,167 +320,223 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
   }
   __syncthreads();
 
-  // ---- 4. eigenvectors of T by twisted factorizations (thread i: lambda_i)
-  if (tid < l) {
-    float lm = lam[tid];
-    float* const Dp = Ws + tid;
-    float* const Xc = Xs + tid;
-    for (int pass = 0; pass < 2; ++pass) {
-      float q = dd[0] - lm;
-      if (fabsf(q) < pivmin) q = -pivmin;
-      Dp[0] = q;
-      for (int k = 1; k < l; ++k) {
-        q = (dd[k] - lm) - __fdividef(e2[k - 1], q);
+  // ---- 4. eigenvectors of T by twisted factorizations: threads 2i (forward
+  // pivots D+, into Ws) and 2i+1 (backward pivots D-, into Xs) for lambda_i
+  {
+    const int i = tid >> 1;
+    const bool fwd = !(tid & 1);
+    if (i < l) {
+      const float lm = lam[i];
+      float* const Dp = Ws + i;
+      float* const Xc = Xs + i;
+      if (fwd) {
+        float q = dd[0] - lm;
         if (fabsf(q) < pivmin) q = -pivmin;
-        Dp[k * ldx] = q;
+        Dp[0] = q;
+        for (int k = 1; k < l; ++k) {
+          q = (dd[k] - lm) - __fdividef(de[k].y, q);
+          if (fabsf(q) < pivmin) q = -pivmin;
+          Dp[k * ldx] = q;
+        }
+      } else {
+        float q = dd[l - 1] - lm;
+        if (fabsf(q) < pivmin) q = -pivmin;
+        Xc[(l - 1) * ldx] = q;
+        for (int k = l - 2; k >= 0; --k) {
+          q = (dd[k] - lm) - __fdividef(de[k + 1].y, q);
+          if (fabsf(q) < pivmin) q = -pivmin;
+          Xc[k * ldx] = q;
+        }
       }
-      // backward pivots D-_k (kept in the vector's column until overwritten)
-      float qm = dd[l - 1] - lm;
-      if (fabsf(qm) < pivmin) qm = -pivmin;
-      Xc[(l - 1) * ldx] = qm;
-      float gb = q;  // gamma_{l-1} = D+_{l-1}
-      int r = l - 1;
-      for (int k = l - 2; k >= 0; --k) {
-        const float bm = __fdividef(e2[k], qm);
-        const float gk = Dp[k * ldx] - bm;
-        if (fabsf(gk) <= fabsf(gb)) { gb = gk; r = k; }
-        qm = (dd[k] - lm) - bm;
-        if (fabsf(qm) < pivmin) qm = -pivmin;
-        Xc[k * ldx] = qm;
+      __syncwarp(3u << (lane & 30));
+      // twist index: gamma_k = D+_k - e_k^2 / D-_{k+1} (gamma_{l-1} = D+_{l-1});
+      // the forward thread scans k < l/2, the backward one the rest
+      const int h = l >> 1;
+      float gb = FLT_MAX;
+      int r = l;
+      for (int k = fwd ? 0 : h; k < (fwd ? h : l); ++k) {
+        const float gk = k + 1 < l ? Dp[k * ldx] - __fdividef(de[k + 1].y, Xc[(k + 1) * ldx])
+                                   : Dp[k * ldx];
+        if (fabsf(gk) < gb) { gb = fabsf(gk); r = k; }
       }
-      float xv = 1.f, n2 = 1.f;
-      Xc[r * ldx] = 1.f;
-      for (int k = r - 1; k >= 0; --k) {
-        xv = -__fdividef(ee[k], Dp[k * ldx]) * xv;
-        Xc[k * ldx] = xv;
-        n2 = fmaf(xv, xv, n2);
-      }
-      xv = 1.f;
-      for (int k = r; k + 1 < l; ++k) {
-        xv = -__fdividef(ee[k], Xc[(k + 1) * ldx]) * xv;
-        Xc[(k + 1) * ldx] = xv;
-        n2 = fmaf(xv, xv, n2);
-      }
-      if (!(n2 <= FLT_MAX)) {  // overflow: fall back to e_r (the cluster pass may replace it)
-        for (int k = 0; k < l; ++k) Xc[k * ldx] = k == r ? 1.f : 0.f;
+      const unsigned pmask = 3u << (lane & 30);
+      const float gbo = __shfl_xor_sync(pmask, gb, 1);
+      const int ro = __shfl_xor_sync(pmask, r, 1);
+      if (gbo < gb || (gbo == gb && ro < r)) r = ro;
+      if (r >= l) r = 0;  // every gamma non-finite: any twist index will do
+      __syncwarp(pmask);
+      float xv = 1.f, n2 = 0.f;
+      if (fwd) {
+        Xc[r * ldx] = 1.f;
         n2 = 1.f;
+        for (int k = r - 1; k >= 0; --k) {
+          xv = -__fdividef(ee[k], Dp[k * ldx]) * xv;
+          Xc[k * ldx] = xv;
+          n2 = fmaf(xv, xv, n2);
+        }
+      } else {
+        for (int k = r; k + 1 < l; ++k) {
+          xv = -__fdividef(ee[k], Xc[(k + 1) * ldx]) * xv;
+          Xc[(k + 1) * ldx] = xv;
+          n2 = fmaf(xv, xv, n2);
+        }
       }
-      if (pass == 0) {
-        lm += gb / n2;
+      n2 += __shfl_xor_sync(pmask, n2, 1);
+      __syncwarp(pmask);
+      if (!(n2 <= FLT_MAX)) {  // overflow: e_r instead (the cluster pass may replace it)
+        for (int k = fwd ? 0 : 1; k < l; k += 2) Xc[k * ldx] = k == r ? 1.f : 0.f;
       } else {
         const float s = rsqrtf(n2);
-        for (int k = 0; k < l; ++k) Xc[k * ldx] *= s;
+        if (fwd) {
+          for (int k = 0; k <= r; ++k) Xc[k * ldx] *= s;
+        } else {
+          for (int k = r + 1; k < l; ++k) Xc[k * ldx] *= s;
+        }
       }
     }
   }
   __syncthreads();
 
-  // ---- 5. orthogonalise vectors of close eigenvalues (warp 0)
-  if (warp == 0) {
-    const float ctol = 1e-4f * fmaxf(fabsf(lam[0]), fabsf(lam[l - 1]));
+  // ---- 5. orthogonalise vectors of close eigenvalues.  Per vector a of a
+  // cluster, two classical Gram-Schmidt passes against the cluster's
+  // earlier (already orthonormal) vectors: the dots by one warp each, the
+  // update by 16 threads per row.  A vector that loses more than half its
+  // norm (a multiple eigenvalue) is replaced by a pseudo-random vector
+  // that warp 0 orthogonalises against all others by modified Gram-Schmidt
+  // (the cluster's later vectors may still coincide, which classical
+  // Gram-Schmidt would subtract twice).  The forward-pivot array is free
+  // again and holds the dot products.
+  {
+    float* const dts = Ws;
+    __shared__ float s_n2;
+    // eigenvalues closer than 1e-15 are one cluster even in a (near) zero matrix
+    const float ctol = fmaxf(1e-5f * fmaxf(fabsf(lam[0]), fabsf(lam[l - 1])), 1e-15f);
+    const int part = tid & 15, rsub = tid >> 4;
+    const unsigned hmask = 0xFFFFu << (lane & 16);
     int start = 0, nrep = 0;
     for (int i = 1; i <= l; ++i) {
       if (i < l && lam[i] - lam[i - 1] <= ctol) continue;
       for (int a = start + 1; a < i; ++a) {
-        float xa[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int r = lane + 32 * u;
-          xa[u] = r < l ? Xs[r * ldx + a] : 0.f;
-        }
-        for (int b = start; b < a; ++b) {
-          float xb[4], dt = 0.f;
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int r = lane + 32 * u;
-            xb[u] = r < l ? Xs[r * ldx + b] : 0.f;
-            dt = fmaf(xa[u], xb[u], dt);
+        for (int pass = 0; pass < 2; ++pass) {
+          for (int b = start + warp; b < a; b += nt >> 5) {
+            float dt = 0.f;
+            for (int r = lane; r < l; r += 32) dt = fmaf(Xs[r * ldx + b], Xs[r * ldx + a], dt);
+            dt = warp_sum(dt);
+            if (lane == 0) dts[b] = dt;
           }
-          dt = warp_sum(dt);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) xa[u] = fmaf(-dt, xb[u], xa[u]);
-        }
-        float n2 = 0.f;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) n2 = fmaf(xa[u], xa[u], n2);
-        n2 = warp_sum(n2);
-        if (n2 < 0.25f) {
-          // a multiple eigenvalue: a pseudo-random vector orthogonal to all others
-          ++nrep;
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int r = lane + 32 * u;
-            const uint32_t h = mix32((uint32_t)(a * 131 + r) * 2654435761u + 12345u);
-            xa[u] = r < l ? (float)(h >> 8) * (1.f / 8388608.f) - 1.f : 0.f;
+          __syncthreads();
+          for (int r0 = 0; r0 < l; r0 += nt >> 4) {
+            const int r = r0 + rsub;
+            float acc = 0.f;
+            if (r < l)
+              for (int b = start + part; b < a; b += 16) acc = fmaf(dts[b], Xs[r * ldx + b], acc);
+            acc += __shfl_xor_sync(hmask, acc, 1);
+            acc += __shfl_xor_sync(hmask, acc, 2);
+            acc += __shfl_xor_sync(hmask, acc, 4);
+            acc += __shfl_xor_sync(hmask, acc, 8);
+            if (r < l && part == 0) Xs[r * ldx + a] -= acc;
           }
-          for (int rep = 0; rep < 2; ++rep)
-            for (int b = 0; b < l; ++b) {
-              if (b == a) continue;
-              float xb[4], dt = 0.f;
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const int r = lane + 32 * u;
-                xb[u] = r < l ? Xs[r * ldx + b] : 0.f;
-                dt = fmaf(xa[u], xb[u], dt);
-              }
-              dt = warp_sum(dt);
-#pragma unroll
-              for (int u = 0; u < 4; ++u) xa[u] = fmaf(-dt, xb[u], xa[u]);
-            }
-          n2 = 0.f;
-#pragma unroll
-          for (int u = 0; u < 4; ++u) n2 = fmaf(xa[u], xa[u], n2);
+          __syncthreads();
+        }
+        if (warp == 0) {
+          float n2 = 0.f;
+          for (int r = lane; r < l; r += 32) n2 = fmaf(Xs[r * ldx + a], Xs[r * ldx + a], n2);
           n2 = warp_sum(n2);
-        }
-        const float s = n2 > 0.f ? rsqrtf(n2) : 0.f;
+          if (n2 < 0.25f) {
+            ++nrep;
+            float xa[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int r = lane + 32 * u;
-          if (r < l) Xs[r * ldx + a] = xa[u] * s;
+            for (int u = 0; u < 4; ++u) {
+              const int r = lane + 32 * u;
+              const uint32_t hsh = mix32((uint32_t)(a * 131 + r) * 2654435761u + 12345u);
+              xa[u] = r < l ? (float)(hsh >> 8) * (1.f / 8388608.f) - 1.f : 0.f;
+            }
+            for (int rep = 0; rep < 2; ++rep)
+              for (int b = 0; b < l; ++b) {
+                if (b == a) continue;
+                float xb[4], dt = 0.f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  const int r = lane + 32 * u;
+                  xb[u] = r < l ? Xs[r * ldx + b] : 0.f;
+                  dt = fmaf(xa[u], xb[u], dt);
+                }
+                dt = warp_sum(dt);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) xa[u] = fmaf(-dt, xb[u], xa[u]);
+              }
+            n2 = 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) n2 = fmaf(xa[u], xa[u], n2);
+            n2 = warp_sum(n2);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int r = lane + 32 * u;
+              if (r < l) Xs[r * ldx + a] = xa[u];
+            }
+          }
+          if (lane == 0) s_n2 = n2;
         }
-        __syncwarp();
+        __syncthreads();
+        const float n2 = s_n2;
+        const float sc = n2 > 0.f ? rsqrtf(n2) : 0.f;
+        for (int r = tid; r < l; r += nt) Xs[r * ldx + a] *= sc;
+        __syncthreads();
       }
       start = i;
     }
     // diagnostic word at byte 16 of the status block: replaced vectors
-    if (lane == 0) status[4] = (unsigned)nrep;
+    if (tid == 0) status[4] = (unsigned)nrep;
   }
-  __syncthreads();
 
-  // ---- 6. back-transformation X = H_0 ... H_{l-2} Z (8 threads per column)
+  // ---- 6. back-transformation X = H_0 ... H_{l-2} Z: 8 threads per column,
+  // thread t8 holding rows 32u + 4 t8 + i (u, i < 4) in registers; row j of
+  // A is the full vector v_j
   {
     const int c = tid / kGrp, t8 = tid % kGrp;
     const unsigned gmask = 0xFFu << (lane & 24);
     if (c < l) {
-      float xr[kRowsPerThread], vr[kRowsPerThread];
+      float xr[16];
 #pragma unroll
-      for (int u = 0; u < kRowsPerThread; ++u) {
-        const int r = t8 + kGrp * u;
-        xr[u] = r < l ? Xs[r * ldx + c] : 0.f;
-      }
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = 32 * u + 4 * t8 + i;
+          xr[4 * u + i] = r < l ? Xs[r * ldx + c] : 0.f;
+        }
       for (int j = l - 2; j >= 0; --j) {
         const float t = tau[j];
         if (t == 0.f) continue;
         const float* vj = A + j * lda;
-        float s = 0.f;
+        float4 vv[4];
+        float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-        for (int u = 0; u < kRowsPerThread; ++u) {
-          const int r = t8 + kGrp * u;
-          vr[u] = (r > j + 1 && r < l) ? vj[r] : (r == j + 1 ? 1.f : 0.f);
-          s = fmaf(vr[u], xr[u], s);
+        for (int u = 0; u < 4; ++u) {
+          const int cc = 32 * u + 4 * t8;
+          vv[u] = cc < lda ? *reinterpret_cast<const float4*>(vj + cc) : z4;
+          s0 = fmaf(vv[u].x, xr[4 * u + 0], fmaf(vv[u].y, xr[4 * u + 1], s0));
+          s1 = fmaf(vv[u].z, xr[4 * u + 2], fmaf(vv[u].w, xr[4 * u + 3], s1));
         }
+        float s = s0 + s1;
         s += __shfl_xor_sync(gmask, s, 1);
         s += __shfl_xor_sync(gmask, s, 2);
         s += __shfl_xor_sync(gmask, s, 4);
-        const float f = t * s;
+        const float f = -t * s;
 #pragma unroll
-        for (int u = 0; u < kRowsPerThread; ++u) xr[u] = fmaf(-f, vr[u], xr[u]);
+        for (int u = 0; u < 4; ++u) {
+          xr[4 * u + 0] = fmaf(f, vv[u].x, xr[4 * u + 0]);
+          xr[4 * u + 1] = fmaf(f, vv[u].y, xr[4 * u + 1]);
+          xr[4 * u + 2] = fmaf(f, vv[u].z, xr[4 * u + 2]);
+          xr[4 * u + 3] = fmaf(f, vv[u].w, xr[4 * u + 3]);
+        }
       }
 #pragma unroll
-      for (int u = 0; u < kRowsPerThread; ++u) {
-        const int r = t8 + kGrp * u;
-        if (r < l) Xout[r + (size_t)c * l] = (double)xr[u];
-      }
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = 32 * u + 4 * t8 + i;
+          if (r < l) Xout[r + (size_t)c * l] = (double)xr[4 * u + i];
+        }
     }
   }
 }

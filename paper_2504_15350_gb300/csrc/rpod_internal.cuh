@@ -76,7 +76,7 @@ cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma,
                     double* Uhat, double* work, unsigned* status, int refine_iters);
 
 // FP32 starting eigenvectors X (l x l, FP64, column-major, ascending
-// eigenvalues) of the symmetric G (l x l, FP64, lower triangle read) from
+// eigenvalues) of the symmetric G (l x l, FP64; column i is read as row i) from
 // one CTA: Householder tridiagonalization, multisection, twisted
 // factorizations.  Writes the number of replaced vectors of multiple
 // eigenvalues to status[4] (diagnostic).
