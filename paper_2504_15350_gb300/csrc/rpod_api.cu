@@ -134,7 +134,20 @@ struct Run {
   // is Q1 X with X = R^{-1} left in off_x (FP64) and off_xw (W); the caller
   // folds X into the small matrices (T = X^T Q1^T S, U = Q1 (X Uhat)), which
   // saves one n x l x l product.
-  int orth(W* in, W* tmp, int64_t rows, int rounds, W** out, bool exact_last, bool defer = false) {
+  // Outputs of the last apply of a CholeskyQR on the tensor-core path:
+  // the basis rounded to the 16-bit type (h16) and/or to TF32 (tf), the
+  // FP32 basis itself only when f32 is set; `used` reports whether the
+  // tensor-core apply ran (else the FP32 basis was formed on the SIMT path
+  // and the rounded copies were not written).
+  struct TcOut {
+    void* h16;
+    float* tf;
+    bool f32;
+    bool used;
+  };
+
+  int orth(W* in, W* tmp, int64_t rows, int rounds, W** out, bool exact_last, bool defer = false,
+           TcOut* tco = nullptr) {
     const int l = P->l;
     const double tol = sizeof(W) == 8 ? 1e-13 : 1e-5;
     // FP32 Gram: two row chunks per SM (the kernel fits two blocks per SM)
@@ -148,8 +161,17 @@ struct Run {
       CK((cholesky<W>(st, l, G, tol, r, dbuf(P->off_x), buf(P->off_xw), l, status,
                       sizeof(W) == 4 ? (const float*)src : nullptr, rows, dbuf(P->off_gpart), ns)));
       if (defer && r == rounds - 1) break;
-      CK((gemm<W, W, W, W>(st, false, rows, l, l, 1, src, rows, buf(P->off_xw), l, dst, 1, rows, 0,
-                           status, false)));
+      const bool last_apply = r == rounds - 1 - (defer ? 1 : 0);
+      int rc = RPOD_ERR_UNSUPPORTED;
+      if (sizeof(W) == 4 && tco && last_apply)
+        rc = tc_apply(st, (const float*)src, rows, rows, l, (const float*)buf(P->off_xw), l,
+                      tco->f32 ? (float*)dst : nullptr, rows, P->compute, tco->h16, P->n_ld,
+                      tco->tf, P->n_ld, status);
+      if (rc == RPOD_ERR_CUDA) return rc;
+      if (tco && last_apply) tco->used = rc == RPOD_OK;
+      if (rc != RPOD_OK)
+        CK((gemm<W, W, W, W>(st, false, rows, l, l, 1, src, rows, buf(P->off_xw), l, dst, 1, rows, 0,
+                             status, false)));
       W* t = src; src = dst; dst = t;
     }
     *out = src;
@@ -322,6 +344,10 @@ struct Run {
       prof_end(P, st, pb16, pass_flops);
     }
     float* Q = nullptr;
+    const bool refine_req = (P->flags & RPOD_FLAG_REFINE_FP32) && Sref;
+    const bool refine_tma = refine_req && (((uintptr_t)Sref & 15) == 0) && ((ldr * 4) % 16 == 0);
+    float* const Atf = (float*)(ws + P->off_atf);
+    bool tf_ready = false;
     for (int it = 0; it <= q; ++it) {
       if (it > 0) {
         // Alg. 1 subspace iteration: Z = S^T Q, orthonormalise, Y = S Z
@@ -336,12 +362,17 @@ struct Run {
         CR(tc_ypass(st, dt, Zh, mld, Sh, ldh, n, m, l, Y, n, status));
         prof_end(P, st, pb16, pass_flops);
       }
-      CR(orth(Y, Qbuf, n, it == q ? 2 : 1, &Q, it == q, it == q));
-      if (it < q) CK(to16(Q, n, n, Qh, nld));
+      // the final basis is kept in FP32 (lift, Gram of the deferred round)
+      // and rounded to TF32 for the refinement pass; intermediate ones are
+      // needed only as the 16-bit operand of the next W-pass
+      TcOut tco{it < q ? Qh : nullptr, it == q && refine_tma ? Atf : nullptr, it == q, false};
+      CR(orth(Y, Qbuf, n, it == q ? 2 : 1, &Q, it == q, it == q, &tco));
+      if (it < q && !tco.used) CK(to16(Q, n, n, Qh, nld));
+      tf_ready = it == q && tco.used && refine_tma;
     }
     // Alg. 1: T = Q^T S (TF32 from the FP32 copy when refining)
-    const bool refine = (P->flags & RPOD_FLAG_REFINE_FP32) && Sref;
-    const bool ref_tma = refine && (((uintptr_t)Sref & 15) == 0) && ((ldr * 4) % 16 == 0);
+    const bool refine = refine_req;
+    const bool ref_tma = refine_tma;
     if (refine && !ref_tma) {
       // FP32 copy not addressable by TMA: the SIMT FP32 pass computes T
       prof_begin(P, st);
@@ -353,8 +384,7 @@ struct Run {
       return finish(Q, Tt, U, ldu, sigma, C, ldc, true);
     }
     if (refine) {
-      float* Atf = (float*)(ws + P->off_atf);
-      CK(round_tf32(st, n, l, Q, n, Atf, nld));
+      if (!tf_ready) CK(round_tf32(st, n, l, Q, n, Atf, nld));
       prof_begin(P, st);
       CR(tc_wpass(st, RPOD_F32, Atf, nld, n, l, Sref, ldr, m, wpart, P->nsplit_w, status));
       prof_end(P, st, 4.0 * ((double)n * m + (double)n * l + (double)m * l), pass_flops);

@@ -21,6 +21,7 @@
 // kernel records ST_TIMEOUT, stops issuing work, frees its TMEM and returns.
 #include <cuda.h>
 
+#include <algorithm>
 #include <mutex>
 #include <type_traits>
 
@@ -81,6 +82,14 @@ __device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile in
       return false;
     }
   }
+}
+// Bounded wait that ignores the abort flag: used after an abort to let this
+// thread's own copies or MMAs finish before the shared memory and TMEM they
+// target are released.
+__device__ __noinline__ void mbar_wait_drain(uint64_t* b, uint32_t parity) {
+  const uint64_t t0 = gtimer();
+  while (!mbar_try(b, parity))
+    if (gtimer() - t0 > kTimeoutNs) return;
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
                                             int c1) {
@@ -697,6 +706,205 @@ k_ypass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   if (warp == 0) tmem_dealloc(tmem, BN);
 }
 
+// ---------------------------------------------------------------------------
+// CholeskyQR apply Q = Y X (Alg. 1, QR of the sampled matrix) for the
+// 16-bit forms: Y n x l FP32 and X l x l FP32 (the inverse Cholesky factor),
+// both rounded to TF32 (round to nearest), one kind::tf32 product with FP32
+// accumulation.  The rounding of Y (2^-12 relative) is below the BF16
+// error of the passes that produced Y, and the basis this apply returns is
+// either rounded to BF16 for the next pass or re-orthonormalised by a
+// CholeskyQR round on an exact FP32 Gram, so one TF32 product suffices.
+// Persistent CTAs over 128-row tiles: warp 0 TMA-loads 128 x 32 column-major
+// FP32 tiles of Y (one per 32-column k-block), warps 2-5 round them and
+// transpose them into the K-major SW128 operand layout, warp 1 issues the
+// MMAs against X (resident in shared memory as the B operand) into one of two
+// TMEM accumulators, and warps 6-9 drain the other accumulator and write any
+// of: Q (FP32), Q rounded to the 16-bit type (the next W-pass operand), Q
+// rounded to TF32 (the refinement pass operand).
+template <int STAGES>
+struct ApplySmem {
+  static constexpr uint32_t KB = 128 * 32 * 4;  // 128 rows x 32 columns of FP32
+  static constexpr uint32_t STAGE = 2 * KB;     // raw TMA tile + converted operand
+  static constexpr uint32_t XOP = 4 * KB;       // X: 4 k-blocks x 128 (j) x 32 (k)
+  static constexpr uint32_t BARS = STAGES * STAGE + XOP;
+  static constexpr size_t TOTAL = 1024 + (size_t)BARS + 256;
+};
+
+template <int KIND16, int STAGES>
+__global__ void __launch_bounds__(320, 1)
+k_apply_tf32(const __grid_constant__ CUtensorMap tmY, const float* __restrict__ X, int64_t ldx,
+             int64_t n, int l, float* __restrict__ Q, int64_t ldq, void* __restrict__ Qh,
+             int64_t ldh, float* __restrict__ Qt, int64_t ldt, unsigned* status) {
+  using L = ApplySmem<STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* xop = smem + STAGES * L::STAGE;
+  uint64_t* full = (uint64_t*)(smem + L::BARS);
+  uint64_t* empty = full + STAGES;
+  uint64_t* conv = empty + STAGES;
+  uint64_t* tfull = conv + STAGES;   // [2]
+  uint64_t* tempty = tfull + 2;      // [2]
+  uint64_t* mdone = tempty + 2;
+  uint32_t* tslot = (uint32_t*)(mdone + 1);
+  volatile int* abort_flag = (volatile int*)(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nkb = (l + 31) / 32;
+  const int64_t ntiles = (n + 127) / 128;
+  // tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...
+  const int nlt = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      mbar_init(&conv[s], 4);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    mbar_init(mdone, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  // X as the B operand (N = j, K = k), K-major SW128, rounded to TF32, zero
+  // outside l x l
+  if (warp >= 2 && warp < 6) {
+    const int ct = threadIdx.x - 64;
+    for (int e = ct; e < 4 * 128 * 8; e += 128) {
+      const int kb = e >> 10, j = (e >> 3) & 127, c4 = e & 7;
+      const int k = kb * 32 + 4 * c4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j < l) {
+        const float* xc = X + (int64_t)j * ldx;
+        if (k + 0 < l) v.x = tf32_rna(xc[k + 0]);
+        if (k + 1 < l) v.y = tf32_rna(xc[k + 1]);
+        if (k + 2 < l) v.z = tf32_rna(xc[k + 2]);
+        if (k + 3 < l) v.w = tf32_rna(xc[k + 3]);
+      }
+      *(float4*)(xop + kb * L::KB + (j >> 3) * 1024 + (j & 7) * 128 + ((c4 ^ (j & 7)) << 4)) = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tslot, 256);
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0 && lane == 0) {
+    int it = 0;  // loads issued
+    bool go = true;
+    for (int lt = 0; lt < nlt && go; ++lt) {
+      const int64_t t = blockIdx.x + (int64_t)lt * gridDim.x;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+        if (it >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, abort_flag)) { go = false; break; }
+        mbar_expect_tx(&full[s], L::KB);
+        tma_load_2d(smem + s * L::STAGE, &tmY, &full[s], (int)(t * 128), kb * 32);
+        ++it;
+      }
+    }
+    // on an abort, wait (bounded) for the copies still in flight
+    if (*abort_flag)
+      for (int i2 = it > STAGES ? it - STAGES : 0; i2 < it; ++i2)
+        mbar_wait_drain(&full[i2 % STAGES], (uint32_t)(i2 / STAGES) & 1u);
+  } else if (warp >= 2 && warp < 6) {
+    const int ct = threadIdx.x - 64;
+    bool go = true;
+    for (int lt = 0, it = 0; lt < nlt && go; ++lt)
+      for (int kb = 0; kb < nkb; ++kb, ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[s], ph, abort_flag));
+        if (!ok) { go = false; break; }
+        const float* raw = (const float*)(smem + s * L::STAGE);  // column k at k * 128
+        uint8_t* aop = smem + s * L::STAGE + L::KB;
+#pragma unroll 2
+        for (int e = ct; e < 128 * 8; e += 128) {
+          const int m = e & 127, c4 = e >> 7;
+          float4 v;
+          v.x = tf32_rna(raw[(4 * c4 + 0) * 128 + m]);
+          v.y = tf32_rna(raw[(4 * c4 + 1) * 128 + m]);
+          v.z = tf32_rna(raw[(4 * c4 + 2) * 128 + m]);
+          v.w = tf32_rna(raw[(4 * c4 + 3) * 128 + m]);
+          *(float4*)(aop + (m >> 3) * 1024 + (m & 7) * 128 + ((c4 ^ (m & 7)) << 4)) = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&conv[s]);
+      }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t id = idesc(2, false, 128, 128);
+    bool go = true, issued = false;
+    for (int lt = 0, it = 0; lt < nlt && go; ++lt) {
+      const int buf = lt & 1;
+      if (lt >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((lt >> 1) - 1) & 1u, abort_flag)) break;
+      tc_after();
+      const uint32_t d = tmem + (uint32_t)(buf * 128);
+      for (int kb = 0; kb < nkb; ++kb, ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+        if (!mbar_wait(&conv[s], ph, abort_flag)) { go = false; break; }
+        tc_after();
+        const uint32_t a = su32(smem + s * L::STAGE + L::KB), b = su32(xop + kb * L::KB);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          mma<2>(d, sdesc(a + 32 * kk, 16, 1024), sdesc(b + 32 * kk, 16, 1024), id,
+                 (kb > 0 || kk > 0) ? 1u : 0u);
+        mma_commit(&empty[s]);
+        issued = true;
+      }
+      if (go) mma_commit(&tfull[buf]);
+    }
+    // every MMA of this CTA complete before the accumulators are freed
+    if (issued) {
+      mma_commit(mdone);
+      mbar_wait_drain(mdone, 0);
+    }
+  } else if (warp >= 6) {
+    const int q = warp & 3;  // TMEM lane quarter this warp may read
+    for (int lt = 0; lt < nlt; ++lt) {
+      const int buf = lt & 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&tfull[buf], (uint32_t)(lt >> 1) & 1u, abort_flag));
+      if (!ok) break;
+      tc_after();
+      const int64_t t = blockIdx.x + (int64_t)lt * gridDim.x;
+      const int64_t m = t * 128 + q * 32 + lane;
+      for (int cc = 0; cc < l; cc += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 128 + cc), v);
+        if (m < n) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int j = cc + i;
+            if (j < l) {
+              if (Q) Q[m + j * ldq] = v[i];
+              if (Qt) Qt[m + j * ldt] = tf32_rna(v[i]);
+              if (Qh) {
+                if (KIND16 == 0)
+                  ((__nv_bfloat16*)Qh)[m + j * ldh] = __float2bfloat16_rn(v[i]);
+                else
+                  ((__half*)Qh)[m + j * ldh] = __float2half_rn(v[i]);
+              }
+            }
+          }
+        }
+      }
+      tc_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+    }
+  }
+  __syncwarp();
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
+  tc_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
 }  // namespace tc
 
 // ---------------------------------------------------------------------------
@@ -735,7 +943,7 @@ int esize(int dt) { return (dt == RPOD_BF16 || dt == RPOD_F16) ? 2 : 4; }
 
 // 2-D column-major matrix (rows contiguous): dims {rows, cols}, box {br, bc}.
 int make_map(CUtensorMap* map, const void* ptr, int dt, int64_t rows, int64_t cols, int64_t ld,
-             int br, int bc) {
+             int br, int bc, bool swizzle = true) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return RPOD_ERR_CUDA;
   const int es = esize(dt);
@@ -745,7 +953,8 @@ int make_map(CUtensorMap* map, const void* ptr, int dt, int64_t rows, int64_t co
   cuuint32_t box[2] = {(cuuint32_t)br, (cuuint32_t)bc};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, tmap_type(dt), 2, const_cast<void*>(ptr), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? RPOD_OK : RPOD_ERR_CUDA;
 }
@@ -754,6 +963,20 @@ constexpr int kBN = 256;
 constexpr int kStages = 4;
 constexpr int kGramStages = 3;  // 96 KB: two CTAs per SM
 constexpr int kYcvtStages = 3;  // 192 KB
+constexpr int kApplyStages = 4;  // 128 KB of stages + 64 KB for X
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      n = v;
+    else
+      n = 152;
+  }
+  return n;
+}
 
 }  // namespace
 
@@ -772,6 +995,9 @@ void prepare_kernels_tc() {
     const int yc = (int)tc::YcvtSmem<kYcvtStages>::TOTAL;
     cudaFuncSetAttribute(tc::k_ypass_cvt<0, kYcvtStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, yc);
     cudaFuncSetAttribute(tc::k_ypass_cvt<1, kYcvtStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, yc);
+    const int ap = (int)tc::ApplySmem<kApplyStages>::TOTAL;
+    cudaFuncSetAttribute(tc::k_apply_tf32<0, kApplyStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, ap);
+    cudaFuncSetAttribute(tc::k_apply_tf32<1, kApplyStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, ap);
   });
 }
 
@@ -859,6 +1085,28 @@ int tc_ypass_cvt(cudaStream_t st, int dt, const void* A, int64_t lda, const floa
     tc::k_ypass_cvt<0, kYcvtStages><<<grid, 192, L::TOTAL, st>>>(ta, tf, n, m, l, Y, ldy, Sh, ldh, status);
   else
     tc::k_ypass_cvt<1, kYcvtStages><<<grid, 192, L::TOTAL, st>>>(ta, tf, n, m, l, Y, ldy, Sh, ldh, status);
+  note_launch();
+  return cudaGetLastError() == cudaSuccess ? RPOD_OK : RPOD_ERR_CUDA;
+}
+
+int tc_apply(cudaStream_t st, const float* Y, int64_t ldy, int64_t n, int l, const float* X,
+             int64_t ldx, float* Q, int64_t ldq, int dt16, void* Qh, int64_t ldh, float* Qt,
+             int64_t ldt, unsigned* status) {
+  if (l < 1 || l > 128 || n < 1 || ldx < l) return RPOD_ERR_INVALID_ARG;
+  if (Qh && dt16 != RPOD_BF16 && dt16 != RPOD_F16) return RPOD_ERR_INVALID_ARG;
+  if ((Q && ldq < n) || (Qh && ldh < n) || (Qt && ldt < n)) return RPOD_ERR_INVALID_ARG;
+  CUtensorMap ty;
+  if (int rc = make_map(&ty, Y, RPOD_F32, n, l, ldy, 128, 32, false)) return rc;
+  const int64_t ntiles = (n + 127) / 128;
+  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, sm_count());
+  using L = tc::ApplySmem<kApplyStages>;
+  prepare_kernels_tc();
+  if (dt16 == RPOD_F16)
+    tc::k_apply_tf32<1, kApplyStages><<<grid, 320, L::TOTAL, st>>>(ty, X, ldx, n, l, Q, ldq, Qh, ldh, Qt,
+                                                                   ldt, status);
+  else
+    tc::k_apply_tf32<0, kApplyStages><<<grid, 320, L::TOTAL, st>>>(ty, X, ldx, n, l, Q, ldq, Qh, ldh, Qt,
+                                                                   ldt, status);
   note_launch();
   return cudaGetLastError() == cudaSuccess ? RPOD_OK : RPOD_ERR_CUDA;
 }
