@@ -104,15 +104,15 @@ struct Run {
   double* dbuf(size_t off) { return (double*)(ws + off); }
 
   // Gram G = A^T A (A rows x l, ld lda) in FP64: products in W, summed in W
-  // within a split of rows, then in FP64 across splits.
-  // Gram partials of the l columns of A, summed in FP64 into G.  FP32: the
-  // tensor-core split-TF32 kernel when `fast` (and A is TMA-addressable),
-  // else FP32 products on the SIMT pipes.
+  // within a split of rows, then in FP64 across splits.  FP32 (when A is
+  // TMA-addressable): the tensor-core split-TF32 kernel, with a two-part
+  // split when `fast` (only the conditioning of the basis depends on it)
+  // and an exact three-part split otherwise; else FP32 products on the SIMT
+  // pipes.
   int gram(const W* A, int64_t rows, int64_t lda, double* G, int nsplit, bool fast) {
     const int l = P->l;
     if (sizeof(W) == 4) {
-      int rc = fast ? tc_gram(st, (const float*)A, lda, rows, l, dbuf(P->off_gpart), nsplit, status)
-                    : RPOD_ERR_UNSUPPORTED;
+      int rc = tc_gram(st, (const float*)A, lda, rows, l, dbuf(P->off_gpart), nsplit, status, !fast);
       if (rc == RPOD_ERR_CUDA) return rc;
       if (rc != RPOD_OK)
         CK(gram_f32(st, rows, l, (const float*)A, lda, nsplit, dbuf(P->off_gpart)));
@@ -202,13 +202,14 @@ struct Run {
                               (int64_t)l * l, status, false)));
     CK((reduce_splits<double, double>(st, l, l, ns, dbuf(P->off_gpart), GT, 1, l)));
     double* Uhat = dbuf(P->off_uhat);
-    // FP32 start from the tridiagonal reduction, then FP64 refinement
-    // passes, each of which squares the eigenvector error outside clusters;
-    // the cluster threshold of a pass scales with the norm of all remaining
-    // off-diagonal terms, so eigenvalues closer than that are separated only
-    // by a later pass: three passes for the FP32 forms, five for the FP64
-    // form.
-    CK((sym_eig(st, l, GT, sigma, Uhat, dbuf(P->off_eig), status, sizeof(W) == 8 ? 5 : 3)));
+    // FP32 start from the tridiagonal reduction (eigenvectors to about
+    // 1e-5), then FP64 refinement passes, each of which squares the
+    // eigenvector error outside clusters; the cluster threshold of a pass
+    // scales with the norm of all remaining off-diagonal terms, so
+    // eigenvalues closer than that are separated only by a later pass: two
+    // passes for the FP32 forms (orthogonality near 1e-9), five for the
+    // FP64 form.
+    CK((sym_eig(st, l, GT, sigma, Uhat, dbuf(P->off_eig), status, sizeof(W) == 8 ? 5 : 2)));
     CK((check_finite_vec(st, l, sigma, status)));
     // Alg. 1: lift U = Q Uhat (first k or all l columns), then the sign rule
     const int ku = (P->flags & RPOD_FLAG_RETURN_ALL_L) ? l : k;

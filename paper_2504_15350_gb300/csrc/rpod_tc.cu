@@ -492,9 +492,10 @@ k_gram3(const __grid_constant__ CUtensorMap tmY, int64_t rows, int l, int kchunk
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
         const uint64_t dh = sdesc(h + 32 * kk, 16, 1024), dl = sdesc(lo + 32 * kk, 16, 1024);
-        mma<2>(tmem, dh, dh, id, (it > 0 || kk > 0) ? 1u : 0u);
+        // smallest terms first
+        mma<2>(tmem, dl, dh, id, (it > 0 || kk > 0) ? 1u : 0u);
         mma<2>(tmem, dh, dl, id, 1u);
-        mma<2>(tmem, dl, dh, id, 1u);
+        mma<2>(tmem, dh, dh, id, 1u);
       }
       mma_commit(&empty[s]);
     }
@@ -528,6 +529,181 @@ k_gram3(const __grid_constant__ CUtensorMap tmY, int64_t rows, int l, int kchunk
   tc_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+// ---------------------------------------------------------------------------
+// Gram matrix with products as accurate as FP32 ones (the last CholeskyQR
+// round, which fixes the orthogonality of the returned basis): every element
+// of Y is split exactly into three TF32 parts h + m + r and the six products
+// above 2^-33 (r h, h r, m m, m h, h m, h h) are accumulated.  The tensor
+// core's FP32 accumulation drifts with the number of MMAs summed into one
+// accumulator (its rounding does not average out), so the MMAs of each two
+// 32-row tiles go into one of two TMEM accumulators, and warps 6-9 add every
+// finished accumulator into FP32 sums in shared memory (round to nearest,
+// upper triangle only) while the MMAs continue in the other one.
+constexpr int kGxChain = 2;  // 32-row tiles per accumulator chain
+
+template <int STAGES>
+struct GramXSmem {
+  static constexpr uint32_t TILE = 128 * 128;  // 128 columns x 32 rows of FP32
+  static constexpr uint32_t STAGE = 3 * TILE;
+  static constexpr uint32_t ACC = 4 * (128 * 129 / 2);  // one float per (c <= j)
+  static constexpr uint32_t BARS = STAGES * STAGE + ACC;
+  static constexpr size_t TOTAL = 1024 + (size_t)BARS + 256;
+};
+
+template <int STAGES>
+__global__ void __launch_bounds__(320, 1)
+k_gram_x(const __grid_constant__ CUtensorMap tmY, int64_t rows, int l, int kchunk,
+         double* __restrict__ part, unsigned* status) {
+  using L = GramXSmem<STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float* acc = (float*)(smem + STAGES * L::STAGE);
+  uint64_t* full = (uint64_t*)(smem + L::BARS);
+  uint64_t* empty = full + STAGES;
+  uint64_t* conv = empty + STAGES;
+  uint64_t* tfull = conv + STAGES;  // [2]
+  uint64_t* tempty = tfull + 2;     // [2]
+  uint64_t* mdone = tempty + 2;
+  uint32_t* tslot = (uint32_t*)(mdone + 1);
+  volatile int* abort_flag = (volatile int*)(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ktiles = (rows + 31) / 32;
+  const int64_t kt0 = (int64_t)blockIdx.x * kchunk;
+  const int64_t kt1 = (kt0 + kchunk < ktiles) ? kt0 + kchunk : ktiles;
+  const int nk = kt1 > kt0 ? (int)(kt1 - kt0) : 0;
+  const int nch = (nk + kGxChain - 1) / kGxChain;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      mbar_init(&conv[s], 4);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    mbar_init(mdone, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp >= 6)
+    for (int e = threadIdx.x - 192; e < 128 * 129 / 2; e += 128) acc[e] = 0.f;
+  if (warp == 0) tmem_alloc(tslot, 256);
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0 && lane == 0) {
+    int it = 0;
+    for (; it < nk; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (it >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+      mbar_expect_tx(&full[s], L::TILE);
+      tma_load_2d(smem + s * L::STAGE, &tmY, &full[s], (int)((kt0 + it) * 32), 0);
+    }
+    if (*abort_flag)
+      for (int i2 = it > STAGES ? it - STAGES : 0; i2 < it; ++i2)
+        mbar_wait_drain(&full[i2 % STAGES], (uint32_t)(i2 / STAGES) & 1u);
+  } else if (warp >= 2 && warp < 6) {
+    const int ct = threadIdx.x - 64;
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (!__all_sync(0xffffffffu, mbar_wait(&full[s], ph, abort_flag))) break;
+      float4* h4 = (float4*)(smem + s * L::STAGE);
+      float4* m4 = (float4*)(smem + s * L::STAGE + L::TILE);
+      float4* r4 = (float4*)(smem + s * L::STAGE + 2 * L::TILE);
+#pragma unroll 4
+      for (int e = ct; e < (int)(L::TILE / 16); e += 128) {
+        const float4 v = h4[e];
+        float4 h, m, r;
+        h.x = tf32_rna(v.x); m.x = tf32_rna(v.x - h.x); r.x = tf32_rna((v.x - h.x) - m.x);
+        h.y = tf32_rna(v.y); m.y = tf32_rna(v.y - h.y); r.y = tf32_rna((v.y - h.y) - m.y);
+        h.z = tf32_rna(v.z); m.z = tf32_rna(v.z - h.z); r.z = tf32_rna((v.z - h.z) - m.z);
+        h.w = tf32_rna(v.w); m.w = tf32_rna(v.w - h.w); r.w = tf32_rna((v.w - h.w) - m.w);
+        h4[e] = h;
+        m4[e] = m;
+        r4[e] = r;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&conv[s]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t id = idesc(2, false, 128, 128);
+    bool go = true, issued = false;
+    for (int ch = 0, it = 0; ch < nch && go; ++ch) {
+      const int buf = ch & 1;
+      if (ch >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((ch >> 1) - 1) & 1u, abort_flag)) break;
+      tc_after();
+      const uint32_t d = tmem + (uint32_t)(buf * 128);
+      for (int c2 = 0; c2 < kGxChain && it < nk; ++c2, ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+        if (!mbar_wait(&conv[s], ph, abort_flag)) { go = false; break; }
+        tc_after();
+        const uint32_t h = su32(smem + s * L::STAGE), mm = h + L::TILE, r = h + 2 * L::TILE;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t dh = sdesc(h + 32 * kk, 16, 1024), dm = sdesc(mm + 32 * kk, 16, 1024),
+                         dr = sdesc(r + 32 * kk, 16, 1024);
+          mma<2>(d, dr, dh, id, (c2 > 0 || kk > 0) ? 1u : 0u);
+          mma<2>(d, dh, dr, id, 1u);
+          mma<2>(d, dm, dm, id, 1u);
+          mma<2>(d, dm, dh, id, 1u);
+          mma<2>(d, dh, dm, id, 1u);
+          mma<2>(d, dh, dh, id, 1u);
+        }
+        mma_commit(&empty[s]);
+        issued = true;
+      }
+      if (go) mma_commit(&tfull[buf]);
+    }
+    if (issued) {
+      mma_commit(mdone);
+      mbar_wait_drain(mdone, 0);
+    }
+  } else if (warp >= 6) {
+    const int q = warp & 3;
+    const int c = q * 32 + lane;
+    for (int ch = 0; ch < nch; ++ch) {
+      const int buf = ch & 1;
+      if (!__all_sync(0xffffffffu, mbar_wait(&tfull[buf], (uint32_t)(ch >> 1) & 1u, abort_flag))) break;
+      tc_after();
+      for (int cc = 0; cc < l; cc += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 128 + cc), v);
+        if (c < l) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int j = cc + i;
+            if (j >= c && j < l) acc[j * (j + 1) / 2 + c] += v[i];
+          }
+        }
+      }
+      tc_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+    }
+    double* pz = part + (int64_t)blockIdx.x * l * l;
+    if (c < l)
+      for (int j = c; j < l; ++j) {
+        const double g = *abort_flag ? 0.0 : (double)acc[j * (j + 1) / 2 + c];
+        pz[c + (int64_t)j * l] = g;
+        pz[j + (int64_t)c * l] = g;
+      }
+  }
+  __syncwarp();
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
+  tc_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 256);
 }
 
 // ---------------------------------------------------------------------------
@@ -963,6 +1139,7 @@ constexpr int kBN = 256;
 constexpr int kStages = 4;
 constexpr int kGramStages = 3;  // 96 KB: two CTAs per SM
 constexpr int kYcvtStages = 3;  // 192 KB
+constexpr int kGramXStages = 3;  // 144 KB of stages + 33 KB of sums
 constexpr int kApplyStages = 4;  // 128 KB of stages + 64 KB for X
 
 int sm_count() {
@@ -992,6 +1169,8 @@ void prepare_kernels_tc() {
     cudaFuncSetAttribute(tc::k_ypass<1, kBN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     cudaFuncSetAttribute(tc::k_gram3<kGramStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tc::GramSmem<kGramStages>::TOTAL);
+    cudaFuncSetAttribute(tc::k_gram_x<kGramXStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tc::GramXSmem<kGramXStages>::TOTAL);
     const int yc = (int)tc::YcvtSmem<kYcvtStages>::TOTAL;
     cudaFuncSetAttribute(tc::k_ypass_cvt<0, kYcvtStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, yc);
     cudaFuncSetAttribute(tc::k_ypass_cvt<1, kYcvtStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, yc);
@@ -1057,15 +1236,19 @@ int tc_ypass(cudaStream_t st, int dt, const void* A, int64_t lda, const void* S,
 }
 
 int tc_gram(cudaStream_t st, const float* Y, int64_t ldy, int64_t rows, int l, double* part,
-            int nsplit, unsigned* status) {
+            int nsplit, unsigned* status, bool exact) {
   if (l < 1 || l > 128 || rows < 1 || nsplit < 1) return RPOD_ERR_INVALID_ARG;
   CUtensorMap ty;
   if (int rc = make_map(&ty, Y, RPOD_F32, rows, l, ldy, 32, 128)) return rc;
   const int64_t ktiles = (rows + 31) / 32;
   const int kchunk = (int)((ktiles + nsplit - 1) / nsplit);
-  using L = tc::GramSmem<kGramStages>;
   prepare_kernels_tc();
-  tc::k_gram3<kGramStages><<<(unsigned)nsplit, 192, L::TOTAL, st>>>(ty, rows, l, kchunk, part, status);
+  if (exact)
+    tc::k_gram_x<kGramXStages><<<(unsigned)nsplit, 320, tc::GramXSmem<kGramXStages>::TOTAL, st>>>(
+        ty, rows, l, kchunk, part, status);
+  else
+    tc::k_gram3<kGramStages><<<(unsigned)nsplit, 192, tc::GramSmem<kGramStages>::TOTAL, st>>>(
+        ty, rows, l, kchunk, part, status);
   note_launch();
   return cudaGetLastError() == cudaSuccess ? RPOD_OK : RPOD_ERR_CUDA;
 }

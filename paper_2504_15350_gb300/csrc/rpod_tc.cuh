@@ -30,13 +30,15 @@ int tc_ypass_cvt(cudaStream_t st, int dt, const void* A, int64_t lda, const floa
                  unsigned* status);
 
 // Gram partials part[z][c + j l] (FP64) = sum over rows of split z of
-// Y(i, c) Y(i, j) for c, j < l <= 128, on the TF32 tensor path with a hi/lo
-// split of every element (about 2^-21 relative error per product, FP32
-// accumulation); nsplit CTAs, each a contiguous run of 32-row tiles.  Y FP32
-// column-major (ld ldy); base 16-byte aligned and ldy a multiple of 4, else
-// RPOD_ERR_UNSUPPORTED.
+// Y(i, c) Y(i, j) for c, j < l <= 128, on the TF32 tensor path with FP32
+// accumulation; nsplit CTAs, each a contiguous run of 32-row tiles.  Every
+// element is split into TF32 parts: hi/lo with three products (about 2^-21
+// relative error per product), or with `exact` an exact three-part split
+// and the six products above 2^-33 (products as accurate as FP32 ones).
+// Y FP32 column-major (ld ldy); base 16-byte aligned and ldy a multiple of
+// 4, else RPOD_ERR_UNSUPPORTED.
 int tc_gram(cudaStream_t st, const float* Y, int64_t ldy, int64_t rows, int l, double* part,
-            int nsplit, unsigned* status);
+            int nsplit, unsigned* status, bool exact = false);
 
 // CholeskyQR apply Q = Y X for Y n x l FP32 (column-major, ld ldy; base
 // 16-byte aligned, ldy a multiple of 4, else RPOD_ERR_UNSUPPORTED) and X
