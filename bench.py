@@ -284,8 +284,19 @@ def run_learned(dev, epochs):
     r = rom.run(rom.ROMConfig(epochs=epochs, patience=max(4, epochs)), device=dev)
     return {"epochs": r.epochs_run, "train_windows_per_s": r.samples_per_s,
             "rollout_steps_per_s": r.rollout_steps_per_s, "rollout_seconds": r.rollout_seconds,
-            "rel_err_lstm": r.err_lstm, "rel_err_persistence": r.err_persistence,
-            "rel_err_nearest_mu": r.err_nearest, "final_val_loss": r.val_loss[-1]}
+            "final_val_loss": r.val_loss[-1],
+            # relative L2 coefficient errors against the Galerkin projection of
+            # the held-out snapshots: one step from true windows, the first 10
+            # and all 500 autoregressive steps; then Eq. (l2-error) on the
+            # time-averaged field with the projection's own floor
+            "onestep_err": {"lstm": r.onestep_err_lstm, "persistence": r.onestep_err_persistence},
+            "first10_err": {"lstm": r.err_lstm_first10, "persistence": r.err_persistence_first10,
+                            "nearest_mu": r.err_nearest_first10},
+            "rollout500_err": {"lstm": r.err_lstm, "persistence": r.err_persistence,
+                               "nearest_mu": r.err_nearest},
+            "tavg_field_err": {"lstm": r.tavg_err_lstm, "persistence": r.tavg_err_persistence,
+                               "nearest_mu": r.tavg_err_nearest,
+                               "projection_floor": r.tavg_err_projection}}
 
 
 def main():

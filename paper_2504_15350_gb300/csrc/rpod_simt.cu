@@ -266,7 +266,11 @@ cudaError_t gemm_ex(cudaStream_t st, bool akc, bool bkc, int64_t M, int64_t N, i
     if (N <= 64) return launch_gemm<TA, TB, TC, TO, 128, 64, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
     return launch_gemm<TA, TB, TC, TO, 128, 128, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
   } else {
-    if (M <= 32 && N <= 32) return launch_gemm<TA, TB, TC, TO, 32, 32, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
+    // small FP64 products (the l x l steps of the eigensolver) on 32 x 32
+    // tiles: GB300 issues about two FP64 FMAs per clock per SM, so the tile
+    // count, not the tile efficiency, sets their time
+    if ((M <= 32 && N <= 32) || (M <= 128 && N <= 128))
+      return launch_gemm<TA, TB, TC, TO, 32, 32, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
     if (N <= 32) return launch_gemm<TA, TB, TC, TO, 64, 32, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
     return launch_gemm<TA, TB, TC, TO, 64, 64, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
   }
@@ -947,11 +951,6 @@ template cudaError_t cholesky<float>(cudaStream_t, int, const double*, double, i
 // |lambda_i - lambda_j| > delta, else R_ij / 2, E_ii = R_ii / 2,
 // X <- X + X E; each pass squares the error.
 
-__global__ void k_add_inplace(int64_t n, double* __restrict__ X, const double* __restrict__ D) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) X[i] += D[i];
-}
-
 __global__ void k_frob(int64_t n, const double* __restrict__ A, double* out) {
   __shared__ double rs[32];
   double s = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
@@ -1005,10 +1004,11 @@ k_sort_eig(int l, const double* __restrict__ lam, const double* __restrict__ X,
 }
 
 // Ogita-Aishima update: from XtX = X^T X and S = X^T A X (l x l) write the
-// eigenvalue estimates lambda and the correction E (FP64); ||A||_F is read
-// from the device.  Every block recomputes the two norms of delta (l^2 reads
-// from L2) and then fills its share of E, so the FP64 divisions spread over
-// the grid.
+// eigenvalue estimates lambda and I + E, E the correction (FP64), so that
+// the next basis is X (I + E); ||A||_F is read from the device.  Every
+// block recomputes the two norms of delta (l^2 reads from L2, summed in
+// FP32: delta is only a threshold) and then fills its share of I + E, so
+// the FP64 divisions spread over the grid.
 __global__ void __launch_bounds__(256)
 k_oa_update_dev(int l, const double* __restrict__ XtX, const double* __restrict__ S,
                 const double* __restrict__ normA, double* __restrict__ lam, double* __restrict__ E) {
@@ -1017,27 +1017,27 @@ k_oa_update_dev(int l, const double* __restrict__ XtX, const double* __restrict_
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < l; i += nt) lm[i] = S[i + i * l] / XtX[i + i * l];
   __syncthreads();
-  double so = 0.0, sr = 0.0;
+  float so = 0.f, sr = 0.f;
   for (int e = tid; e < l * l; e += nt) {
     const int i = e % l, j = e / l;
-    const double rij = (i == j ? 1.0 : 0.0) - XtX[e];
-    const double sij = S[e] - (i == j ? lm[i] : 0.0);
-    so += sij * sij;
-    sr += rij * rij;
+    const float rij = (float)((i == j ? 1.0 : 0.0) - XtX[e]);
+    const float sij = (float)(S[e] - (i == j ? lm[i] : 0.0));
+    so = fmaf(sij, sij, so);
+    sr = fmaf(rij, rij, sr);
   }
   for (int o = 16; o > 0; o >>= 1) {
     so += __shfl_xor_sync(0xffffffffu, so, o);
     sr += __shfl_xor_sync(0xffffffffu, sr, o);
   }
-  __shared__ double rs[2][32];
+  __shared__ float rs[2][32];
   __shared__ double s_delta;
   const int w = tid >> 5, lane = tid & 31;
   if (lane == 0) { rs[0][w] = so; rs[1][w] = sr; }
   __syncthreads();
   if (tid == 0) {
-    double a = 0.0, b = 0.0;
+    float a = 0.f, b = 0.f;
     for (int k = 0; k < (nt >> 5); ++k) { a += rs[0][k]; b += rs[1][k]; }
-    s_delta = 2.0 * (sqrt(a) + (*normA) * sqrt(b));
+    s_delta = 2.0 * (sqrt((double)a) + (*normA) * sqrt((double)b));
   }
   __syncthreads();
   const double delta = s_delta;
@@ -1045,7 +1045,7 @@ k_oa_update_dev(int l, const double* __restrict__ XtX, const double* __restrict_
     const int i = e % l, j = e / l;
     const double rij = (i == j ? 1.0 : 0.0) - XtX[e];
     double v;
-    if (i == j) v = 0.5 * rij;
+    if (i == j) v = 1.0 + 0.5 * rij;
     else if (fabs(lm[i] - lm[j]) > delta) v = (S[e] + lm[j] * rij) / (lm[j] - lm[i]);
     else v = 0.5 * rij;
     E[e] = v;
@@ -1093,14 +1093,13 @@ cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma, doub
     if ((e = reduce_splits<double, double>(st, l, l, nsp, part, S, 1, l))) return e;
     k_oa_update_dev<<<oa_blocks(l), 256, l * sizeof(double), st>>>(l, XtX, S, normA, lam, E); note_launch();
     if ((e = cudaGetLastError())) return e;
-    // X <- X + X E
+    // X <- X (I + E), into the other buffer
     if ((e = gemm<double, double, double, double>(st, false, l, l, l, nsp, X, l, E, l, part, 1, l, ll, status, false))) return e;
     if ((e = reduce_splits<double, double>(st, l, l, nsp, part, XE, 1, l))) return e;
-    k_add_inplace<<<(unsigned)((ll + 255) / 256), 256, 0, st>>>((int64_t)ll, X, XE); note_launch();
-    if ((e = cudaGetLastError())) return e;
+    double* t = X; X = XE; XE = t;
   }
   if (refine_iters == 0) {
-    // eigenvalues from the Rayleigh quotients of the Jacobi vectors
+    // eigenvalues from the Rayleigh quotients of the starting vectors
     if ((e = gemm<double, double, double, double>(st, false, l, l, l, nsp, G, l, X, l, part, 1, l, ll, status, false))) return e;
     if ((e = reduce_splits<double, double>(st, l, l, nsp, part, AX, 1, l))) return e;
     if ((e = gemm<double, double, double, double>(st, true, l, l, l, nsp, X, l, AX, l, part, 1, l, ll, status, false))) return e;
