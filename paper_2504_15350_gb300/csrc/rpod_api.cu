@@ -112,7 +112,13 @@ struct Run {
   int gram(const W* A, int64_t rows, int64_t lda, double* G, int nsplit, bool fast) {
     const int l = P->l;
     if (sizeof(W) == 4) {
-      int rc = tc_gram(st, (const float*)A, lda, rows, l, dbuf(P->off_gpart), nsplit, status, !fast);
+      // the exact kernel holds one CTA per SM: one wave of partials
+      const int ns = fast ? nsplit : std::min(nsplit, tc_sm_count());
+      int rc = tc_gram(st, (const float*)A, lda, rows, l, dbuf(P->off_gpart), ns, status, !fast);
+      if (rc == RPOD_OK) {
+        CK((reduce_splits<double, double>(st, l, l, ns, dbuf(P->off_gpart), G, 1, l)));
+        return RPOD_OK;
+      }
       if (rc == RPOD_ERR_CUDA) return rc;
       if (rc != RPOD_OK)
         CK(gram_f32(st, rows, l, (const float*)A, lda, nsplit, dbuf(P->off_gpart)));

@@ -558,7 +558,8 @@ k_cholesky_blk(int l, const double* __restrict__ G, float tol, int* gate, double
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       const int e = e0 + u * 256 + tid, i = e & 127, j = e >> 7;
-      v[u] = (i < l && j < l) ? (float)G[i + j * l] : 0.f;
+      // upper triangle of G only (the exact-product Gram leaves the lower one unset)
+      v[u] = (i < l && j < l) ? (float)G[min(i, j) + max(i, j) * l] : 0.f;
     }
 #pragma unroll
     for (int u = 0; u < 16; ++u) {

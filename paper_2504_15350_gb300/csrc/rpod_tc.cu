@@ -691,13 +691,11 @@ k_gram_x(const __grid_constant__ CUtensorMap tmY, int64_t rows, int l, int kchun
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[buf]);
     }
+    // upper triangle only (coalesced); the lower one is left unset
     double* pz = part + (int64_t)blockIdx.x * l * l;
     if (c < l)
-      for (int j = c; j < l; ++j) {
-        const double g = *abort_flag ? 0.0 : (double)acc[j * (j + 1) / 2 + c];
-        pz[c + (int64_t)j * l] = g;
-        pz[j + (int64_t)c * l] = g;
-      }
+      for (int j = c; j < l; ++j)
+        pz[c + (int64_t)j * l] = *abort_flag ? 0.0 : (double)acc[j * (j + 1) / 2 + c];
   }
   __syncwarp();
   if (threadIdx.x == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
@@ -945,21 +943,38 @@ k_apply_tf32(const __grid_constant__ CUtensorMap tmY, const float* __restrict__ 
     fence_mbar_init();
   }
   // X as the B operand (N = j, K = k), K-major SW128, rounded to TF32, zero
-  // outside l x l
+  // outside l x l; eight loads per thread in flight before their stores
   if (warp >= 2 && warp < 6) {
     const int ct = threadIdx.x - 64;
-    for (int e = ct; e < 4 * 128 * 8; e += 128) {
-      const int kb = e >> 10, j = (e >> 3) & 127, c4 = e & 7;
-      const int k = kb * 32 + 4 * c4;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (j < l) {
-        const float* xc = X + (int64_t)j * ldx;
-        if (k + 0 < l) v.x = tf32_rna(xc[k + 0]);
-        if (k + 1 < l) v.y = tf32_rna(xc[k + 1]);
-        if (k + 2 < l) v.z = tf32_rna(xc[k + 2]);
-        if (k + 3 < l) v.w = tf32_rna(xc[k + 3]);
+    const bool vec = (ldx & 3) == 0 && ((uintptr_t)X & 15) == 0;
+#pragma unroll 1
+    for (int e0 = 0; e0 < 4 * 128 * 8; e0 += 128 * 8) {
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * 128 + ct;
+        const int j = (e >> 3) & 127, k = (e >> 10) * 32 + 4 * (e & 7);
+        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < l && k < l) {
+          const float* xc = X + (int64_t)j * ldx + k;
+          if (vec) {
+            v[u] = *reinterpret_cast<const float4*>(xc);
+          } else {
+            v[u].x = xc[0];
+            if (k + 1 < l) v[u].y = xc[1];
+            if (k + 2 < l) v[u].z = xc[2];
+            if (k + 3 < l) v[u].w = xc[3];
+          }
+        }
       }
-      *(float4*)(xop + kb * L::KB + (j >> 3) * 1024 + (j & 7) * 128 + ((c4 ^ (j & 7)) << 4)) = v;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * 128 + ct;
+        const int kb = e >> 10, j = (e >> 3) & 127, c4 = e & 7;
+        const float4 r = make_float4(tf32_rna(v[u].x), tf32_rna(v[u].y), tf32_rna(v[u].z),
+                                     tf32_rna(v[u].w));
+        *(float4*)(xop + kb * L::KB + (j >> 3) * 1024 + (j & 7) * 128 + ((c4 ^ (j & 7)) << 4)) = r;
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -1271,6 +1286,8 @@ int tc_ypass_cvt(cudaStream_t st, int dt, const void* A, int64_t lda, const floa
   note_launch();
   return cudaGetLastError() == cudaSuccess ? RPOD_OK : RPOD_ERR_CUDA;
 }
+
+int tc_sm_count() { return sm_count(); }
 
 int tc_apply(cudaStream_t st, const float* Y, int64_t ldy, int64_t n, int l, const float* X,
              int64_t ldx, float* Q, int64_t ldq, int dt16, void* Qh, int64_t ldh, float* Qt,

@@ -35,6 +35,7 @@ int tc_ypass_cvt(cudaStream_t st, int dt, const void* A, int64_t lda, const floa
 // element is split into TF32 parts: hi/lo with three products (about 2^-21
 // relative error per product), or with `exact` an exact three-part split
 // and the six products above 2^-33 (products as accurate as FP32 ones).
+// The exact form writes only the upper triangle (c <= j) of each partial.
 // Y FP32 column-major (ld ldy); base 16-byte aligned and ldy a multiple of
 // 4, else RPOD_ERR_UNSUPPORTED.
 int tc_gram(cudaStream_t st, const float* Y, int64_t ldy, int64_t rows, int l, double* part,
@@ -51,5 +52,8 @@ int tc_gram(cudaStream_t st, const float* Y, int64_t ldy, int64_t rows, int l, d
 int tc_apply(cudaStream_t st, const float* Y, int64_t ldy, int64_t n, int l, const float* X,
              int64_t ldx, float* Q, int64_t ldq, int dt16, void* Qh, int64_t ldh, float* Qt,
              int64_t ldt, unsigned* status);
+
+// Streaming multiprocessors of the current device.
+int tc_sm_count();
 
 }  // namespace rpod
