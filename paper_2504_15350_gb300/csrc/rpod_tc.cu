@@ -184,15 +184,15 @@ struct Smem {
 // ---------------------------------------------------------------------------
 // W-pass.  KIND 0 bf16, 1 fp16, 2 tf32 (32-bit containers, 32 per 128-B row).
 template <int KIND, int BN, int STAGES>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(192, 1)
 k_wpass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmS, int64_t n,
         int64_t m, int l, int kchunk, float* __restrict__ part, unsigned* status) {
   using L = Smem<BN, STAGES>;
   constexpr int BKE = (KIND == 2) ? 32 : 64;
   extern __shared__ uint8_t smem_raw[];
   // TF32 form: the FP32 S tile is rounded to TF32 (round to nearest) in shared
-  // memory by warps 2-3 before the MMA reads it, so that the tensor core's
-  // truncation of the low mantissa bits adds no bias.
+  // memory by warps 2-5 before the MMA reads it, so that the tensor core's
+  // truncation of the low mantissa bits adds no bias.  Warps 0-3 drain TMEM.
   constexpr bool RND = (KIND == 2);
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + L::BARS);
@@ -213,7 +213,7 @@ k_wpass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
-      mbar_init(&conv[s], 2);
+      mbar_init(&conv[s], 4);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -241,12 +241,18 @@ k_wpass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     for (int it = 0; it < nk; ++it) {
       const int s = it % STAGES;
       const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-      if (!mbar_wait(&full[s], ph, abort_flag)) break;
+      if (!__all_sync(0xffffffffu, mbar_wait(&full[s], ph, abort_flag))) break;
       float4* b4 = (float4*)(smem + s * L::STAGE + L::A_BYTES);
-      for (int e = ct; e < (int)(L::B_BYTES / 16); e += 64) {
-        float4 v = b4[e];
-        v.x = tf32_rna(v.x); v.y = tf32_rna(v.y); v.z = tf32_rna(v.z); v.w = tf32_rna(v.w);
-        b4[e] = v;
+      for (int e0 = ct; e0 < (int)(L::B_BYTES / 16); e0 += 4 * 128) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = b4[e0 + u * 128];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          v[u].x = tf32_rna(v[u].x); v[u].y = tf32_rna(v[u].y);
+          v[u].z = tf32_rna(v[u].z); v[u].w = tf32_rna(v[u].w);
+          b4[e0 + u * 128] = v[u];
+        }
       }
       // make the generic-proxy stores visible to the tensor core's reads
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -275,25 +281,27 @@ k_wpass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
   if (nk > 0) ok = mbar_wait(done, 0, abort_flag);
   ok = __all_sync(0xffffffffu, ok) && !*abort_flag;
   tc_after();
-  const int c = warp * 32 + lane;
-  float* prow = part + (int64_t)blockIdx.y * (int64_t)l * m + (int64_t)c * m;
-  for (int cc = 0; cc < BN; cc += 32) {
-    float v[32];
-    if (nk > 0 && ok) {
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, v);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = 0.f;
-    }
-    if (c < l) {
-      const int64_t jb = j0 + cc;
-      if (((m & 3) == 0) && jb + 32 <= m) {
-        float4* d4 = (float4*)(prow + jb);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+  if (warp < 4) {
+    const int c = warp * 32 + lane;
+    float* prow = part + (int64_t)blockIdx.y * (int64_t)l * m + (int64_t)c * m;
+    for (int cc = 0; cc < BN; cc += 32) {
+      float v[32];
+      if (nk > 0 && ok) {
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, v);
       } else {
-        for (int i = 0; i < 32; ++i)
-          if (jb + i < m) prow[jb + i] = v[i];
+  #pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+      }
+      if (c < l) {
+        const int64_t jb = j0 + cc;
+        if (((m & 3) == 0) && jb + 32 <= m) {
+          float4* d4 = (float4*)(prow + jb);
+  #pragma unroll
+          for (int i = 0; i < 8; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        } else {
+          for (int i = 0; i < 32; ++i)
+            if (jb + i < m) prow[jb + i] = v[i];
+        }
       }
     }
   }
@@ -1226,7 +1234,7 @@ int tc_wpass(cudaStream_t st, int dt, const void* A, int64_t lda, int64_t n, int
       tc::k_wpass<1, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, kchunk, part, status);
       break;
     default:
-      tc::k_wpass<2, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, kchunk, part, status);
+      tc::k_wpass<2, kBN, kStages><<<grid, 192, L::TOTAL, st>>>(ta, ts, n, m, l, kchunk, part, status);
       break;
   }
   note_launch();
