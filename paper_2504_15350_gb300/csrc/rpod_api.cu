@@ -115,13 +115,16 @@ struct Run {
       // the exact kernel holds one CTA per SM: one wave of partials
       const int ns = fast ? nsplit : std::min(nsplit, tc_sm_count());
       int rc = tc_gram(st, (const float*)A, lda, rows, l, dbuf(P->off_gpart), ns, status, !fast);
+      // FP32 working type: partials summed in FP64, the Gram stored in FP32
+      // for the FP32 Cholesky
       if (rc == RPOD_OK) {
-        CK((reduce_splits<double, double>(st, l, l, ns, dbuf(P->off_gpart), G, 1, l)));
+        CK((reduce_splits<double, float>(st, l, l, ns, dbuf(P->off_gpart), (float*)G, 1, l)));
         return RPOD_OK;
       }
       if (rc == RPOD_ERR_CUDA) return rc;
-      if (rc != RPOD_OK)
-        CK(gram_f32(st, rows, l, (const float*)A, lda, nsplit, dbuf(P->off_gpart)));
+      CK(gram_f32(st, rows, l, (const float*)A, lda, nsplit, dbuf(P->off_gpart)));
+      CK((reduce_splits<double, float>(st, l, l, nsplit, dbuf(P->off_gpart), (float*)G, 1, l)));
+      return RPOD_OK;
     } else
       CK((gemm<W, W, W, double>(st, true, l, l, rows, nsplit, A, lda, A, lda, dbuf(P->off_gpart), 1,
                                 l, (int64_t)l * l, status, false)));
@@ -164,7 +167,10 @@ struct Run {
     for (int r = 0; r < rounds; ++r) {
       double* G = dbuf(P->off_g);
       CR(gram(src, rows, rows, G, ns, !(exact_last && r == rounds - 1)));
-      CK((cholesky<W>(st, l, G, tol, r, dbuf(P->off_x), buf(P->off_xw), l, status,
+      // the FP64 copy of R^-1 is read only for a deferred last round (and
+      // by the FP64 form)
+      double* xd = (sizeof(W) == 8 || (defer && r == rounds - 1)) ? dbuf(P->off_x) : nullptr;
+      CK((cholesky<W>(st, l, G, tol, r, xd, buf(P->off_xw), l, status,
                       sizeof(W) == 4 ? (const float*)src : nullptr, rows, dbuf(P->off_gpart), ns)));
       if (defer && r == rounds - 1) break;
       const bool last_apply = r == rounds - 1 - (defer ? 1 : 0);

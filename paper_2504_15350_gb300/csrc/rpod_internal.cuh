@@ -55,16 +55,17 @@ template <typename T>
 cudaError_t sketch(cudaStream_t st, uint64_t seed, uint64_t stream_id, int64_t m,
                    int l, T* Lam, int64_t ld);
 
-// One-block Cholesky G = R^T R of the FP64 Gram G (l x l, ld = l) with a
-// rank-revealing pivot threshold, then X = R^{-1} on the kept directions
-// (zero rows and columns for dropped ones), written in double and in TW.
-// `round` is the CholeskyQR round (0 = first): for FP32 working types the
-// first round factors in FP32 and, when a pivot signals a condition number
-// beyond FP32 reach, a device-gated FP64 factorization takes over -- of the
-// Gram recomputed with FP64 products from Y (rows x l, ld rows) into the
-// nsplit partials at `part`, when Y is given.
+// One-block Cholesky G = R^T R of the Gram G (l x l, ld = l; FP64 for an
+// FP64 TW, FP32 for an FP32 TW; the FP32 kernel reads its upper triangle)
+// with a rank-revealing pivot threshold, then X = R^{-1} on the kept
+// directions (zero rows and columns for dropped ones), written in TW and,
+// when X is not null, in double.  `round` is the CholeskyQR round
+// (0 = first): for FP32 working types the first round factors in FP32 and,
+// when a pivot signals a condition number beyond FP32 reach, a device-gated
+// FP64 factorization takes over -- of the Gram recomputed with exact
+// products from Y (rows x l, ld rows) into the nsplit partials at `part`.
 template <typename TW>
-cudaError_t cholesky(cudaStream_t st, int l, const double* G, double tol, int round,
+cudaError_t cholesky(cudaStream_t st, int l, const void* G, double tol, int round,
                      double* X, TW* Xw, int ldxw, unsigned* status, const float* Y = nullptr,
                      int64_t rows = 0, double* part = nullptr, int nsplit = 0);
 

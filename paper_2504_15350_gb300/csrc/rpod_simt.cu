@@ -541,12 +541,13 @@ constexpr size_t kBlkSmem = (size_t)(128 * kBlkLd + 128 * 8) * sizeof(float);
 
 template <typename TW>
 __global__ void __launch_bounds__(256)
-k_cholesky_blk(int l, const double* __restrict__ G, float tol, int* gate, double* __restrict__ Xout,
+k_cholesky_blk(int l, const float* __restrict__ G, float tol, int* gate, double* __restrict__ Xout,
                TW* __restrict__ Xw, int ldxw, unsigned* status) {
   extern __shared__ __align__(16) float s_R[];  // [128][kBlkLd]: G, then R rows, then X
   float* s_X = s_R + 128 * kBlkLd;              // [128][8]: one block column of X
   __shared__ float s_d0[128];
   __shared__ float s_rd[128];
+  __shared__ float s_ri[128];  // 1 / R_jj (0 for a dropped column)
   __shared__ int s_keep[128];
   __shared__ int s_ill;
   __shared__ double red[32];
@@ -559,7 +560,7 @@ k_cholesky_blk(int l, const double* __restrict__ G, float tol, int* gate, double
     for (int u = 0; u < 16; ++u) {
       const int e = e0 + u * 256 + tid, i = e & 127, j = e >> 7;
       // upper triangle of G only (the exact-product Gram leaves the lower one unset)
-      v[u] = (i < l && j < l) ? (float)G[min(i, j) + max(i, j) * l] : 0.f;
+      v[u] = (i < l && j < l) ? G[min(i, j) + max(i, j) * l] : 0.f;
     }
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
@@ -569,9 +570,10 @@ k_cholesky_blk(int l, const double* __restrict__ G, float tol, int* gate, double
   }
   double dm = 0.0;
   if (tid < 128) {
-    const double g = tid < l ? G[tid + tid * l] : 0.0;
-    s_d0[tid] = (float)g;
+    const float g = tid < l ? G[tid + tid * l] : 0.f;
+    s_d0[tid] = g;
     s_rd[tid] = 0.f;
+    s_ri[tid] = 0.f;
     s_keep[tid] = 0;
     dm = g;
   }
@@ -594,8 +596,8 @@ k_cholesky_blk(int l, const double* __restrict__ G, float tol, int* gate, double
         const float d = A[t][t], d0 = s_d0[j];
         const bool keep = (j < l) && (d0 > 1e-30f) && (d0 > 1e-30f * gmax) && (d > tol * d0);
         if (j < l && d < 1e-4f * d0) ill = 1;
-        const float rd = keep ? sqrtf(d) : 0.f;
-        const float rinv = keep ? 1.f / rd : 0.f;
+        const float rinv = keep ? rsqrtf(d) : 0.f;
+        const float rd = d * rinv;
 #pragma unroll
         for (int b = 0; b < 8; ++b) A[t][b] = (b > t) ? A[t][b] * rinv : (b == t ? rd : 0.f);
 #pragma unroll
@@ -604,6 +606,7 @@ k_cholesky_blk(int l, const double* __restrict__ G, float tol, int* gate, double
           for (int b = t + 1; b < 8; ++b) A[a][b] -= A[t][a] * A[t][b];
         s_keep[j] = keep ? 1 : 0;
         s_rd[j] = rd;
+        s_ri[j] = rinv;
       }
       if (ill) s_ill = 1;
 #pragma unroll
@@ -616,8 +619,7 @@ k_cholesky_blk(int l, const double* __restrict__ G, float tol, int* gate, double
       // row block k: R_kj = R_kk^{-T} A_kj, forward substitution over rows t
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
-        const float rd = s_rd[k0 + t];
-        const float rinv = rd > 0.f ? 1.f / rd : 0.f;
+        const float rinv = s_ri[k0 + t];
 #pragma unroll
         for (int s = 0; s < t; ++s) {
           const float rst = s_R[(k0 + s) * kBlkLd + k0 + t];
@@ -665,8 +667,7 @@ k_cholesky_blk(int l, const double* __restrict__ G, float tol, int* gate, double
     if (tx == k && ty <= k) {
 #pragma unroll
       for (int b = 0; b < 8; ++b) {
-        const float rd = s_rd[k0 + b];
-        const float rinv = rd > 0.f ? 1.f / rd : 0.f;
+        const float rinv = s_ri[k0 + b];
 #pragma unroll
         for (int s = 0; s < b; ++s) {
           const float rsb = s_R[(k0 + s) * kBlkLd + k0 + b];
@@ -707,12 +708,13 @@ k_cholesky_blk(int l, const double* __restrict__ G, float tol, int* gate, double
 #pragma unroll
     for (int b = 0; b < 8; ++b) s_R[(c0 + b) * kBlkLd + r0 + a] = (r0 + a <= c0 + b) ? W[a][b] : 0.f;
   __syncthreads();
-  for (int e = tid; e < l * l; e += 256) {
-    const int i = e % l, j = e / l;
-    const float v = s_R[j * kBlkLd + i];
-    Xout[e] = (double)v;
-    Xw[i + (int64_t)j * ldxw] = (TW)v;
-  }
+  // column j by warp j % 8 (no index division); the FP64 copy only when asked
+  for (int j = tid >> 5; j < l; j += 8)
+    for (int i = tid & 31; i < l; i += 32) {
+      const float v = s_R[j * kBlkLd + i];
+      if (Xout) Xout[i + j * l] = (double)v;
+      Xw[i + (int64_t)j * ldxw] = (TW)v;
+    }
   if (tid == 0) {
     int ndropped = 0;
     for (int j = 0; j < l; ++j) ndropped += s_keep[j] ? 0 : 1;
@@ -818,10 +820,12 @@ k_gram_df_gated(int64_t rows, int l, const float* __restrict__ Y, int64_t ldy, i
 }
 
 template <typename TW>
-cudaError_t cholesky(cudaStream_t st, int l, const double* G, double tol, int round, double* X,
+cudaError_t cholesky(cudaStream_t st, int l, const void* Gv, double tol, int round, double* X,
                      TW* Xw, int ldxw, unsigned* status, const float* Y, int64_t rows,
                      double* part, int nsplit) {
-  if (sizeof(TW) == 8) return launch_cholesky<double, double, TW>(st, l, G, tol, X, Xw, ldxw, status);
+  if (sizeof(TW) == 8)
+    return launch_cholesky<double, double, TW>(st, l, (const double*)Gv, tol, X, Xw, ldxw, status);
+  const float* G = (const float*)Gv;
   // the gate word sits next to the status word (same 256-byte status block)
   int* gate = (int*)(status + 2);
   prepare_kernels();
@@ -829,6 +833,8 @@ cudaError_t cholesky(cudaStream_t st, int l, const double* G, double tol, int ro
                                        status);
   note_launch();
   if (round != 0) return cudaGetLastError();
+  // the FP64 refactorization needs the exact-product Gram of Y
+  if (!(Y && part && nsplit > 0)) return cudaGetLastError();
   const double* gp = nullptr;
   if (Y && part && nsplit > 0) {
     int64_t chunk = (rows + nsplit - 1) / nsplit;
@@ -841,7 +847,7 @@ cudaError_t cholesky(cudaStream_t st, int l, const double* G, double tol, int ro
     gp = part;
   }
   const size_t sm64 = (size_t)l * (l + 1) * sizeof(double) + 16 + (size_t)l * (sizeof(double) + sizeof(float));
-  k_cholesky64_gated<TW><<<1, 256, sm64, st>>>(l, G, 1e-13, gate, X, Xw, ldxw, status, gp, nsplit);
+  k_cholesky64_gated<TW><<<1, 256, sm64, st>>>(l, nullptr, 1e-13, gate, X, Xw, ldxw, status, gp, nsplit);
   note_launch();
   return cudaGetLastError();
 }
@@ -926,7 +932,7 @@ k_cholesky64_gated(int l, const double* __restrict__ G, double tol, int* gate,
   for (int e = tid; e < l * l; e += nt) {
     const int i = e % l, j = e / l;
     const double v = (i <= j) ? A[i + j * ld] : 0.0;
-    Xout[e] = v;
+    if (Xout) Xout[e] = v;
     Xw[i + (int64_t)j * ldxw] = (TW)v;
   }
   if (tid == 0) {
@@ -935,8 +941,8 @@ k_cholesky64_gated(int l, const double* __restrict__ G, double tol, int* gate,
   }
   (void)tol;
 }
-template cudaError_t cholesky<double>(cudaStream_t, int, const double*, double, int, double*, double*, int, unsigned*, const float*, int64_t, double*, int);
-template cudaError_t cholesky<float>(cudaStream_t, int, const double*, double, int, double*, float*, int, unsigned*, const float*, int64_t, double*, int);
+template cudaError_t cholesky<double>(cudaStream_t, int, const void*, double, int, double*, double*, int, unsigned*, const float*, int64_t, double*, int);
+template cudaError_t cholesky<float>(cudaStream_t, int, const void*, double, int, double*, float*, int, unsigned*, const float*, int64_t, double*, int);
 
 // ------------------------------------------------------------------------
 // Symmetric eigensolver for the small SVD.  T T^T = Uhat Sigma^2 Uhat^T, so
