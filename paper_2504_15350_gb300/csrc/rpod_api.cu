@@ -155,8 +155,10 @@ struct Run {
     bool used;
   };
 
+  // `ld`: leading dimension of in and tmp (rows when 0).
   int orth(W* in, W* tmp, int64_t rows, int rounds, W** out, bool exact_last, bool defer = false,
-           TcOut* tco = nullptr) {
+           TcOut* tco = nullptr, int64_t ld = 0) {
+    if (ld == 0) ld = rows;
     const int l = P->l;
     const double tol = sizeof(W) == 8 ? 1e-13 : 1e-5;
     // FP32 Gram: two row chunks per SM (the kernel fits two blocks per SM)
@@ -166,23 +168,23 @@ struct Run {
     W* dst = tmp;
     for (int r = 0; r < rounds; ++r) {
       double* G = dbuf(P->off_g);
-      CR(gram(src, rows, rows, G, ns, !(exact_last && r == rounds - 1)));
+      CR(gram(src, rows, ld, G, ns, !(exact_last && r == rounds - 1)));
       // the FP64 copy of R^-1 is read only for a deferred last round (and
       // by the FP64 form)
       double* xd = (sizeof(W) == 8 || (defer && r == rounds - 1)) ? dbuf(P->off_x) : nullptr;
       CK((cholesky<W>(st, l, G, tol, r, xd, buf(P->off_xw), l, status,
-                      sizeof(W) == 4 ? (const float*)src : nullptr, rows, dbuf(P->off_gpart), ns)));
+                      sizeof(W) == 4 ? (const float*)src : nullptr, rows, dbuf(P->off_gpart), ns, ld)));
       if (defer && r == rounds - 1) break;
       const bool last_apply = r == rounds - 1 - (defer ? 1 : 0);
       int rc = RPOD_ERR_UNSUPPORTED;
       if (sizeof(W) == 4 && tco && last_apply)
-        rc = tc_apply(st, (const float*)src, rows, rows, l, (const float*)buf(P->off_xw), l,
+        rc = tc_apply(st, (const float*)src, ld, rows, l, (const float*)buf(P->off_xw), l,
                       tco->f32 ? (float*)dst : nullptr, rows, P->compute, tco->h16, P->n_ld,
                       tco->tf, P->n_ld, status);
       if (rc == RPOD_ERR_CUDA) return rc;
       if (tco && last_apply) tco->used = rc == RPOD_OK;
       if (rc != RPOD_OK)
-        CK((gemm<W, W, W, W>(st, false, rows, l, l, 1, src, rows, buf(P->off_xw), l, dst, 1, rows, 0,
+        CK((gemm<W, W, W, W>(st, false, rows, l, l, 1, src, ld, buf(P->off_xw), l, dst, 1, ld, 0,
                              status, false)));
       W* t = src; src = dst; dst = t;
     }
@@ -367,10 +369,13 @@ struct Run {
         prof_begin(P, st);
         CR(tc_wpass(st, dt, Qh, nld, n, l, Sh, ldh, m, wpart, P->nsplit_w, status));
         prof_end(P, st, pb16, pass_flops);
-        CK((reduce_splits<float, float>(st, m, l, P->nsplit_w, wpart, Z, 1, m)));
+        // Z with a 16-byte aligned leading dimension, so that its Gram
+        // takes the tensor-core path at any m
+        const int64_t m4 = round_up(m, 4);
+        CK((reduce_splits<float, float>(st, m, l, P->nsplit_w, wpart, Z, 1, m4)));
         float* Zo = nullptr;
-        CR(orth(Z, Zq, m, 1, &Zo, false));
-        CK(to16(Zo, m, m, Zh, mld));
+        CR(orth(Z, Zq, m, 1, &Zo, false, false, nullptr, m4));
+        CK(to16(Zo, m, m4, Zh, mld));
         prof_begin(P, st);
         CR(tc_ypass(st, dt, Zh, mld, Sh, ldh, n, m, l, Y, n, status));
         prof_end(P, st, pb16, pass_flops);
@@ -506,8 +511,8 @@ static int plan_create_impl(rpod_plan** out, int64_t n, int64_t m, int32_t k, in
   P->off_lam = take(w * m * L);
   P->off_y = take(w * n * L);
   P->off_q = take(w * n * L);
-  P->off_z = take(w * m * L);
-  P->off_zq = take(w * m * L);
+  P->off_z = take(w * round_up(m, 4) * L);
+  P->off_zq = take(w * round_up(m, 4) * L);
   P->off_tt = take(w * m * L);
   P->off_part = take(w * P->part_elems);
   P->off_gpart = take(8 * P->gpart_elems);

@@ -63,11 +63,12 @@ cudaError_t sketch(cudaStream_t st, uint64_t seed, uint64_t stream_id, int64_t m
 // (0 = first): for FP32 working types the first round factors in FP32 and,
 // when a pivot signals a condition number beyond FP32 reach, a device-gated
 // FP64 factorization takes over -- of the Gram recomputed with exact
-// products from Y (rows x l, ld rows) into the nsplit partials at `part`.
+// products from Y (rows x l, ld ldy, rows when 0) into the nsplit partials at
+// `part`.
 template <typename TW>
 cudaError_t cholesky(cudaStream_t st, int l, const void* G, double tol, int round,
                      double* X, TW* Xw, int ldxw, unsigned* status, const float* Y = nullptr,
-                     int64_t rows = 0, double* part = nullptr, int nsplit = 0);
+                     int64_t rows = 0, double* part = nullptr, int nsplit = 0, int64_t ldy = 0);
 
 // Symmetric eigen-decomposition of G (l x l, FP64): an FP32 start from the
 // tridiagonal reduction, then FP64 Ogita-Aishima refinement.  Outputs

@@ -822,7 +822,8 @@ k_gram_df_gated(int64_t rows, int l, const float* __restrict__ Y, int64_t ldy, i
 template <typename TW>
 cudaError_t cholesky(cudaStream_t st, int l, const void* Gv, double tol, int round, double* X,
                      TW* Xw, int ldxw, unsigned* status, const float* Y, int64_t rows,
-                     double* part, int nsplit) {
+                     double* part, int nsplit, int64_t ldy) {
+  if (ldy == 0) ldy = rows;
   if (sizeof(TW) == 8)
     return launch_cholesky<double, double, TW>(st, l, (const double*)Gv, tol, X, Xw, ldxw, status);
   const float* G = (const float*)Gv;
@@ -840,9 +841,9 @@ cudaError_t cholesky(cudaStream_t st, int l, const void* Gv, double tol, int rou
     int64_t chunk = (rows + nsplit - 1) / nsplit;
     chunk = (chunk + 31) / 32 * 32;
     if (l <= 64)
-      k_gram_df_gated<4><<<nsplit, 256, 0, st>>>(rows, l, Y, rows, chunk, part, gate);
+      k_gram_df_gated<4><<<nsplit, 256, 0, st>>>(rows, l, Y, ldy, chunk, part, gate);
     else
-      k_gram_df_gated<8><<<nsplit, 256, 0, st>>>(rows, l, Y, rows, chunk, part, gate);
+      k_gram_df_gated<8><<<nsplit, 256, 0, st>>>(rows, l, Y, ldy, chunk, part, gate);
     note_launch();
     gp = part;
   }
@@ -941,8 +942,8 @@ k_cholesky64_gated(int l, const double* __restrict__ G, double tol, int* gate,
   }
   (void)tol;
 }
-template cudaError_t cholesky<double>(cudaStream_t, int, const void*, double, int, double*, double*, int, unsigned*, const float*, int64_t, double*, int);
-template cudaError_t cholesky<float>(cudaStream_t, int, const void*, double, int, double*, float*, int, unsigned*, const float*, int64_t, double*, int);
+template cudaError_t cholesky<double>(cudaStream_t, int, const void*, double, int, double*, double*, int, unsigned*, const float*, int64_t, double*, int, int64_t);
+template cudaError_t cholesky<float>(cudaStream_t, int, const void*, double, int, double*, float*, int, unsigned*, const float*, int64_t, double*, int, int64_t);
 
 // ------------------------------------------------------------------------
 // Symmetric eigensolver for the small SVD.  T T^T = Uhat Sigma^2 Uhat^T, so
