@@ -1160,6 +1160,11 @@ int make_map(CUtensorMap* map, const void* ptr, int dt, int64_t rows, int64_t co
 
 constexpr int kBN = 256;
 constexpr int kStages = 4;
+// passes over less than 1 GiB (the instances of a batch) use two stages
+// (96 KB): two CTAs, of one pass or of two instances' passes, share an SM
+// and hide each other's pipeline fill and drain
+constexpr int kStagesSmall = 2;
+constexpr size_t kSmallPassBytes = (size_t)1 << 30;
 constexpr int kGramStages = 3;  // 96 KB: two CTAs per SM
 constexpr int kYcvtStages = 3;  // 192 KB
 constexpr int kGramXStages = 3;  // 144 KB of stages + 33 KB of sums
@@ -1190,6 +1195,12 @@ void prepare_kernels_tc() {
     cudaFuncSetAttribute(tc::k_wpass<2, kBN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     cudaFuncSetAttribute(tc::k_ypass<0, kBN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     cudaFuncSetAttribute(tc::k_ypass<1, kBN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    const int bs = (int)tc::Smem<kBN, kStagesSmall>::TOTAL;
+    cudaFuncSetAttribute(tc::k_wpass<0, kBN, kStagesSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize, bs);
+    cudaFuncSetAttribute(tc::k_wpass<1, kBN, kStagesSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize, bs);
+    cudaFuncSetAttribute(tc::k_wpass<2, kBN, kStagesSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize, bs);
+    cudaFuncSetAttribute(tc::k_ypass<0, kBN, kStagesSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize, bs);
+    cudaFuncSetAttribute(tc::k_ypass<1, kBN, kStagesSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize, bs);
     cudaFuncSetAttribute(tc::k_gram3<kGramStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tc::GramSmem<kGramStages>::TOTAL);
     cudaFuncSetAttribute(tc::k_gram_x<kGramXStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1224,18 +1235,35 @@ int tc_wpass(cudaStream_t st, int dt, const void* A, int64_t lda, int64_t n, int
   const int64_t ktiles = (n + bke - 1) / bke;
   const int kchunk = (int)((ktiles + nsplit - 1) / nsplit);
   dim3 grid((unsigned)((m + kBN - 1) / kBN), (unsigned)nsplit);
-  using L = tc::Smem<kBN, kStages>;
   prepare_kernels_tc();
-  switch (dt) {
-    case RPOD_BF16:
-      tc::k_wpass<0, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, kchunk, part, status);
-      break;
-    case RPOD_F16:
-      tc::k_wpass<1, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, kchunk, part, status);
-      break;
-    default:
-      tc::k_wpass<2, kBN, kStages><<<grid, 192, L::TOTAL, st>>>(ta, ts, n, m, l, kchunk, part, status);
-      break;
+  const bool small = (size_t)n * (size_t)m * (size_t)esize(dt) < kSmallPassBytes;
+  using L = tc::Smem<kBN, kStages>;
+  using Ls = tc::Smem<kBN, kStagesSmall>;
+  const unsigned nt = dt == RPOD_F32 ? 192 : 128;
+  if (small) {
+    switch (dt) {
+      case RPOD_BF16:
+        tc::k_wpass<0, kBN, kStagesSmall><<<grid, nt, Ls::TOTAL, st>>>(ta, ts, n, m, l, kchunk, part, status);
+        break;
+      case RPOD_F16:
+        tc::k_wpass<1, kBN, kStagesSmall><<<grid, nt, Ls::TOTAL, st>>>(ta, ts, n, m, l, kchunk, part, status);
+        break;
+      default:
+        tc::k_wpass<2, kBN, kStagesSmall><<<grid, nt, Ls::TOTAL, st>>>(ta, ts, n, m, l, kchunk, part, status);
+        break;
+    }
+  } else {
+    switch (dt) {
+      case RPOD_BF16:
+        tc::k_wpass<0, kBN, kStages><<<grid, nt, L::TOTAL, st>>>(ta, ts, n, m, l, kchunk, part, status);
+        break;
+      case RPOD_F16:
+        tc::k_wpass<1, kBN, kStages><<<grid, nt, L::TOTAL, st>>>(ta, ts, n, m, l, kchunk, part, status);
+        break;
+      default:
+        tc::k_wpass<2, kBN, kStages><<<grid, nt, L::TOTAL, st>>>(ta, ts, n, m, l, kchunk, part, status);
+        break;
+    }
   }
   note_launch();
   return cudaGetLastError() == cudaSuccess ? RPOD_OK : RPOD_ERR_CUDA;
@@ -1248,12 +1276,21 @@ int tc_ypass(cudaStream_t st, int dt, const void* A, int64_t lda, const void* S,
   if (int rc = make_map(&ta, A, dt, m, l, lda, 64, 128)) return rc;
   if (int rc = make_map(&ts, S, dt, n, m, lds, 64, 64)) return rc;
   dim3 grid((unsigned)((n + kBN - 1) / kBN));
-  using L = tc::Smem<kBN, kStages>;
   prepare_kernels_tc();
-  if (dt == RPOD_BF16)
-    tc::k_ypass<0, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, Y, ldy, status);
-  else
-    tc::k_ypass<1, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, Y, ldy, status);
+  const bool small = (size_t)n * (size_t)m * 2 < kSmallPassBytes;
+  using L = tc::Smem<kBN, kStages>;
+  using Ls = tc::Smem<kBN, kStagesSmall>;
+  if (small) {
+    if (dt == RPOD_BF16)
+      tc::k_ypass<0, kBN, kStagesSmall><<<grid, 128, Ls::TOTAL, st>>>(ta, ts, n, m, l, Y, ldy, status);
+    else
+      tc::k_ypass<1, kBN, kStagesSmall><<<grid, 128, Ls::TOTAL, st>>>(ta, ts, n, m, l, Y, ldy, status);
+  } else {
+    if (dt == RPOD_BF16)
+      tc::k_ypass<0, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, Y, ldy, status);
+    else
+      tc::k_ypass<1, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, Y, ldy, status);
+  }
   note_launch();
   return cudaGetLastError() == cudaSuccess ? RPOD_OK : RPOD_ERR_CUDA;
 }
