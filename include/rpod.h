@@ -200,7 +200,7 @@ int rpod_batch_workspace_bytes(const rpod_batch* batch, size_t* bytes);
 /* Enqueues the whole batch on `stream` (graph capture on first use). */
 int rpod_batch_run(rpod_batch* batch, void* workspace, size_t workspace_bytes, void* stream);
 /* Autotuner: times the candidate launch configurations (worker streams in
- * {1, 2, 4, 8, 16, 32, 64} x split-K scale in {1/2, 1, 2} of the passes' default
+ * {1, 2, 4, 8, 16, 32, 64} x split-K scale in {1/4, 1/2, 1, 2} of the passes' default
  * split) `trials` times each with CUDA events on `stream` (synchronising),
  * keeps the fastest, re-captures, and returns it through best_streams and
  * best_split_pct (may be NULL).  Runs the batch many times: outputs hold the

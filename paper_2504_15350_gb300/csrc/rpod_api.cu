@@ -900,7 +900,7 @@ int rpod_batch_tune(rpod_batch* B, void* workspace, size_t workspace_bytes, void
   if (!B || trials < 1) return RPOD_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   const int stream_opts[7] = {1, 2, 4, 8, 16, 32, 64};
-  const int split_opts[3] = {50, 100, 200};
+  const int split_opts[4] = {25, 50, 100, 200};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return RPOD_ERR_CUDA;
   float best = 1e30f;
@@ -908,7 +908,7 @@ int rpod_batch_tune(rpod_batch* B, void* workspace, size_t workspace_bytes, void
   int rc = RPOD_OK;
   for (int a = 0; a < 7 && rc == RPOD_OK; ++a) {
     if (stream_opts[a] > std::max(1, B->count)) continue;
-    for (int b = 0; b < 3 && rc == RPOD_OK; ++b) {
+    for (int b = 0; b < 4 && rc == RPOD_OK; ++b) {
       rc = rpod_batch_configure(B, stream_opts[a], split_opts[b]);
       if (rc == RPOD_OK) rc = rpod_batch_run(B, workspace, workspace_bytes, stream);  // capture + warm
       if (rc != RPOD_OK) break;
