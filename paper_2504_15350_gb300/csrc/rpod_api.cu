@@ -239,7 +239,16 @@ struct Run {
     // GB300).  off_xw (l x l in W) is free after fold_t.
     W* Uw = buf(P->off_xw);
     CK((convert_matrix<double, W>(st, l, ku, Ul, l, Uw, l)));
-    CK((gemm<W, W, W, W>(st, false, n, ku, l, 1, Q, n, Uw, l, U, 1, ldu, 0, status, false)));
+    // 16-bit forms: the lift on the tensor cores with a hi/lo TF32 split of
+    // both operands (about 2^-21 relative error); the plain forms, or a basis
+    // that TMA cannot address, on the SIMT pipes
+    int rc = RPOD_ERR_UNSUPPORTED;
+    if (sizeof(W) == 4 && is16(P->compute))
+      rc = tc_apply(st, (const float*)Q, n, n, l, (const float*)Uw, l, (float*)U, ldu, 0, nullptr, 0,
+                    nullptr, 0, status, ku, true);
+    if (rc == RPOD_ERR_CUDA) return rc;
+    if (rc != RPOD_OK)
+      CK((gemm<W, W, W, W>(st, false, n, ku, l, 1, Q, n, Uw, l, U, 1, ldu, 0, status, false)));
     CK((sign_fix<W>(st, n, ku, U, ldu, Uhat, l, ws + P->off_sign, P->sign_bytes)));
     // Sec. 4.3 coefficients C = U_k^T S = Uhat_k^T T (k x m), Uhat with the signs
     CK((convert_matrix<double, W>(st, l, k, Uhat, l, Uw, l)));

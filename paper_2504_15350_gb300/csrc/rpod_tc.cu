@@ -903,21 +903,24 @@ k_ypass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 // TMEM accumulators, and warps 6-9 drain the other accumulator and write any
 // of: Q (FP32), Q rounded to the 16-bit type (the next W-pass operand), Q
 // rounded to TF32 (the refinement pass operand).
-template <int STAGES>
+// SPLIT = 2 (the lift U = Q1 (X2 Uhat) of the returned basis): both operands
+// split into TF32 hi and lo parts and three products (lo hi, hi lo, hi hi),
+// about 2^-21 relative error per entry.
+template <int STAGES, int SPLIT>
 struct ApplySmem {
-  static constexpr uint32_t KB = 128 * 32 * 4;  // 128 rows x 32 columns of FP32
-  static constexpr uint32_t STAGE = 2 * KB;     // raw TMA tile + converted operand
-  static constexpr uint32_t XOP = 4 * KB;       // X: 4 k-blocks x 128 (j) x 32 (k)
+  static constexpr uint32_t KB = 128 * 32 * 4;   // 128 rows x 32 columns of FP32
+  static constexpr uint32_t STAGE = (1 + SPLIT) * KB;  // raw TMA tile + converted parts
+  static constexpr uint32_t XOP = SPLIT * 4 * KB;  // X parts: 4 k-blocks x 128 (j) x 32 (k)
   static constexpr uint32_t BARS = STAGES * STAGE + XOP;
   static constexpr size_t TOTAL = 1024 + (size_t)BARS + 256;
 };
 
-template <int KIND16, int STAGES>
+template <int KIND16, int STAGES, int SPLIT>
 __global__ void __launch_bounds__(320, 1)
 k_apply_tf32(const __grid_constant__ CUtensorMap tmY, const float* __restrict__ X, int64_t ldx,
-             int64_t n, int l, float* __restrict__ Q, int64_t ldq, void* __restrict__ Qh,
+             int64_t n, int l, int ncol, float* __restrict__ Q, int64_t ldq, void* __restrict__ Qh,
              int64_t ldh, float* __restrict__ Qt, int64_t ldt, unsigned* status) {
-  using L = ApplySmem<STAGES>;
+  using L = ApplySmem<STAGES, SPLIT>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* xop = smem + STAGES * L::STAGE;
@@ -963,7 +966,7 @@ k_apply_tf32(const __grid_constant__ CUtensorMap tmY, const float* __restrict__ 
         const int e = e0 + u * 128 + ct;
         const int j = (e >> 3) & 127, k = (e >> 10) * 32 + 4 * (e & 7);
         v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (j < l && k < l) {
+        if (j < ncol && k < l) {
           const float* xc = X + (int64_t)j * ldx + k;
           if (vec) {
             v[u] = *reinterpret_cast<const float4*>(xc);
@@ -981,7 +984,12 @@ k_apply_tf32(const __grid_constant__ CUtensorMap tmY, const float* __restrict__ 
         const int kb = e >> 10, j = (e >> 3) & 127, c4 = e & 7;
         const float4 r = make_float4(tf32_rna(v[u].x), tf32_rna(v[u].y), tf32_rna(v[u].z),
                                      tf32_rna(v[u].w));
-        *(float4*)(xop + kb * L::KB + (j >> 3) * 1024 + (j & 7) * 128 + ((c4 ^ (j & 7)) << 4)) = r;
+        const uint32_t off = kb * L::KB + (j >> 3) * 1024 + (j & 7) * 128 + ((c4 ^ (j & 7)) << 4);
+        *(float4*)(xop + off) = r;
+        if (SPLIT == 2)
+          *(float4*)(xop + 4 * L::KB + off) =
+              make_float4(tf32_rna(v[u].x - r.x), tf32_rna(v[u].y - r.y), tf32_rna(v[u].z - r.z),
+                          tf32_rna(v[u].w - r.w));
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1024,12 +1032,17 @@ k_apply_tf32(const __grid_constant__ CUtensorMap tmY, const float* __restrict__ 
 #pragma unroll 2
         for (int e = ct; e < 128 * 8; e += 128) {
           const int m = e & 127, c4 = e >> 7;
-          float4 v;
-          v.x = tf32_rna(raw[(4 * c4 + 0) * 128 + m]);
-          v.y = tf32_rna(raw[(4 * c4 + 1) * 128 + m]);
-          v.z = tf32_rna(raw[(4 * c4 + 2) * 128 + m]);
-          v.w = tf32_rna(raw[(4 * c4 + 3) * 128 + m]);
-          *(float4*)(aop + (m >> 3) * 1024 + (m & 7) * 128 + ((c4 ^ (m & 7)) << 4)) = v;
+          float4 x, v;
+          x.x = raw[(4 * c4 + 0) * 128 + m];
+          x.y = raw[(4 * c4 + 1) * 128 + m];
+          x.z = raw[(4 * c4 + 2) * 128 + m];
+          x.w = raw[(4 * c4 + 3) * 128 + m];
+          v.x = tf32_rna(x.x); v.y = tf32_rna(x.y); v.z = tf32_rna(x.z); v.w = tf32_rna(x.w);
+          const uint32_t off = (m >> 3) * 1024 + (m & 7) * 128 + ((c4 ^ (m & 7)) << 4);
+          *(float4*)(aop + off) = v;
+          if (SPLIT == 2)
+            *(float4*)(aop + L::KB + off) = make_float4(tf32_rna(x.x - v.x), tf32_rna(x.y - v.y),
+                                                        tf32_rna(x.z - v.z), tf32_rna(x.w - v.w));
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
@@ -1050,9 +1063,17 @@ k_apply_tf32(const __grid_constant__ CUtensorMap tmY, const float* __restrict__ 
         tc_after();
         const uint32_t a = su32(smem + s * L::STAGE + L::KB), b = su32(xop + kb * L::KB);
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma<2>(d, sdesc(a + 32 * kk, 16, 1024), sdesc(b + 32 * kk, 16, 1024), id,
-                 (kb > 0 || kk > 0) ? 1u : 0u);
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
+          if (SPLIT == 2) {
+            // smallest terms first: lo hi, hi lo, then hi hi
+            mma<2>(d, sdesc(a + L::KB + 32 * kk, 16, 1024), sdesc(b + 32 * kk, 16, 1024), id, acc0);
+            mma<2>(d, sdesc(a + 32 * kk, 16, 1024), sdesc(b + 4 * L::KB + 32 * kk, 16, 1024), id, 1u);
+            mma<2>(d, sdesc(a + 32 * kk, 16, 1024), sdesc(b + 32 * kk, 16, 1024), id, 1u);
+          } else {
+            mma<2>(d, sdesc(a + 32 * kk, 16, 1024), sdesc(b + 32 * kk, 16, 1024), id, acc0);
+          }
+        }
         mma_commit(&empty[s]);
         issued = true;
       }
@@ -1072,14 +1093,14 @@ k_apply_tf32(const __grid_constant__ CUtensorMap tmY, const float* __restrict__ 
       tc_after();
       const int64_t t = blockIdx.x + (int64_t)lt * gridDim.x;
       const int64_t m = t * 128 + q * 32 + lane;
-      for (int cc = 0; cc < l; cc += 32) {
+      for (int cc = 0; cc < ncol; cc += 32) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 128 + cc), v);
         if (m < n) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
             const int j = cc + i;
-            if (j < l) {
+            if (j < ncol) {
               if (Q) Q[m + j * ldq] = v[i];
               if (Qt) Qt[m + j * ldt] = tf32_rna(v[i]);
               if (Qh) {
@@ -1169,6 +1190,7 @@ constexpr int kGramStages = 3;  // 96 KB: two CTAs per SM
 constexpr int kYcvtStages = 3;  // 192 KB
 constexpr int kGramXStages = 3;  // 144 KB of stages + 33 KB of sums
 constexpr int kApplyStages = 4;  // 128 KB of stages + 64 KB for X
+constexpr int kApply2Stages = 2;  // two-part form: 96 KB of stages + 128 KB for X
 
 int sm_count() {
   static int n = 0;
@@ -1208,9 +1230,11 @@ void prepare_kernels_tc() {
     const int yc = (int)tc::YcvtSmem<kYcvtStages>::TOTAL;
     cudaFuncSetAttribute(tc::k_ypass_cvt<0, kYcvtStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, yc);
     cudaFuncSetAttribute(tc::k_ypass_cvt<1, kYcvtStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, yc);
-    const int ap = (int)tc::ApplySmem<kApplyStages>::TOTAL;
-    cudaFuncSetAttribute(tc::k_apply_tf32<0, kApplyStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, ap);
-    cudaFuncSetAttribute(tc::k_apply_tf32<1, kApplyStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, ap);
+    const int ap = (int)tc::ApplySmem<kApplyStages, 1>::TOTAL;
+    cudaFuncSetAttribute(tc::k_apply_tf32<0, kApplyStages, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ap);
+    cudaFuncSetAttribute(tc::k_apply_tf32<1, kApplyStages, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ap);
+    const int ap2 = (int)tc::ApplySmem<kApply2Stages, 2>::TOTAL;
+    cudaFuncSetAttribute(tc::k_apply_tf32<0, kApply2Stages, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, ap2);
   });
 }
 
@@ -1336,22 +1360,26 @@ int tc_sm_count() { return sm_count(); }
 
 int tc_apply(cudaStream_t st, const float* Y, int64_t ldy, int64_t n, int l, const float* X,
              int64_t ldx, float* Q, int64_t ldq, int dt16, void* Qh, int64_t ldh, float* Qt,
-             int64_t ldt, unsigned* status) {
-  if (l < 1 || l > 128 || n < 1 || ldx < l) return RPOD_ERR_INVALID_ARG;
+             int64_t ldt, unsigned* status, int ncol, bool precise) {
+  if (ncol == 0) ncol = l;
+  if (l < 1 || l > 128 || ncol < 1 || ncol > 128 || n < 1 || ldx < l) return RPOD_ERR_INVALID_ARG;
   if (Qh && dt16 != RPOD_BF16 && dt16 != RPOD_F16) return RPOD_ERR_INVALID_ARG;
+  if (precise && (Qh || Qt)) return RPOD_ERR_INVALID_ARG;
   if ((Q && ldq < n) || (Qh && ldh < n) || (Qt && ldt < n)) return RPOD_ERR_INVALID_ARG;
   CUtensorMap ty;
   if (int rc = make_map(&ty, Y, RPOD_F32, n, l, ldy, 128, 32, false)) return rc;
   const int64_t ntiles = (n + 127) / 128;
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, sm_count());
-  using L = tc::ApplySmem<kApplyStages>;
   prepare_kernels_tc();
-  if (dt16 == RPOD_F16)
-    tc::k_apply_tf32<1, kApplyStages><<<grid, 320, L::TOTAL, st>>>(ty, X, ldx, n, l, Q, ldq, Qh, ldh, Qt,
-                                                                   ldt, status);
+  if (precise)
+    tc::k_apply_tf32<0, kApply2Stages, 2><<<grid, 320, tc::ApplySmem<kApply2Stages, 2>::TOTAL, st>>>(
+        ty, X, ldx, n, l, ncol, Q, ldq, Qh, ldh, Qt, ldt, status);
+  else if (dt16 == RPOD_F16)
+    tc::k_apply_tf32<1, kApplyStages, 1><<<grid, 320, tc::ApplySmem<kApplyStages, 1>::TOTAL, st>>>(
+        ty, X, ldx, n, l, ncol, Q, ldq, Qh, ldh, Qt, ldt, status);
   else
-    tc::k_apply_tf32<0, kApplyStages><<<grid, 320, L::TOTAL, st>>>(ty, X, ldx, n, l, Q, ldq, Qh, ldh, Qt,
-                                                                   ldt, status);
+    tc::k_apply_tf32<0, kApplyStages, 1><<<grid, 320, tc::ApplySmem<kApplyStages, 1>::TOTAL, st>>>(
+        ty, X, ldx, n, l, ncol, Q, ldq, Qh, ldh, Qt, ldt, status);
   note_launch();
   return cudaGetLastError() == cudaSuccess ? RPOD_OK : RPOD_ERR_CUDA;
 }

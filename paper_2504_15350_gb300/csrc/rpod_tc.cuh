@@ -43,15 +43,18 @@ int tc_gram(cudaStream_t st, const float* Y, int64_t ldy, int64_t rows, int l, d
 
 // CholeskyQR apply Q = Y X for Y n x l FP32 (column-major, ld ldy; base
 // 16-byte aligned, ldy a multiple of 4, else RPOD_ERR_UNSUPPORTED) and X
-// l x l FP32 (ld ldx), both rounded to TF32, one tensor-core product with
-// FP32 accumulation (about 2^-11 relative error per entry).  Writes each
-// output that is not null: Q (FP32, ld ldq), Q rounded to dt16 (RPOD_BF16 or
-// RPOD_F16) into Qh (ld ldh), Q rounded to TF32 into Qt (ld ldt).  Meant for
-// bases that are rounded to 16 bits next or re-orthonormalised from an exact
-// Gram; l <= 128.
+// l x ncol FP32 (ld ldx; ncol = l when 0, at most 128).  Default: both
+// rounded to TF32, one tensor-core product with FP32 accumulation (about
+// 2^-11 relative error per entry); writes each output that is not null: Q
+// (FP32, ld ldq), Q rounded to dt16 (RPOD_BF16 or RPOD_F16) into Qh (ld ldh),
+// Q rounded to TF32 into Qt (ld ldt) -- for bases that are rounded to 16 bits
+// next or re-orthonormalised from an exact Gram.  With `precise` both
+// operands are split into TF32 hi and lo parts and three products are summed
+// (about 2^-21 relative error), Q only -- for the lift of the returned basis.
+// l <= 128.
 int tc_apply(cudaStream_t st, const float* Y, int64_t ldy, int64_t n, int l, const float* X,
              int64_t ldx, float* Q, int64_t ldq, int dt16, void* Qh, int64_t ldh, float* Qt,
-             int64_t ldt, unsigned* status);
+             int64_t ldt, unsigned* status, int ncol = 0, bool precise = false);
 
 // Streaming multiprocessors of the current device.
 int tc_sm_count();
