@@ -81,7 +81,10 @@ typedef struct rpod_plan rpod_plan;
  * l = k + p <= min(n, m, 128).  `seed` keys the Philox4x64-10 stream of the
  * sketch: entry (i, j) of Lambda uses the counter (e/2, 0, 0, 0), e = i + j*m,
  * under the key (seed, 0), and a Box-Muller transform (z0 for even e, z1 for
- * odd e).  `compute` is an rpod_dtype.  The plan is host memory only.
+ * odd e).  `compute` is an rpod_dtype.  The plan owns no device memory; a
+ * plan of a 16-bit compute type holds a CUDA stream and two events of the
+ * device current at creation (the last CholeskyQR round runs on that stream
+ * beside the refinement pass) and is used on that device.
  * Errors: RPOD_ERR_INVALID_ARG for bad sizes or a NULL `out`. */
 int rpod_plan_create(rpod_plan** out, int64_t n, int64_t m, int32_t k, int32_t p,
                      int32_t q, uint64_t seed, int32_t compute, uint32_t flags);
@@ -192,7 +195,8 @@ typedef struct rpod_instance {
 typedef struct rpod_batch rpod_batch;
 
 /* Creates a batch of `count` instances (copied; compute and flags as for
- * rpod_plan_create, s_dtype as for rpod_basis).  Host memory only.
+ * rpod_plan_create, s_dtype as for rpod_basis).  No device memory (16-bit
+ * instances hold a stream and two events each, as their plans do).
  * RPOD_ERR_INVALID_ARG if any instance is invalid for rpod_plan_create. */
 int rpod_batch_create(rpod_batch** out, int32_t count, const rpod_instance* inst,
                       int32_t compute, uint32_t flags, int32_t s_dtype);

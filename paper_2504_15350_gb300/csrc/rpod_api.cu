@@ -39,6 +39,10 @@ struct rpod_plan {
   int prof_n;
   cudaEvent_t prof_ev[2 * 64];
   double prof_bytes, prof_flops;
+  // side stream and fork/join events (16-bit forms: the last CholeskyQR
+  // round runs beside the refinement pass); null when they could not be made
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
 };
 
 namespace rpod {
@@ -189,6 +193,20 @@ struct Run {
       W* t = src; src = dst; dst = t;
     }
     *out = src;
+    return RPOD_OK;
+  }
+
+  // The deferred last CholeskyQR round of the basis Q1 (rows x l, ld rows):
+  // exact Gram and its factor X2 = R2^{-1} (in off_x and off_xw), no apply.
+  int last_factor(const W* Q1, int64_t rows) {
+    const int l = P->l;
+    const double tol = sizeof(W) == 8 ? 1e-13 : 1e-5;
+    const int ns = sizeof(W) == 8 ? splits_for(rows, 4096, 256)
+                                  : (int)std::max<int64_t>(1, std::min<int64_t>(2 * 152, rows / 256));
+    double* G = dbuf(P->off_g);
+    CR(gram(Q1, rows, rows, G, ns, false));
+    CK((cholesky<W>(st, l, G, tol, 1, dbuf(P->off_x), buf(P->off_xw), l, status,
+                    sizeof(W) == 4 ? (const float*)Q1 : nullptr, rows, dbuf(P->off_gpart), ns, rows)));
     return RPOD_OK;
   }
 
@@ -393,10 +411,33 @@ struct Run {
       // and rounded to TF32 for the refinement pass; intermediate ones are
       // needed only as the 16-bit operand of the next W-pass
       TcOut tco{it < q ? Qh : nullptr, it == q && refine_tma ? Atf : nullptr, it == q, false};
-      CR(orth(Y, Qbuf, n, it == q ? 2 : 1, &Q, it == q, it == q, &tco));
+      if (it == q && P->side) {
+        // first round only: the exact second round (which fixes the returned
+        // basis' orthogonality, not the span the refinement pass reads) runs
+        // on the side stream beside the refinement pass
+        CR(orth(Y, Qbuf, n, 1, &Q, false, false, &tco));
+      } else {
+        CR(orth(Y, Qbuf, n, it == q ? 2 : 1, &Q, it == q, it == q, &tco));
+      }
       if (it < q && !tco.used) CK(to16(Q, n, n, Qh, nld));
       tf_ready = it == q && tco.used && refine_tma;
     }
+    bool forked = false;
+    if (P->side) {
+      CK(cudaEventRecord(P->ev_fork, st));
+      CK(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
+      cudaStream_t main_st = st;
+      st = P->side;
+      const int rc = last_factor(Q, n);
+      st = main_st;
+      CR(rc);
+      CK(cudaEventRecord(P->ev_join, P->side));
+      forked = true;
+    }
+    // join before the factor is used (fold_t, finish)
+    auto join = [&]() -> cudaError_t {
+      return forked ? cudaStreamWaitEvent(st, P->ev_join, 0) : cudaSuccess;
+    };
     // Alg. 1: T = Q^T S (TF32 from the FP32 copy when refining)
     const bool refine = refine_req;
     const bool ref_tma = refine_tma;
@@ -407,6 +448,7 @@ struct Run {
                                            (float*)buf(P->off_part), 1, m, m * l, status, false)));
       prof_end(P, st, 4.0 * ((double)n * m + (double)n * l + (double)m * l), pass_flops);
       CK((reduce_splits<float, float>(st, m, l, P->nsplit_z, (float*)buf(P->off_part), Zq, 1, m)));
+      CK(join());
       CR(fold_t(Zq, Tt));
       return finish(Q, Tt, U, ldu, sigma, C, ldc, true);
     }
@@ -422,6 +464,7 @@ struct Run {
       prof_end(P, st, pb16, pass_flops);
     }
     CK((reduce_splits<float, float>(st, m, l, P->nsplit_w, wpart, Zq, 1, m)));
+    CK(join());
     CR(fold_t(Zq, Tt));
     return finish(Q, Tt, U, ldu, sigma, C, ldc, true);
   }
@@ -550,6 +593,20 @@ static int plan_create_impl(rpod_plan** out, int64_t n, int64_t m, int32_t k, in
     P->off_wpart = take(4 * P->wpart_elems);
   }
   P->total = off;
+  P->side = nullptr;
+  if (is16(compute)) {
+    // made here (not during a call, which may be inside a stream capture);
+    // without a device the fork is skipped
+    cudaStream_t ss = nullptr;
+    if (cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking) == cudaSuccess) {
+      if (cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+          cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) == cudaSuccess)
+        P->side = ss;
+      else
+        cudaStreamDestroy(ss);
+    }
+    cudaGetLastError();
+  }
   P->last_launches = 0;
   *out = P;
   return RPOD_OK;
@@ -570,6 +627,11 @@ int rpod_profile_enable(rpod_plan* P, int enable);
 
 void rpod_plan_destroy(rpod_plan* P) {
   if (P && P->prof_on) rpod_profile_enable(P, 0);
+  if (P && P->side) {
+    cudaEventDestroy(P->ev_fork);
+    cudaEventDestroy(P->ev_join);
+    cudaStreamDestroy(P->side);
+  }
   delete P;
 }
 
