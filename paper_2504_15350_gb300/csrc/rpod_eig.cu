@@ -26,8 +26,9 @@
 //   4. Vectors of eigenvalues closer than 1e-5 ||T|| are orthogonalised
 //      against each other (Gram-Schmidt in ascending order); a
 //      vector that loses more than half its norm there (a multiple
-//      eigenvalue) is replaced by a pseudo-random vector orthogonalised
-//      against all others.  Vectors of eigenvalues further apart come out
+//      eigenvalue) is replaced by inverse iteration with T - lambda I from
+//      a pseudo-random vector, orthogonalised against the cluster's other
+//      vectors.  Vectors of eigenvalues further apart come out
 //      of step 3 orthogonal to a few 1e-5 at most, which the refinement
 //      removes.
 //   5. Back-transformation X = H Z, column by column, each column held in
@@ -401,14 +402,20 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
   // cluster, two classical Gram-Schmidt passes against the cluster's
   // earlier (already orthonormal) vectors: the dots by one warp each, the
   // update by 16 threads per row.  A vector that loses more than half its
-  // norm (a multiple eigenvalue) is replaced by a pseudo-random vector
-  // that warp 0 orthogonalises against all others by modified Gram-Schmidt
-  // (the cluster's later vectors may still coincide, which classical
-  // Gram-Schmidt would subtract twice).  The forward-pivot array is free
-  // again and holds the dot products.
+  // norm (a multiple eigenvalue) is replaced by warp 0: inverse iteration
+  // with T - lambda I from a pseudo-random vector, which keeps the
+  // replacement in its own cluster's invariant subspace (orthogonalising a
+  // random vector against all other vectors does not: while another
+  // cluster still holds a duplicate, that complement mixes both clusters'
+  // missing directions), then modified Gram-Schmidt against the cluster's
+  // processed vectors.  The forward-pivot array is free again and holds the
+  // dot products.
   {
     float* const dts = Ws;
     __shared__ float s_n2;
+    // inverse iteration of a replaced vector: LU of T - lambda I and the vector
+    __shared__ float s_d[kMaxL], s_du[kMaxL], s_dl[kMaxL], s_du2[kMaxL], s_iv[kMaxL];
+    __shared__ int s_piv[kMaxL];
     // eigenvalues closer than 1e-15 are one cluster even in a (near) zero matrix
     const float ctol = fmaxf(1e-5f * fmaxf(fabsf(lam[0]), fabsf(lam[l - 1])), 1e-15f);
     const int part = tid & 15, rsub = tid >> 4;
@@ -443,17 +450,85 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
           for (int r = lane; r < l; r += 32) n2 = fmaf(Xs[r * ldx + a], Xs[r * ldx + a], n2);
           n2 = warp_sum(n2);
           if (n2 < 0.25f) {
+            // a multiple eigenvalue: two steps of inverse iteration with
+            // T - lambda_a I from a pseudo-random vector (the cluster's own
+            // invariant subspace grows by about 1/eps against every other
+            // eigenvector), then Gram-Schmidt against the cluster's
+            // processed vectors
             ++nrep;
+            const float lm = lam[a];
+            for (int r = lane; r < l; r += 32) {
+              const uint32_t hsh = mix32((uint32_t)(a * 131 + r) * 2654435761u + 12345u);
+              s_iv[r] = (float)(hsh >> 8) * (1.f / 8388608.f) - 1.f;
+            }
+            __syncwarp();
+            if (lane == 0) {
+              // LU with partial pivoting of the tridiagonal T - lm I
+              const float tn = fmaxf(fmaxf(fabsf(lam[0]), fabsf(lam[l - 1])), 1e-30f);
+              const float tiny = FLT_EPSILON * tn;
+              for (int k = 0; k < l; ++k) {
+                s_d[k] = dd[k] - lm;
+                s_du[k] = k + 1 < l ? ee[k] : 0.f;
+                s_dl[k] = k + 1 < l ? ee[k] : 0.f;
+                s_du2[k] = 0.f;
+                s_piv[k] = 0;
+              }
+              for (int k = 0; k + 1 < l; ++k) {
+                if (fabsf(s_d[k]) >= fabsf(s_dl[k])) {
+                  if (!(fabsf(s_d[k]) >= tiny)) s_d[k] = s_d[k] < 0.f ? -tiny : tiny;
+                  const float f = s_dl[k] / s_d[k];
+                  s_dl[k] = f;
+                  s_d[k + 1] -= f * s_du[k];
+                } else {
+                  const float f = s_d[k] / s_dl[k];
+                  s_d[k] = s_dl[k];
+                  s_dl[k] = f;
+                  const float t = s_du[k];
+                  s_du[k] = s_d[k + 1];
+                  s_d[k + 1] = t - f * s_d[k + 1];
+                  if (k + 2 < l) {
+                    s_du2[k] = s_du[k + 1];
+                    s_du[k + 1] = -f * s_du[k + 1];
+                  }
+                  s_piv[k] = 1;
+                }
+              }
+              // pivots below eps ||T|| are raised to it (a perturbation of
+              // T at rounding level) so the solves cannot overflow
+              for (int k = 0; k < l; ++k)
+                if (!(fabsf(s_d[k]) >= tiny)) s_d[k] = s_d[k] < 0.f ? -tiny : tiny;
+              for (int step = 0; step < 2; ++step) {
+                for (int k = 0; k + 1 < l; ++k) {
+                  if (s_piv[k]) {
+                    const float t = s_iv[k];
+                    s_iv[k] = s_iv[k + 1];
+                    s_iv[k + 1] = t - s_dl[k] * s_iv[k + 1];
+                  } else {
+                    s_iv[k + 1] -= s_dl[k] * s_iv[k];
+                  }
+                }
+                float mx = 0.f;
+                for (int k = l - 1; k >= 0; --k) {
+                  float v = s_iv[k];
+                  if (k + 1 < l) v -= s_du[k] * s_iv[k + 1];
+                  if (k + 2 < l) v -= s_du2[k] * s_iv[k + 2];
+                  v /= s_d[k];
+                  s_iv[k] = v;
+                  mx = fmaxf(mx, fabsf(v));
+                }
+                const float sc = mx > 0.f && mx <= FLT_MAX ? 1.f / mx : 0.f;
+                for (int k = 0; k < l; ++k) s_iv[k] = sc > 0.f ? s_iv[k] * sc : (k == a ? 1.f : 0.f);
+              }
+            }
+            __syncwarp();
             float xa[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const int r = lane + 32 * u;
-              const uint32_t hsh = mix32((uint32_t)(a * 131 + r) * 2654435761u + 12345u);
-              xa[u] = r < l ? (float)(hsh >> 8) * (1.f / 8388608.f) - 1.f : 0.f;
+              xa[u] = r < l ? s_iv[r] : 0.f;
             }
             for (int rep = 0; rep < 2; ++rep)
-              for (int b = 0; b < l; ++b) {
-                if (b == a) continue;
+              for (int b = start; b < a; ++b) {
                 float xb[4], dt = 0.f;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {

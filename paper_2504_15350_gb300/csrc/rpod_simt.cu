@@ -1045,7 +1045,12 @@ k_oa_update_dev(int l, const double* __restrict__ XtX, const double* __restrict_
   if (tid == 0) {
     float a = 0.f, b = 0.f;
     for (int k = 0; k < (nt >> 5); ++k) { a += rs[0][k]; b += rs[1][k]; }
-    s_delta = 2.0 * (sqrt((double)a) + (*normA) * sqrt((double)b));
+    // floor: once the passes have converged, delta falls to the rounding
+    // level, where the Rayleigh quotients of an exactly multiple eigenvalue
+    // differ by rounding alone; without the floor such a pair counts as
+    // separated and E divides by that difference
+    s_delta = fmax(2.0 * (sqrt((double)a) + (*normA) * sqrt((double)b)),
+                   64.0 * DBL_EPSILON * (double)l * (*normA));
   }
   __syncthreads();
   const double delta = s_delta;
