@@ -14,8 +14,10 @@ Modules
              convention.
   rpod    -- Alg. 1 step by step (sketch, subspace iterations with
              re-orthonormalisation, QR, T = Q^T S, SVD of T, lift) plus the
-             modal coefficients C = U_N^T S (Sec. 4.3) and deterministic POD
-             (Eq. (svd)).
+             modal coefficients C = U_N^T S (Sec. 4.3), deterministic POD
+             (Eq. (svd)), the per-sample time averages and fluctuation
+             snapshots (Eqs. (time_av), (fluct_q)) and the energy-based rank
+             (Eq. (energy)).
   lstm    -- LSTM forward, backpropagation through time and Adam in FP64.
 
 Every function is pinned by tests under tests/ against something other than

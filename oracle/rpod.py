@@ -121,9 +121,50 @@ def pod(S: np.ndarray, N: int):
 
 
 def energy_rank(sigma: np.ndarray, delta: float) -> int:
-    """Smallest N^r with sum_{i<=N} sigma_i / sum_i sigma_i >= delta, Eq. (energy)."""
-    c = np.cumsum(sigma) / np.sum(sigma)
-    return int(np.searchsorted(c, delta) + 1)
+    """Eq. (energy): the smallest N^r with sum_{i<=N} sigma_i / sum_i sigma_i
+    >= delta, over the singular values given (descending).  The denominator
+    is the last of the same sequential partial sums, so the ratio reaches
+    exactly 1 at the end; a spectrum with no positive sum retains nothing and
+    gives 0.  0 < delta <= 1 (the paper asks 0 < delta < 1)."""
+    s = np.asarray(sigma, dtype=np.float64)
+    if not 0.0 < delta <= 1.0:
+        raise ValueError("delta must lie in (0, 1]")
+    if s.size == 0:
+        return 0
+    c = np.cumsum(s)
+    total = c[-1]
+    if not total > 0.0:
+        return 0
+    for N in range(1, s.size + 1):
+        if c[N - 1] / total >= delta:
+            return N
+    return s.size
+
+
+def time_average(S: np.ndarray, nt: int) -> np.ndarray:
+    """Time-averaged fields of Eq. (time_av), one per parameter sample.  The
+    snapshot matrix holds M = m / nt samples of nt consecutive snapshots
+    (the column order of the matrix after Eq. (fluct_psi): by sample, then
+    time); column g of the n x M result is the mean of columns g*nt ..
+    g*nt + nt - 1."""
+    S = np.asarray(S, dtype=np.float64)
+    n, m = S.shape
+    if nt < 1 or m % nt != 0:
+        raise ValueError("nt must divide the number of snapshots")
+    M = m // nt
+    out = np.empty((n, M))
+    for g in range(M):
+        out[:, g] = S[:, g * nt:(g + 1) * nt].sum(axis=1) / nt
+    return out
+
+
+def fluctuations(S: np.ndarray, nt: int):
+    """Fluctuation snapshots of Eqs. (fluct_q), (fluct_psi): every snapshot
+    minus the time average of its own parameter sample.  Returns (F, Sbar)
+    with F n x m and Sbar the n x M time averages of Eq. (time_av)."""
+    S = np.asarray(S, dtype=np.float64)
+    Sbar = time_average(S, nt)
+    return S - np.repeat(Sbar, nt, axis=1), Sbar
 
 
 def max_principal_angle(A: np.ndarray, B: np.ndarray) -> float:
