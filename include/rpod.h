@@ -285,6 +285,51 @@ int rpod_lstm_rollout(rpod_lstm* net, const float* window, int32_t B, int32_t mu
 int rpod_lstm_last_launch_count(const rpod_lstm* net);
 void rpod_lstm_destroy(rpod_lstm* net);
 
+/* ---- Time averages, fluctuations and rank selection (Sec. 4.1) ----------
+ * The snapshot matrix S (n x m, element type s_dtype, leading dimension
+ * lds >= n) holds M = m / nt parameter samples of nt consecutive snapshots
+ * each (columns ordered by sample, then time, as in the matrix after
+ * Eq. (fluct_psi)); nt must divide m.  Computes the time average of every
+ * sample, Eq. (time_av),
+ *   Sbar(:, g) = (1/nt) sum_{p < nt} S(:, g nt + p),   g < M,
+ * into Sbar (n x M, ldb >= n; double for an FP64 S, float otherwise; rows
+ * summed with compensation in that type), and the fluctuation snapshots of
+ * Eqs. (fluct_q), (fluct_psi),
+ *   F(:, g nt + p) = S(:, g nt + p) - Sbar(:, g),
+ * (the difference formed in Sbar's type, then rounded to the output type)
+ * into F (ldf >= n, type f_dtype) and/or H (ldh >= n, type h_dtype); either
+ * may be NULL (Sbar alone when both are).  Supported types:
+ *   s_dtype F64:       F in F64; no H
+ *   s_dtype F32:       F in F32, BF16 or F16; H in BF16 or F16 (the 16-bit
+ *                      copy the tensor-core forms of rpod_basis read while F
+ *                      stays their FP32 refinement copy)
+ *   s_dtype BF16/F16:  F in the same type; no H
+ * F may be S itself (in place: same type and leading dimension); otherwise
+ * F, H, Sbar and S must not overlap.  One kernel, enqueued on `stream`; it
+ * reads S once from HBM (a tile of rows of one sample at a time staged in
+ * shared memory) unless a 128-byte-high tile of nt snapshots exceeds
+ * shared memory (about 1600 FP32 snapshots per sample), when S is read a
+ * second time for the write.  Non-finite entries propagate into the means of
+ * their rows.  Errors: RPOD_ERR_INVALID_ARG for bad sizes, leading dimensions,
+ * types or NULL S/Sbar, or F == S with another type or leading dimension;
+ * RPOD_ERR_UNSUPPORTED for a type combination not listed; RPOD_ERR_CUDA when
+ * the launch fails. */
+int rpod_fluctuations(int64_t n, int64_t m, int64_t nt, const void* S, int64_t lds,
+                      int32_t s_dtype, void* F, int64_t ldf, int32_t f_dtype, void* H,
+                      int64_t ldh, int32_t h_dtype, void* Sbar, int64_t ldb, void* stream);
+
+/* Energy-based rank of Eq. (energy) on the device: from `count` singular
+ * values (device array, double, descending, e.g. rpod_basis's sigma) writes
+ * to the device int *rank the smallest N with c_N / c_count >= delta, where
+ * c_N = sigma_1 + ... + sigma_N are summed sequentially in double; 0 when
+ * c_count is not positive.  With the l values of an rPOD the denominator is
+ * the energy of those l values only (the full sum over min(n, m) values of
+ * Eq. (energy) is exact when rank(S) <= l).  0 < delta <= 1.  One
+ * single-thread kernel on `stream`.  Errors: RPOD_ERR_INVALID_ARG for NULL
+ * pointers, count < 1 or delta outside (0, 1]. */
+int rpod_energy_rank(const double* sigma, int32_t count, double delta, int32_t* rank,
+                     void* stream);
+
 /* Synchronises `stream`, reads and clears the workspace status word.  Returns
  * the device-detected error (RPOD_OK if none) and stores warning bits in
  * *flags_out when it is not NULL. */

@@ -82,6 +82,9 @@ SIGNATURES = {
                                    ctypes.c_size_t, _p]),
     "rpod_project_static": (ctypes.c_int, [_p, _p, _c_i64, _c_i32, _p, _c_i64, _c_i64, _c_i32, _p,
                                            _c_i64, _p]),
+    "rpod_fluctuations": (ctypes.c_int, [_c_i64, _c_i64, _c_i64, _p, _c_i64, _c_i32, _p, _c_i64,
+                                         _c_i32, _p, _c_i64, _c_i32, _p, _c_i64, _p]),
+    "rpod_energy_rank": (ctypes.c_int, [_p, _c_i32, ctypes.c_double, _p, _p]),
     "rpod_profile_enable": (ctypes.c_int, [_p, ctypes.c_int]),
     "rpod_profile_read": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -176,6 +179,16 @@ def rpod_project_static(plan, U, ldu, kc, S_new, lds, m_new, s_dtype, C, ldc, st
     return load().rpod_project_static(plan, U, ldu, kc, S_new, lds, m_new, s_dtype, C, ldc, stream)
 
 
+def rpod_fluctuations(n, m, nt, S, lds, s_dtype, F, ldf, f_dtype, H, ldh, h_dtype, Sbar, ldb,
+                      stream):
+    return load().rpod_fluctuations(n, m, nt, S, lds, s_dtype, F, ldf, f_dtype, H, ldh, h_dtype,
+                                    Sbar, ldb, stream)
+
+
+def rpod_energy_rank(sigma, count, delta, rank, stream):
+    return load().rpod_energy_rank(sigma, count, delta, rank, stream)
+
+
 def rpod_profile_enable(plan, enable):
     return load().rpod_profile_enable(plan, int(enable))
 
@@ -253,6 +266,57 @@ def colmajor_ld(A) -> int:
 def empty_colmajor(rows, cols, dtype, device):
     torch = _torch()
     return torch.empty((cols, rows), dtype=dtype, device=device).t()
+
+
+def fluctuations(S, nt, f_dtype="same", h_dtype=None, in_place=False, out=None):
+    """Per-sample time averages and fluctuation snapshots (Eqs. (time_av),
+    (fluct_q)) of the column-major n x m tensor S holding m / nt samples of nt
+    snapshots.  Returns (F, H, Sbar): F in `f_dtype` ("same" for S's dtype, a
+    torch dtype, or None for no F; S itself when in_place), H a 16-bit copy
+    (h_dtype a torch dtype or None), Sbar n x (m / nt) (float64 for a float64
+    S, float32 otherwise).  `out` = (F, H, Sbar) reuses caller tensors."""
+    torch = _torch()
+    n, m = S.shape
+    if nt < 1 or m % nt:
+        raise ValueError("nt must divide the number of snapshots")
+    dev = S.device
+    if f_dtype == "same":
+        f_dtype = S.dtype
+    sb_dtype = torch.float64 if S.dtype == torch.float64 else torch.float32
+    if out is not None:
+        F, H, Sbar = out
+    else:
+        Sbar = empty_colmajor(n, m // nt, sb_dtype, dev)
+        if in_place:
+            F = S
+        else:
+            F = empty_colmajor(n, m, f_dtype, dev) if f_dtype is not None else None
+        H = empty_colmajor(n, m, h_dtype, dev) if h_dtype is not None else None
+    rc = rpod_fluctuations(n, m, nt, S.data_ptr(), colmajor_ld(S), dtype_code(S.dtype),
+                           F.data_ptr() if F is not None else None,
+                           colmajor_ld(F) if F is not None else 0,
+                           dtype_code(F.dtype) if F is not None else 0,
+                           H.data_ptr() if H is not None else None,
+                           colmajor_ld(H) if H is not None else 0,
+                           dtype_code(H.dtype) if H is not None else 0,
+                           Sbar.data_ptr(), colmajor_ld(Sbar),
+                           torch.cuda.current_stream(dev).cuda_stream)
+    _check(rc, "rpod_fluctuations")
+    return F, H, Sbar
+
+
+def energy_rank(sigma, delta, out=None):
+    """Eq. (energy) on the device: a 1-element int32 tensor holding the
+    smallest N whose leading singular values retain the fraction delta of the
+    sum of all values given (0 for a spectrum with no positive sum)."""
+    torch = _torch()
+    if sigma.dtype != torch.float64 or not sigma.is_contiguous():
+        raise ValueError("sigma must be a contiguous float64 tensor")
+    rank = out if out is not None else torch.empty(1, dtype=torch.int32, device=sigma.device)
+    _check(rpod_energy_rank(sigma.data_ptr(), sigma.numel(), float(delta), rank.data_ptr(),
+                            torch.cuda.current_stream(sigma.device).cuda_stream),
+           "rpod_energy_rank")
+    return rank
 
 
 class Plan:

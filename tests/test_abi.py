@@ -77,3 +77,32 @@ def test_strerror_covers_codes(lib):
     for c in range(9):
         assert R.rpod_strerror(c) != "unknown status"
     assert R.rpod_strerror(99) == "unknown status"
+
+
+def test_fluctuation_and_energy_rank_argument_checks(lib):
+    # nt must divide m; S and Sbar must be given; leading dimensions >= n
+    assert lib.rpod_fluctuations(10, 9, 2, 1, 10, R.RPOD_F32, None, 0, 0, None, 0, 0, 1, 10,
+                                 None) == R.RPOD_ERR_INVALID_ARG
+    assert lib.rpod_fluctuations(10, 8, 2, None, 10, R.RPOD_F32, None, 0, 0, None, 0, 0, 1, 10,
+                                 None) == R.RPOD_ERR_INVALID_ARG
+    assert lib.rpod_fluctuations(10, 8, 2, 1, 10, R.RPOD_F32, None, 0, 0, None, 0, 0, None, 10,
+                                 None) == R.RPOD_ERR_INVALID_ARG
+    assert lib.rpod_fluctuations(10, 8, 2, 1, 9, R.RPOD_F32, None, 0, 0, None, 0, 0, 1, 10,
+                                 None) == R.RPOD_ERR_INVALID_ARG
+    assert lib.rpod_fluctuations(10, 8, 0, 1, 10, R.RPOD_F32, None, 0, 0, None, 0, 0, 1, 10,
+                                 None) == R.RPOD_ERR_INVALID_ARG
+    assert lib.rpod_fluctuations(10, 8, 2, 1, 10, 7, None, 0, 0, None, 0, 0, 1, 10,
+                                 None) == R.RPOD_ERR_INVALID_ARG
+    # in place with another type, and unsupported type pairs
+    assert lib.rpod_fluctuations(10, 8, 2, 64, 10, R.RPOD_F32, 64, 10, R.RPOD_BF16, None, 0, 0,
+                                 1, 10, None) == R.RPOD_ERR_INVALID_ARG
+    assert lib.rpod_fluctuations(10, 8, 2, 64, 10, R.RPOD_F64, 128, 10, R.RPOD_F32, None, 0, 0,
+                                 1, 10, None) == R.RPOD_ERR_UNSUPPORTED
+    assert lib.rpod_fluctuations(10, 8, 2, 64, 10, R.RPOD_F64, None, 0, 0, 128, 10, R.RPOD_BF16,
+                                 1, 10, None) == R.RPOD_ERR_UNSUPPORTED
+    assert lib.rpod_fluctuations(10, 8, 2, 64, 10, R.RPOD_F32, None, 0, 0, 128, 10, R.RPOD_F32,
+                                 1, 10, None) == R.RPOD_ERR_UNSUPPORTED
+    assert lib.rpod_energy_rank(1, 4, 0.0, 1, None) == R.RPOD_ERR_INVALID_ARG
+    assert lib.rpod_energy_rank(1, 4, 1.5, 1, None) == R.RPOD_ERR_INVALID_ARG
+    assert lib.rpod_energy_rank(1, 0, 0.5, 1, None) == R.RPOD_ERR_INVALID_ARG
+    assert lib.rpod_energy_rank(None, 4, 0.5, 1, None) == R.RPOD_ERR_INVALID_ARG
