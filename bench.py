@@ -56,6 +56,10 @@ def parse():
                     help="time only the headline form (skip the other precision form)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-instance batched leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the LSTM leg")
+    ap.add_argument("--no-centered", action="store_true",
+                    help="skip the leg with per-sample centering (Eqs. time_av, fluct_q)")
+    ap.add_argument("--nt", type=int, default=400,
+                    help="snapshots per parameter sample for the centered leg")
     ap.add_argument("--learned-epochs", type=int, default=15)
     ap.add_argument("--ny", type=int, default=512,
                     help="grid rows (n = 512 * ny); smaller values make the small profiling case")
@@ -436,6 +440,68 @@ def main():
     roof["pass_ms_avg"] = per_ms
     roof["passes_per_step"] = hr["passes"] / hr["steps"]
 
+    # centering (Eqs. time_av, fluct_q) of M = m / nt samples, then the 16-bit
+    # rPOD of the fluctuations: F (FP32) is the refinement copy, H (BF16) the
+    # copy the tensor-core passes read
+    centered = None
+    if not args.no_centered and head == "bf16" and m % args.nt == 0:
+        nt = args.nt
+        M = m // nt
+        F = R.empty_colmajor(n, m, torch.float32, dev)
+        H = R.empty_colmajor(n, m, torch.bfloat16, dev)
+        Sbar = R.empty_colmajor(n, M, torch.float32, dev)
+        fl_out = (F, H, Sbar)
+        cplan = R.Plan(n, m, k, p, q, seed=w["seed"], compute="bf16",
+                       flags=R.RPOD_FLAG_REFINE_FP32, device=dev)
+        Uc = R.empty_colmajor(n, k, torch.float32, dev)
+        sigc = torch.empty(l, dtype=torch.float64, device=dev)
+        Cc = R.empty_colmajor(k, m, torch.float32, dev)
+        stream = torch.cuda.current_stream(dev)
+
+        def centered_step():
+            R.fluctuations(S, nt, out=fl_out)
+            cplan.basis(H, S_refine=F, out=(Uc, sigc, Cc))
+
+        for _ in range(args.warmup):
+            centered_step()
+        rc, _ = cplan.status()
+        if rc != R.RPOD_OK:
+            raise RuntimeError(f"centered: device status {R.rpod_strerror(rc)}")
+        csteps = max(3, min(args.steps, 5))
+        barrier()
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(csteps):
+            R.fluctuations(S, nt, out=fl_out)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        fl_ms = max_over_ranks(c0.elapsed_time(c1) / csteps)
+        c0.record(stream)
+        for _ in range(csteps):
+            centered_step()
+        c1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        cms = max_over_ranks(c0.elapsed_time(c1) / csteps)
+        rc, _ = cplan.status()
+        if rc != R.RPOD_OK:
+            raise RuntimeError(f"centered: device status {R.rpod_strerror(rc)}")
+        fl_bytes = n * m * (4 + 4 + 2) + 4 * n * M
+        hbm = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
+        fl_gbs = fl_bytes / (fl_ms * 1e-3) / 1e9
+        centered = {
+            "nt": nt, "samples": M, "fluct_ms": fl_ms, "fluct_bytes": fl_bytes,
+            "fluct_gbs": fl_gbs, "fluct_frac": fl_gbs / hbm,
+            "fluct_peak_source": f"{peak_src} hbm_gbs",
+            "time_to_basis_s": cms / 1e3, "steps": csteps,
+            "energy_rank_delta_0.9": int(R.energy_rank(sigc, 0.9).item()),
+            "energy_rank_delta_0.99": int(R.energy_rank(sigc, 0.99).item()),
+            "sigma_1": float(sigc[0]),
+        }
+        del F, H, Sbar, fl_out, cplan
+
     # end to end through the public API: pinned host S in, U/sigma/C out
     e2e = None
     if not args.no_e2e:
@@ -501,6 +567,7 @@ def main():
         "batched": batched,
         "batched_f32": batched_f32,
         "learned": learned,
+        "centered": centered,
     }
     for f, r in results.items():
         if f != head:
