@@ -154,7 +154,7 @@ __device__ __forceinline__ void lds_vec(const double* p, double* v) {
 }
 
 template <typename TA, typename TB, typename TC, typename TO, int BM, int BN, int BK, bool AKC>
-__global__ void __launch_bounds__(256, (sizeof(TC) == 4 && BM * BN >= 128 * 128) ? 2 : 1)
+__global__ void __launch_bounds__(256, (sizeof(TC) == 4 && BM * BN >= 32 * 128) ? 2 : 1)
 k_gemm(int64_t M, int64_t N, int64_t K, int64_t kchunk, const TA* __restrict__ A, int64_t lda,
        const TB* __restrict__ B, int64_t ldb, TO* __restrict__ C, int64_t ci, int64_t cj,
        int64_t csplit, unsigned* status, int check, int bkc) {
@@ -264,6 +264,15 @@ cudaError_t gemm_ex(cudaStream_t st, bool akc, bool bkc, int64_t M, int64_t N, i
   if (sizeof(TC) == 4) {
     if (N <= 32) return launch_gemm<TA, TB, TC, TO, 128, 32, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
     if (N <= 64) return launch_gemm<TA, TB, TC, TO, 128, 64, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
+    // products with few 128 x 128 tiles (the m x l by l x l steps: 79 tiles
+    // at m = 10000) on 64 x 128 tiles when that fills every SM once, else
+    // 32 x 128 (one wave either way, two CTAs per SM allowed)
+    const int64_t ny = (N + 127) / 128;
+    if (((M + 127) / 128) * ny * nsplit < 2 * 152) {
+      if (((M + 63) / 64) * ny * nsplit >= 152)
+        return launch_gemm<TA, TB, TC, TO, 64, 128, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
+      return launch_gemm<TA, TB, TC, TO, 32, 128, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
+    }
     return launch_gemm<TA, TB, TC, TO, 128, 128, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
   } else {
     // small FP64 products (the l x l steps of the eigensolver) on 32 x 32
