@@ -4,7 +4,9 @@ Pipeline (every numerical step of the method runs in librpod's kernels;
 torch holds device memory and does the data bookkeeping around them):
   1. snapshot matrix S = [S(mu_1) ... S(mu_M)] (Sec. 4.1 column order: by
      parameter sample, then time) of the synthetic parametric recipe;
-  2. randomized POD (Alg. 1) -> basis U_N and coefficients C = U_N^T S;
+  2. with `center`: per-sample time averages and fluctuation snapshots
+     (Eqs. (time_av), (fluct_q)) in place, by rpod_fluctuations; then
+     randomized POD (Alg. 1) -> basis U_N and coefficients C = U_N^T S;
   3. z-scored coefficient series and parameters, windows of sigma_L steps
      (Eq. (input) without the time column) -> next coefficients;
   4. LSTM training (MSE, Adam with Table tab:hyperparam's learning rate and
@@ -15,6 +17,10 @@ torch holds device memory and does the data bookkeeping around them):
      steps, and two predictors without the network: persistence of the last
      seed step, and the coefficients of the nearest training parameter sample
      at the same times (the zero-order choice of Eq. (time_av_zero)).
+     With `center` the held-out coefficients are those of the snapshots minus
+     the zero-order field of Eq. (time_av_zero) (the time average of the
+     nearest training sample) and the reconstructed field is that zero-order
+     field plus the modes, Eq. (q_approx).
 """
 from __future__ import annotations
 
@@ -50,6 +56,10 @@ class ROMConfig:
     seed: int = 0
     patience: int = 25
     fp32_weights: bool = False
+    # steady part of the synthetic snapshots (synth.steady_field; 0: none)
+    # and per-sample centering with the zero-order field of Eq. (time_av_zero)
+    mean_amp: float = 0.0
+    center: bool = False
 
 
 @dataclass
@@ -83,12 +93,16 @@ class ROMResult:
 
 
 def _snapshots(cfg: ROMConfig, mus, m, device, noise_stream0):
-    from synth import parametric_recipe, snapshot_matrix
+    from synth import parametric_recipe, snapshot_matrix, steady_field
     blocks = []
     for i, mu in enumerate(mus):
         rec = parametric_recipe(cfg.nx, cfg.ny, m, cfg.J, mu, seed=cfg.seed,
                                 noise_stream=noise_stream0 + i)
-        blocks.append(snapshot_matrix(rec, device=device, dtype=torch.float32).t())  # (m, n)
+        blk = snapshot_matrix(rec, device=device, dtype=torch.float32).t()  # (m, n)
+        if cfg.mean_amp:
+            sf = steady_field(cfg.nx, cfg.ny, mu, cfg.mean_amp)
+            blk += torch.from_numpy(sf).to(device=device, dtype=torch.float32)[None, :]
+        blocks.append(blk)
     return torch.cat(blocks, 0).t()   # column-major n x (M m)
 
 
@@ -116,6 +130,10 @@ def run(cfg: ROMConfig = ROMConfig(), device="cuda", log=None) -> ROMResult:
     # 1-2: snapshots and randomized POD
     S = _snapshots(cfg, mu_tr, cfg.n_steps, dev, 100)
     n, m = S.shape
+    Sbar = None
+    if cfg.center:
+        # Eqs. (time_av), (fluct_q): S becomes the fluctuation snapshots
+        _, _, Sbar = R.fluctuations(S, cfg.n_steps, in_place=True)   # n x M
     plan = R.Plan(n, m, cfg.k, cfg.p, cfg.q, seed=cfg.seed, compute="f32", device=dev)
     U, sig, C = plan.basis(S)
     rc, _ = plan.status()
@@ -181,10 +199,19 @@ def run(cfg: ROMConfig = ROMConfig(), device="cuda", log=None) -> ROMResult:
     if best_theta is not None:
         net.set_params(best_theta)
     # 5: held-out parameters, judged by Galerkin projection
+    dist = torch.cdist(torch.tensor(mu_te), torch.tensor(mu_tr))
+    near = dist.argmin(1).to(dev)
     Ste = _snapshots(cfg, mu_te, T + cfg.rollout, dev, 500)
     Cte = plan.project(U, Ste)                                   # k x (M' (T + r))
-    # time-averaged true fields over the prediction window, one per sample
     L_ = T + cfg.rollout
+    q0 = None
+    if cfg.center:
+        # zero-order fields of Eq. (time_av_zero): the time average of the
+        # nearest training sample; coefficients of the snapshots minus it
+        q0 = Sbar[:, near.cpu()].t().contiguous().t()               # n x M'
+        c0 = plan.project(U, q0)                                  # k x M'
+        Cte = Cte - c0.repeat_interleave(L_, dim=1)
+    # time-averaged true fields over the prediction window, one per sample
     fom_avg = torch.stack([Ste[:, i * L_ + T:(i + 1) * L_].mean(1) for i in range(cfg.n_test_mu)], 0)
     del Ste
     truth = Cte.t().contiguous().reshape(cfg.n_test_mu, T + cfg.rollout, O)
@@ -201,8 +228,6 @@ def run(cfg: ROMConfig = ROMConfig(), device="cuda", log=None) -> ROMResult:
     ref = truth[:, T:]
     res.err_lstm = _rel_err(pred, ref)
     res.err_persistence = _rel_err(truth[:, T - 1:T].expand(-1, cfg.rollout, -1), ref)
-    dist = torch.cdist(torch.tensor(mu_te), torch.tensor(mu_tr))
-    near = dist.argmin(1).to(dev)
     res.err_nearest = _rel_err(series[near, T:T + cfg.rollout], ref)
     res.err_lstm_first50 = _rel_err(pred[:, :50], ref[:, :50])
     res.err_lstm_first10 = _rel_err(pred[:, :10], ref[:, :10])
@@ -222,6 +247,8 @@ def run(cfg: ROMConfig = ROMConfig(), device="cuda", log=None) -> ROMResult:
 
     def tavg_err(coeffs):   # coeffs (M', r, N) -> mean over samples of Eq. (l2-error)
         rom_avg = coeffs.mean(1) @ U.t()                       # (M', n)
+        if q0 is not None:                                     # Eq. (q_approx)
+            rom_avg = rom_avg + q0.t()
         num = torch.linalg.vector_norm(rom_avg - fom_avg, dim=1)
         return float((num / torch.linalg.vector_norm(fom_avg, dim=1)).mean())
 

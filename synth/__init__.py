@@ -13,4 +13,5 @@ from .snapshots import (  # noqa: F401
     snapshot_matrix,
     parametric_recipe,
     batched_recipes,
+    steady_field,
 )

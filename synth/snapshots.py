@@ -165,6 +165,23 @@ def mode_matrix(rec: ModeRecipe) -> np.ndarray:
     return (sy[:, None, :] * sx[None, :, :]).reshape(rec.n, rec.J)
 
 
+def steady_field(nx: int, ny: int, mu, amp: float = 1.0) -> np.ndarray:
+    """A time-independent, parameter-dependent field standing in for the
+    time-averaged part of the flow (the paper's snapshots have one; the
+    oscillating recipe above averages to about zero):
+    amp * [(1 + mu_1) phi_(1,1) + (0.5 + mu_2) phi_(1,2) + (0.25 + mu_3) phi_(2,1)]
+    with phi_(a,b)(x, y) = sin(pi a x) sin(pi b y / 2) on the recipe's cell
+    centres, as an n-vector (row i + nx * r)."""
+    mu = np.asarray(mu, dtype=np.float64)
+    x = (np.arange(nx) + 0.5) / nx
+    y = 2.0 * (np.arange(ny) + 0.5) / ny
+
+    def phi(a, b):
+        return (np.sin(np.pi * b * y / 2.0)[:, None] * np.sin(np.pi * a * x)[None, :]).reshape(-1)
+
+    return amp * ((1.0 + mu[0]) * phi(1, 1) + (0.5 + mu[1]) * phi(1, 2) + (0.25 + mu[2]) * phi(2, 1))
+
+
 def time_matrix(rec: ModeRecipe) -> np.ndarray:
     """A (m x J), A[p, j] = cos(omega_j t_p + theta_j)."""
     return np.cos(np.outer(rec.times(), rec.omega) + rec.theta[None, :])
