@@ -21,10 +21,23 @@ beta2 = 0.999, eps = 1e-8, bias-corrected moments.
 Flat parameter layout (shared by the oracle and the library's interface, not
 its code): for each layer l: W_x (4H x I_l, row-major), W_h (4H x H), b (4H);
 then W_y (O x H), b_y (O).  I_0 = in_dim, I_l = H above.
+
+Dropout (Table tab:hyperparam gives probability 0.1 for the stream-function
+networks and no placement): in training, the input of every layer above the
+first (the h_1..h_T of the layer below) is multiplied by keep / (1 - p), the
+usual placement between stacked layers; the recurrent state, the first
+layer's input and the head's input are not masked, and inference uses no
+mask.  keep for element e = (t B + b) H + j of the input to layer l at
+training pass s comes from a counter-based generator so that any
+implementation draws the same mask: word e mod 4 of the Philox4x64-10 block
+with counter (e div 4, l, s, 0) and key (seed, 1); keep = 1 when that word
+shifted right by 11 bits is at least ceil(p 2^53).
 """
 from __future__ import annotations
 
 import numpy as np
+
+from .philox import philox4x64
 
 
 def param_shapes(in_dim: int, hidden: int, layers: int, out_dim: int):
@@ -53,8 +66,26 @@ def _sig(x):
     return 1.0 / (1.0 + np.exp(-x))
 
 
-def forward(theta, X, hidden, layers, out_dim):
-    """X: (B, T, I).  Returns (y (B, O), cache)."""
+def dropout_keep(p: float, seed: int, step: int, layer: int, T: int, B: int, H: int) -> np.ndarray:
+    """The keep mask (T, B, H) of the input to `layer` at training pass
+    `step`, as defined in the module header (1 = kept)."""
+    n = T * B * H
+    e = np.arange(n, dtype=np.uint64)
+    blocks = np.arange((n + 3) // 4, dtype=np.uint64)
+    ctr = np.zeros((len(blocks), 4), dtype=np.uint64)
+    ctr[:, 0] = blocks
+    ctr[:, 1] = np.uint64(layer)
+    ctr[:, 2] = np.uint64(step)
+    key = np.array([seed, 1], dtype=np.uint64)
+    w = philox4x64(ctr, key)                                  # (blocks, 4)
+    word = w[(e >> np.uint64(2)).astype(np.int64), (e & np.uint64(3)).astype(np.int64)]
+    thr = np.uint64(int(np.ceil(p * 2.0 ** 53)))
+    return ((word >> np.uint64(11)) >= thr).astype(np.float64).reshape(T, B, H)
+
+
+def forward(theta, X, hidden, layers, out_dim, dropout=None):
+    """X: (B, T, I).  Returns (y (B, O), cache).  dropout = (p, seed, step)
+    for a training pass with dropout, None for none."""
     X = np.asarray(X, dtype=np.float64)
     B, T, I = X.shape
     P = unflatten(theta, I, hidden, layers, out_dim)
@@ -63,6 +94,12 @@ def forward(theta, X, hidden, layers, out_dim):
     cache = []
     for l in range(layers):
         Wx, Wh, b = P[3 * l], P[3 * l + 1], P[3 * l + 2]
+        scale = None
+        if dropout is not None and l > 0 and dropout[0] > 0.0:
+            p, seed, step = dropout
+            keep = dropout_keep(p, seed, step, l, T, B, H)          # (T, B, H)
+            scale = keep.transpose(1, 0, 2) / (1.0 - p)            # (B, T, H)
+            inp = inp * scale
         h = np.zeros((B, H))
         c = np.zeros((B, H))
         hs, cs, gates = [h], [c], []
@@ -77,7 +114,7 @@ def forward(theta, X, hidden, layers, out_dim):
             hs.append(h)
             cs.append(c)
             gates.append((i, f, g, o))
-        cache.append((inp, hs, cs, gates))
+        cache.append((inp, hs, cs, gates, scale))
         inp = np.stack(hs[1:], axis=1)
     Wy, by = P[3 * layers], P[3 * layers + 1]
     hT = cache[-1][1][-1]
@@ -105,7 +142,7 @@ def backward(theta, cache, dy, hidden, layers, out_dim):
     dh_ext[:, T - 1, :] = dy @ Wy
     for l in reversed(range(layers)):
         Wx, Wh = P[3 * l], P[3 * l + 1]
-        inp, hs, cs, gates = cache[l]
+        inp, hs, cs, gates, scale = cache[l]
         dWx = np.zeros_like(Wx)
         dWh = np.zeros_like(Wh)
         db = np.zeros(4 * H)
@@ -131,7 +168,8 @@ def backward(theta, cache, dy, hidden, layers, out_dim):
             dinp[:, t, :] = dz @ Wx
             dh_rec = dz @ Wh
         G[3 * l], G[3 * l + 1], G[3 * l + 2] = dWx, dWh, db
-        dh_ext = dinp
+        # the masked input was scale * h of the layer below
+        dh_ext = dinp if scale is None else dinp * scale
     return np.concatenate([g.ravel() for g in G])
 
 

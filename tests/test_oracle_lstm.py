@@ -120,3 +120,82 @@ def test_rollout_shifts_window():
     w1 = np.concatenate([win[:, 1:], np.concatenate([win[:, -1:, :2], y0[:, None]], axis=2)], axis=1)
     y1, _ = L.forward(theta, w1, H, Ly, O)
     assert np.allclose(out[:, 1], y1)
+
+
+# ---- dropout between stacked layers (Table tab:hyperparam) ----------------
+def test_dropout_mask_words_from_numpy_philox():
+    # word e mod 4 of the block with counter (e div 4, layer, step, 0) under
+    # key (seed, 1): numpy's Philox increments the counter before each block
+    seed, step, layer, T, B, H, p = 11, 7, 2, 3, 5, 6, 0.3
+    keep = L.dropout_keep(p, seed, step, layer, T, B, H).ravel()
+    thr = int(np.ceil(p * 2.0 ** 53))
+    n = T * B * H
+    ref = np.empty(n)
+    for blk in range((n + 3) // 4):
+        c = blk + (layer << 64) + (step << 128)
+        c -= 1
+        ctr = np.array([(c >> (64 * i)) & (2**64 - 1) for i in range(4)], dtype=np.uint64)
+        bg = np.random.Philox(key=np.array([seed, 1], dtype=np.uint64), counter=ctr)
+        w = bg.random_raw(4)
+        for q in range(4):
+            if 4 * blk + q < n:
+                ref[4 * blk + q] = 1.0 if (int(w[q]) >> 11) >= thr else 0.0
+    assert np.array_equal(keep, ref)
+
+
+def test_dropout_zero_probability_is_no_dropout():
+    I, H, Ly, O, T, B = 5, 4, 3, 3, 4, 3
+    theta = _rand_theta(I, H, Ly, O, seed=5)
+    rng = np.random.default_rng(6)
+    X = rng.standard_normal((B, T, I))
+    tgt = rng.standard_normal((B, O))
+    y0, c0 = L.forward(theta, X, H, Ly, O)
+    y1, c1 = L.forward(theta, X, H, Ly, O, dropout=(0.0, 3, 9))
+    assert np.array_equal(y0, y1)
+    _, dy = L.mse(y0, tgt)
+    assert np.array_equal(L.backward(theta, c0, dy, H, Ly, O), L.backward(theta, c1, dy, H, Ly, O))
+
+
+def test_dropout_keep_fraction_and_independence():
+    p, T, B, H = 0.1, 10, 64, 50
+    k = L.dropout_keep(p, 1, 0, 1, T, B, H)
+    n = k.size
+    assert abs(k.mean() - (1 - p)) <= 5 * np.sqrt(p * (1 - p) / n)
+    # other passes, layers and seeds draw other masks
+    for args in ((1, 1, 1), (1, 0, 2), (2, 0, 1)):
+        k2 = L.dropout_keep(p, args[0], args[1], args[2], T, B, H)
+        agree = (k == k2).mean()
+        # independent masks agree on (1-p)^2 + p^2 of the entries
+        assert abs(agree - ((1 - p) ** 2 + p * p)) <= 5 * np.sqrt(0.25 / n)
+
+
+def test_dropout_grad_central_differences():
+    # with a fixed mask the loss is a smooth function of theta
+    I, H, Ly, O, T, B = 4, 5, 3, 2, 3, 4
+    theta = _rand_theta(I, H, Ly, O, seed=8)
+    rng = np.random.default_rng(9)
+    X = rng.standard_normal((B, T, I))
+    tgt = rng.standard_normal((B, O))
+    drop = (0.3, 21, 4)
+    y, cache = L.forward(theta, X, H, Ly, O, dropout=drop)
+    _, dy = L.mse(y, tgt)
+    g = L.backward(theta, cache, dy, H, Ly, O)
+    # the mask really removes inputs of layers 1 and 2
+    assert cache[1][4] is not None and (cache[1][4] == 0).any()
+    h = 1e-6
+    fd = np.zeros_like(theta)
+    for j in range(theta.size):
+        tp = theta.copy(); tp[j] += h
+        tm = theta.copy(); tm[j] -= h
+        fd[j] = (L.mse(L.forward(tp, X, H, Ly, O, dropout=drop)[0], tgt)[0]
+                 - L.mse(L.forward(tm, X, H, Ly, O, dropout=drop)[0], tgt)[0]) / (2 * h)
+    assert np.linalg.norm(g - fd) <= 1e-7 * np.linalg.norm(fd)
+
+
+def test_dropout_first_layer_input_untouched():
+    # one layer: nothing to mask, dropout changes nothing
+    I, H, O, T, B = 3, 4, 2, 3, 2
+    theta = _rand_theta(I, H, 1, O, seed=10)
+    X = np.random.default_rng(11).standard_normal((B, T, I))
+    assert np.array_equal(L.forward(theta, X, H, 1, O)[0],
+                          L.forward(theta, X, H, 1, O, dropout=(0.5, 1, 0))[0])
