@@ -282,6 +282,17 @@ int rpod_lstm_gather(const rpod_lstm* net, const float* series, const float* mu,
 int rpod_lstm_rollout(rpod_lstm* net, const float* window, int32_t B, int32_t mu_cols,
                       int32_t steps, float* out, void* workspace, size_t workspace_bytes,
                       void* stream);
+/* Dropout between stacked layers (Table tab:hyperparam: 0.1 for the
+ * stream-function networks), 0 <= p < 1 (0 switches it off).  In every later
+ * training pass (rpod_lstm_loss_grad, rpod_lstm_train_step) the input of each
+ * layer above the first is multiplied by keep / (1 - p); forward and
+ * rollout never mask.  keep for element e = (t B + b) H + j of the input to
+ * layer l (t < window, b < B, j < hidden) at training pass s (counted from 0
+ * by this call) is word e mod 4 of the Philox4x64-10 block with counter
+ * (e div 4, l, s, 0) and key (seed, 1): kept when that word shifted right by
+ * 11 bits is at least ceil(p 2^53).  Errors: RPOD_ERR_INVALID_ARG for a NULL
+ * net or p outside [0, 1). */
+int rpod_lstm_set_dropout(rpod_lstm* net, double p, uint64_t seed);
 int rpod_lstm_last_launch_count(const rpod_lstm* net);
 void rpod_lstm_destroy(rpod_lstm* net);
 

@@ -21,6 +21,22 @@ enum : unsigned {
 
 constexpr int kMaxL = 128;  // one-block limit of the small dense kernels
 
+// Philox4x64-10 (Salmon et al., SC'11): the counter c becomes the block's
+// four output words under the key (k0, k1).  Used by the sketch and by the
+// LSTM's dropout masks.
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += W0; k1 += W1; }
+    const uint64_t lo0 = M0 * c[0], hi0 = __umul64hi(M0, c[0]);
+    const uint64_t lo1 = M1 * c[2], hi1 = __umul64hi(M1, c[2]);
+    const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+  }
+}
+
 // Kernels enqueued by the calling host thread since the last reset (the
 // C ABI reports it per call).
 extern thread_local int g_launches;

@@ -7,6 +7,14 @@
 // Precision: FP32 master parameters, BF16 copies of the weight matrices read
 // by every product, FP32 activations and accumulation.
 //
+// Dropout (Table tab:hyperparam, 0.1 for the stream-function networks): in
+// training passes (loss_grad, train_step) the input of every layer above the
+// first is multiplied by keep / (1 - p); keep for element e = (t B + b) H + j
+// of the input to layer l at training pass s is word e mod 4 of the
+// Philox4x64-10 block with counter (e div 4, l, s, 0) and key (seed, 1),
+// kept when that word shifted right by 11 is at least ceil(p 2^53).  The
+// backward pass regenerates the same mask for the gradient it hands down.
+//
 // Kernels: the input projection of all T steps of a layer is one GEMM; each
 // recurrent step is one fused kernel (h_{t-1} W_h^T tile GEMM whose epilogue
 // applies the gate activations and the c/h update); BPTT runs one fused
@@ -31,6 +39,11 @@ struct rpod_lstm {
   int64_t step;
   int last_launches;
   int wfp32;  // products read the FP32 master weights instead of BF16 copies
+  // dropout between stacked layers (training passes only)
+  double drop_p;
+  uint64_t drop_seed, drop_thr;
+  int64_t drop_pass;
+  size_t o_xd;  // masked inputs of layers 1..L-1 (T x Bmax x H each)
 };
 
 namespace rpod {
@@ -39,6 +52,23 @@ namespace {
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 __device__ __forceinline__ float sigm(float x) { return 1.f / (1.f + __expf(-x)); }
+
+// out[e] = keep(e) ? in[e] * scale : 0 for e < n (in == out allowed): one
+// thread per Philox block of four elements
+__global__ void k_dropout(int64_t n, const float* in, float* out, uint64_t seed, uint64_t layer,
+                          uint64_t pass, uint64_t thr, float scale) {
+  const int64_t nb = (n + 3) / 4;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nb;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t c[4] = {(uint64_t)k, layer, pass, 0ull};
+    philox4x64_10(c, seed, 1ull);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t e = 4 * k + q;
+      if (e < n) out[e] = (c[q] >> 11) >= thr ? in[e] * scale : 0.f;
+    }
+  }
+}
 
 __global__ void k_to_time_major(int B, int T, int I, const float* __restrict__ X, float* __restrict__ Xt) {
   const int64_t n = (int64_t)B * T * I;
@@ -279,6 +309,20 @@ struct Net {
   float* gates(int l) const { return f(N->o_gates) + l * layer_stride_gx(); }
   float* cc(int l) const { return f(N->o_c) + l * layer_stride_ch(); }
   float* hh(int l) const { return f(N->o_h) + l * layer_stride_ch(); }
+  float* xd(int l) const { return f(N->o_xd) + (size_t)(l - 1) * N->T * N->Bmax * N->H; }
+  // the (masked, in training) input of layer l >= 1
+  const float* layer_input(int l, int B) const {
+    return train_drop ? xd(l) : hh(l - 1) + (size_t)B * N->H;
+  }
+  bool train_drop = false;  // this call is a training pass with dropout
+  int dropout(int l, int B, const float* in, float* out) const {
+    const int64_t n = (int64_t)N->T * B * N->H;
+    k_dropout<<<blocks_for((n + 3) / 4), 256, 0, st>>>(n, in, out, N->drop_seed, (uint64_t)l,
+                                                      (uint64_t)N->drop_pass, N->drop_thr,
+                                                      (float)(1.0 / (1.0 - N->drop_p)));
+    LL();
+    return RPOD_OK;
+  }
 
   template <typename TW>
   const TW* weights() const {
@@ -298,7 +342,9 @@ struct Net {
     const TW* W = weights<TW>();
     for (int l = 0; l < N->L; ++l) {
       const int Il = in_dim(l);
-      const float* Xin = l == 0 ? Xt : hh(l - 1) + (size_t)B * H;  // h_1..h_T of the layer below
+      // h_1..h_T of the layer below, masked in a training pass with dropout
+      if (l > 0 && train_drop) CR2(dropout(l, B, hh(l - 1) + (size_t)B * H, xd(l)));
+      const float* Xin = l == 0 ? Xt : layer_input(l, B);
       // hoisted input projection for all T steps
       LK((gemm_ex<float, TW, float, float>(st, true, true, (int64_t)T * B, 4 * H, Il, 1, Xin, Il,
                                                      W + N->off_w[l][0], Il, gx(l), 4 * H, 1, 0,
@@ -366,16 +412,19 @@ struct Net {
                                                          W + N->off_w[l][1], H, dhrec, H, 1, 0, nullptr,
                                                          false)));
       }
-      const float* Xin = l == 0 ? Xt : hh(l - 1) + (size_t)B * H;
+      const float* Xin = l == 0 ? Xt : layer_input(l, B);
       const int64_t rows = (int64_t)T * B;
       CR2(wgrad(dz, rows, 4 * H, Xin, Il, G + N->off_w[l][0]));
       CR2(wgrad(dz, rows, 4 * H, hh(l), H, G + N->off_w[l][1]));  // h_0..h_{T-1}
       k_colsum<<<(4 * H + 127) / 128, 128, 0, st>>>(rows, 4 * H, dz, G + N->off_w[l][2]);
       LL();
-      if (l > 0)
+      if (l > 0) {
         LK((gemm_ex<float, TW, float, float>(st, true, false, rows, Il, 4 * H, 1, dz, 4 * H,
                                                        W + N->off_w[l][0], Il, dhext, Il, 1, 0, nullptr,
                                                        false)));
+        // the input of layer l was keep / (1 - p) times h of layer l - 1
+        if (train_drop) CR2(dropout(l, B, dhext, dhext));
+      }
     }
     return RPOD_OK;
   }
@@ -432,6 +481,11 @@ int rpod_lstm_create(rpod_lstm** out, int32_t in_dim, int32_t hidden, int32_t la
   N->o_dx = take(4);
   N->part_floats = (size_t)32 * 4 * H * maxI;
   N->o_part = take(4 * N->part_floats);
+  N->o_xd = take(4 * (size_t)(layers - 1) * T * B * H);
+  N->drop_p = 0.0;
+  N->drop_seed = 0;
+  N->drop_thr = 0;
+  N->drop_pass = 0;
   N->total = o;
   N->step = 0;
   *out = N;
@@ -505,11 +559,13 @@ int rpod_lstm_loss_grad(rpod_lstm* N, const float* X, const float* Yt, int32_t B
   float* Xt = net.f(N->o_xtm);
   k_to_time_major<<<blocks_for((int64_t)B * N->T * N->I), 256, 0, st>>>(B, N->T, N->I, X, Xt);
   LL();
+  net.train_drop = N->drop_p > 0.0 && N->L > 1;
   if (int rc = net.forward(Xt, B)) return rc;
   k_head_loss<<<1, 1024, 0, st>>>(B, N->O, net.f(N->o_y), net.f(N->o_theta) + N->off_by, Yt,
                                    net.f(N->o_dy), net.f(N->o_loss));
   LL();
   if (int rc = net.backward(Xt, B)) return rc;
+  if (net.train_drop) N->drop_pass += 1;
   if (loss) LK(cudaMemcpyAsync(loss, net.f(N->o_loss), 4, cudaMemcpyDefault, st));
   if (grad) LK(cudaMemcpyAsync(grad, net.f(N->o_grad), 4 * N->P, cudaMemcpyDefault, st));
   N->last_launches = g_launches;
@@ -571,6 +627,15 @@ int rpod_lstm_rollout(rpod_lstm* N, const float* window, int32_t B, int32_t mu_c
     std::swap(cur, nxt);
   }
   N->last_launches = g_launches;
+  return RPOD_OK;
+}
+
+int rpod_lstm_set_dropout(rpod_lstm* N, double p, uint64_t seed) {
+  if (!N || !(p >= 0.0) || !(p < 1.0)) return RPOD_ERR_INVALID_ARG;
+  N->drop_p = p;
+  N->drop_seed = seed;
+  N->drop_thr = (uint64_t)ceil(p * 9007199254740992.0);  // ceil(p 2^53), exact scaling
+  N->drop_pass = 0;
   return RPOD_OK;
 }
 

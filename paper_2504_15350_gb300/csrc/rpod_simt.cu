@@ -24,19 +24,7 @@ template <> __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(double x
 template <> __device__ __forceinline__ __half cvt<__half>(double x) { return __double2half(x); }
 
 // ------------------------------------------------------------------------
-// Philox4x64-10 (Salmon et al., SC'11) and the Box-Muller sketch entries.
-__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
-  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
-  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r) { k0 += W0; k1 += W1; }
-    const uint64_t lo0 = M0 * c[0], hi0 = __umul64hi(M0, c[0]);
-    const uint64_t lo1 = M1 * c[2], hi1 = __umul64hi(M1, c[2]);
-    const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
-  }
-}
+// The Box-Muller sketch entries (Philox4x64-10 in rpod_internal.cuh).
 
 // Entry e = i + j m of Lambda is z0 (e even) or z1 (e odd) of the
 // Box-Muller pair of Philox block e / 2: u1 = (w0 >> 11 + 1) 2^-53,

@@ -64,6 +64,7 @@ SIGNATURES = {
                                             ctypes.c_size_t, _p]),
     "rpod_lstm_gather": (ctypes.c_int, [_p, _p, _p, _c_i32, _c_i32, _c_i32, _p, _c_i32, _p, _p, _p]),
     "rpod_lstm_rollout": (ctypes.c_int, [_p, _p, _c_i32, _c_i32, _c_i32, _p, _p, ctypes.c_size_t, _p]),
+    "rpod_lstm_set_dropout": (ctypes.c_int, [_p, ctypes.c_double, _c_u64]),
     "rpod_lstm_last_launch_count": (ctypes.c_int, [_p]),
     "rpod_lstm_destroy": (None, [_p]),
     "rpod_plan_create": (ctypes.c_int, [ctypes.POINTER(_p), _c_i64, _c_i64, _c_i32, _c_i32, _c_i32,
@@ -519,6 +520,10 @@ def rpod_lstm_rollout(net, window, B, mu_cols, steps, out, ws, ws_bytes, stream)
     return load().rpod_lstm_rollout(net, window, B, mu_cols, steps, out, ws, ws_bytes, stream)
 
 
+def rpod_lstm_set_dropout(net, p, seed):
+    return load().rpod_lstm_set_dropout(net, float(p), int(seed))
+
+
 def rpod_lstm_last_launch_count(net):
     return load().rpod_lstm_last_launch_count(net)
 
@@ -567,6 +572,11 @@ class LSTM:
         self._theta_in = t
         _check(rpod_lstm_set_params(self.handle, t.data_ptr(), self.ws_ptr, self.ws_bytes, self._stream()),
                "rpod_lstm_set_params")
+
+    def set_dropout(self, p, seed=0):
+        """Dropout between stacked layers in later training passes (the
+        mask definition is in include/rpod.h); p = 0 switches it off."""
+        _check(rpod_lstm_set_dropout(self.handle, p, seed), "rpod_lstm_set_dropout")
 
     def get_params(self):
         torch = _torch()

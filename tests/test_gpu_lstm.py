@@ -116,3 +116,43 @@ def test_gather_builds_windows():
             assert torch.equal(X[b, t, :2], m_[si])
             assert torch.equal(X[b, t, 2:], s[si, t0 + t])
         assert torch.equal(Y[b], s[si, t0 + T])
+
+
+@pytest.mark.parametrize("p", [0.1, 0.5])
+@pytest.mark.parametrize("I,H,L,O,T,B", [(54, 50, 3, 50, 10, 16), (6, 32, 2, 4, 5, 13)])
+def test_dropout_training_passes_match_oracle(I, H, L, O, T, B, p):
+    """Training passes with dropout between stacked layers (Table
+    tab:hyperparam's stream-function networks: 3 layers x 50, dropout 0.1):
+    loss and gradients of passes 0 and 1 against the oracle drawing the same
+    counter-based masks; inference is unmasked."""
+    rng = np.random.default_rng(I + H + L + int(10 * p))
+    theta = rng.uniform(-0.3, 0.3, OL.param_count(I, H, L, O)).astype(np.float32).astype(np.float64)
+    X = rng.standard_normal((B, T, I)).astype(np.float32)
+    Yt = rng.standard_normal((B, O)).astype(np.float32)
+    te = bf16_weights(theta, I, H, L, O)
+    seed = 1234
+    net = R.LSTM(I, H, L, O, T, max_batch=64, theta=theta)
+    net.set_dropout(p, seed)
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Yt).cuda()
+    for step in range(2):
+        y_o, cache = OL.forward(te, X.astype(np.float64), H, L, O, dropout=(p, seed, step))
+        loss_o, dy = OL.mse(y_o, Yt.astype(np.float64))
+        g_o = OL.backward(te, cache, dy, H, L, O)
+        loss, g = net.loss_grad(Xd, Yd)
+        torch.cuda.synchronize()
+        assert abs(loss.item() - loss_o) <= 1e-5 * loss_o, step
+        g = g.cpu().numpy()
+        off = 0
+        for shp in OL.param_shapes(I, H, L, O):
+            n = int(np.prod(shp))
+            assert rel(g[off:off + n], g_o[off:off + n]) < 2e-4, (step, shp)
+            off += n
+    # inference ignores the mask
+    y_o, _ = OL.forward(te, X.astype(np.float64), H, L, O)
+    assert rel(net.forward(Xd).cpu().numpy(), y_o) < 2e-5
+    # p = 0 switches it off again
+    net.set_dropout(0.0, seed)
+    y_o, cache = OL.forward(te, X.astype(np.float64), H, L, O)
+    loss_o, _ = OL.mse(y_o, Yt.astype(np.float64))
+    loss, _ = net.loss_grad(Xd, Yd)
+    assert abs(loss.item() - loss_o) <= 1e-5 * loss_o
