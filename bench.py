@@ -56,6 +56,9 @@ def parse():
                     help="time only the headline form (skip the other precision form)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-instance batched leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the LSTM leg")
+    ap.add_argument("--fields-epochs", type=int, default=0,
+                    help="epochs of an extra leg with one ROM per field and Table tab:hyperparam's "
+                         "networks (0: skipped)")
     ap.add_argument("--no-centered", action="store_true",
                     help="skip the leg with per-sample centering (Eqs. time_av, fluct_q)")
     ap.add_argument("--nt", type=int, default=400,
@@ -309,6 +312,25 @@ def run_learned(dev, epochs):
                                "projection_floor": r.tavg_err_projection}}
 
 
+def run_fields_leg(dev, epochs):
+    """One centered rPOD-LSTM ROM per field (q1, q2, psi1, psi2) with the
+    paper's per-field networks (M_q: 1 x 100, batch 8; M_psi: 3 x 50, batch
+    16, dropout 0.1) on the learned leg's data size."""
+    from paper_2504_15350_gb300 import rom
+    base = rom.ROMConfig(epochs=epochs, patience=max(4, epochs), mean_amp=1.0, center=True)
+    out = {}
+    for f, r in rom.run_fields(base, device=dev).items():
+        out[f] = {"network": r.network, "epochs": r.epochs_run,
+                  "train_windows_per_s": r.samples_per_s, "final_val_loss": r.val_loss[-1],
+                  "onestep_err": {"lstm": r.onestep_err_lstm, "persistence": r.onestep_err_persistence},
+                  "first10_err": {"lstm": r.err_lstm_first10, "persistence": r.err_persistence_first10,
+                                  "nearest_mu": r.err_nearest_first10},
+                  "tavg_field_err": {"lstm": r.tavg_err_lstm, "persistence": r.tavg_err_persistence,
+                                     "nearest_mu": r.tavg_err_nearest,
+                                     "projection_floor": r.tavg_err_projection}}
+    return out
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -549,6 +571,8 @@ def main():
         batched = run_batched(dev, max_over_ranks, barrier, rank, world, form="bf16")
         batched_f32 = run_batched(dev, max_over_ranks, barrier, rank, world, form="f32")
     learned = None if (args.no_learned or rank != 0) else run_learned(dev, args.learned_epochs)
+    fields = (run_fields_leg(dev, args.fields_epochs)
+              if (args.fields_epochs > 0 and rank == 0) else None)
 
     if rank != 0:
         if world > 1:
@@ -575,6 +599,8 @@ def main():
         "learned": learned,
         "centered": centered,
     }
+    if fields is not None:
+        line["fields"] = fields
     for f, r in results.items():
         if f != head:
             line[f"{f}_time_to_basis_s"] = r["ms"] / 1e3

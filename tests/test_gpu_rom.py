@@ -58,3 +58,25 @@ def test_centered_rom_zero_order_field():
     assert res.tavg_err_projection <= 0.02
     assert res.tavg_err_lstm <= 0.6 * res.tavg_err_persistence
     assert res.onestep_err_lstm <= 0.8 * res.onestep_err_persistence
+
+
+def test_per_field_networks_of_the_paper():
+    """One ROM per field (q1, q2, psi1, psi2) with Table tab:hyperparam's
+    networks: M_q 1 layer x 100 cells, batch 8; M_psi 3 layers x 50 cells,
+    batch 16, dropout 0.1.  A small configuration (8 samples x 300 steps,
+    10 epochs): every field's validation loss falls by at least 5x and its
+    basis reproduces the held-out time-averaged field to within 5 %.  (At
+    this size the networks do not yet beat persistence on held-out samples;
+    that comparison is the 2 x 256 network's, above.)"""
+    from paper_2504_15350_gb300.build import build
+    build()
+    base = rom.ROMConfig(mean_amp=1.0, center=True, n_train_mu=8, n_steps=300, n_test_mu=4,
+                         rollout=100, k=20, p=10, epochs=10, patience=10)
+    res = rom.run_fields(base)
+    assert set(res) == set(rom.FIELDS)
+    for f, r in res.items():
+        kind = "q" if f.startswith("q") else "psi"
+        assert r.network == rom.PAPER_NETWORKS[kind], f
+        assert math.isfinite(r.tavg_err_lstm), f
+        assert r.val_loss[-1] <= 0.2 * r.val_loss[0], (f, r.val_loss[0], r.val_loss[-1])
+        assert r.tavg_err_projection <= 0.05, (f, r.tavg_err_projection)
