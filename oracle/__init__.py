@@ -18,7 +18,11 @@ Modules
              (Eq. (svd)), the per-sample time averages and fluctuation
              snapshots (Eqs. (time_av), (fluct_q)) and the energy-based rank
              (Eq. (energy)).
-  lstm    -- LSTM forward, backpropagation through time and Adam in FP64.
+  lstm    -- LSTM forward, backpropagation through time and Adam in FP64,
+             with dropout between stacked layers from counter-based masks.
+  sharded -- Alg. 1 with the rows of S spread over ranks: one sum over ranks
+             per pass (the algebra of a row-sharded multi-GPU rPOD, checked
+             on gloo CPU ranks against the single-process oracle).
 
 Every function is pinned by tests under tests/ against something other than
 itself (numpy's Philox words, numpy.linalg.svd, closed forms, exact-rank

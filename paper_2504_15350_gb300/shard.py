@@ -1,9 +1,14 @@
-"""Host-side sharding of independent rPOD instances across ranks.
+"""Host-side sharding across ranks.
 
 Instances of the batched form share nothing, so N ranks (one GPU each) split
 them with no collective on the data path: instance b goes to the rank with the
 least accumulated cost, largest instances first (longest-processing-time
 greedy).  The cost of an instance is its streamed work, (2q + 2) n m_b l_b.
+
+A single large rPOD splits by rows instead (`row_blocks`): every pass over S
+then ends in one sum over ranks of its small result (the Gram of the
+sampled matrix, S^T Q, Q^T S), the algebra that oracle/sharded.py states and
+the gloo tests check on CPU ranks.
 """
 from __future__ import annotations
 
@@ -22,6 +27,27 @@ def shard(costs, world: int):
         parts[r].append(i)
         load[r] += costs[i]
     return [sorted(p) for p in parts]
+
+
+def row_blocks(n: int, world: int, align: int = 64):
+    """Contiguous row blocks [(row0, rows), ...] of an n-row matrix over
+    `world` ranks: as even as `align`-row granularity allows (every block
+    but the last starts and ends on a multiple of `align`, the row count of
+    one 16-bit TMA tile), later ranks taking the extra tiles so that the
+    ragged last tile sits in one of the longer blocks (block sizes differ by
+    at most `align` rows); ranks beyond the tile count get empty blocks."""
+    if n < 0 or world < 1 or align < 1:
+        raise ValueError("need n >= 0, world >= 1, align >= 1")
+    tiles = (n + align - 1) // align
+    base, extra = divmod(tiles, world)
+    out, t0 = [], 0
+    for r in range(world):
+        nt = base + (1 if r >= world - extra else 0)
+        r0 = min(t0 * align, n)
+        r1 = min((t0 + nt) * align, n)
+        out.append((r0, r1 - r0))
+        t0 += nt
+    return out
 
 
 def max_over_ranks(value: float, group=None) -> float:
