@@ -13,7 +13,7 @@ torch holds device memory and does the data bookkeeping around them):
      weight decay) on 80 % of the windows, validation loss on the rest, stop
      when it has not improved for `patience` epochs;
   5. held-out parameters: Galerkin projection C' = U_N^T S' of their
-     snapshots (the judge), LSTM rollout from the first sigma_L projected
+     snapshots (the reference coefficients), LSTM rollout from the first sigma_L projected
      steps, and two predictors without the network: persistence of the last
      seed step, and the coefficients of the nearest training parameter sample
      at the same times (the zero-order choice of Eq. (time_av_zero)).

@@ -42,7 +42,7 @@ def test_centered_rom_zero_order_field():
     """Snapshots with steady parameter-dependent mean fields, centered per
     training sample (Eqs. (time_av), (fluct_q)) before the rPOD; held-out
     fields reconstructed as the nearest sample's time average plus the modes
-    (Eqs. (q_approx), (time_av_zero)).  The time-averaged-field judge of
+    (Eqs. (q_approx), (time_av_zero)).  The time-averaged-field error of
     Eq. (l2-error) is then well posed: the projection floor is small, and the
     LSTM's time-averaged field beats persistence of the seed window (measured
     0.16 vs 0.44, floor 0.003, at 15 epochs)."""
