@@ -58,7 +58,8 @@ typedef enum {
   RPOD_ERR_NO_CONVERGENCE = 5,/* small SVD did not converge */
   RPOD_ERR_TIMEOUT = 6,       /* a device-side wait gave up */
   RPOD_ERR_CUDA = 7,          /* a CUDA runtime call failed */
-  RPOD_ERR_WORKSPACE = 8      /* workspace missing, too small or misaligned */
+  RPOD_ERR_WORKSPACE = 8,     /* workspace missing, too small or misaligned */
+  RPOD_ERR_IO = 9             /* a model file could not be read or written, or is not one */
 } rpod_status;
 
 /* Warning bits returned through rpod_status_sync()'s flags_out. */
@@ -282,6 +283,39 @@ int rpod_lstm_gather(const rpod_lstm* net, const float* series, const float* mu,
 int rpod_lstm_rollout(rpod_lstm* net, const float* window, int32_t B, int32_t mu_cols,
                       int32_t steps, float* out, void* workspace, size_t workspace_bytes,
                       void* stream);
+/* One training epoch: for each of the floor(n_windows / batch) full
+ * batches of the window list idx (device, n_windows x 2 int32 pairs
+ * (series, first step) in the order to train -- shuffle it beforehand),
+ * gather the windows (as rpod_lstm_gather) into the workspace and take one
+ * training step (as rpod_lstm_train_step); the last n_windows mod batch
+ * windows are left out.  *loss_out (device or host float; may be NULL)
+ * receives the mean of the batch losses.  Each pair must satisfy series <
+ * n_series and first step + window < t_len (not checked).  Requires
+ * batch <= max_batch.  Errors as for rpod_lstm_gather and
+ * rpod_lstm_train_step, and RPOD_ERR_INVALID_ARG when no full batch fits. */
+int rpod_lstm_train_epoch(rpod_lstm* net, const float* series, const float* mu, int32_t n_series,
+                          int32_t t_len, int32_t d, const int32_t* idx, int32_t n_windows,
+                          int32_t batch, float lr, float weight_decay, float* loss_out,
+                          void* workspace, size_t workspace_bytes, void* stream);
+
+/* Model files.  rpod_lstm_save synchronises `stream` and writes the network's
+ * dimensions (in_dim, hidden, layers, out_dim, window, max_batch, flags), its
+ * Adam step count, dropout settings, flat FP32 parameters and both Adam
+ * moments to `path` (little-endian binary, magic "RPODLSTM", version 1).
+ * rpod_lstm_load creates a network of the file's dimensions and keeps the
+ * file's state on the host; rpod_lstm_restore then copies that state into a
+ * workspace of rpod_lstm_workspace_bytes for the new network, after which
+ * it continues exactly where the saved one stopped.  Errors: RPOD_ERR_IO
+ * when the file cannot be opened, read or written, or is not a model file of
+ * this version; RPOD_ERR_INVALID_ARG for NULL arguments or, for restore, a
+ * network without loaded state. */
+int rpod_lstm_save(const rpod_lstm* net, const char* path, void* workspace, size_t workspace_bytes,
+                   void* stream);
+int rpod_lstm_load(rpod_lstm** out, const char* path);
+int rpod_lstm_restore(rpod_lstm* net, void* workspace, size_t workspace_bytes, void* stream);
+/* dims[0..6] = in_dim, hidden, layers, out_dim, window, max_batch, flags. */
+int rpod_lstm_dims(const rpod_lstm* net, int32_t* dims);
+
 /* Dropout between stacked layers (Table tab:hyperparam: 0.1 for the
  * stream-function networks), 0 <= p < 1 (0 switches it off).  In every later
  * training pass (rpod_lstm_loss_grad, rpod_lstm_train_step) the input of each

@@ -526,6 +526,7 @@ const char* rpod_strerror(int s) {
     case RPOD_ERR_TIMEOUT: return "device wait timed out";
     case RPOD_ERR_CUDA: return "CUDA error";
     case RPOD_ERR_WORKSPACE: return "workspace missing or too small";
+    case RPOD_ERR_IO: return "file could not be read or written";
     default: return "unknown status";
   }
 }

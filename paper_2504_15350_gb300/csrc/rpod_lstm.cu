@@ -22,8 +22,12 @@
 // three GEMMs over all steps for dW_x, dW_h and the input gradient.
 #include <math.h>
 
+#include <stdio.h>
+#include <string.h>
+
 #include <algorithm>
 #include <new>
+#include <vector>
 
 #include "rpod_internal.cuh"
 
@@ -44,6 +48,11 @@ struct rpod_lstm {
   uint64_t drop_seed, drop_thr;
   int64_t drop_pass;
   size_t o_xd;  // masked inputs of layers 1..L-1 (T x Bmax x H each)
+  size_t o_bx, o_by, o_lsum;  // train_epoch: the gathered batch, the loss sum
+  // state read by rpod_lstm_load, copied to a workspace by rpod_lstm_restore
+  bool pending = false;
+  int64_t pend_step = 0;
+  std::vector<float> pend;  // theta, m, v (3 P floats)
 };
 
 namespace rpod {
@@ -69,6 +78,10 @@ __global__ void k_dropout(int64_t n, const float* in, float* out, uint64_t seed,
     }
   }
 }
+
+// *sum += *x (one thread); *sum = *sum / count (one thread)
+__global__ void k_acc1(float* sum, const float* x) { *sum += *x; }
+__global__ void k_div1(float* sum, float count) { *sum /= count; }
 
 __global__ void k_to_time_major(int B, int T, int I, const float* __restrict__ X, float* __restrict__ Xt) {
   const int64_t n = (int64_t)B * T * I;
@@ -482,6 +495,9 @@ int rpod_lstm_create(rpod_lstm** out, int32_t in_dim, int32_t hidden, int32_t la
   N->part_floats = (size_t)32 * 4 * H * maxI;
   N->o_part = take(4 * N->part_floats);
   N->o_xd = take(4 * (size_t)(layers - 1) * T * B * H);
+  N->o_bx = take(4 * B * T * I);
+  N->o_by = take(4 * B * (size_t)out_dim);
+  N->o_lsum = take(4);
   N->drop_p = 0.0;
   N->drop_seed = 0;
   N->drop_thr = 0;
@@ -627,6 +643,155 @@ int rpod_lstm_rollout(rpod_lstm* N, const float* window, int32_t B, int32_t mu_c
     std::swap(cur, nxt);
   }
   N->last_launches = g_launches;
+  return RPOD_OK;
+}
+
+int rpod_lstm_train_epoch(rpod_lstm* N, const float* series, const float* mu, int32_t n_series,
+                          int32_t t_len, int32_t d, const int32_t* idx, int32_t n_windows,
+                          int32_t batch, float lr, float weight_decay, float* loss_out, void* ws,
+                          size_t bytes, void* stream) {
+  if (!N || !series || !idx || n_windows < 1 || batch < 1 || batch > N->Bmax || d < 0 ||
+      d + N->O != N->I || t_len <= N->T || n_series < 1 || (d > 0 && !mu))
+    return RPOD_ERR_INVALID_ARG;
+  const int nb = n_windows / batch;
+  if (nb < 1) return RPOD_ERR_INVALID_ARG;
+  if (int rc = lstm_ws(N, ws, bytes)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* w = (char*)ws;
+  float* X = (float*)(w + N->o_bx);
+  float* Y = (float*)(w + N->o_by);
+  float* lsum = (float*)(w + N->o_lsum);
+  LK(cudaMemsetAsync(lsum, 0, 4, st));
+  int launches = 0;
+  for (int b = 0; b < nb; ++b) {
+    if (int rc = rpod_lstm_gather(N, series, mu, n_series, t_len, d, idx + 2 * (int64_t)b * batch,
+                                  batch, X, Y, stream))
+      return rc;
+    if (int rc = rpod_lstm_train_step(N, X, Y, batch, lr, weight_decay, nullptr, ws, bytes, stream))
+      return rc;
+    k_acc1<<<1, 1, 0, st>>>(lsum, (const float*)(w + N->o_loss));
+    if (cudaGetLastError() != cudaSuccess) return RPOD_ERR_CUDA;
+    launches += N->last_launches + 2;
+  }
+  k_div1<<<1, 1, 0, st>>>(lsum, (float)nb);
+  if (cudaGetLastError() != cudaSuccess) return RPOD_ERR_CUDA;
+  if (loss_out) LK(cudaMemcpyAsync(loss_out, lsum, 4, cudaMemcpyDefault, st));
+  N->last_launches = launches + 1;
+  return RPOD_OK;
+}
+
+// ---- model files: "RPODLSTM", version, dimensions, state, theta, m, v
+namespace {
+constexpr char kMagic[8] = {'R', 'P', 'O', 'D', 'L', 'S', 'T', 'M'};
+constexpr uint32_t kVersion = 1;
+struct FileHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t dims[7];  // in_dim, hidden, layers, out_dim, window, max_batch, flags
+  int64_t step;
+  double drop_p;
+  uint64_t drop_seed;
+  int64_t drop_pass;
+  int64_t P;
+};
+}  // namespace
+
+int rpod_lstm_save(const rpod_lstm* N, const char* path, void* ws, size_t bytes, void* stream) {
+  if (!N || !path) return RPOD_ERR_INVALID_ARG;
+  if (int rc = lstm_ws(N, ws, bytes)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<float> buf;
+  try {
+    buf.resize(3 * (size_t)N->P);
+  } catch (...) {
+    return RPOD_ERR_INVALID_ARG;
+  }
+  const char* w = (const char*)ws;
+  LK(cudaMemcpyAsync(buf.data(), w + N->o_theta, 4 * N->P, cudaMemcpyDeviceToHost, st));
+  LK(cudaMemcpyAsync(buf.data() + N->P, w + N->o_m, 4 * N->P, cudaMemcpyDeviceToHost, st));
+  LK(cudaMemcpyAsync(buf.data() + 2 * N->P, w + N->o_v, 4 * N->P, cudaMemcpyDeviceToHost, st));
+  LK(cudaStreamSynchronize(st));
+  FileHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, kMagic, 8);
+  h.version = kVersion;
+  const int32_t dims[7] = {N->I, N->H, N->L, N->O, N->T, N->Bmax,
+                           N->wfp32 ? (int32_t)RPOD_LSTM_FP32_WEIGHTS : 0};
+  memcpy(h.dims, dims, sizeof(dims));
+  h.step = N->step;
+  h.drop_p = N->drop_p;
+  h.drop_seed = N->drop_seed;
+  h.drop_pass = N->drop_pass;
+  h.P = N->P;
+  FILE* f = fopen(path, "wb");
+  if (!f) return RPOD_ERR_IO;
+  bool ok = fwrite(&h, sizeof(h), 1, f) == 1 &&
+            fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  ok = (fclose(f) == 0) && ok;
+  return ok ? RPOD_OK : RPOD_ERR_IO;
+}
+
+int rpod_lstm_load(rpod_lstm** out, const char* path) {
+  if (!out || !path) return RPOD_ERR_INVALID_ARG;
+  FILE* f = fopen(path, "rb");
+  if (!f) return RPOD_ERR_IO;
+  FileHeader h;
+  if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != kVersion) {
+    fclose(f);
+    return RPOD_ERR_IO;
+  }
+  rpod_lstm* N = nullptr;
+  if (rpod_lstm_create(&N, h.dims[0], h.dims[1], h.dims[2], h.dims[3], h.dims[4], h.dims[5],
+                       (uint32_t)h.dims[6]) != RPOD_OK ||
+      N->P != h.P || !(h.drop_p >= 0.0 && h.drop_p < 1.0) || h.step < 0 || h.drop_pass < 0) {
+    if (N) rpod_lstm_destroy(N);
+    fclose(f);
+    return RPOD_ERR_IO;
+  }
+  try {
+    N->pend.resize(3 * (size_t)N->P);
+  } catch (...) {
+    rpod_lstm_destroy(N);
+    fclose(f);
+    return RPOD_ERR_INVALID_ARG;
+  }
+  const bool ok = fread(N->pend.data(), sizeof(float), N->pend.size(), f) == N->pend.size();
+  fclose(f);
+  if (!ok) {
+    rpod_lstm_destroy(N);
+    return RPOD_ERR_IO;
+  }
+  N->pending = true;
+  N->pend_step = h.step;
+  if (h.drop_p > 0.0) rpod_lstm_set_dropout(N, h.drop_p, h.drop_seed);
+  N->drop_pass = h.drop_pass;
+  *out = N;
+  return RPOD_OK;
+}
+
+int rpod_lstm_restore(rpod_lstm* N, void* ws, size_t bytes, void* stream) {
+  if (!N || !N->pending) return RPOD_ERR_INVALID_ARG;
+  if (int rc = lstm_ws(N, ws, bytes)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* w = (char*)ws;
+  g_launches = 0;
+  // pageable source: each copy returns once its data is staged
+  LK(cudaMemcpyAsync(w + N->o_theta, N->pend.data(), 4 * N->P, cudaMemcpyHostToDevice, st));
+  LK(cudaMemcpyAsync(w + N->o_m, N->pend.data() + N->P, 4 * N->P, cudaMemcpyHostToDevice, st));
+  LK(cudaMemcpyAsync(w + N->o_v, N->pend.data() + 2 * N->P, 4 * N->P, cudaMemcpyHostToDevice, st));
+  k_to_bf16<<<blocks_for(N->P), 256, 0, st>>>(N->P, (const float*)(w + N->o_theta),
+                                               (__nv_bfloat16*)(w + N->o_wbf));
+  LL();
+  N->step = N->pend_step;
+  N->last_launches = g_launches;
+  return RPOD_OK;
+}
+
+int rpod_lstm_dims(const rpod_lstm* N, int32_t* dims) {
+  if (!N || !dims) return RPOD_ERR_INVALID_ARG;
+  const int32_t d[7] = {N->I, N->H, N->L, N->O, N->T, N->Bmax,
+                        N->wfp32 ? (int32_t)RPOD_LSTM_FP32_WEIGHTS : 0};
+  memcpy(dims, d, sizeof(d));
   return RPOD_OK;
 }
 

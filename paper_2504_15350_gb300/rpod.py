@@ -25,6 +25,7 @@ RPOD_ERR_NO_CONVERGENCE = 5
 RPOD_ERR_TIMEOUT = 6
 RPOD_ERR_CUDA = 7
 RPOD_ERR_WORKSPACE = 8
+RPOD_ERR_IO = 9
 RPOD_WARN_RANK_DEFICIENT = 1
 RPOD_FLAG_REFINE_FP32 = 1
 RPOD_FLAG_RETURN_ALL_L = 4
@@ -65,6 +66,13 @@ SIGNATURES = {
     "rpod_lstm_gather": (ctypes.c_int, [_p, _p, _p, _c_i32, _c_i32, _c_i32, _p, _c_i32, _p, _p, _p]),
     "rpod_lstm_rollout": (ctypes.c_int, [_p, _p, _c_i32, _c_i32, _c_i32, _p, _p, ctypes.c_size_t, _p]),
     "rpod_lstm_set_dropout": (ctypes.c_int, [_p, ctypes.c_double, _c_u64]),
+    "rpod_lstm_train_epoch": (ctypes.c_int, [_p, _p, _p, _c_i32, _c_i32, _c_i32, _p, _c_i32, _c_i32,
+                                             ctypes.c_float, ctypes.c_float, _p, _p, ctypes.c_size_t,
+                                             _p]),
+    "rpod_lstm_save": (ctypes.c_int, [_p, ctypes.c_char_p, _p, ctypes.c_size_t, _p]),
+    "rpod_lstm_load": (ctypes.c_int, [ctypes.POINTER(_p), ctypes.c_char_p]),
+    "rpod_lstm_restore": (ctypes.c_int, [_p, _p, ctypes.c_size_t, _p]),
+    "rpod_lstm_dims": (ctypes.c_int, [_p, _pi32]),
     "rpod_lstm_last_launch_count": (ctypes.c_int, [_p]),
     "rpod_lstm_destroy": (None, [_p]),
     "rpod_plan_create": (ctypes.c_int, [ctypes.POINTER(_p), _c_i64, _c_i64, _c_i32, _c_i32, _c_i32,
@@ -524,6 +532,32 @@ def rpod_lstm_set_dropout(net, p, seed):
     return load().rpod_lstm_set_dropout(net, float(p), int(seed))
 
 
+def rpod_lstm_train_epoch(net, series, mu, n_series, t_len, d, idx, n_windows, batch, lr, wd,
+                          loss_out, ws, ws_bytes, stream):
+    return load().rpod_lstm_train_epoch(net, series, mu, n_series, t_len, d, idx, n_windows, batch,
+                                        lr, wd, loss_out, ws, ws_bytes, stream)
+
+
+def rpod_lstm_save(net, path, ws, ws_bytes, stream):
+    return load().rpod_lstm_save(net, os.fsencode(path), ws, ws_bytes, stream)
+
+
+def rpod_lstm_load(path) -> int:
+    h = _p()
+    _check(load().rpod_lstm_load(ctypes.byref(h), os.fsencode(path)), "rpod_lstm_load")
+    return h.value
+
+
+def rpod_lstm_restore(net, ws, ws_bytes, stream):
+    return load().rpod_lstm_restore(net, ws, ws_bytes, stream)
+
+
+def rpod_lstm_dims(net):
+    d = (_c_i32 * 7)()
+    _check(load().rpod_lstm_dims(net, d), "rpod_lstm_dims")
+    return tuple(int(v) for v in d)
+
+
 def rpod_lstm_last_launch_count(net):
     return load().rpod_lstm_last_launch_count(net)
 
@@ -537,14 +571,15 @@ class LSTM:
     torch tensors out; all arithmetic in the library's kernels)."""
 
     def __init__(self, in_dim, hidden, layers, out_dim, window, max_batch, theta=None, device="cuda",
-                 fp32_weights=False):
+                 fp32_weights=False, _handle=None):
         torch = _torch()
         self.device = torch.device(device)
         self.dims = (in_dim, hidden, layers, out_dim, window)
         self.max_batch = max_batch
         self.fp32_weights = fp32_weights
-        self.handle = rpod_lstm_create(in_dim, hidden, layers, out_dim, window, max_batch,
-                                       RPOD_LSTM_FP32_WEIGHTS if fp32_weights else 0)
+        self.handle = _handle if _handle is not None else rpod_lstm_create(
+            in_dim, hidden, layers, out_dim, window, max_batch,
+            RPOD_LSTM_FP32_WEIGHTS if fp32_weights else 0)
         self.P = rpod_lstm_param_count(self.handle)
         self.ws_bytes = rpod_lstm_workspace_bytes(self.handle)
         self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
@@ -572,6 +607,36 @@ class LSTM:
         self._theta_in = t
         _check(rpod_lstm_set_params(self.handle, t.data_ptr(), self.ws_ptr, self.ws_bytes, self._stream()),
                "rpod_lstm_set_params")
+
+    @classmethod
+    def load(cls, path, device="cuda"):
+        """A network from a model file written by save(), with its
+        parameters, Adam state and dropout settings restored."""
+        h = rpod_lstm_load(path)
+        I, H, L, O, T, Bmax, flags = rpod_lstm_dims(h)
+        net = cls(I, H, L, O, T, Bmax, device=device,
+                  fp32_weights=bool(flags & RPOD_LSTM_FP32_WEIGHTS), _handle=h)
+        _check(rpod_lstm_restore(h, net.ws_ptr, net.ws_bytes, net._stream()), "rpod_lstm_restore")
+        return net
+
+    def save(self, path):
+        _check(rpod_lstm_save(self.handle, path, self.ws_ptr, self.ws_bytes, self._stream()),
+               "rpod_lstm_save")
+
+    def train_epoch(self, series, mu, idx, batch, lr=1e-3, weight_decay=1e-5):
+        """One epoch over the window list idx ((n, 2) int32 device tensor of
+        (series, first step), in training order); returns the mean batch
+        loss as a 1-element device tensor."""
+        torch = _torch()
+        series, mu, idx = series.contiguous(), mu.contiguous(), idx.contiguous()
+        n_series, t_len = series.shape[0], series.shape[1]
+        d = mu.shape[1] if mu.dim() == 2 else 0
+        out = torch.empty(1, dtype=torch.float32, device=self.device)
+        _check(rpod_lstm_train_epoch(self.handle, series.data_ptr(), mu.data_ptr() if d else None,
+                                     n_series, t_len, d, idx.data_ptr(), idx.shape[0], batch, lr,
+                                     weight_decay, out.data_ptr(), self.ws_ptr, self.ws_bytes,
+                                     self._stream()), "rpod_lstm_train_epoch")
+        return out
 
     def set_dropout(self, p, seed=0):
         """Dropout between stacked layers in later training passes (the

@@ -106,3 +106,31 @@ def test_fluctuation_and_energy_rank_argument_checks(lib):
     assert lib.rpod_energy_rank(1, 4, 1.5, 1, None) == R.RPOD_ERR_INVALID_ARG
     assert lib.rpod_energy_rank(1, 0, 0.5, 1, None) == R.RPOD_ERR_INVALID_ARG
     assert lib.rpod_energy_rank(None, 4, 0.5, 1, None) == R.RPOD_ERR_INVALID_ARG
+
+
+def test_lstm_file_and_epoch_argument_checks(lib, tmp_path):
+    h = ctypes.c_void_p()
+    assert lib.rpod_lstm_load(ctypes.byref(h), str(tmp_path / "missing.bin").encode()) == R.RPOD_ERR_IO
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(b"not a model file" * 10)
+    assert lib.rpod_lstm_load(ctypes.byref(h), str(bad).encode()) == R.RPOD_ERR_IO
+    assert lib.rpod_lstm_load(None, str(bad).encode()) == R.RPOD_ERR_INVALID_ARG
+    assert R.rpod_strerror(R.RPOD_ERR_IO) == "file could not be read or written"
+    net = R.rpod_lstm_create(6, 8, 2, 2, 3, 4)
+    try:
+        assert R.rpod_lstm_dims(net) == (6, 8, 2, 2, 3, 4, 0)
+        # no loaded state to restore
+        assert lib.rpod_lstm_restore(net, None, 0, None) == R.RPOD_ERR_INVALID_ARG
+        # batch above max_batch, no full batch, d + out_dim != in_dim
+        assert lib.rpod_lstm_train_epoch(net, 1, 1, 2, 10, 4, 1, 10, 8, 1e-3, 1e-5, None, None, 0,
+                                         None) == R.RPOD_ERR_INVALID_ARG
+        assert lib.rpod_lstm_train_epoch(net, 1, 1, 2, 10, 4, 1, 3, 4, 1e-3, 1e-5, None, None, 0,
+                                         None) == R.RPOD_ERR_INVALID_ARG
+        assert lib.rpod_lstm_train_epoch(net, 1, 1, 2, 10, 3, 1, 10, 4, 1e-3, 1e-5, None, None, 0,
+                                         None) == R.RPOD_ERR_INVALID_ARG
+        # a valid call without a workspace
+        assert lib.rpod_lstm_train_epoch(net, 1, 1, 2, 10, 4, 1, 10, 4, 1e-3, 1e-5, None, None, 0,
+                                         None) == R.RPOD_ERR_WORKSPACE
+        assert lib.rpod_lstm_save(net, b"x", None, 0, None) == R.RPOD_ERR_WORKSPACE
+    finally:
+        R.rpod_lstm_destroy(net)

@@ -156,3 +156,62 @@ def test_dropout_training_passes_match_oracle(I, H, L, O, T, B, p):
     loss_o, _ = OL.mse(y_o, Yt.astype(np.float64))
     loss, _ = net.loss_grad(Xd, Yd)
     assert abs(loss.item() - loss_o) <= 1e-5 * loss_o
+
+
+def _series(n_series=5, t_len=40, O=4, d=2, seed=0):
+    g = torch.Generator().manual_seed(seed)
+    series = torch.randn((n_series, t_len, O), generator=g).cuda()
+    mu = torch.rand((n_series, d), generator=g).cuda()
+    return series, mu
+
+
+def test_train_epoch_equals_step_loop():
+    """rpod_lstm_train_epoch = gather + train_step over the same batches:
+    the same kernels in the same order, so the parameters agree bit for bit
+    and the reported loss is the mean of the step losses."""
+    I, H, L, O, T, B = 6, 16, 2, 4, 5, 8
+    series, mu = _series(O=O, d=I - O)
+    n_series, t_len = series.shape[:2]
+    g = torch.Generator().manual_seed(3)
+    pairs = torch.stack(torch.meshgrid(torch.arange(n_series), torch.arange(t_len - T),
+                                       indexing="ij"), -1).reshape(-1, 2)
+    idx = pairs[torch.randperm(pairs.shape[0], generator=g)].to(torch.int32).cuda()
+    theta = np.random.default_rng(1).uniform(-0.3, 0.3, OL.param_count(I, H, L, O))
+    a = R.LSTM(I, H, L, O, T, max_batch=B, theta=theta)
+    b = R.LSTM(I, H, L, O, T, max_batch=B, theta=theta)
+    a.set_dropout(0.2, 9)
+    b.set_dropout(0.2, 9)
+    mean = a.train_epoch(series, mu, idx, B).item()
+    losses = []
+    nb = idx.shape[0] // B
+    for k in range(nb):
+        X, Y = b.gather(series, mu, idx[k * B:(k + 1) * B])
+        losses.append(b.train_step(X, Y)[0].item())
+    torch.cuda.synchronize()
+    assert torch.equal(a.get_params(), b.get_params())
+    assert abs(mean - float(np.mean(losses))) <= 1e-6 * abs(float(np.mean(losses)))
+    assert a.launches() > nb * 10
+
+
+def test_save_load_restore_continues_training(tmp_path):
+    """A saved network, loaded and restored into a new workspace, holds the
+    same parameters and continues with the same Adam state and dropout
+    pass count: the next training step matches the original bit for bit."""
+    I, H, L, O, T, B = 6, 16, 3, 4, 5, 8
+    series, mu = _series(O=O, d=I - O, seed=2)
+    idx = torch.tensor([[s, t] for s in range(3) for t in range(0, 30, 3)], dtype=torch.int32).cuda()
+    theta = np.random.default_rng(2).uniform(-0.3, 0.3, OL.param_count(I, H, L, O))
+    a = R.LSTM(I, H, L, O, T, max_batch=B, theta=theta)
+    a.set_dropout(0.1, 4)
+    a.train_epoch(series, mu, idx, B)
+    path = tmp_path / "net.rpodlstm"
+    a.save(path)
+    c = R.LSTM.load(path)
+    assert c.dims == a.dims and c.max_batch == a.max_batch
+    assert torch.equal(a.get_params(), c.get_params())
+    X, Y = a.gather(series, mu, idx[:B])
+    la = a.train_step(X, Y)[0].item()
+    lc = c.train_step(X, Y)[0].item()
+    torch.cuda.synchronize()
+    assert la == lc
+    assert torch.equal(a.get_params(), c.get_params())
