@@ -375,6 +375,25 @@ int rpod_fluctuations(int64_t n, int64_t m, int64_t nt, const void* S, int64_t l
 int rpod_energy_rank(const double* sigma, int32_t count, double delta, int32_t* rank,
                      void* stream);
 
+/* Basis files (checkpoints of Alg. 1's output).  rpod_basis_save
+ * synchronises `stream` and writes the plan's parameters (n, m, k, p, q,
+ * seed, compute, flags) and the outputs of rpod_basis -- U (n x ku, ku = k or
+ * l with RPOD_FLAG_RETURN_ALL_L), sigma (l), C (k x m), in the plan's output
+ * type, ldu/ldc as for rpod_basis, device or host pointers -- to `path`
+ * (little-endian binary, magic "RPODBASE", version 1, column-major packed).
+ * rpod_basis_file_info reads info[0..8] = n, m, k, p, q, seed (the 64 bits),
+ * compute, flags, ku, enough to allocate the outputs and to recreate the
+ * plan; rpod_basis_load copies the three arrays into caller buffers (device
+ * or host, leading dimensions >= n and >= k) and synchronises `stream`.
+ * Errors: RPOD_ERR_IO for a file that cannot be opened, read or written or
+ * is not a basis file of this version; RPOD_ERR_INVALID_ARG for NULL
+ * pointers or short leading dimensions; RPOD_ERR_CUDA for a failed copy. */
+int rpod_basis_save(const rpod_plan* plan, const char* path, const void* U, int64_t ldu,
+                    const double* sigma, const void* C, int64_t ldc, void* stream);
+int rpod_basis_file_info(const char* path, int64_t* info);
+int rpod_basis_load(const char* path, void* U, int64_t ldu, double* sigma, void* C, int64_t ldc,
+                    void* stream);
+
 /* Synchronises `stream`, reads and clears the workspace status word.  Returns
  * the device-detected error (RPOD_OK if none) and stores warning bits in
  * *flags_out when it is not NULL. */

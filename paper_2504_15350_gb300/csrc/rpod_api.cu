@@ -1050,3 +1050,134 @@ int rpod_status_sync(const rpod_plan* P, void* workspace, void* stream, uint32_t
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Basis files: "RPODBASE", version 1, the plan's parameters, then U (n x ku),
+// sigma (l) and C (k x m), column-major and packed.
+namespace {
+constexpr char kBasisMagic[8] = {'R', 'P', 'O', 'D', 'B', 'A', 'S', 'E'};
+constexpr uint32_t kBasisVersion = 1;
+struct BasisHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t compute;
+  uint32_t flags;
+  int32_t k, p, q, ku, elem;
+  int64_t n, m;
+  uint64_t seed;
+};
+
+int read_basis_header(FILE* f, BasisHeader* h) {
+  if (fread(h, sizeof(*h), 1, f) != 1 || memcmp(h->magic, kBasisMagic, 8) != 0 ||
+      h->version != kBasisVersion || h->n < 1 || h->m < 1 || h->k < 1 || h->p < 0 || h->q < 0 ||
+      h->ku < h->k || h->ku > h->k + h->p || (h->elem != 4 && h->elem != 8))
+    return RPOD_ERR_IO;
+  return RPOD_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int rpod_basis_save(const rpod_plan* P, const char* path, const void* U, int64_t ldu,
+                    const double* sigma, const void* C, int64_t ldc, void* stream) {
+  if (!P || !path || !U || !sigma || !C) return RPOD_ERR_INVALID_ARG;
+  const int ku = (P->flags & RPOD_FLAG_RETURN_ALL_L) ? P->l : P->k;
+  const size_t es = P->compute == RPOD_F64 ? 8 : 4;
+  if (ldu < P->n || ldc < P->k) return RPOD_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<char> u, c;
+  std::vector<double> s;
+  try {
+    u.resize((size_t)P->n * ku * es);
+    c.resize((size_t)P->k * P->m * es);
+    s.resize(P->l);
+  } catch (...) {
+    return RPOD_ERR_INVALID_ARG;
+  }
+  if (cudaMemcpy2DAsync(u.data(), P->n * es, U, ldu * es, P->n * es, ku, cudaMemcpyDefault, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(s.data(), sigma, 8 * (size_t)P->l, cudaMemcpyDefault, st) != cudaSuccess ||
+      cudaMemcpy2DAsync(c.data(), P->k * es, C, ldc * es, P->k * es, P->m, cudaMemcpyDefault, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return RPOD_ERR_CUDA;
+  BasisHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, kBasisMagic, 8);
+  h.version = kBasisVersion;
+  h.compute = P->compute;
+  h.flags = P->flags;
+  h.k = P->k;
+  h.p = P->p;
+  h.q = P->q;
+  h.ku = ku;
+  h.elem = (int32_t)es;
+  h.n = P->n;
+  h.m = P->m;
+  h.seed = P->seed;
+  FILE* f = fopen(path, "wb");
+  if (!f) return RPOD_ERR_IO;
+  bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(u.data(), 1, u.size(), f) == u.size() &&
+            fwrite(s.data(), sizeof(double), s.size(), f) == s.size() &&
+            fwrite(c.data(), 1, c.size(), f) == c.size();
+  ok = (fclose(f) == 0) && ok;
+  return ok ? RPOD_OK : RPOD_ERR_IO;
+}
+
+int rpod_basis_file_info(const char* path, int64_t* info) {
+  if (!path || !info) return RPOD_ERR_INVALID_ARG;
+  FILE* f = fopen(path, "rb");
+  if (!f) return RPOD_ERR_IO;
+  BasisHeader h;
+  const int rc = read_basis_header(f, &h);
+  fclose(f);
+  if (rc) return rc;
+  const int64_t v[9] = {h.n, h.m, h.k, h.p, h.q, (int64_t)h.seed, h.compute, (int64_t)h.flags, h.ku};
+  memcpy(info, v, sizeof(v));
+  return RPOD_OK;
+}
+
+int rpod_basis_load(const char* path, void* U, int64_t ldu, double* sigma, void* C, int64_t ldc,
+                    void* stream) {
+  if (!path || !U || !sigma || !C) return RPOD_ERR_INVALID_ARG;
+  FILE* f = fopen(path, "rb");
+  if (!f) return RPOD_ERR_IO;
+  BasisHeader h;
+  if (int rc = read_basis_header(f, &h)) {
+    fclose(f);
+    return rc;
+  }
+  if (ldu < h.n || ldc < h.k) {
+    fclose(f);
+    return RPOD_ERR_INVALID_ARG;
+  }
+  const size_t es = (size_t)h.elem;
+  const int l = h.k + h.p;
+  std::vector<char> u, c;
+  std::vector<double> s;
+  try {
+    u.resize((size_t)h.n * h.ku * es);
+    c.resize((size_t)h.k * h.m * es);
+    s.resize(l);
+  } catch (...) {
+    fclose(f);
+    return RPOD_ERR_INVALID_ARG;
+  }
+  const bool ok = fread(u.data(), 1, u.size(), f) == u.size() &&
+                  fread(s.data(), sizeof(double), s.size(), f) == s.size() &&
+                  fread(c.data(), 1, c.size(), f) == c.size();
+  fclose(f);
+  if (!ok) return RPOD_ERR_IO;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the host buffers live until the copies are done
+  if (cudaMemcpy2DAsync(U, ldu * es, u.data(), h.n * es, h.n * es, h.ku, cudaMemcpyDefault, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(sigma, s.data(), 8 * (size_t)l, cudaMemcpyDefault, st) != cudaSuccess ||
+      cudaMemcpy2DAsync(C, ldc * es, c.data(), h.k * es, h.k * es, h.m, cudaMemcpyDefault, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return RPOD_ERR_CUDA;
+  return RPOD_OK;
+}
+
+}  // extern "C"

@@ -94,6 +94,9 @@ SIGNATURES = {
     "rpod_fluctuations": (ctypes.c_int, [_c_i64, _c_i64, _c_i64, _p, _c_i64, _c_i32, _p, _c_i64,
                                          _c_i32, _p, _c_i64, _c_i32, _p, _c_i64, _p]),
     "rpod_energy_rank": (ctypes.c_int, [_p, _c_i32, ctypes.c_double, _p, _p]),
+    "rpod_basis_save": (ctypes.c_int, [_p, ctypes.c_char_p, _p, _c_i64, _p, _p, _c_i64, _p]),
+    "rpod_basis_file_info": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_c_i64)]),
+    "rpod_basis_load": (ctypes.c_int, [ctypes.c_char_p, _p, _c_i64, _p, _p, _c_i64, _p]),
     "rpod_profile_enable": (ctypes.c_int, [_p, ctypes.c_int]),
     "rpod_profile_read": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -196,6 +199,37 @@ def rpod_fluctuations(n, m, nt, S, lds, s_dtype, F, ldf, f_dtype, H, ldh, h_dtyp
 
 def rpod_energy_rank(sigma, count, delta, rank, stream):
     return load().rpod_energy_rank(sigma, count, delta, rank, stream)
+
+
+def rpod_basis_save(plan, path, U, ldu, sigma, C, ldc, stream):
+    return load().rpod_basis_save(plan, os.fsencode(path), U, ldu, sigma, C, ldc, stream)
+
+
+def rpod_basis_file_info(path):
+    """(n, m, k, p, q, seed, compute, flags, ku) of a basis file."""
+    v = (_c_i64 * 9)()
+    _check(load().rpod_basis_file_info(os.fsencode(path), v), "rpod_basis_file_info")
+    out = [int(x) for x in v]
+    out[5] &= (1 << 64) - 1
+    return tuple(out)
+
+
+def rpod_basis_load(path, U, ldu, sigma, C, ldc, stream):
+    return load().rpod_basis_load(os.fsencode(path), U, ldu, sigma, C, ldc, stream)
+
+
+def load_basis(path, device="cuda"):
+    """(Plan, U, sigma, C) from a basis file: the plan recreated from the
+    file's parameters, the arrays on `device`."""
+    torch = _torch()
+    n, m, k, p, q, seed, compute, flags, ku = rpod_basis_file_info(path)
+    plan = Plan(n, m, k, p, q, seed=seed, compute=compute, flags=flags, device=device)
+    U = empty_colmajor(n, ku, plan.out_dtype, plan.device)
+    sigma = torch.empty(k + p, dtype=torch.float64, device=plan.device)
+    C = empty_colmajor(k, m, plan.out_dtype, plan.device)
+    _check(rpod_basis_load(path, U.data_ptr(), colmajor_ld(U), sigma.data_ptr(), C.data_ptr(),
+                           colmajor_ld(C), plan._stream()), "rpod_basis_load")
+    return plan, U, sigma, C
 
 
 def rpod_profile_enable(plan, enable):
@@ -388,6 +422,12 @@ class Plan:
                           colmajor_ld(C), self.ws_ptr, self.ws_bytes, self._stream())
         _check(rc, "rpod_project")
         return C
+
+    def save_basis(self, path, U, sigma, C):
+        """Writes the plan's parameters and the outputs of basis() to a file
+        (read back by load_basis)."""
+        _check(rpod_basis_save(self.handle, path, U.data_ptr(), colmajor_ld(U), sigma.data_ptr(),
+                               C.data_ptr(), colmajor_ld(C), self._stream()), "rpod_basis_save")
 
     def status(self):
         """(status code, warning flags) after synchronising the stream."""

@@ -134,3 +134,14 @@ def test_lstm_file_and_epoch_argument_checks(lib, tmp_path):
         assert lib.rpod_lstm_save(net, b"x", None, 0, None) == R.RPOD_ERR_WORKSPACE
     finally:
         R.rpod_lstm_destroy(net)
+
+
+def test_basis_file_errors(lib, tmp_path):
+    info = (ctypes.c_int64 * 9)()
+    assert lib.rpod_basis_file_info(str(tmp_path / "none.bin").encode(), info) == R.RPOD_ERR_IO
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(b"RPODBASE" + b"\0" * 100)      # right magic, wrong version
+    assert lib.rpod_basis_file_info(str(bad).encode(), info) == R.RPOD_ERR_IO
+    assert lib.rpod_basis_file_info(None, info) == R.RPOD_ERR_INVALID_ARG
+    assert lib.rpod_basis_load(str(bad).encode(), None, 1, None, None, 1, None) == R.RPOD_ERR_INVALID_ARG
+    assert lib.rpod_basis_save(None, b"x", 1, 1, 1, 1, 1, None) == R.RPOD_ERR_INVALID_ARG

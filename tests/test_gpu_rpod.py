@@ -217,3 +217,23 @@ def test_config2_fp32_full_size_properties():
     assert np.all(err <= 2e-5)
     del S
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("compute,flags", [("f64", 0), ("bf16", R.RPOD_FLAG_REFINE_FP32 | R.RPOD_FLAG_RETURN_ALL_L)])
+def test_basis_file_roundtrip(compute, flags, tmp_path):
+    """A basis written by rpod_basis_save and read by rpod_basis_load is the
+    same bit for bit, and the plan recreated from the file recomputes it."""
+    rec = make_recipe(32, 32, 300, 100, ("power", 1.5), seed=2, noise=1e-6)
+    S = snapshot_matrix(rec, dtype=torch.float64 if compute == "f64" else torch.float32)
+    plan = R.Plan(rec.n, rec.m, 10, 6, 1, seed=7, compute=compute, flags=flags)
+    Sd = S.t().contiguous().cuda().t()
+    U, sig, C = plan.basis(Sd)
+    path = tmp_path / "basis.rpod"
+    plan.save_basis(path, U, sig, C)
+    assert R.rpod_basis_file_info(path) == (rec.n, rec.m, 10, 6, 1, 7, plan.compute, flags,
+                                            U.shape[1])
+    plan2, U2, sig2, C2 = R.load_basis(path)
+    assert torch.equal(U, U2) and torch.equal(sig, sig2) and torch.equal(C, C2)
+    U3, sig3, C3 = plan2.basis(Sd)
+    torch.cuda.synchronize()
+    assert torch.equal(sig3, sig2) and torch.equal(U3, U2)
