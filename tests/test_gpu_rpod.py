@@ -237,3 +237,38 @@ def test_basis_file_roundtrip(compute, flags, tmp_path):
     U3, sig3, C3 = plan2.basis(Sd)
     torch.cuda.synchronize()
     assert torch.equal(sig3, sig2) and torch.equal(U3, U2)
+
+
+@pytest.mark.parametrize("compute", ["f64", "f32", "bf16"])
+def test_workspace_canary_and_output_padding(compute):
+    """Stands in for a memory checker: the whole workspace filled with NaN
+    bytes before the call changes nothing (no read of workspace bytes the call
+    has not written, the status block included), and the padding rows of U and
+    C (leading dimensions above n and k) keep their sentinel (no write outside
+    the outputs)."""
+    rng = np.random.default_rng(17)
+    n, m, k, p, q = 1003, 301, 9, 7, 1
+    dt = torch.float64 if compute == "f64" else torch.float32
+    S = torch.from_numpy(rng.standard_normal((n, m)) * np.logspace(0, -2, m)[None, :]).to(dt)
+    Sd = S.t().contiguous().cuda().t()
+    flags = R.RPOD_FLAG_REFINE_FP32 if compute == "bf16" else 0
+
+    def run(canary):
+        plan = R.Plan(n, m, k, p, q, seed=4, compute=compute, flags=flags)
+        if canary:
+            plan.ws.fill_(0xFF)
+        Ubuf = torch.full((k, n + 5), -7.0, dtype=plan.out_dtype, device="cuda")
+        U = Ubuf.t()[:n]                                   # n x k, ld n + 5
+        Cbuf = torch.full((m, k + 3), -7.0, dtype=plan.out_dtype, device="cuda")
+        C = Cbuf.t()[:k]                                   # k x m, ld k + 3
+        sig = torch.empty(k + p, dtype=torch.float64, device="cuda")
+        plan.basis(Sd, out=(U, sig, C))
+        rc, _ = plan.status()
+        return rc, Ubuf, sig, Cbuf
+
+    rc0, U0, s0, C0 = run(False)
+    rc1, U1, s1, C1 = run(True)
+    assert rc0 == R.RPOD_OK and rc1 == R.RPOD_OK
+    assert torch.equal(U0, U1) and torch.equal(s0, s1) and torch.equal(C0, C1)
+    assert bool((U1[:, n:] == -7.0).all()) and bool((C1[:, k:] == -7.0).all())
+    assert bool(torch.isfinite(U1[:, :n]).all()) and bool(torch.isfinite(C1[:, :k]).all())
