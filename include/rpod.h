@@ -394,6 +394,15 @@ int rpod_basis_file_info(const char* path, int64_t* info);
 int rpod_basis_load(const char* path, void* U, int64_t ldu, double* sigma, void* C, int64_t ldc,
                     void* stream);
 
+/* Self-test of the device-side bounded waits (failure detection without a
+ * GPU fault): one CTA waits on an mbarrier that nothing arrives on, with the
+ * bounded-wait helper of the staged kernels limited to `seconds` (0 < seconds
+ * <= 2), records the timeout in a status word of the library and returns;
+ * the call synchronises `stream` and returns RPOD_ERR_TIMEOUT (the designed
+ * outcome) or RPOD_OK if the wait completed.  The context stays usable.
+ * Errors: RPOD_ERR_INVALID_ARG for seconds outside (0, 2]. */
+int rpod_selftest_wait_timeout(double seconds, void* stream);
+
 /* Synchronises `stream`, reads and clears the workspace status word.  Returns
  * the device-detected error (RPOD_OK if none) and stores warning bits in
  * *flags_out when it is not NULL. */

@@ -86,12 +86,13 @@ __device__ __forceinline__ bool bar_ready(uint64_t* b) {
 }
 // Bounded wait for the single phase of a box barrier: false after the
 // deadline or once another thread of the CTA gave up.
-__device__ __noinline__ bool bar_wait(uint64_t* b, volatile int* abort_flag) {
+__device__ __noinline__ bool bar_wait(uint64_t* b, volatile int* abort_flag,
+                                      uint64_t limit_ns = kTimeoutNs) {
   if (bar_ready(b)) return true;
   const uint64_t t0 = now_ns();
   while (!bar_ready(b)) {
     if (*abort_flag) return false;
-    if (now_ns() - t0 > kTimeoutNs) {
+    if (now_ns() - t0 > limit_ns) {
       *abort_flag = 1;
       return false;
     }
@@ -405,6 +406,29 @@ k_fluct(const __grid_constant__ CUtensorMap tm_main, const __grid_constant__ CUt
   }
 }
 
+// Self-test of the bounded waits: the CTA waits on an mbarrier that nothing
+// arrives on (no copy is issued), through the same helper as the staged
+// tiles, limited to limit_ns; the expected outcome is the timeout status.
+__device__ unsigned g_selftest_status;
+
+__global__ void k_wait_selftest(uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    g_selftest_status = 0u;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sh32(&bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = bar_wait(&bar, &abort_flag, limit_ns);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!ok || abort_flag) atomicOr(&g_selftest_status, ST_TIMEOUT);
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(sh32(&bar)) : "memory");
+  }
+}
+
 // Eq. (energy) on the device, one thread: the smallest N with
 // c_N / c_count >= delta, c_N the sequential partial sums of sigma; 0 when
 // c_count is not positive.
@@ -630,6 +654,19 @@ extern "C" int rpod_fluctuations(int64_t n, int64_t m, int64_t nt, const void* S
       return dispatch3<__half, NoOut>(n, m, nt, s, lds, F, ldf, nullptr, 0, Sbar, ldb, st);
     }
   }
+}
+
+extern "C" int rpod_selftest_wait_timeout(double seconds, void* stream) {
+  if (!(seconds > 0.0) || !(seconds <= 2.0)) return RPOD_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  k_wait_selftest<<<1, 32, 0, st>>>((uint64_t)(seconds * 1e9));
+  if (cudaGetLastError() != cudaSuccess) return RPOD_ERR_CUDA;
+  unsigned h = 0;
+  if (cudaMemcpyFromSymbolAsync(&h, g_selftest_status, sizeof(h), 0, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return RPOD_ERR_CUDA;
+  return (h & ST_TIMEOUT) ? RPOD_ERR_TIMEOUT : RPOD_OK;
 }
 
 extern "C" int rpod_energy_rank(const double* sigma, int32_t count, double delta, int32_t* rank,

@@ -94,6 +94,7 @@ SIGNATURES = {
     "rpod_fluctuations": (ctypes.c_int, [_c_i64, _c_i64, _c_i64, _p, _c_i64, _c_i32, _p, _c_i64,
                                          _c_i32, _p, _c_i64, _c_i32, _p, _c_i64, _p]),
     "rpod_energy_rank": (ctypes.c_int, [_p, _c_i32, ctypes.c_double, _p, _p]),
+    "rpod_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_double, _p]),
     "rpod_basis_save": (ctypes.c_int, [_p, ctypes.c_char_p, _p, _c_i64, _p, _p, _c_i64, _p]),
     "rpod_basis_file_info": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_c_i64)]),
     "rpod_basis_load": (ctypes.c_int, [ctypes.c_char_p, _p, _c_i64, _p, _p, _c_i64, _p]),
@@ -195,6 +196,10 @@ def rpod_fluctuations(n, m, nt, S, lds, s_dtype, F, ldf, f_dtype, H, ldh, h_dtyp
                       stream):
     return load().rpod_fluctuations(n, m, nt, S, lds, s_dtype, F, ldf, f_dtype, H, ldh, h_dtype,
                                     Sbar, ldb, stream)
+
+
+def rpod_selftest_wait_timeout(seconds, stream):
+    return load().rpod_selftest_wait_timeout(float(seconds), stream)
 
 
 def rpod_energy_rank(sigma, count, delta, rank, stream):

@@ -145,3 +145,8 @@ def test_basis_file_errors(lib, tmp_path):
     assert lib.rpod_basis_file_info(None, info) == R.RPOD_ERR_INVALID_ARG
     assert lib.rpod_basis_load(str(bad).encode(), None, 1, None, None, 1, None) == R.RPOD_ERR_INVALID_ARG
     assert lib.rpod_basis_save(None, b"x", 1, 1, 1, 1, 1, None) == R.RPOD_ERR_INVALID_ARG
+
+
+def test_selftest_wait_argument_checks(lib):
+    for bad in (0.0, -1.0, 3.0, float("nan")):
+        assert lib.rpod_selftest_wait_timeout(bad, None) == R.RPOD_ERR_INVALID_ARG

@@ -272,3 +272,21 @@ def test_workspace_canary_and_output_padding(compute):
     assert torch.equal(U0, U1) and torch.equal(s0, s1) and torch.equal(C0, C1)
     assert bool((U1[:, n:] == -7.0).all()) and bool((C1[:, k:] == -7.0).all())
     assert bool(torch.isfinite(U1[:, :n]).all()) and bool(torch.isfinite(C1[:, :k]).all())
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """Failure detection without a GPU fault: a wait on an mbarrier that
+    nothing arrives on gives up after its limit and reports
+    RPOD_ERR_TIMEOUT through the status path; the context stays usable."""
+    import time
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc = R.rpod_selftest_wait_timeout(0.05, None)
+    dt = time.perf_counter() - t0
+    assert rc == R.RPOD_ERR_TIMEOUT
+    assert 0.05 <= dt < 1.5, dt
+    # the next calls run normally
+    rng = np.random.default_rng(3)
+    S = torch.from_numpy(rng.standard_normal((300, 120))).t().contiguous().t()
+    _, U, sig, C, rc2, _ = run_gpu(dev(S, torch.float64), 5, 3, 1, 1, "f64")
+    assert rc2 == R.RPOD_OK and np.all(np.isfinite(sig))
