@@ -530,25 +530,22 @@ def main():
         }
         del F, H, Sbar, fl_out, cplan
 
-    # end to end through the public API: pinned host S in, U/sigma/C out
+    # end to end through the C ABI with host buffers: a plan with
+    # RPOD_FLAG_HOST_IO takes pinned host S, U, sigma and C, and the copies
+    # run inside rpod_basis
     e2e = None
     if not args.no_e2e:
-        plan = hr["plan"]
-        U, sig, C = hr["out"]
+        hflags = (R.RPOD_FLAG_REFINE_FP32 if head == "bf16" else 0) | R.RPOD_FLAG_HOST_IO
+        plan = R.Plan(n, m, k, p, q, seed=w["seed"], compute=head, flags=hflags, device=dev)
         S_host = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
         S_host.copy_(S.t())
         U_h = torch.empty((k, n), dtype=torch.float32, pin_memory=True)
         s_h = torch.empty(l, dtype=torch.float64, pin_memory=True)
         C_h = torch.empty((m, k), dtype=torch.float32, pin_memory=True)
-        St = S.t()
         stream = torch.cuda.current_stream(dev)
 
         def e2e_step():
-            St.copy_(S_host, non_blocking=True)
-            plan.basis(S, out=(U, sig, C))
-            U_h.copy_(U.t(), non_blocking=True)
-            s_h.copy_(sig, non_blocking=True)
-            C_h.copy_(C.t(), non_blocking=True)
+            plan.basis(S_host.t(), out=(U_h.t(), s_h, C_h.t()))
 
         e2e_step()
         torch.cuda.synchronize()
@@ -562,9 +559,13 @@ def main():
         torch.cuda.synchronize()
         barrier()
         ems = max_over_ranks(a0.elapsed_time(a1) / args.e2e_steps)
+        rc, _ = plan.status()
+        if rc != R.RPOD_OK:
+            raise RuntimeError(f"e2e: device status {R.rpod_strerror(rc)}")
         e2e = {"value": ems / 1e3, "unit": "s", "h2d_bytes_per_step": 4 * n * m,
-               "d2h_bytes_per_step": 4 * n * k + 8 * l + 4 * k * m, "steps": args.e2e_steps}
-        del S_host
+               "d2h_bytes_per_step": 4 * n * k + 8 * l + 4 * k * m, "steps": args.e2e_steps,
+               "api": "rpod_basis with RPOD_FLAG_HOST_IO (pinned host S, U, sigma, C)"}
+        del S_host, plan
 
     batched = batched_f32 = None
     if not args.no_batched:

@@ -71,7 +71,14 @@ enum {
 /* Plan flags. */
 enum {
   RPOD_FLAG_REFINE_FP32 = 1u,  /* 16-bit forms: T = Q^T S reads an FP32 copy */
-  RPOD_FLAG_RETURN_ALL_L = 4u  /* U gets all l = k + p columns, not k */
+  RPOD_FLAG_RETURN_ALL_L = 4u, /* U gets all l = k + p columns, not k */
+  RPOD_FLAG_HOST_IO = 8u       /* rpod_basis takes HOST pointers for S, U, sigma and
+                                  C: S is copied into the workspace (which then holds
+                                  room for it, see rpod_workspace_bytes), the outputs
+                                  are copied back, all asynchronously on the stream
+                                  (host buffers must stay valid until it completes);
+                                  S in the compute type (FP32 for the 16-bit forms,
+                                  which then refine from it); no S_refine */
 };
 
 typedef struct rpod_plan rpod_plan;

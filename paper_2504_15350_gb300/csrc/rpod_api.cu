@@ -29,6 +29,9 @@ struct rpod_plan {
   // tensor-core forms: 16-bit copy of S, 16-bit operands (128 columns, zero
   // padded), TF32-rounded basis, split-K partials of the W-pass
   size_t off_sb, off_qb, off_zb, off_atf, off_wpart;
+  // RPOD_FLAG_HOST_IO: staging copies of S (ld ld_hs) and of U, sigma, C
+  size_t off_hs, off_hu, off_hsig, off_hc;
+  int64_t ld_hs;
   int64_t n_ld, m_ld;
   int nsplit_z, nsplit_t, nsplit_w;
   int nsz_def, nsw_def, split_cap;  // default split counts and the scale the buffers allow
@@ -542,7 +545,8 @@ static int plan_create_impl(rpod_plan** out, int64_t n, int64_t m, int32_t k, in
   if (n < 1 || m < 1 || k < 1 || p < 0 || q < 0 || l > n || l > m || l > kMaxL)
     return RPOD_ERR_INVALID_ARG;
   if (compute < RPOD_F64 || compute > RPOD_F16) return RPOD_ERR_INVALID_ARG;
-  if (flags & ~(uint32_t)(RPOD_FLAG_REFINE_FP32 | RPOD_FLAG_RETURN_ALL_L)) return RPOD_ERR_INVALID_ARG;
+  if (flags & ~(uint32_t)(RPOD_FLAG_REFINE_FP32 | RPOD_FLAG_RETURN_ALL_L | RPOD_FLAG_HOST_IO))
+    return RPOD_ERR_INVALID_ARG;
   if (n > ((int64_t)1 << 31) - 1024 || m > ((int64_t)1 << 31) - 1024) return RPOD_ERR_UNSUPPORTED;
   rpod_plan* P = new (std::nothrow) rpod_plan();
   if (!P) return RPOD_ERR_INVALID_ARG;
@@ -592,6 +596,18 @@ static int plan_create_impl(rpod_plan** out, int64_t n, int64_t m, int32_t k, in
     P->off_zb = take((size_t)2 * P->m_ld * 128);
     P->off_atf = take((size_t)4 * P->n_ld * 128);
     P->off_wpart = take(4 * P->wpart_elems);
+  }
+  P->off_hs = P->off_hu = P->off_hsig = P->off_hc = 0;
+  P->ld_hs = 0;
+  if (flags & RPOD_FLAG_HOST_IO) {
+    // S staged in the compute type (FP32 for the 16-bit forms, converted on
+    // the first pass), 16-element-aligned columns so the tensor maps apply
+    const size_t es = compute == RPOD_F64 ? 8 : 4;
+    P->ld_hs = round_up(n, 16);
+    P->off_hs = take(es * (size_t)P->ld_hs * m);
+    P->off_hu = take(w * n * L);
+    P->off_hsig = take(8 * L);
+    P->off_hc = take(w * (size_t)k * m);
   }
   P->total = off;
   P->side = nullptr;
@@ -643,10 +659,50 @@ static int check_ws(const rpod_plan* P, void* ws, size_t bytes) {
   return RPOD_OK;
 }
 
+static int basis_device(rpod_plan* P, const void* S, int64_t lds, int32_t s_dtype,
+                        const float* S_refine, int64_t ldr, void* U, int64_t ldu, double* sigma,
+                        void* C, int64_t ldc, void* workspace, size_t workspace_bytes,
+                        void* stream);
+
 int rpod_basis(rpod_plan* P, const void* S, int64_t lds, int32_t s_dtype, const float* S_refine,
                int64_t ldr, void* U, int64_t ldu, double* sigma, void* C, int64_t ldc,
                void* workspace, size_t workspace_bytes, void* stream) {
   if (!P || !S || !U || !sigma || !C) return RPOD_ERR_INVALID_ARG;
+  if (!(P->flags & RPOD_FLAG_HOST_IO))
+    return basis_device(P, S, lds, s_dtype, S_refine, ldr, U, ldu, sigma, C, ldc, workspace,
+                        workspace_bytes, stream);
+  // host buffers: S in (the compute type, or FP32 for the 16-bit forms),
+  // U, sigma, C out, through the workspace's staging copies
+  const int c = P->compute;
+  const int want = (c == RPOD_F64) ? RPOD_F64 : RPOD_F32;
+  if (s_dtype != want || S_refine) return RPOD_ERR_UNSUPPORTED;
+  if (lds < P->n || ldc < P->k || ldu < P->n) return RPOD_ERR_INVALID_ARG;
+  if (int rc = check_ws(P, workspace, workspace_bytes)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  const size_t es = c == RPOD_F64 ? 8 : 4;
+  const int ku = (P->flags & RPOD_FLAG_RETURN_ALL_L) ? P->l : P->k;
+  if (cudaMemcpy2DAsync(ws + P->off_hs, P->ld_hs * es, S, lds * es, P->n * es, P->m,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return RPOD_ERR_CUDA;
+  const int rc = basis_device(P, ws + P->off_hs, P->ld_hs, s_dtype, nullptr, 0, ws + P->off_hu,
+                              P->n, (double*)(ws + P->off_hsig), ws + P->off_hc, P->k, workspace,
+                              workspace_bytes, stream);
+  if (rc) return rc;
+  if (cudaMemcpy2DAsync(U, ldu * es, ws + P->off_hu, P->n * es, P->n * es, ku,
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(sigma, ws + P->off_hsig, 8 * (size_t)P->l, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaMemcpy2DAsync(C, ldc * es, ws + P->off_hc, P->k * es, P->k * es, P->m,
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return RPOD_ERR_CUDA;
+  return RPOD_OK;
+}
+
+static int basis_device(rpod_plan* P, const void* S, int64_t lds, int32_t s_dtype,
+                        const float* S_refine, int64_t ldr, void* U, int64_t ldu, double* sigma,
+                        void* C, int64_t ldc, void* workspace, size_t workspace_bytes,
+                        void* stream) {
   if (lds < P->n || ldc < P->k || ldu < P->n) return RPOD_ERR_INVALID_ARG;
   if (int rc = check_ws(P, workspace, workspace_bytes)) return rc;
   cudaStream_t st = (cudaStream_t)stream;
@@ -911,6 +967,8 @@ int rpod_batch_create(rpod_batch** out, int32_t count, const rpod_instance* inst
                       uint32_t flags, int32_t s_dtype) {
   if (!out || count < 1 || !inst) return RPOD_ERR_INVALID_ARG;
   *out = nullptr;
+  // batch instances live in device memory (one graph over all of them)
+  if (flags & RPOD_FLAG_HOST_IO) return RPOD_ERR_UNSUPPORTED;
   if ((compute == RPOD_F64 || compute == RPOD_F32) ? (s_dtype != compute)
                                                    : !(s_dtype == compute || s_dtype == RPOD_F32))
     return RPOD_ERR_INVALID_ARG;

@@ -29,6 +29,7 @@ RPOD_ERR_IO = 9
 RPOD_WARN_RANK_DEFICIENT = 1
 RPOD_FLAG_REFINE_FP32 = 1
 RPOD_FLAG_RETURN_ALL_L = 4
+RPOD_FLAG_HOST_IO = 8
 
 _c_i64, _c_i32, _c_u64, _c_u32, _p = (ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
                                       ctypes.c_uint32, ctypes.c_void_p)
@@ -402,7 +403,12 @@ class Plan:
         U n x k (or n x l), sigma (l,) float64, C k x m (column-major views)."""
         torch = _torch()
         ku = self.l if (self.flags & RPOD_FLAG_RETURN_ALL_L) else self.k
-        if out is None:
+        if out is None and (self.flags & RPOD_FLAG_HOST_IO):
+            # host outputs (pinned) for a plan that takes host buffers
+            U = torch.empty((ku, self.n), dtype=self.out_dtype, pin_memory=True).t()
+            sigma = torch.empty(self.l, dtype=torch.float64, pin_memory=True)
+            C = torch.empty((self.m, self.k), dtype=self.out_dtype, pin_memory=True).t()
+        elif out is None:
             U = empty_colmajor(self.n, ku, self.out_dtype, self.device)
             sigma = torch.empty(self.l, dtype=torch.float64, device=self.device)
             C = empty_colmajor(self.k, self.m, self.out_dtype, self.device)

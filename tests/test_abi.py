@@ -150,3 +150,20 @@ def test_basis_file_errors(lib, tmp_path):
 def test_selftest_wait_argument_checks(lib):
     for bad in (0.0, -1.0, 3.0, float("nan")):
         assert lib.rpod_selftest_wait_timeout(bad, None) == R.RPOD_ERR_INVALID_ARG
+
+
+def test_host_io_plan_workspace_and_batch_rejection(lib):
+    p0 = R.rpod_plan_create(5000, 300, 10, 5, 1, 0, R.RPOD_F32, 0)
+    p1 = R.rpod_plan_create(5000, 300, 10, 5, 1, 0, R.RPOD_F32, R.RPOD_FLAG_HOST_IO)
+    try:
+        # room for S (16-element-aligned columns) plus U, sigma and C
+        assert R.rpod_workspace_bytes(p1) >= R.rpod_workspace_bytes(p0) + 4 * 5008 * 300
+    finally:
+        R.rpod_plan_destroy(p0)
+        R.rpod_plan_destroy(p1)
+    inst = R.Instance(n=100, m=50, k=5, p=2, q=1, seed=0, S=1, lds=100, S_refine=None, ldr=0,
+                      U=1, ldu=100, sigma=1, C=1, ldc=5)
+    h = ctypes.c_void_p()
+    arr = (R.Instance * 1)(inst)
+    assert lib.rpod_batch_create(ctypes.byref(h), 1, arr, R.RPOD_F32, R.RPOD_FLAG_HOST_IO,
+                                 R.RPOD_F32) == R.RPOD_ERR_UNSUPPORTED

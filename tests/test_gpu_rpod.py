@@ -290,3 +290,31 @@ def test_bounded_wait_times_out_and_context_survives():
     S = torch.from_numpy(rng.standard_normal((300, 120))).t().contiguous().t()
     _, U, sig, C, rc2, _ = run_gpu(dev(S, torch.float64), 5, 3, 1, 1, "f64")
     assert rc2 == R.RPOD_OK and np.all(np.isfinite(sig))
+
+
+@pytest.mark.parametrize("compute", ["f64", "f32", "bf16"])
+def test_host_io_plan_matches_device_plan(compute):
+    """RPOD_FLAG_HOST_IO: rpod_basis on pinned host S, U, sigma and C (the
+    copies inside the call) gives the device plan's result."""
+    rng = np.random.default_rng(21)
+    n, m, k, p, q = 1030, 257, 8, 6, 1
+    dt = torch.float64 if compute == "f64" else torch.float32
+    S = torch.from_numpy(rng.standard_normal((n, m)) * np.logspace(0, -2, m)[None, :]).to(dt)
+    flags = R.RPOD_FLAG_REFINE_FP32 if compute == "bf16" else 0
+    pd = R.Plan(n, m, k, p, q, seed=6, compute=compute, flags=flags)
+    # the device S with the staging copy's 16-element-aligned columns, so both
+    # plans take the same (tensor-map) path
+    Sd = torch.zeros((m, (n + 15) // 16 * 16), dtype=dt, device="cuda").t()[:n]
+    Sd.copy_(S)
+    U0, s0, C0 = pd.basis(Sd)
+    ph = R.Plan(n, m, k, p, q, seed=6, compute=compute, flags=flags | R.RPOD_FLAG_HOST_IO)
+    Sh = torch.empty((m, n + 3), dtype=dt, pin_memory=True).t()[:n]    # ld n + 3
+    Sh.copy_(S)
+    U1, s1, C1 = ph.basis(Sh)
+    torch.cuda.synchronize()
+    assert not U1.is_cuda and not C1.is_cuda
+    assert ph.status()[0] == R.RPOD_OK
+    tol = 1e-12 if compute == "f64" else 1e-6
+    assert np.abs(s1.numpy() - s0.cpu().numpy()).max() <= tol * float(s0[0])
+    assert np.abs(U1.double().numpy() - U0.double().cpu().numpy()).max() <= 1e3 * tol
+    assert np.abs(C1.double().numpy() - C0.double().cpu().numpy()).max() <= tol * 10 * float(s0[0])
