@@ -72,8 +72,9 @@ def _worker(rank, world, port, align, q, out):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world,align,q", [(2, 64, 1), (3, 32, 2)])
+@pytest.mark.parametrize("world,align,q", [(2, 64, 1), (3, 32, 2), (3, 256, 0)])
 def test_row_sharded_rpod_equals_oracle(world, align, q):
+    # (3, 256, 0): 320 rows in two 256-row tiles, so rank 0 holds no rows
     port = _free_port()
     with mp.Manager() as mgr:
         out = mgr.dict()
