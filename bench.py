@@ -71,6 +71,13 @@ def parse():
                          "JSON object")
     ap.add_argument("--batched-config", default=None,
                     help="STREAMS,SPLIT_PCT: skip the tuner and use this launch configuration")
+    ap.add_argument("--no-small-configs", action="store_true",
+                    help="skip the config-1 (FP64) and config-3 (16-bit + refinement) timings")
+    ap.add_argument("--no-config6", action="store_true",
+                    help="skip the paper-shaped leg (n=8192, m=90225, k=10, p=75, q=1)")
+    ap.add_argument("--no-oracle-full", action="store_true",
+                    help="skip the full-size FP64 oracle run (cpu_baseline and parity); the "
+                         "baseline is then extrapolated from row samples")
     return ap.parse_args()
 
 
@@ -174,6 +181,56 @@ def cpu_oracle_time(rows: int) -> float:
     return time.perf_counter() - t0
 
 
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def cpu_single_thread_sample(rows=4096):
+    """The oracle on `rows` of the n grid cells (all m snapshots) in a fresh
+    interpreter whose BLAS is limited to one thread."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.cpu_oracle_time(%d)))" % (ROOT, rows))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=1800,
+                         env=env)
+    if out.returncode != 0:
+        return None
+    return {"seconds": json.loads(out.stdout.strip().splitlines()[-1]), "threads": 1, "rows": rows,
+            "sample": f"FP64 oracle, one BLAS thread, first {rows} of the "
+                      f"{WORKLOAD['nx'] * WORKLOAD['ny']} rows, all {WORKLOAD['m']} snapshots"}
+
+
+def oracle_full_size(S, U, sigma, k, p, q, seed):
+    """Runs the FP64 oracle (all host cores) on the full bench matrix -- the
+    same device data, copied to the host -- and compares the GPU result
+    with it: sigma_i relative error for i <= k and the largest principal
+    angle between span(U_k) of the two.  Returns the timing and errors."""
+    import numpy as np
+    from oracle.rpod import max_principal_angle
+    from oracle.rpod import rpod as oracle_rpod
+    S64 = S.cpu().double().numpy()                  # column-major (Fortran order)
+    t0 = time.perf_counter()
+    o = oracle_rpod(S64, k, p, q, seed=seed)
+    secs = time.perf_counter() - t0
+    del S64
+    sg = sigma.cpu().numpy()
+    Ug = U.double().cpu().numpy()
+    rel = np.abs(sg[:k] - o.sigma[:k]) / o.sigma[:k]
+    return {"seconds": secs, "cores": os.cpu_count(), "cpu": cpu_model(),
+            "sigma_max_rel_err_i_le_k": float(rel.max()),
+            "sigma_rel_err_at": int(rel.argmax()) + 1,
+            "max_principal_angle_Uk": max_principal_angle(o.U[:, :k], Ug),
+            "bounds": {"sigma": 1e-4, "angle": 1e-2},
+            "what": "GPU bf16+f32-refine result vs FP64 oracle (Alg. 1 in numpy, same S and sketch)"}
+
+
 def cpu_baseline(samples=CPU_SAMPLE_ROWS, repeats=1):
     """Times the oracle in a spawned interpreter at two row counts and
     extrapolates linearly in n (passes, QR of Y, lift and C scale with n;
@@ -251,7 +308,7 @@ def run_batched(dev, max_over_ranks, barrier, rank=0, world=1, steps=5, form="f3
         best = tuple(int(v) for v in config.split(","))
         B.configure(*best)
     else:
-        best = B.tune(trials=1)
+        best = B.tune(trials=3)
     B.run()
     rc, bad, _ = B.status()
     if rc != R.RPOD_OK:
@@ -279,6 +336,90 @@ def run_batched(dev, max_over_ranks, barrier, rank=0, world=1, steps=5, form="f3
            "effective_GBps": nbytes / (ms * 1e-3) / 1e9, "streams": best[0], "split_pct": best[1],
            "gpu_launches_per_batch": B.launches(), "graph_launches_per_batch": 1}
     del B, S
+    torch.cuda.empty_cache()
+    return out
+
+
+def time_basis(dev, S, k, p, q, compute, flags, warmup, steps, seed=0):
+    """Mean CUDA-event time (ms) of rpod_basis on the device matrix S, and
+    the plan's pass profile of the timed steps."""
+    import torch
+    import paper_2504_15350_gb300.rpod as R
+    n, m = S.shape
+    plan = R.Plan(n, m, k, p, q, seed=seed, compute=compute, flags=flags, device=dev)
+    l = k + p
+    odt = torch.float64 if compute == "f64" else torch.float32
+    out = (R.empty_colmajor(n, k, odt, dev), torch.empty(l, dtype=torch.float64, device=dev),
+           R.empty_colmajor(k, m, odt, dev))
+    for _ in range(warmup):
+        plan.basis(S, out=out)
+    rc, _ = plan.status()
+    if rc != R.RPOD_OK:
+        raise RuntimeError(f"{compute}: device status {R.rpod_strerror(rc)}")
+    plan.profile(True)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.basis(S, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    passes, pass_ms, pbytes, _ = plan.profile_read()
+    plan.profile(False)
+    if plan.status()[0] != R.RPOD_OK:
+        raise RuntimeError(f"{compute}: device status after timing")
+    return e0.elapsed_time(e1) / steps, passes, pass_ms, pbytes, plan.launches()
+
+
+def run_small_configs(dev, warmup):
+    """The config-1 shape (n = 4096 on a 64 x 64 grid, m = 500, 400 modes with
+    amplitudes j^-1.5, k = 20, p = 10, q = 1): the plain FP64 form and the
+    precision forms (BF16 and FP16 passes with the FP32 refinement pass).  S
+    (16 MB in FP64) stays in L2, so these are latency-bound: time-to-basis
+    only.  Their accuracy against the oracle is asserted by the GPU tests."""
+    import torch
+    import paper_2504_15350_gb300.rpod as R
+    from synth import make_recipe, snapshot_matrix
+    rec = make_recipe(64, 64, 500, 400, ("power", 1.5), seed=0, noise=1e-6)
+    S = snapshot_matrix(rec)
+    out = {}
+    for name, compute, dtype, flags in (("config1_f64", "f64", torch.float64, 0),
+                                        ("config3_bf16_refine", "bf16", torch.float32,
+                                         R.RPOD_FLAG_REFINE_FP32),
+                                        ("config3_f16_refine", "f16", torch.float32,
+                                         R.RPOD_FLAG_REFINE_FP32)):
+        Sd = S.t().contiguous().to(dtype).to(dev).t()
+        ms, _, _, _, launches = time_basis(dev, Sd, 20, 10, 1, compute, flags, warmup, 20)
+        out[name] = {"time_to_basis_s": ms / 1e3, "n": rec.n, "m": rec.m, "k": 20, "p": 10, "q": 1,
+                     "form": compute, "kernels_per_call": launches,
+                     "note": "S resident in L2: latency-bound, no roofline"}
+    return out
+
+
+def run_config6(dev, warmup, hbm_peak):
+    """The paper's own shape (Sec. 4.2, Table tab:cpu_time): n = 8192 grid
+    cells (64 x 128, h = 1/64), m = 90225 snapshots (225 parameter samples x
+    401 times), k = N^r = 10, p = 75, q = 1, synthetic modes with amplitudes
+    j^-1.5 (2.96 GB FP32).  Time-to-basis of both forms, next to the paper's
+    worst-case rPOD time of about 6 s on an unstated CPU (context only)."""
+    import torch
+    import paper_2504_15350_gb300.rpod as R
+    from synth import make_recipe, snapshot_matrix
+    rec = make_recipe(64, 128, 90225, 400, ("power", 1.5), seed=0, noise=1e-6)
+    S = snapshot_matrix(rec, device=dev, dtype=torch.float32)
+    out = {"n": rec.n, "m": rec.m, "k": 10, "p": 75, "q": 1,
+           "paper_rpod_s": 6.0, "paper_hardware": "CPU, unstated (Table tab:cpu_time)"}
+    for compute, flags in (("bf16", R.RPOD_FLAG_REFINE_FP32), ("f32", 0)):
+        ms, passes, pass_ms, pbytes, _ = time_basis(dev, S, 10, 75, 1, compute, flags, warmup, 5)
+        d = {"time_to_basis_s": ms / 1e3, "pass_ms_avg": pass_ms / max(passes, 1),
+             "passes_per_step": passes / 5}
+        if compute == "bf16":
+            gbs = pbytes / (pass_ms * 1e-3) / 1e9
+            d.update(pass_GBps=gbs, pass_frac_of_measured_hbm=gbs / hbm_peak)
+        out[compute] = d
+    out["speedup_vs_paper_bf16"] = out["paper_rpod_s"] / out["bf16"]["time_to_basis_s"]
+    del S
     torch.cuda.empty_cache()
     return out
 
@@ -339,11 +480,14 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    cpu, cpu_err, cpu1 = None, None, None
+    full_oracle = (not args.no_cpu_baseline and not args.no_oracle_full and rank == 0 and world == 1
+                   and args.ny == 512)
     if not args.no_cpu_baseline and rank == 0 and world == 1:
-        # the oracle runs in a spawned interpreter before any CUDA work here
-        cpu, cpu_err = cpu_baseline()
-    else:
-        cpu, cpu_err = None, None
+        # the sampled oracle runs in spawned interpreters before any CUDA work here
+        cpu1 = cpu_single_thread_sample()
+        if not full_oracle:
+            cpu, cpu_err = cpu_baseline()
 
     import torch
     import torch.distributed as dist
@@ -571,6 +715,9 @@ def main():
     if not args.no_batched:
         batched = run_batched(dev, max_over_ranks, barrier, rank, world, form="bf16")
         batched_f32 = run_batched(dev, max_over_ranks, barrier, rank, world, form="f32")
+    small = None if (args.no_small_configs or rank != 0) else run_small_configs(dev, args.warmup)
+    hbm_peak = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
+    cfg6 = None if (args.no_config6 or rank != 0) else run_config6(dev, args.warmup, hbm_peak)
     learned = None if (args.no_learned or rank != 0) else run_learned(dev, args.learned_epochs)
     fields = (run_fields_leg(dev, args.fields_epochs)
               if (args.fields_epochs > 0 and rank == 0) else None)
@@ -579,6 +726,19 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return
+    oracle_full = None
+    if full_oracle and "bf16" in results:
+        # the FP64 oracle on the same device matrix: the measured CPU baseline
+        # and the headline result's parity at full size
+        Ub, sb, _ = results["bf16"]["out"]
+        oracle_full = oracle_full_size(S, Ub, sb, k, p, q, w["seed"])
+        cpu = {"value": oracle_full["seconds"], "unit": "s", "cores": oracle_full["cores"],
+               "kind": "oracle", "cpu": oracle_full["cpu"],
+               "sample": (f"the full matrix ({n} x {m}, FP64 copy of the device data), numpy "
+                          f"BLAS on all {oracle_full['cores']} host cores, one run"),
+               "single_thread_sample": cpu1}
+    elif cpu is not None:
+        cpu["single_thread_sample"] = cpu1
     line = {
         "metric": METRIC, "value": hr["ms"] / 1e3, "unit": "s", "n_gpus": world,
         "steps": hr["steps"], "warmup": args.warmup, "ms_per_step": hr["ms"],
@@ -599,6 +759,9 @@ def main():
         "batched_f32": batched_f32,
         "learned": learned,
         "centered": centered,
+        "oracle_full": oracle_full,
+        "small_configs": small,
+        "config6_paper_shape": cfg6,
     }
     if fields is not None:
         line["fields"] = fields

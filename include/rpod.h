@@ -45,8 +45,16 @@ extern "C" {
 #endif
 
 /* Element types.  RPOD_F64/RPOD_F32 select the plain paths; RPOD_BF16 and
- * RPOD_F16 select the tensor-core precision forms (X in 16-bit, FP32
- * accumulation, FP64 Cholesky and small SVD). */
+ * RPOD_F16 select the tensor-core precision forms (passes over a 16-bit S,
+ * FP32 accumulation).  Small steps by form:
+ *   F64:         FP64 Grams and Cholesky factors (a shifted first round,
+ *                CholeskyQR3); the small SVD is one-sided Jacobi in FP64 on
+ *                the transposed Cholesky factor of T T^T (relative accuracy
+ *                of small singular values).
+ *   F32, 16-bit: FP64 sums of the Gram partials, an FP32 Cholesky factor with
+ *                a device-gated FP64 refactorization when a pivot shows a
+ *                condition number beyond FP32 reach; the small SVD is the FP32
+ *                eigen start of the FP64 Gram T T^T refined in FP64. */
 typedef enum { RPOD_F64 = 0, RPOD_F32 = 1, RPOD_BF16 = 2, RPOD_F16 = 3 } rpod_dtype;
 
 typedef enum {
@@ -59,7 +67,8 @@ typedef enum {
   RPOD_ERR_TIMEOUT = 6,       /* a device-side wait gave up */
   RPOD_ERR_CUDA = 7,          /* a CUDA runtime call failed */
   RPOD_ERR_WORKSPACE = 8,     /* workspace missing, too small or misaligned */
-  RPOD_ERR_IO = 9             /* a model file could not be read or written, or is not one */
+  RPOD_ERR_IO = 9,            /* a model file could not be read or written, or is not one */
+  RPOD_ERR_EXCHANGE = 10      /* the exchange callback of rpod_basis_rows reported a failure */
 } rpod_status;
 
 /* Warning bits returned through rpod_status_sync()'s flags_out. */
@@ -96,6 +105,16 @@ typedef struct rpod_plan rpod_plan;
  * Errors: RPOD_ERR_INVALID_ARG for bad sizes or a NULL `out`. */
 int rpod_plan_create(rpod_plan** out, int64_t n, int64_t m, int32_t k, int32_t p,
                      int32_t q, uint64_t seed, int32_t compute, uint32_t flags);
+
+/* Caps the one-sided Jacobi sweeps of the FP64 form's small SVD (Alg. 1,
+ * SVD of T; default 30, 1 <= max_sweeps <= 1000).  A sweep visits every
+ * pair of columns once; the iteration has converged when a sweep rotates no
+ * pair.  When the cap is reached first, rpod_basis still writes its outputs
+ * (from the last sweep) and rpod_status_sync reports
+ * RPOD_ERR_NO_CONVERGENCE.  Errors: RPOD_ERR_INVALID_ARG for a NULL plan or a
+ * cap outside the range; RPOD_ERR_UNSUPPORTED for a plan whose compute type
+ * is not RPOD_F64 (those forms take no Jacobi sweeps). */
+int rpod_plan_set_svd_sweeps(rpod_plan* plan, int32_t max_sweeps);
 
 /* Bytes of device workspace the plan needs (for any of its calls). */
 int rpod_workspace_bytes(const rpod_plan* plan, size_t* bytes);
@@ -146,7 +165,7 @@ int rpod_sample(const rpod_plan* plan, const void* A, int64_t lda, const void* S
 /* Pass profiling.  rpod_profile_enable(plan, 1) creates CUDA events and
  * resets the counters; from then on rpod_basis records events on its stream
  * around every pass over S (the products S Lambda, S^T Q, S Z and Q^T S), up
- * to 64 passes in total.  rpod_profile_read synchronises on the last recorded
+ * to 1024 passes in total.  rpod_profile_read synchronises on the last recorded
  * event and returns, summed over the recorded passes, their number, their
  * device time in ms and their algorithmic bytes and flops (bytes of S and of
  * the skinny operands read or written; 2 n m l flops per product). */
@@ -164,15 +183,72 @@ int rpod_profile_read(const rpod_plan* plan, int* passes, double* pass_ms, doubl
  * partial sums live in a 16 MiB array inside the library that every GPU which
  * loads the library holds until the process exits; nothing is allocated.
  * Limit: kc * m_new * sizeof(element) <= 16 MiB, else RPOD_ERR_UNSUPPORTED
- * (project larger S' in column blocks).  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  All calls share the array: calls whose kernels
+ * (project larger S' in column blocks).  Every call outside a stream capture
+ * looks up the array's device address (cudaGetSymbolAddress), so a device
+ * reset is followed correctly; a call during a capture reuses the address
+ * the last call outside one found, so make one call on the device before
+ * capturing.  All calls share the array: calls whose kernels
  * overlap on the GPU (several streams or host threads) race and must be
  * serialised by the caller.  No part of the array needs clearing between
  * calls.  Asynchronous on `stream`; argument errors are returned at once. */
 int rpod_project_static(const rpod_plan* plan, const void* U, int64_t ldu, int32_t kc,
                         const void* S_new, int64_t lds, int64_t m_new, int32_t s_dtype,
                         void* C, int64_t ldc, void* stream);
+
+/* ---- Row-sharded rPOD --------------------------------------------------
+ * Alg. 1 on a matrix whose rows (grid cells) are split into contiguous
+ * blocks held by different calls -- one per GPU, each in its own process or
+ * host thread.  Every call runs the passes over its own block; at each point
+ * where Alg. 1 needs a quantity of the whole matrix the call hands a partial
+ * result to the caller's exchange callback, which must combine it with the
+ * other blocks' and leave the combined values in place on every block:
+ *   the l x l Gram P^T P of each CholeskyQR round   sum   (l^2 values)
+ *   Z = S^T Q of each subspace iteration            sum   (m l values)
+ *   T = Q^T S                                       sum   (m l values)
+ *   the sign rule (largest-magnitude entry of each column of U over all
+ *   rows, ties to the lowest global row)            max, min, sum (ku values each)
+ * so a pass over S costs one exchange of its small result.  The sketch, the
+ * QR of Z, the small SVD and C = Uhat_k^T T are computed identically by
+ * every call; U's rows stay with their block.  With q subspace iterations
+ * the FP64 form makes 3q + 7 exchanges, in the same order on every block:
+ * the Grams of two CholeskyQR rounds per intermediate basis and of three
+ * for the final one (2q + 3), Z (q), T (1) and the signs (3).
+ *
+ * The callback runs on the calling host thread after the work producing
+ * buf was enqueued on `stream` (buf is a device pointer into the
+ * workspace, `count` values of `dtype` RPOD_F64 or RPOD_F32).  It must
+ * complete the combination before later work on `stream` reads buf, e.g.
+ * by ncclAllReduce(buf, buf, count, ..., stream) on a communicator over the
+ * blocks, or by synchronising the stream and combining on the host.  It
+ * returns 0 on success; any other value makes rpod_basis_rows return
+ * RPOD_ERR_EXCHANGE at once (the other blocks' calls then wait on their
+ * next exchange: the caller must fail them too). */
+enum { RPOD_REDUCE_SUM = 0, RPOD_REDUCE_MAX = 1, RPOD_REDUCE_MIN = 2 };
+typedef int (*rpod_exchange_fn)(void* ctx, void* buf, int64_t count, int32_t dtype, int32_t op,
+                                void* stream);
+
+/* Plan for the row block row0 .. row0 + n_rows - 1 (1 <= n_rows,
+ * row0 + n_rows <= n_total) of an n_total x m matrix; k, p, q, seed, compute
+ * and flags as for rpod_plan_create, with l <= min(n_total, m, 128).
+ * Supported: compute RPOD_F64 (RPOD_ERR_UNSUPPORTED otherwise), flags 0 or
+ * RPOD_FLAG_RETURN_ALL_L.  Every block's plan must use the same n_total, m,
+ * k, p, q, seed, compute and flags.  Use with rpod_basis_rows only
+ * (rpod_basis and rpod_project refuse it with RPOD_ERR_INVALID_ARG). */
+int rpod_rows_plan_create(rpod_plan** out, int64_t n_total, int64_t row0, int64_t n_rows,
+                          int64_t m, int32_t k, int32_t p, int32_t q, uint64_t seed,
+                          int32_t compute, uint32_t flags);
+
+/* Alg. 1 on this plan's row block S_rows (n_rows x m, leading dimension
+ * lds >= n_rows, type RPOD_F64).  Writes this block's rows of U (n_rows x ku,
+ * ldu >= n_rows), and the whole sigma (l) and C (k x m), identical on every
+ * block.  Workspace as for rpod_basis (rpod_workspace_bytes of this plan).
+ * Errors: RPOD_ERR_INVALID_ARG for a plan not made by
+ * rpod_rows_plan_create, NULL pointers or short leading dimensions;
+ * RPOD_ERR_EXCHANGE when the callback fails; device errors through
+ * rpod_status_sync as for rpod_basis. */
+int rpod_basis_rows(rpod_plan* plan, const void* S_rows, int64_t lds, int32_t s_dtype, void* U_rows,
+                    int64_t ldu, double* sigma, void* C, int64_t ldc, void* workspace,
+                    size_t workspace_bytes, void* stream, rpod_exchange_fn exchange, void* ctx);
 
 /* ---- Batched rPOD ------------------------------------------------------
  * Many independent instances of Alg. 1 (e.g. the 4 fields psi_1, psi_2, q_1,

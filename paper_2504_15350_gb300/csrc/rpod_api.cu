@@ -1,5 +1,6 @@
 // C ABI of librpod (declared in include/rpod.h): plans, workspace layout and
 // the host-side orchestration of Alg. 1 (Sec. 4.2) on one CUDA stream.
+#include <float.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -37,10 +38,20 @@ struct rpod_plan {
   int nsz_def, nsw_def, split_cap;  // default split counts and the scale the buffers allow
   size_t part_elems, gpart_elems, sign_bytes, wpart_elems;
   int last_launches;
+  int svd_sweeps;  // cap on the FP64 form's one-sided Jacobi sweeps
+  // row-sharded plans (rpod_rows_plan_create): this plan's rows are rows
+  // row0 .. row0 + n - 1 of an n_total x m matrix whose other row blocks
+  // belong to other calls; the exchange callback is set for one
+  // rpod_basis_rows call at a time
+  int rows_mode;
+  int64_t n_total, row0;
+  rpod_exchange_fn xch;
+  void* xch_ctx;
+  size_t off_xch;  // 3 l doubles: the sign rule's exchanged candidates
   // pass profiling
   int prof_on;
   int prof_n;
-  cudaEvent_t prof_ev[2 * 64];
+  cudaEvent_t* prof_ev;  // 2 * kProfPasses events while profiling
   double prof_bytes, prof_flops;
   // side stream and fork/join events (16-bit forms: the last CholeskyQR
   // round runs beside the refinement pass); null when they could not be made
@@ -49,6 +60,10 @@ struct rpod_plan {
 };
 
 namespace rpod {
+// Passes a profiled plan records (begin and end event each); later passes
+// are not recorded.
+constexpr int kProfPasses = 1024;
+
 // Read-only view of a plan for the allocation-free projection.
 __attribute__((visibility("hidden"))) void plan_shape(const rpod_plan* P, int64_t* n, int32_t* l,
                                                       int32_t* compute, int32_t* nsplit) {
@@ -60,11 +75,11 @@ __attribute__((visibility("hidden"))) void plan_shape(const rpod_plan* P, int64_
 
 // Pass profiling hooks used by the pipelines.
 void prof_begin(rpod_plan* P, cudaStream_t st) {
-  if (!P->prof_on || P->prof_n >= 64) return;
+  if (!P->prof_on || P->prof_n >= kProfPasses) return;
   cudaEventRecord(P->prof_ev[2 * P->prof_n], st);
 }
 void prof_end(rpod_plan* P, cudaStream_t st, double bytes, double flops) {
-  if (!P->prof_on || P->prof_n >= 64) return;
+  if (!P->prof_on || P->prof_n >= kProfPasses) return;
   cudaEventRecord(P->prof_ev[2 * P->prof_n + 1], st);
   ++P->prof_n;
   P->prof_bytes += bytes;
@@ -109,6 +124,14 @@ struct Run {
 
   W* buf(size_t off) { return (W*)(ws + off); }
   double* dbuf(size_t off) { return (double*)(ws + off); }
+
+  // Row-sharded plans: combine `count` values at the device pointer p with
+  // every other row block through the caller's exchange callback (after the
+  // work that produced them was enqueued on st); no-op otherwise.
+  int exchange(void* p, int64_t count, int dtype, int op) {
+    if (!P->rows_mode) return RPOD_OK;
+    return P->xch(P->xch_ctx, p, count, dtype, op, (void*)st) == 0 ? RPOD_OK : RPOD_ERR_EXCHANGE;
+  }
 
   // Gram G = A^T A (A rows x l, ld lda) in FP64: products in W, summed in W
   // within a split of rows, then in FP64 across splits.  FP32 (when A is
@@ -163,8 +186,10 @@ struct Run {
   };
 
   // `ld`: leading dimension of in and tmp (rows when 0).
+  // `dist`: the rows are this plan's block of a row-sharded matrix, so each
+  // round's Gram is summed over the row blocks before its factorization.
   int orth(W* in, W* tmp, int64_t rows, int rounds, W** out, bool exact_last, bool defer = false,
-           TcOut* tco = nullptr, int64_t ld = 0) {
+           TcOut* tco = nullptr, int64_t ld = 0, bool dist = false) {
     if (ld == 0) ld = rows;
     const int l = P->l;
     const double tol = sizeof(W) == 8 ? 1e-13 : 1e-5;
@@ -173,14 +198,22 @@ struct Run {
                                   : (int)std::max<int64_t>(1, std::min<int64_t>(2 * 152, rows / 256));
     W* src = in;
     W* dst = tmp;
+    // FP64 form: shifted CholeskyQR (the first round factors G + s I), so
+    // that sampled matrices whose condition number reaches u^-1 keep every
+    // direction; the callers add one round for it
+    const double grows = (dist && P->rows_mode) ? (double)P->n_total : (double)rows;
+    const double shift_coef =
+        sizeof(W) == 8 ? 11.0 * (grows * l + (double)l * (l + 1)) * (DBL_EPSILON / 2) : 0.0;
     for (int r = 0; r < rounds; ++r) {
       double* G = dbuf(P->off_g);
       CR(gram(src, rows, ld, G, ns, !(exact_last && r == rounds - 1)));
+      if (dist) CR(exchange(G, (int64_t)l * l, sizeof(W) == 8 ? RPOD_F64 : RPOD_F32, RPOD_REDUCE_SUM));
       // the FP64 copy of R^-1 is read only for a deferred last round (and
       // by the FP64 form)
       double* xd = (sizeof(W) == 8 || (defer && r == rounds - 1)) ? dbuf(P->off_x) : nullptr;
       CK((cholesky<W>(st, l, G, tol, r, xd, buf(P->off_xw), l, status,
-                      sizeof(W) == 4 ? (const float*)src : nullptr, rows, dbuf(P->off_gpart), ns, ld)));
+                      sizeof(W) == 4 ? (const float*)src : nullptr, rows, dbuf(P->off_gpart), ns, ld,
+                      r == 0 ? shift_coef : 0.0, sizeof(W) == 8 && r > 0)));
       if (defer && r == rounds - 1) break;
       const bool last_apply = r == rounds - 1 - (defer ? 1 : 0);
       int rc = RPOD_ERR_UNSUPPORTED;
@@ -237,14 +270,21 @@ struct Run {
                               (int64_t)l * l, status, false)));
     CK((reduce_splits<double, double>(st, l, l, ns, dbuf(P->off_gpart), GT, 1, l)));
     double* Uhat = dbuf(P->off_uhat);
-    // FP32 start from the tridiagonal reduction (eigenvectors to about
-    // 1e-5), then FP64 refinement passes, each of which squares the
-    // eigenvector error outside clusters; the cluster threshold of a pass
-    // scales with the norm of all remaining off-diagonal terms, so
-    // eigenvalues closer than that are separated only by a later pass: two
-    // passes for the FP32 forms (orthogonality near 1e-9), five for the
-    // FP64 form.
-    CK((sym_eig(st, l, GT, sigma, Uhat, dbuf(P->off_eig), status, sizeof(W) == 8 ? 5 : 2)));
+    if (sizeof(W) == 8) {
+      // FP64 form: one-sided Jacobi sweeps on the transposed Cholesky factor
+      // of the Gram, which keep the relative accuracy of small singular
+      // values (an eigen-decomposition of the Gram is accurate only
+      // relative to sigma_1^2)
+      CK(jacobi_svd(st, l, GT, Uhat, sigma, status, P->svd_sweeps));
+    } else {
+      // FP32 and 16-bit forms: FP32 start from the tridiagonal reduction
+      // (eigenvectors to about 1e-5), then two FP64 refinement passes, each
+      // of which squares the eigenvector error outside clusters
+      // (orthogonality near 1e-9); the cluster threshold of a pass scales
+      // with the norm of all remaining off-diagonal terms, so eigenvalues
+      // closer than that are separated only by a later pass
+      CK((sym_eig(st, l, GT, sigma, Uhat, dbuf(P->off_eig), status, 2)));
+    }
     CK((check_finite_vec(st, l, sigma, status)));
     // Alg. 1: lift U = Q Uhat (first k or all l columns), then the sign rule
     const int ku = (P->flags & RPOD_FLAG_RETURN_ALL_L) ? l : k;
@@ -270,7 +310,22 @@ struct Run {
     if (rc == RPOD_ERR_CUDA) return rc;
     if (rc != RPOD_OK)
       CK((gemm<W, W, W, W>(st, false, n, ku, l, 1, Q, n, Uw, l, U, 1, ldu, 0, status, false)));
-    CK((sign_fix<W>(st, n, ku, U, ldu, Uhat, l, ws + P->off_sign, P->sign_bytes)));
+    if (P->rows_mode) {
+      // the largest-magnitude entry of each column over all row blocks (ties
+      // to the lowest global row) decides its sign: three exchanges of l
+      // values -- the largest magnitude, the lowest row holding it, the sign
+      // of the entry there
+      double* xb = dbuf(P->off_xch);
+      CK((sign_rows_candidates<W>(st, n, ku, U, ldu, P->row0, xb, ws + P->off_sign, P->sign_bytes)));
+      CR(exchange(xb, ku, RPOD_F64, RPOD_REDUCE_MAX));
+      CK(sign_rows_step(st, ku, xb, 1));
+      CR(exchange(xb + ku, ku, RPOD_F64, RPOD_REDUCE_MIN));
+      CK(sign_rows_step(st, ku, xb, 2));
+      CR(exchange(xb + 2 * ku, ku, RPOD_F64, RPOD_REDUCE_SUM));
+      CK((sign_rows_apply<W>(st, n, ku, U, ldu, Uhat, l, xb)));
+    } else {
+      CK((sign_fix<W>(st, n, ku, U, ldu, Uhat, l, ws + P->off_sign, P->sign_bytes)));
+    }
     // Sec. 4.3 coefficients C = U_k^T S = Uhat_k^T T (k x m), Uhat with the signs
     CK((convert_matrix<double, W>(st, l, k, Uhat, l, Uw, l)));
     CK((gemm<W, W, W, W>(st, false, m, k, l, 1, Tt, m, Uw, l, C, ldc, 1, 0, status, false)));
@@ -290,6 +345,8 @@ struct Run {
     const double sw = sizeof(W);
     const double pass_bytes = sw * ((double)n * m + (double)n * l + (double)m * l);
     const double pass_flops = 2.0 * n * m * l;
+    // the shifted first CholeskyQR round of the FP64 form (see orth)
+    const int extra = sizeof(W) == 8 ? 1 : 0;
     // Alg. 1: Gaussian sketch
     CK((sketch<W>(st, P->seed, 0, m, l, Lam, m)));
     // Alg. 1: P = S Lambda (pass over S; flags non-finite input)
@@ -305,15 +362,16 @@ struct Run {
                              status, false)));
         prof_end(P, st, pass_bytes, pass_flops);
         CK((reduce_splits<W, W>(st, m, l, P->nsplit_z, part, Z, 1, m)));
+        CR(exchange(Z, m * l, sizeof(W) == 8 ? RPOD_F64 : RPOD_F32, RPOD_REDUCE_SUM));
         W* Zo = nullptr;
-        CR(orth(Z, Zq, m, 1, &Zo, false));
+        CR(orth(Z, Zq, m, 1 + extra, &Zo, false));
         prof_begin(P, st);
         CK((gemm<W, W, W, W>(st, false, n, l, m, 1, S, lds, Zo, m, Y, 1, n, 0, status, false)));
         prof_end(P, st, pass_bytes, pass_flops);
       }
       // Alg. 1 QR of the sampled matrix (CholeskyQR2 for the final basis);
       // Y's buffer is free again once Z = S^T Q is formed
-      CR(orth(Y, Qb, n, it == q ? 2 : 1, &Q, it == q, it == q));
+      CR(orth(Y, Qb, n, (it == q ? 2 : 1) + extra, &Q, it == q, it == q, nullptr, 0, true));
     }
     // Alg. 1: T = Q^T S, stored transposed (m x l), with the deferred last
     // CholeskyQR factor folded in afterwards
@@ -322,6 +380,7 @@ struct Run {
                          false)));
     prof_end(P, st, pass_bytes, pass_flops);
     CK((reduce_splits<W, W>(st, m, l, P->nsplit_z, part, Zq, 1, m)));
+    CR(exchange(Zq, m * l, sizeof(W) == 8 ? RPOD_F64 : RPOD_F32, RPOD_REDUCE_SUM));
     CR(fold_t(Zq, Tt));
     return finish(Q, Tt, U, ldu, sigma, C, ldc, true);
   }
@@ -390,7 +449,12 @@ struct Run {
     }
     float* Q = nullptr;
     const bool refine_req = (P->flags & RPOD_FLAG_REFINE_FP32) && Sref;
-    const bool refine_tma = refine_req && (((uintptr_t)Sref & 15) == 0) && ((ldr * 4) % 16 == 0);
+    // BF16: the refinement pass on the TF32 tensor path (S and Q rounded to
+    // TF32, about 2e-5 relative error in sigma, below the form's 1e-4 bound).
+    // FP16 stores S to 2^-11 and is held to 1e-5: its refinement pass keeps
+    // exact FP32 products (SIMT), which the TF32 rounding would not
+    const bool refine_tma = refine_req && dt == RPOD_BF16 && (((uintptr_t)Sref & 15) == 0) &&
+                            ((ldr * 4) % 16 == 0);
     float* const Atf = (float*)(ws + P->off_atf);
     bool tf_ready = false;
     for (int it = 0; it <= q; ++it) {
@@ -530,19 +594,22 @@ const char* rpod_strerror(int s) {
     case RPOD_ERR_CUDA: return "CUDA error";
     case RPOD_ERR_WORKSPACE: return "workspace missing or too small";
     case RPOD_ERR_IO: return "file could not be read or written";
+    case RPOD_ERR_EXCHANGE: return "exchange callback failed";
     default: return "unknown status";
   }
 }
 
 // split_cap: the split-K counts of the passes may later be scaled up to this
 // factor (the batch autotuner), so the partial buffers are sized for it.
+// n_rank: the row count that bounds l (n, or n_total for a row block).
 static int plan_create_impl(rpod_plan** out, int64_t n, int64_t m, int32_t k, int32_t p,
                             int32_t q, uint64_t seed, int32_t compute, uint32_t flags,
-                            int split_cap) {
+                            int split_cap, int64_t n_rank = 0) {
   if (!out) return RPOD_ERR_INVALID_ARG;
   *out = nullptr;
   const int64_t l = (int64_t)k + p;
-  if (n < 1 || m < 1 || k < 1 || p < 0 || q < 0 || l > n || l > m || l > kMaxL)
+  if (n_rank == 0) n_rank = n;
+  if (n < 1 || m < 1 || k < 1 || p < 0 || q < 0 || l > n_rank || l > m || l > kMaxL)
     return RPOD_ERR_INVALID_ARG;
   if (compute < RPOD_F64 || compute > RPOD_F16) return RPOD_ERR_INVALID_ARG;
   if (flags & ~(uint32_t)(RPOD_FLAG_REFINE_FP32 | RPOD_FLAG_RETURN_ALL_L | RPOD_FLAG_HOST_IO))
@@ -581,6 +648,7 @@ static int plan_create_impl(rpod_plan** out, int64_t n, int64_t m, int32_t k, in
   P->off_sigma = take(8 * L);
   P->off_uhat = take(8 * L * L);
   P->off_sign = take(P->sign_bytes);
+  P->off_xch = take(8 * 6 * L);
   P->n_ld = round_up(n, 64);
   P->m_ld = round_up(m, 64);
   P->off_sb = P->off_qb = P->off_zb = P->off_atf = P->off_wpart = 0;
@@ -625,6 +693,7 @@ static int plan_create_impl(rpod_plan** out, int64_t n, int64_t m, int32_t k, in
     cudaGetLastError();
   }
   P->last_launches = 0;
+  P->svd_sweeps = 30;
   *out = P;
   return RPOD_OK;
 }
@@ -632,6 +701,32 @@ static int plan_create_impl(rpod_plan** out, int64_t n, int64_t m, int32_t k, in
 int rpod_plan_create(rpod_plan** out, int64_t n, int64_t m, int32_t k, int32_t p, int32_t q,
                      uint64_t seed, int32_t compute, uint32_t flags) {
   return plan_create_impl(out, n, m, k, p, q, seed, compute, flags, 1);
+}
+
+int rpod_rows_plan_create(rpod_plan** out, int64_t n_total, int64_t row0, int64_t n_rows, int64_t m,
+                          int32_t k, int32_t p, int32_t q, uint64_t seed, int32_t compute,
+                          uint32_t flags) {
+  if (!out) return RPOD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n_rows < 1 || row0 < 0 || n_total < 1 || row0 + n_rows > n_total) return RPOD_ERR_INVALID_ARG;
+  if (flags & ~(uint32_t)RPOD_FLAG_RETURN_ALL_L) return RPOD_ERR_UNSUPPORTED;
+  if (compute != RPOD_F64) return (compute >= RPOD_F64 && compute <= RPOD_F16) ? RPOD_ERR_UNSUPPORTED
+                                                                              : RPOD_ERR_INVALID_ARG;
+  rpod_plan* P = nullptr;
+  const int rc = plan_create_impl(&P, n_rows, m, k, p, q, seed, compute, flags, 1, n_total);
+  if (rc != RPOD_OK) return rc;
+  P->rows_mode = 1;
+  P->n_total = n_total;
+  P->row0 = row0;
+  *out = P;
+  return RPOD_OK;
+}
+
+int rpod_plan_set_svd_sweeps(rpod_plan* P, int32_t max_sweeps) {
+  if (!P || max_sweeps < 1 || max_sweeps > 1000) return RPOD_ERR_INVALID_ARG;
+  if (P->compute != RPOD_F64) return RPOD_ERR_UNSUPPORTED;
+  P->svd_sweeps = max_sweeps;
+  return RPOD_OK;
 }
 
 int rpod_workspace_bytes(const rpod_plan* P, size_t* bytes) {
@@ -664,10 +759,25 @@ static int basis_device(rpod_plan* P, const void* S, int64_t lds, int32_t s_dtyp
                         void* C, int64_t ldc, void* workspace, size_t workspace_bytes,
                         void* stream);
 
+int rpod_basis_rows(rpod_plan* P, const void* S, int64_t lds, int32_t s_dtype, void* U, int64_t ldu,
+                    double* sigma, void* C, int64_t ldc, void* workspace, size_t workspace_bytes,
+                    void* stream, rpod_exchange_fn exchange, void* ctx) {
+  if (!P || !P->rows_mode || !S || !U || !sigma || !C || !exchange) return RPOD_ERR_INVALID_ARG;
+  if (s_dtype != P->compute) return RPOD_ERR_INVALID_ARG;
+  P->xch = exchange;
+  P->xch_ctx = ctx;
+  const int rc = basis_device(P, S, lds, s_dtype, nullptr, 0, U, ldu, sigma, C, ldc, workspace,
+                              workspace_bytes, stream);
+  P->xch = nullptr;
+  P->xch_ctx = nullptr;
+  return rc;
+}
+
 int rpod_basis(rpod_plan* P, const void* S, int64_t lds, int32_t s_dtype, const float* S_refine,
                int64_t ldr, void* U, int64_t ldu, double* sigma, void* C, int64_t ldc,
                void* workspace, size_t workspace_bytes, void* stream) {
   if (!P || !S || !U || !sigma || !C) return RPOD_ERR_INVALID_ARG;
+  if (P->rows_mode) return RPOD_ERR_INVALID_ARG;  // needs the exchange: rpod_basis_rows
   if (!(P->flags & RPOD_FLAG_HOST_IO))
     return basis_device(P, S, lds, s_dtype, S_refine, ldr, U, ldu, sigma, C, ldc, workspace,
                         workspace_bytes, stream);
@@ -743,7 +853,7 @@ int rpod_project(const rpod_plan* P, const void* U, int64_t ldu, int32_t kc, con
                  int64_t lds, int64_t m_new, int32_t s_dtype, void* C, int64_t ldc, void* workspace,
                  size_t workspace_bytes, void* stream) {
   if (!P || !U || !S_new || !C || kc < 1 || kc > P->l || m_new < 1) return RPOD_ERR_INVALID_ARG;
-  if (ldu < P->n || lds < P->n || ldc < kc) return RPOD_ERR_INVALID_ARG;
+  if (P->rows_mode || ldu < P->n || lds < P->n || ldc < kc) return RPOD_ERR_INVALID_ARG;
   if (int rc = check_ws(P, workspace, workspace_bytes)) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   char* ws = (char*)workspace;
@@ -803,11 +913,20 @@ int rpod_sample(const rpod_plan* P, const void* A, int64_t lda, const void* S, i
 int rpod_profile_enable(rpod_plan* P, int enable) {
   if (!P) return RPOD_ERR_INVALID_ARG;
   if (enable && !P->prof_on) {
-    for (int i = 0; i < 2 * 64; ++i)
-      if (cudaEventCreate(&P->prof_ev[i]) != cudaSuccess) return RPOD_ERR_CUDA;
+    P->prof_ev = new (std::nothrow) cudaEvent_t[2 * kProfPasses];
+    if (!P->prof_ev) return RPOD_ERR_INVALID_ARG;
+    for (int i = 0; i < 2 * kProfPasses; ++i)
+      if (cudaEventCreate(&P->prof_ev[i]) != cudaSuccess) {
+        for (int j = 0; j < i; ++j) cudaEventDestroy(P->prof_ev[j]);
+        delete[] P->prof_ev;
+        P->prof_ev = nullptr;
+        return RPOD_ERR_CUDA;
+      }
     P->prof_on = 1;
   } else if (!enable && P->prof_on) {
-    for (int i = 0; i < 2 * 64; ++i) cudaEventDestroy(P->prof_ev[i]);
+    for (int i = 0; i < 2 * kProfPasses; ++i) cudaEventDestroy(P->prof_ev[i]);
+    delete[] P->prof_ev;
+    P->prof_ev = nullptr;
     P->prof_on = 0;
   }
   P->prof_n = 0;

@@ -80,11 +80,16 @@ cudaError_t sketch(cudaStream_t st, uint64_t seed, uint64_t stream_id, int64_t m
 // when a pivot signals a condition number beyond FP32 reach, a device-gated
 // FP64 factorization takes over -- of the Gram recomputed with exact
 // products from Y (rows x l, ld ldy, rows when 0) into the nsplit partials at
-// `part`.
+// `part`.  FP64 working type only: shift_coef > 0 factors G + shift_coef *
+// trace(G) * I (the shifted first round of a shifted CholeskyQR3; only
+// exactly vanishing columns are dropped), and flag_tiny raises
+// ST_RANK_DEF, without dropping, for columns of squared norm below 1e-16
+// (rounds after a shifted one, whose basis is near orthonormal).
 template <typename TW>
 cudaError_t cholesky(cudaStream_t st, int l, const void* G, double tol, int round,
                      double* X, TW* Xw, int ldxw, unsigned* status, const float* Y = nullptr,
-                     int64_t rows = 0, double* part = nullptr, int nsplit = 0, int64_t ldy = 0);
+                     int64_t rows = 0, double* part = nullptr, int nsplit = 0, int64_t ldy = 0,
+                     double shift_coef = 0.0, bool flag_tiny = false);
 
 // Symmetric eigen-decomposition of G (l x l, FP64): an FP32 start from the
 // tridiagonal reduction, then FP64 Ogita-Aishima refinement.  Outputs
@@ -101,6 +106,15 @@ cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma,
 cudaError_t tridiag_eig32(cudaStream_t st, int l, const double* G, double* X, unsigned* status);
 size_t sym_eig_work_doubles(int l);
 
+// Relatively accurate small SVD from the Gram G = T T^T (l x l, FP64) of a
+// row-graded T: FP64 Cholesky G = R^T R, then one-sided Jacobi sweeps on the
+// columns of L = R^T.  Writes the left singular vectors of T to Uhat (l x l)
+// and the singular values to sigma (descending); ST_NO_CONV when max_sweeps
+// sweeps still rotate; the sweep count goes to status[5] (diagnostic).
+cudaError_t jacobi_svd(cudaStream_t st, int l, const double* G, double* Uhat, double* sigma,
+                       unsigned* status, int max_sweeps);
+void prepare_jacobi_kernels();
+
 // Column-sign convention: per column c < ncols of U (rows n, ld ldu) find the
 // largest |entry| (ties: lowest row) and multiply the column by its sign; the
 // same sign is applied to column c of Uhat (l rows, ld l).
@@ -108,6 +122,21 @@ template <typename T>
 cudaError_t sign_fix(cudaStream_t st, int64_t n, int ncols, T* U, int64_t ldu,
                      double* Uhat, int l, void* scratch, size_t scratch_bytes);
 size_t sign_fix_scratch_bytes(int64_t n, int ncols);
+
+// The sign rule when the rows of U are split over row blocks held by
+// different calls (row0: this block's first global row).  xb holds 6 ncols
+// doubles; between the steps the caller combines over all blocks: xb[0, nc)
+// by max after sign_rows_candidates, xb[nc, 2nc) by min after
+// sign_rows_step(1), xb[2nc, 3nc) by sum after sign_rows_step(2); then
+// sign_rows_apply flips the columns of U and Uhat whose chosen entry is
+// negative.  Ties go to the lowest global row, as in sign_fix.
+template <typename T>
+cudaError_t sign_rows_candidates(cudaStream_t st, int64_t n, int ncols, const T* U, int64_t ldu,
+                                 int64_t row0, double* xb, void* scratch, size_t scratch_bytes);
+cudaError_t sign_rows_step(cudaStream_t st, int ncols, double* xb, int step);
+template <typename T>
+cudaError_t sign_rows_apply(cudaStream_t st, int64_t n, int ncols, T* U, int64_t ldu, double* Uhat,
+                            int l, double* xb);
 
 template <typename TS, typename TD>
 cudaError_t convert_matrix(cudaStream_t st, int64_t rows, int64_t cols, const TS* src,

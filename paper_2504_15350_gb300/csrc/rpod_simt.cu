@@ -430,10 +430,22 @@ __device__ double block_max(double v, double* red) {
 // FP32 (its rounding is removed by the next CholeskyQR round).  Column j of
 // the factor lives in column j of the shared array (stride l + 1) and is
 // overwritten by column j of the inverse.
+//
+// shift_coef > 0 (round 0 of the FP64 form's shifted CholeskyQR3, Fukaya,
+// Kannan, Nakatsukasa, Yamamoto & Yanagisawa, SIAM J. Sci. Comput. 42, 2020):
+// factors G + s I with s = shift_coef * trace(G) (shift_coef = 11 (rows l +
+// l (l + 1)) u; the trace bounds ||Y||_2^2), so the factorization cannot
+// break down and Q = Y R^{-1} has a condition number of order u^{-1/2}
+// whatever that of Y; only exactly vanishing columns are dropped.
+// flag_tiny (the rounds after a shifted one): a column of the
+// near-orthonormal basis with squared norm below 1e-16 -- a direction of the
+// sampled matrix below about 1e-13 of its norm, i.e. rounding noise -- raises
+// the rank-deficiency warning but is kept and normalised, which completes the
+// basis with orthonormal directions as Householder QR would.
 template <typename TF, typename TI, typename TW>
 __global__ void __launch_bounds__(256)
 k_cholesky(int l, const double* __restrict__ G, double tol, double* __restrict__ Xout,
-           TW* __restrict__ Xw, int ldxw, unsigned* status) {
+           TW* __restrict__ Xw, int ldxw, unsigned* status, double shift_coef, int flag_tiny) {
   extern __shared__ double sm[];
   const int ld = l + 1;
   TF* A = (TF*)sm;                                        // l x l, column-major, stride ld
@@ -461,7 +473,21 @@ k_cholesky(int l, const double* __restrict__ G, double tol, double* __restrict__
   double dm = 0.0;
   for (int j = tid; j < l; j += nt) { d0[j] = G[j + j * l]; dm = fmax(dm, d0[j]); }
   const double gmax = block_max(dm, red);   // also orders the loads above
-  int ndropped = 0;
+  if (shift_coef > 0.0) {
+    double tr = 0.0;
+    for (int j = tid; j < l; j += nt) tr += d0[j];
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    __shared__ double s_tr[8];
+    if ((tid & 31) == 0) s_tr[tid >> 5] = tr;
+    __syncthreads();
+    tr = 0.0;
+    for (int w = 0; w < (nt >> 5); ++w) tr += s_tr[w];
+    const double shift = shift_coef * tr;
+    for (int j = tid; j < l; j += nt)
+      if (d0[j] > 1e-300) A[j + j * ld] += (TF)shift;
+    __syncthreads();
+  }
+  int ndropped = 0, ntiny = 0;
   const int cb = tid & 127, rg = tid >> 7, ng = nt >> 7;
   for (int j = 0; j < l; ++j) {
     if (tid == 0) {
@@ -475,6 +501,7 @@ k_cholesky(int l, const double* __restrict__ G, double tol, double* __restrict__
     __syncthreads();
     const TF rinv = s_rinv;
     if (!s_keep[j]) ++ndropped;
+    else if (flag_tiny && d0[j] < 1e-16) ++ntiny;
     for (int c = j + 1 + tid; c < l; c += nt) A[j + c * ld] *= rinv;
     __syncthreads();
     // trailing update of the upper triangle: column b = j + 1 + cb, rows a <= b
@@ -511,14 +538,17 @@ k_cholesky(int l, const double* __restrict__ G, double tol, double* __restrict__
     Xw[i + (int64_t)j * ldxw] = (TW)v;
   }
   if (tid == 0 && ndropped > 0) atomicOr(status, ndropped == l ? (ST_RANK_DEF | ST_BREAKDOWN) : ST_RANK_DEF);
+  if (tid == 0 && ntiny > 0) atomicOr(status, ST_RANK_DEF);
 }
 
 template <typename TF, typename TI, typename TW>
 static cudaError_t launch_cholesky(cudaStream_t st, int l, const double* G, double tol, double* X,
-                                   TW* Xw, int ldxw, unsigned* status) {
+                                   TW* Xw, int ldxw, unsigned* status, double shift_coef,
+                                   int flag_tiny) {
   const size_t sm = (size_t)l * (l + 1) * sizeof(TF) + 16 + (size_t)l * (sizeof(double) + sizeof(TI));
   prepare_kernels();
-  k_cholesky<TF, TI, TW><<<1, 256, sm, st>>>(l, G, tol, X, Xw, ldxw, status); note_launch();
+  k_cholesky<TF, TI, TW><<<1, 256, sm, st>>>(l, G, tol, X, Xw, ldxw, status, shift_coef, flag_tiny);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -819,10 +849,11 @@ k_gram_df_gated(int64_t rows, int l, const float* __restrict__ Y, int64_t ldy, i
 template <typename TW>
 cudaError_t cholesky(cudaStream_t st, int l, const void* Gv, double tol, int round, double* X,
                      TW* Xw, int ldxw, unsigned* status, const float* Y, int64_t rows,
-                     double* part, int nsplit, int64_t ldy) {
+                     double* part, int nsplit, int64_t ldy, double shift_coef, bool flag_tiny) {
   if (ldy == 0) ldy = rows;
   if (sizeof(TW) == 8)
-    return launch_cholesky<double, double, TW>(st, l, (const double*)Gv, tol, X, Xw, ldxw, status);
+    return launch_cholesky<double, double, TW>(st, l, (const double*)Gv, tol, X, Xw, ldxw, status,
+                                               shift_coef, flag_tiny ? 1 : 0);
   const float* G = (const float*)Gv;
   // the gate word sits next to the status word (same 256-byte status block)
   int* gate = (int*)(status + 2);
@@ -939,8 +970,8 @@ k_cholesky64_gated(int l, const double* __restrict__ G, double tol, int* gate,
   }
   (void)tol;
 }
-template cudaError_t cholesky<double>(cudaStream_t, int, const void*, double, int, double*, double*, int, unsigned*, const float*, int64_t, double*, int, int64_t);
-template cudaError_t cholesky<float>(cudaStream_t, int, const void*, double, int, double*, float*, int, unsigned*, const float*, int64_t, double*, int, int64_t);
+template cudaError_t cholesky<double>(cudaStream_t, int, const void*, double, int, double*, double*, int, unsigned*, const float*, int64_t, double*, int, int64_t, double, bool);
+template cudaError_t cholesky<float>(cudaStream_t, int, const void*, double, int, double*, float*, int, unsigned*, const float*, int64_t, double*, int, int64_t, double, bool);
 
 // ------------------------------------------------------------------------
 // Symmetric eigensolver for the small SVD.  T T^T = Uhat Sigma^2 Uhat^T, so
@@ -1242,6 +1273,79 @@ cudaError_t sign_fix(cudaStream_t st, int64_t n, int ncols, T* U, int64_t ldu, d
 template cudaError_t sign_fix<double>(cudaStream_t, int64_t, int, double*, int64_t, double*, int, void*, size_t);
 template cudaError_t sign_fix<float>(cudaStream_t, int64_t, int, float*, int64_t, double*, int, void*, size_t);
 
+// Sign rule over row blocks held by different calls.  xb (6 ncols doubles):
+// [0, nc) the largest magnitude per column (exchanged, max), [nc, 2nc) the
+// lowest global row holding it (exchanged, min), [2nc, 3nc) the sign of that
+// entry (exchanged, sum: exactly one block contributes), [3nc, 6nc) this
+// block's own candidate (magnitude, global row, sign).
+constexpr double kNoRow = 1e300;
+
+__global__ void k_sign_rows_local(int ncols, int nblk, const ArgMax* __restrict__ part, int64_t row0,
+                                  double* __restrict__ xb) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncols) return;
+  double ba = -1.0, bv = 0.0;
+  long long bi = LLONG_MAX;
+  for (int b = 0; b < nblk; ++b) {
+    const ArgMax p = part[c * nblk + b];
+    const double a = fabs(p.v);
+    if (p.i != LLONG_MAX && (a > ba || (a == ba && p.i < bi))) { ba = a; bv = p.v; bi = p.i; }
+  }
+  const bool any = bi != LLONG_MAX;
+  xb[c] = any ? ba : -1.0;
+  xb[3 * ncols + c] = any ? ba : -1.0;
+  xb[4 * ncols + c] = any ? (double)(row0 + bi) : kNoRow;
+  xb[5 * ncols + c] = bv < 0.0 ? -1.0 : 1.0;
+}
+
+// step 1 (after the max): offer this block's row if it holds the largest
+// magnitude; step 2 (after the min): offer the sign if that row is ours.
+__global__ void k_sign_rows_step(int ncols, double* __restrict__ xb, int step) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncols) return;
+  const bool holds = xb[3 * ncols + c] >= 0.0 && xb[3 * ncols + c] == xb[c];
+  if (step == 1)
+    xb[ncols + c] = holds ? xb[4 * ncols + c] : kNoRow;
+  else
+    xb[2 * ncols + c] = (holds && xb[4 * ncols + c] == xb[ncols + c]) ? xb[5 * ncols + c] : 0.0;
+}
+
+__global__ void k_sign_rows_uhat(int ncols, double* __restrict__ xb, double* __restrict__ Uhat, int l) {
+  const int c = blockIdx.x;
+  const double sg = xb[2 * ncols + c] < 0.0 ? -1.0 : 1.0;
+  __syncthreads();
+  if (threadIdx.x == 0) xb[2 * ncols + c] = sg;
+  for (int i = threadIdx.x; i < l; i += blockDim.x) Uhat[i + c * l] *= sg;
+}
+
+template <typename T>
+cudaError_t sign_rows_candidates(cudaStream_t st, int64_t n, int ncols, const T* U, int64_t ldu,
+                                 int64_t row0, double* xb, void* scratch, size_t) {
+  const int64_t rpb = 8192;
+  const int nblk = (int)((n + rpb - 1) / rpb);
+  ArgMax* part = (ArgMax*)scratch;
+  k_colmax_partial<T><<<dim3(nblk, ncols), 256, 0, st>>>(n, rpb, U, ldu, part, nblk); note_launch();
+  k_sign_rows_local<<<(ncols + 127) / 128, 128, 0, st>>>(ncols, nblk, part, row0, xb); note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t sign_rows_candidates<double>(cudaStream_t, int64_t, int, const double*, int64_t, int64_t, double*, void*, size_t);
+template cudaError_t sign_rows_candidates<float>(cudaStream_t, int64_t, int, const float*, int64_t, int64_t, double*, void*, size_t);
+
+cudaError_t sign_rows_step(cudaStream_t st, int ncols, double* xb, int step) {
+  k_sign_rows_step<<<(ncols + 127) / 128, 128, 0, st>>>(ncols, xb, step); note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t sign_rows_apply(cudaStream_t st, int64_t n, int ncols, T* U, int64_t ldu, double* Uhat,
+                            int l, double* xb) {
+  k_sign_rows_uhat<<<ncols, 128, 0, st>>>(ncols, xb, Uhat, l); note_launch();
+  k_scale_cols<T><<<col_grid(n, ncols), 256, 0, st>>>(n, ncols, U, ldu, xb + 2 * ncols); note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t sign_rows_apply<double>(cudaStream_t, int64_t, int, double*, int64_t, double*, int, double*);
+template cudaError_t sign_rows_apply<float>(cudaStream_t, int64_t, int, float*, int64_t, double*, int, double*);
+
 // ------------------------------------------------------------------------
 // grid: x = column, y = chunks of 1024 rows (grid-stride), four loads in
 // flight per thread.
@@ -1507,6 +1611,7 @@ void prepare_kernels() {
     cudaFuncSetAttribute(k_cholesky<double, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_cholesky64_gated<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     prepare_eig_kernels();
+    prepare_jacobi_kernels();
     cudaFuncSetAttribute(k_cholesky_blk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlkSmem);
     cudaFuncSetAttribute(k_cholesky_blk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlkSmem);
   });

@@ -29,13 +29,18 @@ __device__ __align__(256) unsigned char g_project_scratch[kStaticScratchBytes];
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
 
-// Device address of the array on the current device, looked up once per
-// device (the name is only a host-side stand-in for it).
-int scratch_address(void** out) {
+// Device address of the array on the current device.  The name is only a
+// host-side stand-in for it.  Outside a stream capture the address is looked
+// up on every call (a device reset or a new primary context reloads the
+// module and may move the array); during a capture the address recorded by
+// the last call outside one is used, since a lookup may load the module.
+int scratch_address(cudaStream_t st, void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RPOD_ERR_CUDA;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return RPOD_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone || !g_scratch_ptr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_project_scratch) != cudaSuccess || !p) return RPOD_ERR_CUDA;
     g_scratch_ptr[dev] = p;
@@ -53,7 +58,7 @@ int project_static(int64_t n, int nsplit_max, const W* U, int64_t ldu, int kc, c
   if (nsplit > nsplit_max) nsplit = nsplit_max;
   if (nsplit < 1) nsplit = 1;
   void* scratch = nullptr;
-  if (int rc = scratch_address(&scratch)) return rc;
+  if (int rc = scratch_address(st, &scratch)) return rc;
   W* part = (W*)scratch;
   // C'^T (m_new x kc) = S'^T U: partial sums per split of rows, then their
   // deterministic reduction into C'

@@ -26,6 +26,8 @@ RPOD_ERR_TIMEOUT = 6
 RPOD_ERR_CUDA = 7
 RPOD_ERR_WORKSPACE = 8
 RPOD_ERR_IO = 9
+RPOD_ERR_EXCHANGE = 10
+RPOD_REDUCE_SUM, RPOD_REDUCE_MAX, RPOD_REDUCE_MIN = 0, 1, 2
 RPOD_WARN_RANK_DEFICIENT = 1
 RPOD_FLAG_REFINE_FP32 = 1
 RPOD_FLAG_RETURN_ALL_L = 4
@@ -79,6 +81,11 @@ SIGNATURES = {
     "rpod_plan_create": (ctypes.c_int, [ctypes.POINTER(_p), _c_i64, _c_i64, _c_i32, _c_i32, _c_i32,
                                         _c_u64, _c_i32, _c_u32]),
     "rpod_workspace_bytes": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "rpod_plan_set_svd_sweeps": (ctypes.c_int, [_p, _c_i32]),
+    "rpod_rows_plan_create": (ctypes.c_int, [ctypes.POINTER(_p), _c_i64, _c_i64, _c_i64, _c_i64, _c_i32,
+                                             _c_i32, _c_i32, _c_u64, _c_i32, _c_u32]),
+    "rpod_basis_rows": (ctypes.c_int, [_p, _p, _c_i64, _c_i32, _p, _c_i64, _p, _p, _c_i64, _p,
+                                       ctypes.c_size_t, _p, _p, _p]),
     "rpod_basis": (ctypes.c_int, [_p, _p, _c_i64, _c_i32, _p, _c_i64, _p, _c_i64, _p, _p, _c_i64,
                                   _p, ctypes.c_size_t, _p]),
     "rpod_project": (ctypes.c_int, [_p, _p, _c_i64, _c_i32, _p, _c_i64, _c_i64, _c_i32, _p, _c_i64,
@@ -148,6 +155,10 @@ def rpod_workspace_bytes(plan) -> int:
     b = ctypes.c_size_t()
     _check(load().rpod_workspace_bytes(plan, ctypes.byref(b)), "rpod_workspace_bytes")
     return b.value
+
+
+def rpod_plan_set_svd_sweeps(plan, max_sweeps):
+    return load().rpod_plan_set_svd_sweeps(plan, max_sweeps)
 
 
 def rpod_basis(plan, S, lds, s_dtype, S_refine, ldr, U, ldu, sigma, C, ldc, ws, ws_bytes, stream):
@@ -446,6 +457,18 @@ class Plan:
 
     def launches(self):
         return rpod_last_launch_count(self.handle)
+
+    def set_svd_sweeps(self, max_sweeps):
+        """Caps the FP64 form's one-sided Jacobi sweeps (rpod_plan_set_svd_sweeps)."""
+        _check(rpod_plan_set_svd_sweeps(self.handle, max_sweeps), "rpod_plan_set_svd_sweeps")
+
+    def svd_sweeps(self):
+        """Jacobi sweeps the last FP64 basis call ran (diagnostic word 5 of the
+        workspace's status block); synchronises the device."""
+        torch = _torch()
+        torch.cuda.synchronize(self.device)
+        off = self.ws_ptr - self.ws.data_ptr()
+        return int(self.ws[off + 20:off + 24].cpu().view(torch.int32).item())
 
     def sketch(self, dtype=None):
         """The plan's Gaussian sketch Lambda (m x l, column-major)."""

@@ -2,10 +2,18 @@
 import numpy as np
 
 
+# Below this fraction of sigma_1 the FP64 forms compare sigma_i absolutely:
+# values there sit at the rounding level of S itself (a sampled direction
+# of S below about u ||S|| is noise on both sides).
+F64_FLOOR = 1e-9
+
+
 def sigma_close(sg, so, rel, abs_frac, floor=1e-3):
     """sigma_i agree to `rel` where sigma_i >= floor * sigma_1, else to
-    abs_frac * sigma_1 (rounding in a Gram-based small SVD is absolute
-    relative to sigma_1 there)."""
+    abs_frac * sigma_1.  The FP64 form is relatively accurate down to
+    F64_FLOOR (Jacobi small SVD); the FP32 and 16-bit forms take their
+    small SVD from eigenpairs of the Gram T T^T, whose rounding is absolute
+    relative to sigma_1^2, so their tests keep the default floor."""
     sg = np.asarray(sg, np.float64)
     so = np.asarray(so, np.float64)
     s1 = so[0]

@@ -19,8 +19,9 @@ def declared_functions():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z][a-z0-9_]*)\s*\(",
-                             src, flags=re.M):
+        # function declarations; typedefs of callback types are not symbols
+        for m in re.finditer(r"^\s*(?!typedef\b)(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*"
+                             r"([a-z][a-z0-9_]*)\s*\(", src, flags=re.M):
             names.add(m.group(1))
     return names
 

@@ -76,11 +76,19 @@ def _oracles(S64, k, p, q, form):
     return lowp, orig
 
 
+# sigma (i <= k) and largest principal angle of span(U_k) for the 16-bit
+# forms with the refinement pass: BF16 (TF32 refinement) 1e-4 and 1e-2; FP16
+# (exact FP32 refinement) 1e-5 and 2e-3.
+BOUNDS_16 = {"bf16": (1e-4, 1e-2), "f16": (1e-5, 2e-3)}
+
+
 @pytest.mark.parametrize("form", ["bf16", "f16"])
 def test_basis_16bit_refine_config1(form):
     """Config 1 shape (n = 4096, m = 500, k = 20, p = 10, q = 1), 16-bit
     passes with the FP32 refinement pass; S handed over in FP32 and
-    converted on the device."""
+    converted on the device.  Against the oracle on the 16-bit-rounded
+    passes (the storage floor) and on the FP32 snapshots, with each form's
+    own bounds."""
     rec = make_recipe(64, 64, 500, 400, ("power", 1.5), seed=0, noise=1e-6)
     S = snapshot_matrix(rec, dtype=torch.float32)
     S64 = S.double().numpy()
@@ -92,11 +100,11 @@ def test_basis_16bit_refine_config1(form):
     assert rc == R.RPOD_OK
     sig = sig.cpu().numpy()
     U = U.double().cpu().numpy()
-    ok, er, ea = sigma_close(sig[:k], lowp.sigma[:k], 1e-4, 1e-5)
-    assert ok, ("vs rounded-input oracle", er, ea)
-    ok, er, ea = sigma_close(sig[:k], orig.sigma[:k], 1e-4, 1e-5)
-    assert ok, ("vs FP32-input oracle", er, ea)
-    assert max_angle(lowp.U[:, :k], U) <= 1e-2
+    srel, ang = BOUNDS_16[form]
+    for name, o in (("rounded-input", lowp), ("FP32-input", orig)):
+        err = np.abs(sig[:k] - o.sigma[:k]) / o.sigma[:k]
+        assert err.max() <= srel, (name, err.max())
+        assert max_angle(o.U[:, :k], U) <= ang, (name, max_angle(o.U[:, :k], U))
     assert orth_err(U) <= 1e-5
 
 
@@ -157,3 +165,27 @@ def test_fp32_input_first_pass_conversion_matches_16bit_input(n, m, ld):
     Sd[n - 1, m - 1] = float("nan")
     fused.basis(Sd)
     assert fused.status()[0] == R.RPOD_ERR_NONFINITE
+
+
+def test_basis_bf16_refine_65536_rows_matches_oracle():
+    """The full-size code paths at a size the oracle finishes in seconds:
+    n = 65536 (256 x 256 grid), m = 4000, k = 100, p = 20 (l = 120), q = 2,
+    400 modes with exp(-j/40) amplitudes, FP32 S converted in the first pass.
+    The Y-passes need two waves of CTAs and the W-passes split n into 48
+    chunks (16 snapshot tiles of 256, about five waves of 152 SMs).  BF16 bounds against both oracles, sigma_i for every i <= k."""
+    rec = make_recipe(256, 256, 4000, 400, ("exp", 40.0), seed=0, noise=1e-6)
+    S = snapshot_matrix(rec, device="cuda", dtype=torch.float32)
+    k, p, q = 100, 20, 2
+    assert rec.n // 256 > 152          # Y-pass: 256 CTAs of 256 rows (512 of 128 in the first)
+    plan = R.Plan(rec.n, rec.m, k, p, q, seed=0, compute="bf16", flags=R.RPOD_FLAG_REFINE_FP32)
+    U, sig, C = plan.basis(S)
+    assert plan.status()[0] == R.RPOD_OK
+    sig = sig.cpu().numpy()
+    U = U.double().cpu().numpy()
+    S64 = S.cpu().double().numpy()
+    lowp, orig = _oracles(S64, k, p, q, "bf16")
+    for name, o in (("rounded-input", lowp), ("FP32-input", orig)):
+        err = np.abs(sig[:k] - o.sigma[:k]) / o.sigma[:k]
+        assert err.max() <= 1e-4, (name, err.max())
+        assert max_angle(o.U[:, :k], U) <= 1e-2, name
+    assert orth_err(U) <= 1e-5

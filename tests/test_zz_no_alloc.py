@@ -27,8 +27,10 @@ def _colmajor(rows, cols, dtype, gen):
     return torch.randn((cols, rows), generator=gen, dtype=torch.float64).to(dtype).cuda().t()
 
 
-@pytest.mark.parametrize("compute,dtype,rel", [("f32", torch.float32, 1e-5), ("f64", torch.float64, 1e-12)])
+@pytest.mark.parametrize("compute,dtype,rel", [("f32", torch.float32, 1e-5), ("f64", torch.float64, 1e-12),
+                                               ("bf16", torch.float32, 1e-5)])
 def test_static_projection_matches_workspace_projection(compute, dtype, rel):
+    """A 16-bit plan projects FP32 U and S' (its FP32 branch) like the F32 one."""
     g = torch.Generator().manual_seed(11)
     n, m, k, p = 20000, 3000, 24, 8
     plan = R.Plan(n, m, k, p, 1, compute=compute)
@@ -59,4 +61,16 @@ def test_static_projection_rejects_oversized_request():
     assert rc == R.RPOD_ERR_UNSUPPORTED
     rc = R.rpod_project_static(plan.handle, U.data_ptr(), 4096, 100, S.data_ptr(), 4096, m_new,
                                R.RPOD_F64, C.data_ptr(), 100, torch.cuda.current_stream().cuda_stream)
+    assert rc == R.RPOD_ERR_INVALID_ARG
+
+
+def test_static_projection_rejects_16bit_snapshots():
+    """Only FP32 (or FP64 for an FP64 plan) operands: 16-bit S' is refused
+    before anything is enqueued."""
+    plan = R.Plan(4096, 512, 16, 8, 1, compute="bf16")
+    U = torch.zeros((16, 4096), device="cuda").t()
+    S = torch.zeros((512, 4096), dtype=torch.bfloat16, device="cuda").t()
+    C = torch.zeros((512, 16), device="cuda").t()
+    rc = R.rpod_project_static(plan.handle, U.data_ptr(), 4096, 16, S.data_ptr(), 4096, 512,
+                               R.RPOD_BF16, C.data_ptr(), 16, torch.cuda.current_stream().cuda_stream)
     assert rc == R.RPOD_ERR_INVALID_ARG
