@@ -62,6 +62,13 @@ class ROMConfig:
     center: bool = False
     # dropout between stacked LSTM layers (training passes only)
     dropout: float = 0.0
+    # pushforward training: in a fraction of the batches the network first
+    # predicts K steps (1 <= K <= pushforward, no gradient through them) from
+    # a true window, and the training step then maps the window made of its
+    # own last predictions to the true next coefficients -- the inputs a
+    # long rollout feeds it (0: one-step training only)
+    pushforward: int = 0
+    pushforward_frac: float = 0.5
 
 
 # Table tab:hyperparam: the networks M_{q_l} (potential vorticity) and
@@ -127,6 +134,22 @@ def _rel_err(pred, ref):
     return float((num / den).mean())
 
 
+def _pushforward_batch(net, zs, zmu, rows, K, d, T, n_steps):
+    """Training pair for pushforward: the true window at (series, t0) (t0
+    moved back so that t0 + T + K is a step of the series), K predictions of
+    the network from it (the library's rollout; only data bookkeeping here),
+    the window of the last T steps of [true window, predictions], and the
+    true coefficients at t0 + T + K."""
+    rows = rows.clone()
+    rows[:, 1] = torch.clamp(rows[:, 1], max=n_steps - T - 1 - K)
+    Xt, _ = net.gather(zs, zmu, rows)
+    pred = net.rollout(Xt, d, K)                                 # (B, K, O)
+    alpha = torch.cat([Xt[:, :, d:], pred], 1)[:, -T:]
+    X = torch.cat([Xt[:, :, :d], alpha], -1).contiguous()
+    Y = zs[rows[:, 0].long(), (rows[:, 1] + T + K).long()].contiguous()
+    return X, Y
+
+
 def init_params(net: "R.LSTM", seed: int) -> torch.Tensor:
     """U(-1/sqrt(H), 1/sqrt(H)) for every parameter (the usual LSTM init)."""
     g = torch.Generator().manual_seed(seed)
@@ -185,11 +208,17 @@ def run(cfg: ROMConfig = ROMConfig(), device="cuda", log=None) -> ROMResult:
     best, best_theta, since = math.inf, None, 0
     t0 = time.perf_counter()
     samples = 0
+    pf_rng = np.random.default_rng(cfg.seed + 7)
     for ep in range(cfg.epochs):
         order = idx_tr[torch.randperm(idx_tr.shape[0], generator=g).to(dev)]
         loss_sum = torch.zeros((), device=dev)
         for b in range(nb):
-            X, Y = net.gather(zs, zmu, order[b * B:(b + 1) * B])
+            rows = order[b * B:(b + 1) * B]
+            if cfg.pushforward > 0 and pf_rng.random() < cfg.pushforward_frac:
+                X, Y = _pushforward_batch(net, zs, zmu, rows, int(pf_rng.integers(1, cfg.pushforward + 1)),
+                                          d, T, cfg.n_steps)
+            else:
+                X, Y = net.gather(zs, zmu, rows)
             loss_sum += net.train_step(X, Y, lr=cfg.lr, weight_decay=cfg.weight_decay)[0]
         samples += nb * B
         vl = torch.zeros((), device=dev)
