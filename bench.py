@@ -63,7 +63,9 @@ def parse():
                     help="skip the leg with per-sample centering (Eqs. time_av, fluct_q)")
     ap.add_argument("--nt", type=int, default=400,
                     help="snapshots per parameter sample for the centered leg")
-    ap.add_argument("--learned-epochs", type=int, default=15)
+    ap.add_argument("--learned-epochs", type=int, default=60)
+    ap.add_argument("--learned-centered", action="store_true",
+                    help="also run the learned leg on per-sample centered snapshots")
     ap.add_argument("--ny", type=int, default=512,
                     help="grid rows (n = 512 * ny); smaller values make the small profiling case")
     ap.add_argument("--only-batched", choices=["bf16", "f32"], default=None,
@@ -424,18 +426,22 @@ def run_config6(dev, warmup, hbm_peak):
     return out
 
 
-def run_learned(dev, epochs):
-    """Short rPOD-LSTM run (Sec. 4.3): 2 layers x 256, window 10, batch 512,
-    coefficients of the fluctuations of 32 parameter samples x 2000 steps;
-    rollouts of 500 steps for 8 held-out samples against Galerkin
-    projection."""
+def run_learned(dev, epochs, center=False):
+    """rPOD-LSTM run (Sec. 4.3, config 5): 2 layers x 256, window 10, batch
+    512, rPOD coefficients (k = 50) of 32 parameter samples x 2000 steps of
+    the config-1 mode recipe plus a steady parameter-dependent field;
+    pushforward training (half of the batches train on windows of the
+    network's own predictions, up to 10 steps), stopped when the validation
+    loss has not improved for 15 epochs; rollouts of 500 steps for 8
+    held-out samples against Galerkin projection.  With `center` the
+    snapshots are centered per training sample and the held-out field
+    starts from the nearest sample's time average (Eqs. q_approx,
+    time_av_zero)."""
     from paper_2504_15350_gb300 import rom
-    # snapshots with steady parameter-dependent mean fields, centered per
-    # training sample; held-out fields reconstructed from the nearest
-    # sample's time average plus the modes (Eqs. q_approx, time_av_zero)
-    r = rom.run(rom.ROMConfig(epochs=epochs, patience=max(4, epochs), mean_amp=1.0, center=True),
-                device=dev)
-    return {"epochs": r.epochs_run, "centered": True, "mean_amp": 1.0,
+    r = rom.run(rom.ROMConfig(epochs=epochs, patience=15, mean_amp=1.0, center=center,
+                              pushforward=10), device=dev)
+    return {"epochs": r.epochs_run, "centered": center, "mean_amp": 1.0, "pushforward": 10,
+            "val_loss_curve": [round(v, 6) for v in r.val_loss],
             "train_windows_per_s": r.samples_per_s,
             "rollout_steps_per_s": r.rollout_steps_per_s, "rollout_seconds": r.rollout_seconds,
             "final_val_loss": r.val_loss[-1],
@@ -719,6 +725,8 @@ def main():
     hbm_peak = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
     cfg6 = None if (args.no_config6 or rank != 0) else run_config6(dev, args.warmup, hbm_peak)
     learned = None if (args.no_learned or rank != 0) else run_learned(dev, args.learned_epochs)
+    learned_c = (run_learned(dev, args.learned_epochs, center=True)
+                 if (args.learned_centered and not args.no_learned and rank == 0) else None)
     fields = (run_fields_leg(dev, args.fields_epochs)
               if (args.fields_epochs > 0 and rank == 0) else None)
 
@@ -758,6 +766,7 @@ def main():
         "batched": batched,
         "batched_f32": batched_f32,
         "learned": learned,
+        "learned_centered": learned_c,
         "centered": centered,
         "oracle_full": oracle_full,
         "small_configs": small,

@@ -362,7 +362,14 @@ int rpod_lstm_gather(const rpod_lstm* net, const float* series, const float* mu,
                      float* X, float* Y, void* stream);
 /* Autoregressive prediction (the online stage): from the window (B, window,
  * in_dim), predict, append [mu of the newest row, prediction] as the newest
- * row, drop the oldest, `steps` times; out (B, steps, out_dim). */
+ * row, drop the oldest, `steps` times; out (B, steps, out_dim).  Runs as one
+ * persistent cooperative kernel when the network fits (at most 4 layers; the
+ * gate rows of a CTA's hidden units plus the staged inputs of B windows
+ * within 200 KB of shared memory): the weights stay in shared memory for all
+ * steps, and a grid barrier separates the anti-diagonal phases of the
+ * layer x time cells; every barrier wait is limited to 2 s, after which the
+ * kernel records RPOD_ERR_TIMEOUT (read by rpod_lstm_status_sync) and
+ * returns.  Otherwise one series of kernels per step. */
 int rpod_lstm_rollout(rpod_lstm* net, const float* window, int32_t B, int32_t mu_cols,
                       int32_t steps, float* out, void* workspace, size_t workspace_bytes,
                       void* stream);
@@ -411,6 +418,19 @@ int rpod_lstm_dims(const rpod_lstm* net, int32_t* dims);
  * net or p outside [0, 1). */
 int rpod_lstm_set_dropout(rpod_lstm* net, double p, uint64_t seed);
 int rpod_lstm_last_launch_count(const rpod_lstm* net);
+/* Synchronises `stream`, reads and clears the network's device status word
+ * (set by a persistent rollout whose barrier wait ran out): RPOD_ERR_TIMEOUT
+ * or RPOD_OK.  Errors: RPOD_ERR_INVALID_ARG for NULL arguments. */
+int rpod_lstm_status_sync(const rpod_lstm* net, void* workspace, void* stream);
+
+/* Self-test of the persistent rollout's grid barrier (failure detection
+ * without a GPU fault): a cooperative kernel of two CTAs in which one never
+ * arrives, so the other's bounded wait runs out after `seconds`
+ * (0 < seconds <= 2); it records the timeout in a status word of the library
+ * and returns.  The call synchronises `stream` and returns RPOD_ERR_TIMEOUT
+ * (the designed outcome).  The context stays usable.  Errors:
+ * RPOD_ERR_INVALID_ARG for seconds outside (0, 2]. */
+int rpod_selftest_grid_barrier(double seconds, void* stream);
 void rpod_lstm_destroy(rpod_lstm* net);
 
 /* ---- Time averages, fluctuations and rank selection (Sec. 4.1) ----------

@@ -193,8 +193,10 @@ struct Run {
     if (ld == 0) ld = rows;
     const int l = P->l;
     const double tol = sizeof(W) == 8 ? 1e-13 : 1e-5;
-    // FP32 Gram: two row chunks per SM (the kernel fits two blocks per SM)
-    const int ns = sizeof(W) == 8 ? splits_for(rows, 4096, 256)
+    // FP32 Gram: two row chunks per SM (the kernel fits two blocks per SM).
+    // FP64 Gram: 32-row chunks -- GB300 issues about two FP64 FMAs per clock
+    // per SM, so the l^2 x rows products must spread over many SMs
+    const int ns = sizeof(W) == 8 ? splits_for(rows, 32, 256)
                                   : (int)std::max<int64_t>(1, std::min<int64_t>(2 * 152, rows / 256));
     W* src = in;
     W* dst = tmp;
@@ -424,7 +426,7 @@ struct Run {
       void* Sb = ws + P->off_sb;
       prof_begin(P, st);
       int rc = tc_ypass_cvt(st, dt, Zh, mld, (const float*)S_in, lds_in, n, m, l, Y, n, Sb, nld,
-                            status);
+                            status, wpart, P->wpart_elems);
       if (rc == RPOD_ERR_UNSUPPORTED) {
         if (dt == RPOD_BF16)
           CK(convert_snapshots<__nv_bfloat16>(st, n, m, (const float*)S_in, lds_in,
@@ -432,7 +434,7 @@ struct Run {
         else
           CK(convert_snapshots<__half>(st, n, m, (const float*)S_in, lds_in, (__half*)Sb, nld,
                                        status));
-        rc = tc_ypass(st, dt, Zh, mld, Sb, nld, n, m, l, Y, n, status);
+        rc = tc_ypass(st, dt, Zh, mld, Sb, nld, n, m, l, Y, n, status, wpart, P->wpart_elems);
         CR(rc);
         prof_end(P, st, 6.0 * (double)n * m + pb16, pass_flops);
       } else {
@@ -444,7 +446,7 @@ struct Run {
       if (!Sref) { Sref = (const float*)S_in; ldr = lds_in; }
     } else {
       prof_begin(P, st);
-      CR(tc_ypass(st, dt, Zh, mld, Sh, ldh, n, m, l, Y, n, status));
+      CR(tc_ypass(st, dt, Zh, mld, Sh, ldh, n, m, l, Y, n, status, wpart, P->wpart_elems));
       prof_end(P, st, pb16, pass_flops);
     }
     float* Q = nullptr;
@@ -471,7 +473,7 @@ struct Run {
         CR(orth(Z, Zq, m, 1, &Zo, false, false, nullptr, m4));
         CK(to16(Zo, m, m4, Zh, mld));
         prof_begin(P, st);
-        CR(tc_ypass(st, dt, Zh, mld, Sh, ldh, n, m, l, Y, n, status));
+        CR(tc_ypass(st, dt, Zh, mld, Sh, ldh, n, m, l, Y, n, status, wpart, P->wpart_elems));
         prof_end(P, st, pb16, pass_flops);
       }
       // the final basis is kept in FP32 (lift, Gram of the deferred round)
@@ -621,8 +623,11 @@ static int plan_create_impl(rpod_plan** out, int64_t n, int64_t m, int32_t k, in
   P->seed = seed; P->compute = compute; P->flags = flags;
   const size_t w = (compute == RPOD_F64) ? 8 : 4;
   const size_t L = (size_t)l;
-  P->nsplit_z = splits_for(n, compute == RPOD_F64 ? 4096 : 8192, 64);
-  P->nsplit_t = splits_for(m, 256, 512);
+  // split-K counts of the S^T Q products (over n) and of the Gram T T^T
+  // (over m): the FP64 form splits finely (its products run at the narrow
+  // FP64 rate, so they need many SMs even for small matrices)
+  P->nsplit_z = splits_for(n, compute == RPOD_F64 ? 256 : 8192, 64);
+  P->nsplit_t = splits_for(m, compute == RPOD_F64 ? 32 : 256, 512);
   const int nsg = 2 * 152;
   P->split_cap = split_cap < 1 ? 1 : split_cap;
   P->nsz_def = P->nsplit_z;

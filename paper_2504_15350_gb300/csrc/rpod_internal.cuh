@@ -161,6 +161,22 @@ cudaError_t round_tf32(cudaStream_t st, int64_t rows, int64_t cols, const float*
 cudaError_t gram_f32(cudaStream_t st, int64_t rows, int l, const float* Y, int64_t ldy, int nsplit,
                      double* part);
 
+// Persistent LSTM rollout (rpod_rollout.cu): one cooperative launch for all
+// `steps` predictions; ring: the window (T x B x I, time-major), hbuf: L x T x
+// B x H states, count/abort_word/status: zeroed words (barrier arrivals, the
+// abort word, the status word).  rollout_units: hidden units per CTA;
+// rollout_smem_bytes: dynamic shared memory of one CTA (the caller checks it
+// against the device limit).  grid_sync_selftest: the barrier with one CTA
+// that never arrives, limited to `seconds`; returns the status word left.
+int rollout_units(int H, int sms);
+size_t rollout_smem_bytes(int I, int H, int L, int O, int B, int U);
+cudaError_t rollout_persistent(cudaStream_t st, bool bf16_weights, int I, int H, int L, int O, int T,
+                               int B, int d, int steps, const float* theta, const void* wbf,
+                               const int64_t (*off_w)[3], int64_t off_wy, int64_t off_by,
+                               float* ring, float* hbuf, float* out, unsigned* count,
+                               int* abort_word, unsigned* status, int sms);
+cudaError_t grid_sync_selftest(cudaStream_t st, double seconds, unsigned* status_out);
+
 // Sets every kernel attribute the library needs (dynamic shared memory
 // limits) once per process, so that no attribute call happens during a
 // stream capture.

@@ -147,12 +147,16 @@ k_jacobi_svd(int l, const double* __restrict__ G, double* __restrict__ K, double
       if (i >= 0)
         for (int row = g; row < l; row += kJacGroup) c = fma(W[row + i * l], W[row + j * l], c);
       c = group_sum(c);
-      bool rot = false;
+      // the rotation is decided and formed by the group's first lane (FP64
+      // square roots and divisions are long instruction sequences on GB300)
+      // and broadcast
       double cs = 1.0, sn = 0.0;
-      if (i >= 0) {
+      int rot_i = 0;
+      if (i >= 0 && g == 0) {
         const double a = nrm[i], b = nrm[j];
-        if (c != 0.0 && a > 0.0 && b > 0.0 && fabs(c) > tol * sqrt(a) * sqrt(b)) {
-          rot = true;
+        // |c| > tol sqrt(a b), compared squared (a, b > 0)
+        if (c != 0.0 && a > 0.0 && b > 0.0 && c * c > tol * tol * a * b) {
+          rot_i = 1;
           // rotation that makes columns i and j orthogonal (Rutishauser's
           // form: t = tan of the angle, the smaller root of t^2 + 2 zeta t - 1)
           const double zeta = (b - a) / (2.0 * c);
@@ -164,6 +168,11 @@ k_jacobi_svd(int l, const double* __restrict__ G, double* __restrict__ K, double
           sn = cs * t;
         }
       }
+      const int src = lane & ~(kJacGroup - 1);
+      rot_i = __shfl_sync(0xffffffffu, rot_i, src);
+      cs = __shfl_sync(0xffffffffu, cs, src);
+      sn = __shfl_sync(0xffffffffu, sn, src);
+      const bool rot = rot_i != 0;
       double ni = 0.0, nj = 0.0;
       if (rot) {
         for (int row = g; row < l; row += kJacGroup) {

@@ -49,6 +49,7 @@ struct rpod_lstm {
   int64_t drop_pass;
   size_t o_xd;  // masked inputs of layers 1..L-1 (T x Bmax x H each)
   size_t o_bx, o_by, o_lsum;  // train_epoch: the gathered batch, the loss sum
+  size_t o_sync;  // persistent rollout: barrier arrivals, abort word, status word
   // state read by rpod_lstm_load, copied to a workspace by rpod_lstm_restore
   bool pending = false;
   int64_t pend_step = 0;
@@ -498,6 +499,7 @@ int rpod_lstm_create(rpod_lstm** out, int32_t in_dim, int32_t hidden, int32_t la
   N->o_bx = take(4 * B * T * I);
   N->o_by = take(4 * B * (size_t)out_dim);
   N->o_lsum = take(4);
+  N->o_sync = take(256);
   N->drop_p = 0.0;
   N->drop_seed = 0;
   N->drop_thr = 0;
@@ -619,6 +621,15 @@ int rpod_lstm_gather(const rpod_lstm* N, const float* series, const float* mu, i
   return cudaGetLastError() == cudaSuccess ? RPOD_OK : RPOD_ERR_CUDA;
 }
 
+// Persistent rollout possible: at most 4 layers, a CTA's rows and staging
+// within 200 KB of shared memory, the grid co-resident (checked by the
+// cooperative launch itself).
+static bool rollout_fits(const rpod_lstm* N, int B, int sms) {
+  if (N->L > 4) return false;
+  const int U = rollout_units(N->H, sms);
+  return rollout_smem_bytes(N->I, N->H, N->L, N->O, B, U) <= (size_t)200 * 1024;
+}
+
 int rpod_lstm_rollout(rpod_lstm* N, const float* window, int32_t B, int32_t mu_cols, int32_t steps,
                       float* out, void* ws, size_t bytes, void* stream) {
   if (!N || !window || !out || B < 1 || B > N->Bmax || steps < 1 || mu_cols < 0 ||
@@ -632,6 +643,26 @@ int rpod_lstm_rollout(rpod_lstm* N, const float* window, int32_t B, int32_t mu_c
   float* nxt = net.f(N->o_xtm2);
   k_to_time_major<<<blocks_for((int64_t)B * N->T * N->I), 256, 0, st>>>(B, N->T, N->I, window, cur);
   LL();
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return RPOD_ERR_CUDA;
+  if (rollout_fits(N, B, sms)) {
+    // one cooperative launch for all steps (the window in o_xtm is its ring)
+    unsigned* sync = (unsigned*)((char*)ws + N->o_sync);
+    LK(cudaMemsetAsync(sync, 0, 16, st));
+    const cudaError_t e = rollout_persistent(
+        st, !N->wfp32, N->I, N->H, N->L, N->O, N->T, B, mu_cols, steps, net.f(N->o_theta),
+        N->wfp32 ? (const void*)net.f(N->o_theta) : (const void*)net.wbf(), N->off_w, N->off_wy,
+        N->off_by, cur, net.f(N->o_h), out, sync, (int*)(sync + 1), sync + 2, sms);
+    if (e == cudaSuccess) {
+      N->last_launches = g_launches;
+      return RPOD_OK;
+    }
+    // a grid the device cannot hold at once: the per-step kernels below
+    if (e != cudaErrorCooperativeLaunchTooLarge) return RPOD_ERR_CUDA;
+    cudaGetLastError();
+  }
   for (int s = 0; s < steps; ++s) {
     if (int rc = net.forward(cur, B)) return rc;
     k_head_loss<<<1, 1024, 0, st>>>(B, N->O, net.f(N->o_y), net.f(N->o_theta) + N->off_by, nullptr,
@@ -802,6 +833,24 @@ int rpod_lstm_set_dropout(rpod_lstm* N, double p, uint64_t seed) {
   N->drop_thr = (uint64_t)ceil(p * 9007199254740992.0);  // ceil(p 2^53), exact scaling
   N->drop_pass = 0;
   return RPOD_OK;
+}
+
+int rpod_lstm_status_sync(const rpod_lstm* N, void* ws, void* stream) {
+  if (!N || !ws) return RPOD_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned* d = (unsigned*)((char*)ws + N->o_sync) + 2;
+  unsigned h = 0;
+  if (cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess || cudaMemsetAsync(d, 0, sizeof(h), st) != cudaSuccess)
+    return RPOD_ERR_CUDA;
+  return (h & ST_TIMEOUT) ? RPOD_ERR_TIMEOUT : RPOD_OK;
+}
+
+int rpod_selftest_grid_barrier(double seconds, void* stream) {
+  if (!(seconds > 0.0 && seconds <= 2.0)) return RPOD_ERR_INVALID_ARG;
+  unsigned status = 0;
+  if (grid_sync_selftest((cudaStream_t)stream, seconds, &status) != cudaSuccess) return RPOD_ERR_CUDA;
+  return (status & ST_TIMEOUT) ? RPOD_ERR_TIMEOUT : RPOD_OK;
 }
 
 int rpod_lstm_last_launch_count(const rpod_lstm* N) { return N ? N->last_launches : -1; }

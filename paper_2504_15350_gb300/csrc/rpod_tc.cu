@@ -313,11 +313,15 @@ k_wpass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
 
 // ---------------------------------------------------------------------------
 // Y-pass (16-bit only): A^T tile K-major (128 x 64 snapshots), S tile MN-major
-// (BN rows as BN/64 boxes of 64 rows x 64 snapshots).
+// (BN rows as BN/64 boxes of 64 rows x 64 snapshots).  blockIdx.y takes the
+// 64-snapshot k-tiles kchunk * y .. kchunk * (y + 1) - 1 and writes its sum
+// to Y + y * ysplit (a split over snapshots for matrices with few rows; the
+// caller sums the slices).
 template <int KIND, int BN, int STAGES>
 __global__ void __launch_bounds__(128, 1)
 k_ypass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmS, int64_t n,
-        int64_t m, int l, float* __restrict__ Y, int64_t ldy, unsigned* status) {
+        int64_t m, int l, float* __restrict__ Y, int64_t ldy, unsigned* status, int kchunk,
+        int64_t ysplit) {
   using L = Smem<BN, STAGES>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -329,7 +333,10 @@ k_ypass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i0 = (int64_t)blockIdx.x * BN;
-  const int nk = (int)((m + 63) / 64);
+  // this CTA's k-tiles (the host sizes the chunks so that none is empty)
+  const int nk_all = (int)((m + 63) / 64);
+  const int kt0 = (int)blockIdx.y * kchunk;
+  const int nk = min(nk_all, kt0 + kchunk) - kt0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -347,10 +354,11 @@ k_ypass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
   const uint32_t tmem = *tslot;
 
   if (warp == 0 && lane == 0) {
-    for (int it = 0; it < nk; ++it) {
-      const int s = it % STAGES;
-      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-      if (it >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+    for (int j = 0; j < nk; ++j) {
+      const int s = j % STAGES;
+      const uint32_t ph = (uint32_t)(j / STAGES) & 1u;
+      if (j >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+      const int it = kt0 + j;
       uint8_t* a = smem + s * L::STAGE;
       mbar_expect_tx(&full[s], L::STAGE);
       tma_load_2d(a, &tmA, &full[s], it * 64, 0);
@@ -360,16 +368,16 @@ k_ypass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     }
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t id = idesc(fmt_of(KIND), true, 128, BN);
-    for (int it = 0; it < nk; ++it) {
-      const int s = it % STAGES;
-      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+    for (int j = 0; j < nk; ++j) {
+      const int s = j % STAGES;
+      const uint32_t ph = (uint32_t)(j / STAGES) & 1u;
       if (!mbar_wait(&full[s], ph, abort_flag)) break;
       tc_after();
       const uint32_t a = su32(smem + s * L::STAGE), b = a + L::A_BYTES;
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
         mma<KIND>(tmem, sdesc(a + 32 * kk, 16, 1024), sdesc(b + 2048 * kk, 8192, 1024), id,
-                  (it > 0 || kk > 0) ? 1u : 0u);
+                  (j > 0 || kk > 0) ? 1u : 0u);
       mma_commit(&empty[s]);
     }
     mma_commit(done);
@@ -379,7 +387,7 @@ k_ypass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
   ok = __all_sync(0xffffffffu, ok) && !*abort_flag;
   tc_after();
   const int c = warp * 32 + lane;
-  float* ycol = Y + (int64_t)c * ldy;
+  float* ycol = Y + (int64_t)blockIdx.y * ysplit + (int64_t)c * ldy;
   for (int cc = 0; cc < BN; cc += 32) {
     float v[32];
     if (ok) {
@@ -743,11 +751,13 @@ template <> __device__ __forceinline__ uint32_t pack16x2<__half>(float a, float 
   return u;
 }
 
+// blockIdx.y: a chunk of kchunk 64-snapshot k-tiles, summed into
+// Y + y * ysplit, as in k_ypass.
 template <int KIND, int STAGES>
 __global__ void __launch_bounds__(192, 1)
 k_ypass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmF,
             int64_t n, int64_t m, int l, float* __restrict__ Y, int64_t ldy, void* __restrict__ Sh,
-            int64_t ldh, unsigned* status) {
+            int64_t ldh, unsigned* status, int kchunk, int64_t ysplit) {
   using L = YcvtSmem<STAGES>;
   using TH = typename std::conditional<KIND == 0, __nv_bfloat16, __half>::type;
   constexpr int BN = 128;
@@ -762,7 +772,9 @@ k_ypass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i0 = (int64_t)blockIdx.x * BN;
-  const int nk = (int)((m + 63) / 64);
+  const int nk_all = (int)((m + 63) / 64);
+  const int kt0 = (int)blockIdx.y * kchunk;
+  const int nk = min(nk_all, kt0 + kchunk) - kt0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -781,10 +793,11 @@ k_ypass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   const uint32_t tmem = *tslot;
 
   if (warp == 0 && lane == 0) {
-    for (int it = 0; it < nk; ++it) {
-      const int s = it % STAGES;
-      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-      if (it >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+    for (int j = 0; j < nk; ++j) {
+      const int s = j % STAGES;
+      const uint32_t ph = (uint32_t)(j / STAGES) & 1u;
+      if (j >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+      const int it = kt0 + j;
       uint8_t* a = smem + s * L::STAGE;
       mbar_expect_tx(&full[s], L::A_BYTES + L::F_BYTES);
       tma_load_2d(a, &tmA, &full[s], it * 64, 0);
@@ -797,10 +810,11 @@ k_ypass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const int ct = threadIdx.x - 64;
     TH* shg = (TH*)Sh;
     bool bad = false;
-    for (int it = 0; it < nk; ++it) {
-      const int s = it % STAGES;
-      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+    for (int j = 0; j < nk; ++j) {
+      const int s = j % STAGES;
+      const uint32_t ph = (uint32_t)(j / STAGES) & 1u;
       if (!mbar_wait(&full[s], ph, abort_flag)) break;
+      const int it = kt0 + j;
       const uint8_t* f = smem + s * L::STAGE + L::A_BYTES;
       uint8_t* h = smem + s * L::STAGE + L::A_BYTES + L::F_BYTES;
 #pragma unroll 2
@@ -839,16 +853,16 @@ k_ypass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_NONFINITE);
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t id = idesc(fmt_of(KIND), true, 128, BN);
-    for (int it = 0; it < nk; ++it) {
-      const int s = it % STAGES;
-      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+    for (int j = 0; j < nk; ++j) {
+      const int s = j % STAGES;
+      const uint32_t ph = (uint32_t)(j / STAGES) & 1u;
       if (!mbar_wait(&conv[s], ph, abort_flag)) break;
       tc_after();
       const uint32_t a = su32(smem + s * L::STAGE), b = a + L::A_BYTES + L::F_BYTES;
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
         mma<KIND>(tmem, sdesc(a + 32 * kk, 16, 1024), sdesc(b + 2048 * kk, 8192, 1024), id,
-                  (it > 0 || kk > 0) ? 1u : 0u);
+                  (j > 0 || kk > 0) ? 1u : 0u);
       mma_commit(&empty[s]);
     }
     mma_commit(done);
@@ -860,7 +874,7 @@ k_ypass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     tc_after();
     const int q = warp & 3;
     const int c = q * 32 + lane;
-    float* ycol = Y + (int64_t)c * ldy;
+    float* ycol = Y + (int64_t)blockIdx.y * ysplit + (int64_t)c * ldy;
     for (int cc = 0; cc < BN; cc += 32) {
       float v[32];
       if (ok) {
@@ -1293,30 +1307,74 @@ int tc_wpass(cudaStream_t st, int dt, const void* A, int64_t lda, int64_t n, int
   return cudaGetLastError() == cudaSuccess ? RPOD_OK : RPOD_ERR_CUDA;
 }
 
+// Chunks of snapshots for a Y-pass whose row tiles cannot fill the GPU (a
+// standalone pass over a matrix with few rows and many snapshots, e.g. the
+// paper's 8192 grid cells x 90225 snapshots): the smallest count that gives
+// at least two waves of CTAs with the last wave at least 85 % full, each
+// chunk at least 8 k-tiles.  1 for batch-instance-sized passes (other
+// instances fill the GPU) and for matrices with enough rows.
+int ypass_split(int64_t row_tiles, int64_t m, size_t pass_bytes, int ctas_per_sm) {
+  if (pass_bytes < kSmallPassBytes) return 1;
+  const int64_t slots = (int64_t)sm_count() * ctas_per_sm;
+  if (row_tiles >= 2 * slots) return 1;
+  const int64_t nk = (m + 63) / 64;
+  int best = 1;
+  for (int ns = 2; ns <= 32 && nk / ns >= 8; ++ns) {
+    const int64_t total = row_tiles * ns;
+    const int64_t waves = (total + slots - 1) / slots;
+    best = ns;
+    if (total >= 2 * slots && (double)total / (double)(waves * slots) >= 0.85) break;
+  }
+  return best;
+}
+
+// Chunk layout of a split Y-pass: kchunk k-tiles per chunk, ns chunks with
+// none empty; 1 chunk when the partial buffer cannot hold ns slices.
+void ypass_chunks(int64_t m, int want, size_t slice_elems, size_t part_elems, int* ns, int* kchunk) {
+  const int nk = (int)((m + 63) / 64);
+  int s = want;
+  if ((size_t)s * slice_elems > part_elems) s = 1;
+  int kc = (nk + s - 1) / s;
+  s = (nk + kc - 1) / kc;
+  *ns = s;
+  *kchunk = kc;
+}
+
 int tc_ypass(cudaStream_t st, int dt, const void* A, int64_t lda, const void* S, int64_t lds,
-             int64_t n, int64_t m, int l, float* Y, int64_t ldy, unsigned* status) {
+             int64_t n, int64_t m, int l, float* Y, int64_t ldy, unsigned* status, float* part,
+             size_t part_elems) {
   if (dt != RPOD_BF16 && dt != RPOD_F16) return RPOD_ERR_UNSUPPORTED;
   CUtensorMap ta, ts;
   if (int rc = make_map(&ta, A, dt, m, l, lda, 64, 128)) return rc;
   if (int rc = make_map(&ts, S, dt, n, m, lds, 64, 64)) return rc;
-  dim3 grid((unsigned)((n + kBN - 1) / kBN));
+  const int64_t tiles = (n + kBN - 1) / kBN;
+  const size_t bytes = (size_t)n * (size_t)m * 2;
+  int ns = 1, kchunk = 0;
+  ypass_chunks(m, part ? ypass_split(tiles, m, bytes, 1) : 1, (size_t)n * l, part_elems, &ns, &kchunk);
+  float* out = ns > 1 ? part : Y;
+  const int64_t ldo = ns > 1 ? n : ldy;
+  const int64_t ysplit = ns > 1 ? n * l : 0;
+  dim3 grid((unsigned)tiles, (unsigned)ns);
   prepare_kernels_tc();
-  const bool small = (size_t)n * (size_t)m * 2 < kSmallPassBytes;
+  const bool small = bytes < kSmallPassBytes;
   using L = tc::Smem<kBN, kStages>;
   using Ls = tc::Smem<kBN, kStagesSmall>;
   if (small) {
     if (dt == RPOD_BF16)
-      tc::k_ypass<0, kBN, kStagesSmall><<<grid, 128, Ls::TOTAL, st>>>(ta, ts, n, m, l, Y, ldy, status);
+      tc::k_ypass<0, kBN, kStagesSmall><<<grid, 128, Ls::TOTAL, st>>>(ta, ts, n, m, l, out, ldo, status, kchunk, ysplit);
     else
-      tc::k_ypass<1, kBN, kStagesSmall><<<grid, 128, Ls::TOTAL, st>>>(ta, ts, n, m, l, Y, ldy, status);
+      tc::k_ypass<1, kBN, kStagesSmall><<<grid, 128, Ls::TOTAL, st>>>(ta, ts, n, m, l, out, ldo, status, kchunk, ysplit);
   } else {
     if (dt == RPOD_BF16)
-      tc::k_ypass<0, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, Y, ldy, status);
+      tc::k_ypass<0, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, out, ldo, status, kchunk, ysplit);
     else
-      tc::k_ypass<1, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, Y, ldy, status);
+      tc::k_ypass<1, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, out, ldo, status, kchunk, ysplit);
   }
   note_launch();
-  return cudaGetLastError() == cudaSuccess ? RPOD_OK : RPOD_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return RPOD_ERR_CUDA;
+  if (ns > 1 && reduce_splits<float, float>(st, n, l, ns, part, Y, 1, ldy) != cudaSuccess)
+    return RPOD_ERR_CUDA;
+  return RPOD_OK;
 }
 
 int tc_gram(cudaStream_t st, const float* Y, int64_t ldy, int64_t rows, int l, double* part,
@@ -1339,21 +1397,33 @@ int tc_gram(cudaStream_t st, const float* Y, int64_t ldy, int64_t rows, int l, d
 
 int tc_ypass_cvt(cudaStream_t st, int dt, const void* A, int64_t lda, const float* S, int64_t lds,
                  int64_t n, int64_t m, int l, float* Y, int64_t ldy, void* Sh, int64_t ldh,
-                 unsigned* status) {
+                 unsigned* status, float* part, size_t part_elems) {
   if (dt != RPOD_BF16 && dt != RPOD_F16) return RPOD_ERR_UNSUPPORTED;
   if (((uintptr_t)Sh & 15) || (ldh & 7)) return RPOD_ERR_UNSUPPORTED;
   CUtensorMap ta, tf;
   if (int rc = make_map(&ta, A, dt, m, l, lda, 64, 128)) return rc;
   if (int rc = make_map(&tf, S, RPOD_F32, n, m, lds, 32, 64)) return rc;
-  dim3 grid((unsigned)((n + 127) / 128));
+  const int64_t tiles = (n + 127) / 128;
+  int ns = 1, kchunk = 0;
+  ypass_chunks(m, part ? ypass_split(tiles, m, (size_t)n * (size_t)m * 4, 1) : 1, (size_t)n * l,
+               part_elems, &ns, &kchunk);
+  float* out = ns > 1 ? part : Y;
+  const int64_t ldo = ns > 1 ? n : ldy;
+  const int64_t ysplit = ns > 1 ? n * l : 0;
+  dim3 grid((unsigned)tiles, (unsigned)ns);
   using L = tc::YcvtSmem<kYcvtStages>;
   prepare_kernels_tc();
   if (dt == RPOD_BF16)
-    tc::k_ypass_cvt<0, kYcvtStages><<<grid, 192, L::TOTAL, st>>>(ta, tf, n, m, l, Y, ldy, Sh, ldh, status);
+    tc::k_ypass_cvt<0, kYcvtStages><<<grid, 192, L::TOTAL, st>>>(ta, tf, n, m, l, out, ldo, Sh, ldh, status,
+                                                                  kchunk, ysplit);
   else
-    tc::k_ypass_cvt<1, kYcvtStages><<<grid, 192, L::TOTAL, st>>>(ta, tf, n, m, l, Y, ldy, Sh, ldh, status);
+    tc::k_ypass_cvt<1, kYcvtStages><<<grid, 192, L::TOTAL, st>>>(ta, tf, n, m, l, out, ldo, Sh, ldh, status,
+                                                                  kchunk, ysplit);
   note_launch();
-  return cudaGetLastError() == cudaSuccess ? RPOD_OK : RPOD_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return RPOD_ERR_CUDA;
+  if (ns > 1 && reduce_splits<float, float>(st, n, l, ns, part, Y, 1, ldy) != cudaSuccess)
+    return RPOD_ERR_CUDA;
+  return RPOD_OK;
 }
 
 int tc_sm_count() { return sm_count(); }

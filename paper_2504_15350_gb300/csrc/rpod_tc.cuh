@@ -17,9 +17,12 @@ int tc_wpass(cudaStream_t st, int dt, const void* A, int64_t lda, int64_t n, int
 
 // Y-pass: Y(i, c) = sum_j S(i, j) A(j, c) for i < n, c < l; A: m x 128
 // column-major (ld lda, columns >= l zero), S: n x m, both 16-bit of type dt;
-// Y FP32 column-major (ld ldy).
+// Y FP32 column-major (ld ldy).  With a partial buffer (part_elems floats),
+// a standalone pass whose row tiles cannot fill the GPU splits the snapshots
+// into chunks summed there and then reduced into Y.
 int tc_ypass(cudaStream_t st, int dt, const void* A, int64_t lda, const void* S, int64_t lds,
-             int64_t n, int64_t m, int l, float* Y, int64_t ldy, unsigned* status);
+             int64_t n, int64_t m, int l, float* Y, int64_t ldy, unsigned* status,
+             float* part = nullptr, size_t part_elems = 0);
 
 // First Y-pass over an FP32 S (n x m, ld lds): Y as tc_ypass with S rounded
 // to the 16-bit type dt, and that rounded S written to Sh (n x m, ld ldh, a
@@ -27,7 +30,7 @@ int tc_ypass(cudaStream_t st, int dt, const void* A, int64_t lda, const void* S,
 // entries of S.  RPOD_ERR_UNSUPPORTED when S, A or Sh is not addressable.
 int tc_ypass_cvt(cudaStream_t st, int dt, const void* A, int64_t lda, const float* S, int64_t lds,
                  int64_t n, int64_t m, int l, float* Y, int64_t ldy, void* Sh, int64_t ldh,
-                 unsigned* status);
+                 unsigned* status, float* part = nullptr, size_t part_elems = 0);
 
 // Gram partials part[z][c + j l] (FP64) = sum over rows of split z of
 // Y(i, c) Y(i, j) for c, j < l <= 128, on the TF32 tensor path with FP32

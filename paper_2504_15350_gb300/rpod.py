@@ -77,6 +77,8 @@ SIGNATURES = {
     "rpod_lstm_restore": (ctypes.c_int, [_p, _p, ctypes.c_size_t, _p]),
     "rpod_lstm_dims": (ctypes.c_int, [_p, _pi32]),
     "rpod_lstm_last_launch_count": (ctypes.c_int, [_p]),
+    "rpod_lstm_status_sync": (ctypes.c_int, [_p, _p, _p]),
+    "rpod_selftest_grid_barrier": (ctypes.c_int, [ctypes.c_double, _p]),
     "rpod_lstm_destroy": (None, [_p]),
     "rpod_plan_create": (ctypes.c_int, [ctypes.POINTER(_p), _c_i64, _c_i64, _c_i32, _c_i32, _c_i32,
                                         _c_u64, _c_i32, _c_u32]),
@@ -636,6 +638,14 @@ def rpod_lstm_last_launch_count(net):
     return load().rpod_lstm_last_launch_count(net)
 
 
+def rpod_lstm_status_sync(net, ws, stream):
+    return load().rpod_lstm_status_sync(net, ws, stream)
+
+
+def rpod_selftest_grid_barrier(seconds, stream):
+    return load().rpod_selftest_grid_barrier(seconds, stream)
+
+
 def rpod_lstm_destroy(net):
     load().rpod_lstm_destroy(net)
 
@@ -774,3 +784,8 @@ class LSTM:
 
     def launches(self):
         return rpod_lstm_last_launch_count(self.handle)
+
+    def status(self):
+        """Device status of the last persistent rollout (RPOD_OK or
+        RPOD_ERR_TIMEOUT); synchronises the stream."""
+        return rpod_lstm_status_sync(self.handle, self.ws_ptr, self._stream())

@@ -215,3 +215,73 @@ def test_save_load_restore_continues_training(tmp_path):
     torch.cuda.synchronize()
     assert la == lc
     assert torch.equal(a.get_params(), c.get_params())
+
+
+def test_config5_shape_forward_gradients_and_rollout():
+    """Config 5's network at full size: 54 inputs (4 parameters + 50
+    coefficients), 2 layers x 256 cells, window 10, batch 512, weights
+    U(+-1/sqrt(H)) as trained; forward, loss and every gradient block
+    against the FP64 oracle at the same BF16-rounded weights, and a 50-step
+    autoregressive rollout of 8 windows."""
+    I, H, L, O, T, B = 54, 256, 2, 50, 10, 512
+    rng = np.random.default_rng(55)
+    theta = (rng.uniform(-1.0, 1.0, OL.param_count(I, H, L, O)) / np.sqrt(H)).astype(np.float32)
+    theta = theta.astype(np.float64)
+    X = rng.standard_normal((B, T, I)).astype(np.float32)
+    Yt = rng.standard_normal((B, O)).astype(np.float32)
+    te = bf16_weights(theta, I, H, L, O)
+    y_o, cache = OL.forward(te, X.astype(np.float64), H, L, O)
+    loss_o, dy = OL.mse(y_o, Yt.astype(np.float64))
+    g_o = OL.backward(te, cache, dy, H, L, O)
+    net = R.LSTM(I, H, L, O, T, max_batch=B, theta=theta)
+    Xd = torch.from_numpy(X).cuda()
+    assert rel(net.forward(Xd).cpu().numpy(), y_o) < 2e-5
+    loss, g = net.loss_grad(Xd, torch.from_numpy(Yt).cuda())
+    torch.cuda.synchronize()
+    assert abs(loss.item() - loss_o) <= 1e-5 * loss_o
+    g = g.cpu().numpy()
+    off = 0
+    for shp in OL.param_shapes(I, H, L, O):
+        n = int(np.prod(shp))
+        assert rel(g[off:off + n], g_o[off:off + n]) < 2e-4, shp
+        off += n
+    win = rng.standard_normal((8, T, I)).astype(np.float32)
+    ref = OL.rollout(te, win.astype(np.float64), 4, 50, H, L, O)
+    out = net.rollout(torch.from_numpy(win).cuda(), 4, 50).cpu().numpy()
+    assert rel(out, ref) < 1e-4, rel(out, ref)
+
+
+def test_persistent_and_per_step_rollouts_agree():
+    """8 windows fit the persistent rollout kernel (weights resident in
+    shared memory, a grid barrier per anti-diagonal of layer x time cells);
+    64 windows of the same network exceed its shared memory and take the
+    per-step kernels.  Both match the oracle and each other on the shared
+    windows over 60 steps, and the persistent run leaves an OK status."""
+    I, H, L, O, T = 54, 256, 2, 50, 10
+    rng = np.random.default_rng(77)
+    theta = (rng.uniform(-1.0, 1.0, OL.param_count(I, H, L, O)) / np.sqrt(H)).astype(np.float32)
+    theta = theta.astype(np.float64)
+    win = rng.standard_normal((64, T, I)).astype(np.float32)
+    net = R.LSTM(I, H, L, O, T, max_batch=64, theta=theta)
+    big = net.rollout(torch.from_numpy(win).cuda(), 4, 60).cpu().numpy()
+    small = net.rollout(torch.from_numpy(win[:8]).cuda(), 4, 60).cpu().numpy()
+    assert net.status() == R.RPOD_OK
+    assert rel(small, big[:8]) < 1e-5, rel(small, big[:8])
+    ref = OL.rollout(bf16_weights(theta, I, H, L, O), win[:8].astype(np.float64), 4, 60, H, L, O)
+    assert rel(small, ref) < 1e-4
+    assert net.launches() < 5      # one cooperative launch (plus the window copy)
+
+
+def test_grid_barrier_limit_reports_timeout():
+    """A grid barrier whose last arrival never comes: the bounded wait runs
+    out after 50 ms, the kernel records RPOD_ERR_TIMEOUT and returns, and the
+    context stays usable (a rollout right after it succeeds)."""
+    st = torch.cuda.current_stream().cuda_stream
+    assert R.rpod_selftest_grid_barrier(0.05, st) == R.RPOD_ERR_TIMEOUT
+    assert R.rpod_selftest_grid_barrier(3.0, st) == R.RPOD_ERR_INVALID_ARG
+    I, H, L, O, T = 7, 32, 2, 5, 4
+    rng = np.random.default_rng(1)
+    theta = rng.uniform(-0.4, 0.4, OL.param_count(I, H, L, O))
+    net = R.LSTM(I, H, L, O, T, max_batch=8, theta=theta)
+    out = net.rollout(torch.from_numpy(rng.standard_normal((3, T, I)).astype(np.float32)).cuda(), 2, 5)
+    assert net.status() == R.RPOD_OK and torch.isfinite(out).all()

@@ -3,13 +3,14 @@ parameter samples x 2000 steps, LSTM trained by the library's kernels, rollouts
 for 8 held-out parameter samples judged against the Galerkin projection of
 their snapshots.
 
-The trained network must do clearly better than the two predictors without
-it -- persistence of the last seed step and the nearest training sample's
-coefficients -- on the held-out one-step (teacher-forced) prediction and on
-the first 10 autoregressive steps.  The 500-step trajectory error is printed
-but not asserted: on this synthetic flow (400 incommensurate oscillators) a
-free-running rollout drifts out of phase after a few dozen steps, and every
-predictor's trajectory error then saturates near 1."""
+The trained network must do better than the two predictors without it --
+persistence of the last seed step and the nearest training sample's
+coefficients -- on the held-out one-step (teacher-forced) prediction, on the
+first 10 autoregressive steps, and at the paper's horizon: over all 500
+autoregressive steps and on the time-averaged field of Eq. (l2-error).  The
+long horizon needs pushforward training (the network also learns from
+windows made of its own predictions): trained one step at a time, its
+free-running rollout drifts out of phase and loses to both predictors."""
 import math
 
 import pytest
@@ -36,6 +37,29 @@ def test_lstm_beats_no_lstm_predictors_short_horizon():
     assert res.onestep_err_lstm <= 0.6 * res.onestep_err_persistence
     assert res.err_lstm_first10 <= 0.5 * min(res.err_persistence_first10,
                                              res.err_nearest_first10)
+
+
+def test_lstm_beats_no_lstm_predictors_at_500_steps():
+    """Config 5 with a steady parameter-dependent part in the snapshots (so
+    that Eq. (l2-error) is well posed), raw rPOD coefficients, pushforward
+    training (up to 10 predicted steps in half of the batches), 60 epochs.
+    Over the 500-step rollout the LSTM's coefficient error is below both
+    predictors without it, and its time-averaged field error is below both
+    and within 0.1, the top of the paper's stated field-error range (1e-2 ..
+    1e-1).  Measured: 500 steps 0.42 vs persistence 0.58 and nearest sample
+    0.48; time-averaged field 0.059 vs 0.44 and 0.100."""
+    from paper_2504_15350_gb300.build import build
+    build()
+    cfg = rom.ROMConfig(epochs=60, patience=15, mean_amp=1.0, center=False, pushforward=10)
+    res = rom.run(cfg)
+    print(f"\n500 steps: LSTM {res.err_lstm:.4f} persistence {res.err_persistence:.4f} nearest-mu "
+          f"{res.err_nearest:.4f}; time-averaged field: LSTM {res.tavg_err_lstm:.4f} persistence "
+          f"{res.tavg_err_persistence:.4f} nearest-mu {res.tavg_err_nearest:.4f} floor "
+          f"{res.tavg_err_projection:.4f}; epochs {res.epochs_run}")
+    assert res.err_lstm <= 0.95 * min(res.err_persistence, res.err_nearest)
+    assert res.tavg_err_lstm <= 0.8 * min(res.tavg_err_persistence, res.tavg_err_nearest)
+    assert res.tavg_err_lstm <= 0.1
+    assert res.tavg_err_projection <= 0.02
 
 
 def test_centered_rom_zero_order_field():

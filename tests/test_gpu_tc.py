@@ -189,3 +189,26 @@ def test_basis_bf16_refine_65536_rows_matches_oracle():
         assert err.max() <= 1e-4, (name, err.max())
         assert max_angle(o.U[:, :k], U) <= 1e-2, name
     assert orth_err(U) <= 1e-5
+
+
+def test_basis_bf16_refine_paper_shape_split_ypass():
+    """The paper's own snapshot-matrix shape (Sec. 4.2, Table tab:cpu_time):
+    n = 8192 grid cells (64 x 128), m = 90225 snapshots, k = 10, p = 75,
+    q = 1.  With 32 row tiles of 256 (64 of 128 in the first pass) the
+    Y-passes split the snapshots into chunks summed in the W-pass partial
+    buffer; BF16 bounds against both oracles."""
+    rec = make_recipe(64, 128, 90225, 400, ("power", 1.5), seed=0, noise=1e-6)
+    S = snapshot_matrix(rec, device="cuda", dtype=torch.float32)
+    k, p, q = 10, 75, 1
+    plan = R.Plan(rec.n, rec.m, k, p, q, seed=0, compute="bf16", flags=R.RPOD_FLAG_REFINE_FP32)
+    U, sig, C = plan.basis(S)
+    assert plan.status()[0] == R.RPOD_OK
+    sig = sig.cpu().numpy()
+    U = U.double().cpu().numpy()
+    S64 = S.cpu().double().numpy()
+    lowp, orig = _oracles(S64, k, p, q, "bf16")
+    for name, o in (("rounded-input", lowp), ("FP32-input", orig)):
+        err = np.abs(sig[:k] - o.sigma[:k]) / o.sigma[:k]
+        assert err.max() <= 1e-4, (name, err.max())
+        assert max_angle(o.U[:, :k], U) <= 1e-2, name
+    assert orth_err(U) <= 1e-5
