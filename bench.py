@@ -71,8 +71,10 @@ def parse():
     ap.add_argument("--only-batched", choices=["bf16", "f32"], default=None,
                     help="profiling aid: run only the batched leg in this form and print its "
                          "JSON object")
+    ap.add_argument("--only-leg", choices=["small-configs", "config6", "learned"], default=None,
+                    help="profiling aid: run only this leg and print its JSON object")
     ap.add_argument("--batched-config", default=None,
-                    help="STREAMS,SPLIT_PCT: skip the tuner and use this launch configuration")
+                    help="STREAMS,SPLIT_PCT[,STAGES]: skip the tuner and use this launch configuration")
     ap.add_argument("--no-small-configs", action="store_true",
                     help="skip the config-1 (FP64) and config-3 (16-bit + refinement) timings")
     ap.add_argument("--no-config6", action="store_true",
@@ -308,6 +310,7 @@ def run_batched(dev, max_over_ranks, barrier, rank=0, world=1, steps=5, form="f3
     B = R.Batch(S, ks, 10, 1, seeds, compute=form, flags=flags, device=dev)
     if config:
         best = tuple(int(v) for v in config.split(","))
+        best = best + (0,) * (3 - len(best))
         B.configure(*best)
     else:
         best = B.tune(trials=3)
@@ -336,6 +339,7 @@ def run_batched(dev, max_over_ranks, barrier, rank=0, world=1, steps=5, form="f3
            "sum_m_this_rank": int(sum(r.m for r in recs)),
            "ms_per_batch": ms, "pass_bytes_GB": nbytes / 1e9,
            "effective_GBps": nbytes / (ms * 1e-3) / 1e9, "streams": best[0], "split_pct": best[1],
+           "pass_stages": best[2],
            "gpu_launches_per_batch": B.launches(), "graph_launches_per_batch": 1}
     del B, S
     torch.cuda.empty_cache()
@@ -518,6 +522,20 @@ def main():
         t = torch.tensor([x], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return t.item()
+
+    if args.only_leg:
+        peaks, _ = load_peaks()
+        if args.only_leg == "small-configs":
+            out = run_small_configs(dev, args.warmup)
+        elif args.only_leg == "config6":
+            out = run_config6(dev, args.warmup, peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+        else:
+            out = run_learned(dev, args.learned_epochs)
+        if rank == 0:
+            print(json.dumps({args.only_leg: out}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     if args.only_batched:
         out = run_batched(dev, max_over_ranks, barrier, rank, world, steps=args.steps,

@@ -287,14 +287,22 @@ int rpod_batch_create(rpod_batch** out, int32_t count, const rpod_instance* inst
 int rpod_batch_workspace_bytes(const rpod_batch* batch, size_t* bytes);
 /* Enqueues the whole batch on `stream` (graph capture on first use). */
 int rpod_batch_run(rpod_batch* batch, void* workspace, size_t workspace_bytes, void* stream);
-/* Autotuner: times the candidate launch configurations (worker streams in
- * {1, 2, 4, 8, 16, 32, 64} x split-K scale in {1/4, 1/2, 1, 2} of the passes' default
- * split) `trials` times each with CUDA events on `stream` (synchronising),
- * keeps the fastest, re-captures, and returns it through best_streams and
- * best_split_pct (may be NULL).  Runs the batch many times: outputs hold the
- * last run's results. */
+/* Autotuner: times the candidate launch configurations -- worker streams in
+ * {1, 2, 4, 8, 16, 32, 64} (up to the instance count) x split-K scale in
+ * {1/4, 1/2, 1, 2} of the passes' default split x, for the 16-bit forms, the
+ * tensor-core passes' pipeline depth in {2, 4} stages -- as `trials` separately
+ * timed replays each (CUDA events on `stream`, synchronising; a point's time
+ * is the fastest replay), keeps the fastest point, re-captures, and returns
+ * it through best_streams, best_split_pct and best_stages (each may be
+ * NULL).  Runs the batch many times: outputs hold the last run's results. */
 int rpod_batch_tune(rpod_batch* batch, void* workspace, size_t workspace_bytes, void* stream,
-                    int32_t trials, int32_t* best_streams, int32_t* best_split_pct);
+                    int32_t trials, int32_t* best_streams, int32_t* best_split_pct,
+                    int32_t* best_stages);
+/* Pipeline depth of every instance's tensor-core W- and Y-passes: 0 (the
+ * default) chooses by pass size -- two 96 KB stages below 1 GiB, so that two
+ * CTAs share an SM, four above -- while 2 or 4 force it (e.g. from a cached
+ * tuning).  Errors: RPOD_ERR_INVALID_ARG for other values. */
+int rpod_batch_set_pass_stages(rpod_batch* batch, int32_t stages);
 /* Sets the launch configuration directly (e.g. from a cached tuning):
  * 1..64 worker streams, split_pct in 10..200. */
 int rpod_batch_configure(rpod_batch* batch, int32_t streams, int32_t split_pct);

@@ -39,6 +39,7 @@ struct rpod_plan {
   size_t part_elems, gpart_elems, sign_bytes, wpart_elems;
   int last_launches;
   int svd_sweeps;  // cap on the FP64 form's one-sided Jacobi sweeps
+  int pass_stages;  // 16-bit passes' pipeline depth: 0 by pass size, else 2 or 4
   // row-sharded plans (rpod_rows_plan_create): this plan's rows are rows
   // row0 .. row0 + n - 1 of an n_total x m matrix whose other row blocks
   // belong to other calls; the exchange callback is set for one
@@ -434,7 +435,7 @@ struct Run {
         else
           CK(convert_snapshots<__half>(st, n, m, (const float*)S_in, lds_in, (__half*)Sb, nld,
                                        status));
-        rc = tc_ypass(st, dt, Zh, mld, Sb, nld, n, m, l, Y, n, status, wpart, P->wpart_elems);
+        rc = tc_ypass(st, dt, Zh, mld, Sb, nld, n, m, l, Y, n, status, wpart, P->wpart_elems, P->pass_stages);
         CR(rc);
         prof_end(P, st, 6.0 * (double)n * m + pb16, pass_flops);
       } else {
@@ -446,7 +447,7 @@ struct Run {
       if (!Sref) { Sref = (const float*)S_in; ldr = lds_in; }
     } else {
       prof_begin(P, st);
-      CR(tc_ypass(st, dt, Zh, mld, Sh, ldh, n, m, l, Y, n, status, wpart, P->wpart_elems));
+      CR(tc_ypass(st, dt, Zh, mld, Sh, ldh, n, m, l, Y, n, status, wpart, P->wpart_elems, P->pass_stages));
       prof_end(P, st, pb16, pass_flops);
     }
     float* Q = nullptr;
@@ -463,7 +464,7 @@ struct Run {
       if (it > 0) {
         // Alg. 1 subspace iteration: Z = S^T Q, orthonormalise, Y = S Z
         prof_begin(P, st);
-        CR(tc_wpass(st, dt, Qh, nld, n, l, Sh, ldh, m, wpart, P->nsplit_w, status));
+        CR(tc_wpass(st, dt, Qh, nld, n, l, Sh, ldh, m, wpart, P->nsplit_w, status, P->pass_stages));
         prof_end(P, st, pb16, pass_flops);
         // Z with a 16-byte aligned leading dimension, so that its Gram
         // takes the tensor-core path at any m
@@ -473,7 +474,7 @@ struct Run {
         CR(orth(Z, Zq, m, 1, &Zo, false, false, nullptr, m4));
         CK(to16(Zo, m, m4, Zh, mld));
         prof_begin(P, st);
-        CR(tc_ypass(st, dt, Zh, mld, Sh, ldh, n, m, l, Y, n, status, wpart, P->wpart_elems));
+        CR(tc_ypass(st, dt, Zh, mld, Sh, ldh, n, m, l, Y, n, status, wpart, P->wpart_elems, P->pass_stages));
         prof_end(P, st, pb16, pass_flops);
       }
       // the final basis is kept in FP32 (lift, Gram of the deferred round)
@@ -524,12 +525,12 @@ struct Run {
     if (refine) {
       if (!tf_ready) CK(round_tf32(st, n, l, Q, n, Atf, nld));
       prof_begin(P, st);
-      CR(tc_wpass(st, RPOD_F32, Atf, nld, n, l, Sref, ldr, m, wpart, P->nsplit_w, status));
+      CR(tc_wpass(st, RPOD_F32, Atf, nld, n, l, Sref, ldr, m, wpart, P->nsplit_w, status, P->pass_stages));
       prof_end(P, st, 4.0 * ((double)n * m + (double)n * l + (double)m * l), pass_flops);
     } else {
       CK(to16(Q, n, n, Qh, nld));
       prof_begin(P, st);
-      CR(tc_wpass(st, dt, Qh, nld, n, l, Sh, ldh, m, wpart, P->nsplit_w, status));
+      CR(tc_wpass(st, dt, Qh, nld, n, l, Sh, ldh, m, wpart, P->nsplit_w, status, P->pass_stages));
       prof_end(P, st, pb16, pass_flops);
     }
     CK((reduce_splits<float, float>(st, m, l, P->nsplit_w, wpart, Zq, 1, m)));
@@ -699,6 +700,7 @@ static int plan_create_impl(rpod_plan** out, int64_t n, int64_t m, int32_t k, in
   }
   P->last_launches = 0;
   P->svd_sweeps = 30;
+  P->pass_stages = 0;
   *out = P;
   return RPOD_OK;
 }
@@ -973,6 +975,7 @@ struct rpod_batch {
   size_t total = 0;
   int nstreams = 4;
   int split_pct = 100;
+  int stages = 0;  // pipeline depth of the instances' passes (0: by pass size)
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> join;
   cudaEvent_t fork = nullptr;
@@ -1139,6 +1142,14 @@ int rpod_batch_configure(rpod_batch* B, int32_t streams, int32_t split_pct) {
   return RPOD_OK;
 }
 
+int rpod_batch_set_pass_stages(rpod_batch* B, int32_t stages) {
+  if (!B || !(stages == 0 || stages == 2 || stages == 4)) return RPOD_ERR_INVALID_ARG;
+  B->stages = stages;
+  for (rpod_plan* P : B->plans) P->pass_stages = stages;
+  drop_graph(B);
+  return RPOD_OK;
+}
+
 int rpod_batch_run(rpod_batch* B, void* workspace, size_t workspace_bytes, void* stream) {
   if (!B) return RPOD_ERR_INVALID_ARG;
   if (!workspace || workspace_bytes < B->total || ((uintptr_t)workspace & 255))
@@ -1150,37 +1161,57 @@ int rpod_batch_run(rpod_batch* B, void* workspace, size_t workspace_bytes, void*
 }
 
 int rpod_batch_tune(rpod_batch* B, void* workspace, size_t workspace_bytes, void* stream,
-                    int32_t trials, int32_t* best_streams, int32_t* best_split_pct) {
+                    int32_t trials, int32_t* best_streams, int32_t* best_split_pct,
+                    int32_t* best_stages) {
   if (!B || trials < 1) return RPOD_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   const int stream_opts[7] = {1, 2, 4, 8, 16, 32, 64};
   const int split_opts[4] = {25, 50, 100, 200};
+  // the passes' pipeline depth matters only for the tensor-core forms
+  const bool tc16 = B->compute == RPOD_BF16 || B->compute == RPOD_F16;
+  const int stage_opts[2] = {2, 4};
+  const int nstage = tc16 ? 2 : 1;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return RPOD_ERR_CUDA;
   float best = 1e30f;
-  int bs = B->nstreams, bp = B->split_pct;
+  int bs = B->nstreams, bp = B->split_pct, bg = B->stages;
   int rc = RPOD_OK;
-  for (int a = 0; a < 7 && rc == RPOD_OK; ++a) {
-    if (stream_opts[a] > std::max(1, B->count)) continue;
-    for (int b = 0; b < 4 && rc == RPOD_OK; ++b) {
-      rc = rpod_batch_configure(B, stream_opts[a], split_opts[b]);
-      if (rc == RPOD_OK) rc = rpod_batch_run(B, workspace, workspace_bytes, stream);  // capture + warm
-      if (rc != RPOD_OK) break;
-      cudaEventRecord(e0, st);
-      for (int t = 0; t < trials && rc == RPOD_OK; ++t) rc = rpod_batch_run(B, workspace, workspace_bytes, stream);
-      cudaEventRecord(e1, st);
-      if (cudaEventSynchronize(e1) != cudaSuccess) rc = RPOD_ERR_CUDA;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (rc == RPOD_OK && ms < best) { best = ms; bs = stream_opts[a]; bp = split_opts[b]; }
+  for (int g = 0; g < nstage && rc == RPOD_OK; ++g) {
+    if (tc16) rc = rpod_batch_set_pass_stages(B, stage_opts[g]);
+    for (int a = 0; a < 7 && rc == RPOD_OK; ++a) {
+      if (stream_opts[a] > std::max(1, B->count)) continue;
+      for (int b = 0; b < 4 && rc == RPOD_OK; ++b) {
+        rc = rpod_batch_configure(B, stream_opts[a], split_opts[b]);
+        if (rc == RPOD_OK) rc = rpod_batch_run(B, workspace, workspace_bytes, stream);  // capture + warm
+        if (rc != RPOD_OK) break;
+        // `trials` separately timed replays; the point's time is their minimum
+        float pt = 1e30f;
+        for (int t = 0; t < trials && rc == RPOD_OK; ++t) {
+          cudaEventRecord(e0, st);
+          rc = rpod_batch_run(B, workspace, workspace_bytes, stream);
+          cudaEventRecord(e1, st);
+          if (cudaEventSynchronize(e1) != cudaSuccess) rc = RPOD_ERR_CUDA;
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          pt = std::min(pt, ms);
+        }
+        if (rc == RPOD_OK && pt < best) {
+          best = pt;
+          bs = stream_opts[a];
+          bp = split_opts[b];
+          bg = tc16 ? stage_opts[g] : B->stages;
+        }
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != RPOD_OK) return rc;
+  CR(rpod_batch_set_pass_stages(B, bg));
   CR(rpod_batch_configure(B, bs, bp));
   if (best_streams) *best_streams = bs;
   if (best_split_pct) *best_split_pct = bp;
+  if (best_stages) *best_stages = bg;
   return RPOD_OK;
 }
 

@@ -34,17 +34,13 @@ namespace rpod {
 namespace {
 
 constexpr int kJacThreads = 1024;
-constexpr int kJacGroup = 16;  // threads per column pair
 
 __device__ __forceinline__ int pk(int a, int b) { return b * (b + 1) / 2 + a; }  // a <= b
 
-// Sum over the 16 lanes of a column-pair group (every lane of the warp takes
-// part).
-__device__ __forceinline__ double group_sum(double v) {
-  v += __shfl_xor_sync(0xffffffffu, v, 8);
-  v += __shfl_xor_sync(0xffffffffu, v, 4);
-  v += __shfl_xor_sync(0xffffffffu, v, 2);
-  v += __shfl_xor_sync(0xffffffffu, v, 1);
+// Sum over the gs lanes of a column-pair group (gs a power of two <= 16;
+// every lane of the warp takes part).
+__device__ __forceinline__ double group_sum(double v, int gs) {
+  for (int o = gs >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
@@ -123,73 +119,73 @@ k_jacobi_svd(int l, const double* __restrict__ G, double* __restrict__ K, double
   __syncthreads();
 
   // ---- one-sided Jacobi sweeps on the columns of W ------------------------
+  // gs lanes per column pair (about four rows each, at most 16); warps that
+  // hold no pair of the round skip its FP64 work -- GB300's FP64 pipe is
+  // shared by every thread of the SM
   const int lp = l + (l & 1);
-  const int grp = tid / kJacGroup, g = tid % kJacGroup;
+  int gs = 1;
+  while (gs < 16 && gs * 4 < l) gs <<= 1;
+  const int grp = tid / gs, g = tid % gs;
+  const int warp_first_pair = (warp * 32) / gs;
+  const bool warp_busy = warp_first_pair < lp / 2;
   int sweep = 0;
   bool converged = false;
   while (sweep < max_sweeps) {
-    // fresh squared norms at the start of every sweep
+    // exact squared norms at the start of every sweep (updated by each
+    // rotation in between)
     for (int c = warp; c < l; c += nw) {
-      double s = 0.0;
-      for (int i = lane; i < l; i += 32) s = fma(W[i + c * l], W[i + c * l], s);
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) nrm[c] = s;
+      double sq = 0.0;
+      for (int i = lane; i < l; i += 32) sq = fma(W[i + c * l], W[i + c * l], sq);
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      if (lane == 0) nrm[c] = sq;
     }
     if (tid == 0) s_rot = 0;
     __syncthreads();
     for (int r = 0; r < lp - 1; ++r) {
-      int i = -1, j = -1;
-      if (grp < lp / 2) {
-        round_pair(lp, r, grp, i, j);
-        if (j >= l) i = -1;  // the extra player of an odd l
-      }
-      double c = 0.0;
-      if (i >= 0)
-        for (int row = g; row < l; row += kJacGroup) c = fma(W[row + i * l], W[row + j * l], c);
-      c = group_sum(c);
-      // the rotation is decided and formed by the group's first lane (FP64
-      // square roots and divisions are long instruction sequences on GB300)
-      // and broadcast
-      double cs = 1.0, sn = 0.0;
-      int rot_i = 0;
-      if (i >= 0 && g == 0) {
-        const double a = nrm[i], b = nrm[j];
-        // |c| > tol sqrt(a b), compared squared (a, b > 0)
-        if (c != 0.0 && a > 0.0 && b > 0.0 && c * c > tol * tol * a * b) {
-          rot_i = 1;
-          // rotation that makes columns i and j orthogonal (Rutishauser's
-          // form: t = tan of the angle, the smaller root of t^2 + 2 zeta t - 1)
-          const double zeta = (b - a) / (2.0 * c);
-          const double az = fabs(zeta);
-          const double t = copysign(1.0, zeta) /
-                           (az > 1.0 ? az * (1.0 + sqrt(1.0 + 1.0 / (zeta * zeta)))
-                                     : az + sqrt(1.0 + zeta * zeta));
-          cs = 1.0 / sqrt(1.0 + t * t);
-          sn = cs * t;
+      if (warp_busy) {
+        int i = -1, j = -1;
+        if (grp < lp / 2) {
+          round_pair(lp, r, grp, i, j);
+          if (j >= l) i = -1;  // the extra player of an odd l
         }
-      }
-      const int src = lane & ~(kJacGroup - 1);
-      rot_i = __shfl_sync(0xffffffffu, rot_i, src);
-      cs = __shfl_sync(0xffffffffu, cs, src);
-      sn = __shfl_sync(0xffffffffu, sn, src);
-      const bool rot = rot_i != 0;
-      double ni = 0.0, nj = 0.0;
-      if (rot) {
-        for (int row = g; row < l; row += kJacGroup) {
-          const double wi = W[row + i * l], wj = W[row + j * l];
-          const double vi = cs * wi - sn * wj, vj = sn * wi + cs * wj;
-          W[row + i * l] = vi;
-          W[row + j * l] = vj;
-          ni = fma(vi, vi, ni);
-          nj = fma(vj, vj, nj);
+        double c = 0.0;
+        if (i >= 0)
+          for (int row = g; row < l; row += gs) c = fma(W[row + i * l], W[row + j * l], c);
+        c = group_sum(c, gs);
+        // the rotation is decided and formed by the group's first lane (FP64
+        // square roots and divisions are long instruction sequences on
+        // GB300) and broadcast
+        double cs = 1.0, sn = 0.0, t = 0.0;
+        int rot_i = 0;
+        if (i >= 0 && g == 0) {
+          const double a = nrm[i], b = nrm[j];
+          // |c| > tol sqrt(a b), compared squared (a, b > 0)
+          if (c != 0.0 && a > 0.0 && b > 0.0 && c * c > tol * tol * a * b) {
+            rot_i = 1;
+            // rotation that makes columns i and j orthogonal (Rutishauser's
+            // form: t = tan of the angle, the smaller root of t^2 + 2 zeta t - 1)
+            const double zeta = (b - a) / (2.0 * c);
+            const double az = fabs(zeta);
+            t = copysign(1.0, zeta) /
+                (az > 1.0 ? az * (1.0 + sqrt(1.0 + 1.0 / (zeta * zeta))) : az + sqrt(1.0 + zeta * zeta));
+            cs = 1.0 / sqrt(1.0 + t * t);
+            sn = cs * t;
+            // the rotated columns' squared norms: a - t c and b + t c
+            nrm[i] = a - t * c;
+            nrm[j] = b + t * c;
+            s_rot = 1;
+          }
         }
-      }
-      ni = group_sum(ni);
-      nj = group_sum(nj);
-      if (rot && g == 0) {
-        nrm[i] = ni;
-        nrm[j] = nj;
-        s_rot = 1;
+        const int src = lane & ~(gs - 1);
+        rot_i = __shfl_sync(0xffffffffu, rot_i, src);
+        cs = __shfl_sync(0xffffffffu, cs, src);
+        sn = __shfl_sync(0xffffffffu, sn, src);
+        if (rot_i)
+          for (int row = g; row < l; row += gs) {
+            const double wi = W[row + i * l], wj = W[row + j * l];
+            W[row + i * l] = cs * wi - sn * wj;
+            W[row + j * l] = sn * wi + cs * wj;
+          }
       }
       __syncthreads();
     }

@@ -92,7 +92,7 @@ __host__ __device__ inline size_t roll_smem_floats(int I, int H, int L, int O, i
   size_t f = 0;
   for (int l = 0; l < L; ++l) {
     const int K = (l == 0 ? I : H) + H;
-    f += (size_t)4 * U * (K + 1) + 4 * U + (size_t)U * B + (size_t)B * K + (size_t)4 * U * B;
+    f += (size_t)4 * U * (K + 1) + 4 * U + (size_t)U * B + (size_t)B * (K + 1) + (size_t)4 * U * B;
   }
   const int rows = (O + G - 1) / G;
   f += (size_t)rows * H + rows;
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(512, 1) k_rollout(RollArgs a) {
     Wl[l] = p; p += (size_t)4 * U * (K + 1);
     bl[l] = p; p += 4 * U;
     cl[l] = p; p += (size_t)U * B;
-    xl[l] = p; p += (size_t)B * K;
+    xl[l] = p; p += (size_t)B * (K + 1);  // rows padded: samples of one warp on distinct banks
     zl[l] = p; p += (size_t)4 * U * B;
     for (int e = tid; e < 4 * U * K; e += nt) {
       const int r = e / K, k = e % K;
@@ -157,12 +157,33 @@ __global__ void __launch_bounds__(512, 1) k_rollout(RollArgs a) {
         const float* xin = l == 0 ? a.ring + (size_t)((s + t) % T) * B * I
                                   : a.hbuf + ((size_t)(l - 1) * T + t) * B * H;
         const float* hprev = t > 0 ? a.hbuf + ((size_t)l * T + t - 1) * B * H : nullptr;
-        for (int e = tid; e < B * K; e += nt) {
-          const int b = e / K, k = e % K;
-          float v;
-          if (k < Il) v = __ldcg(xin + (size_t)b * Il + k);
-          else v = hprev ? __ldcg(hprev + (size_t)b * H + (k - Il)) : 0.f;
-          xl[l][e] = v;
+        // x (B x Il) and h_prev (B x H) are contiguous in global memory: four
+        // independent loads in flight per thread, then the padded stores
+        for (int e0 = 0; e0 < B * Il; e0 += 4 * nt) {
+          float v[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int e = e0 + j * nt + tid;
+            v[j] = e < B * Il ? __ldcg(xin + e) : 0.f;
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int e = e0 + j * nt + tid;
+            if (e < B * Il) xl[l][(e / Il) * (K + 1) + e % Il] = v[j];
+          }
+        }
+        for (int e0 = 0; e0 < B * H; e0 += 4 * nt) {
+          float v[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int e = e0 + j * nt + tid;
+            v[j] = (e < B * H && hprev) ? __ldcg(hprev + e) : 0.f;
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int e = e0 + j * nt + tid;
+            if (e < B * H) xl[l][(e / H) * (K + 1) + Il + e % H] = v[j];
+          }
         }
         if (t == 0)
           for (int e = tid; e < U * B; e += nt) cl[l][e] = 0.f;
@@ -181,8 +202,15 @@ __global__ void __launch_bounds__(512, 1) k_rollout(RollArgs a) {
           if (dot < ndot) {
             const int r = dot / B, b = dot % B;
             const float* w = Wl[l] + (size_t)r * (K + 1);
-            const float* x = xl[l] + (size_t)b * K;
-            for (int k = part; k < K; k += 4) acc = fmaf(w[k], x[k], acc);
+            const float* x = xl[l] + (size_t)b * (K + 1);
+            float acc2 = 0.f;
+            int k = part;
+            for (; k + 4 < K; k += 8) {
+              acc = fmaf(w[k], x[k], acc);
+              acc2 = fmaf(w[k + 4], x[k + 4], acc2);
+            }
+            if (k < K) acc = fmaf(w[k], x[k], acc);
+            acc += acc2;
           }
           acc += __shfl_xor_sync(0xffffffffu, acc, 1);
           acc += __shfl_xor_sync(0xffffffffu, acc, 2);

@@ -1265,7 +1265,7 @@ int tc_wpass_splits(int64_t n, int64_t m, int dt) {
 }
 
 int tc_wpass(cudaStream_t st, int dt, const void* A, int64_t lda, int64_t n, int l, const void* S,
-             int64_t lds, int64_t m, float* part, int nsplit, unsigned* status) {
+             int64_t lds, int64_t m, float* part, int nsplit, unsigned* status, int stages) {
   CUtensorMap ta, ts;
   const int bke = esize(dt) == 2 ? 64 : 32;
   if (int rc = make_map(&ta, A, dt, n, l, lda, bke, 128)) return rc;
@@ -1274,7 +1274,7 @@ int tc_wpass(cudaStream_t st, int dt, const void* A, int64_t lda, int64_t n, int
   const int kchunk = (int)((ktiles + nsplit - 1) / nsplit);
   dim3 grid((unsigned)((m + kBN - 1) / kBN), (unsigned)nsplit);
   prepare_kernels_tc();
-  const bool small = (size_t)n * (size_t)m * (size_t)esize(dt) < kSmallPassBytes;
+  const bool small = stages == 2 || (stages != 4 && (size_t)n * (size_t)m * (size_t)esize(dt) < kSmallPassBytes);
   using L = tc::Smem<kBN, kStages>;
   using Ls = tc::Smem<kBN, kStagesSmall>;
   const unsigned nt = dt == RPOD_F32 ? 192 : 128;
@@ -1342,7 +1342,7 @@ void ypass_chunks(int64_t m, int want, size_t slice_elems, size_t part_elems, in
 
 int tc_ypass(cudaStream_t st, int dt, const void* A, int64_t lda, const void* S, int64_t lds,
              int64_t n, int64_t m, int l, float* Y, int64_t ldy, unsigned* status, float* part,
-             size_t part_elems) {
+             size_t part_elems, int stages) {
   if (dt != RPOD_BF16 && dt != RPOD_F16) return RPOD_ERR_UNSUPPORTED;
   CUtensorMap ta, ts;
   if (int rc = make_map(&ta, A, dt, m, l, lda, 64, 128)) return rc;
@@ -1356,7 +1356,7 @@ int tc_ypass(cudaStream_t st, int dt, const void* A, int64_t lda, const void* S,
   const int64_t ysplit = ns > 1 ? n * l : 0;
   dim3 grid((unsigned)tiles, (unsigned)ns);
   prepare_kernels_tc();
-  const bool small = bytes < kSmallPassBytes;
+  const bool small = stages == 2 || (stages != 4 && bytes < kSmallPassBytes);
   using L = tc::Smem<kBN, kStages>;
   using Ls = tc::Smem<kBN, kStagesSmall>;
   if (small) {

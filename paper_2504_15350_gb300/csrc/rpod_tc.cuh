@@ -12,8 +12,10 @@ int tc_wpass_splits(int64_t n, int64_t m, int dt);
 // (ld lds), both of type dt (RPOD_BF16, RPOD_F16, or RPOD_F32 read as TF32).
 // Base pointers 16-byte aligned and ld * sizeof multiple of 16, else
 // RPOD_ERR_UNSUPPORTED.
+// `stages`: 0 picks the pipeline depth from the pass size (two 96 KB stages
+// below 1 GiB, so that two CTAs share an SM, else four), 2 or 4 force it.
 int tc_wpass(cudaStream_t st, int dt, const void* A, int64_t lda, int64_t n, int l, const void* S,
-             int64_t lds, int64_t m, float* part, int nsplit, unsigned* status);
+             int64_t lds, int64_t m, float* part, int nsplit, unsigned* status, int stages = 0);
 
 // Y-pass: Y(i, c) = sum_j S(i, j) A(j, c) for i < n, c < l; A: m x 128
 // column-major (ld lda, columns >= l zero), S: n x m, both 16-bit of type dt;
@@ -22,7 +24,7 @@ int tc_wpass(cudaStream_t st, int dt, const void* A, int64_t lda, int64_t n, int
 // into chunks summed there and then reduced into Y.
 int tc_ypass(cudaStream_t st, int dt, const void* A, int64_t lda, const void* S, int64_t lds,
              int64_t n, int64_t m, int l, float* Y, int64_t ldy, unsigned* status,
-             float* part = nullptr, size_t part_elems = 0);
+             float* part = nullptr, size_t part_elems = 0, int stages = 0);
 
 // First Y-pass over an FP32 S (n x m, ld lds): Y as tc_ypass with S rounded
 // to the 16-bit type dt, and that rounded S written to Sh (n x m, ld ldh, a

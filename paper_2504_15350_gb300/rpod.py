@@ -51,7 +51,8 @@ SIGNATURES = {
                                          _c_u32, _c_i32]),
     "rpod_batch_workspace_bytes": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_size_t)]),
     "rpod_batch_run": (ctypes.c_int, [_p, _p, ctypes.c_size_t, _p]),
-    "rpod_batch_tune": (ctypes.c_int, [_p, _p, ctypes.c_size_t, _p, _c_i32, _pi32, _pi32]),
+    "rpod_batch_tune": (ctypes.c_int, [_p, _p, ctypes.c_size_t, _p, _c_i32, _pi32, _pi32, _pi32]),
+    "rpod_batch_set_pass_stages": (ctypes.c_int, [_p, _c_i32]),
     "rpod_batch_configure": (ctypes.c_int, [_p, _c_i32, _c_i32]),
     "rpod_batch_status_sync": (ctypes.c_int, [_p, _p, _p, _pi32, ctypes.POINTER(_c_u32)]),
     "rpod_batch_last_launch_count": (ctypes.c_int, [_p]),
@@ -281,10 +282,15 @@ def rpod_batch_run(batch, ws, ws_bytes, stream):
 
 
 def rpod_batch_tune(batch, ws, ws_bytes, stream, trials):
-    s, p = _c_i32(), _c_i32()
-    _check(load().rpod_batch_tune(batch, ws, ws_bytes, stream, trials, ctypes.byref(s), ctypes.byref(p)),
-           "rpod_batch_tune")
-    return s.value, p.value
+    """(streams, split_pct, stages) of the fastest configuration."""
+    s, p, g = _c_i32(), _c_i32(), _c_i32()
+    _check(load().rpod_batch_tune(batch, ws, ws_bytes, stream, trials, ctypes.byref(s), ctypes.byref(p),
+                                  ctypes.byref(g)), "rpod_batch_tune")
+    return s.value, p.value, g.value
+
+
+def rpod_batch_set_pass_stages(batch, stages):
+    return load().rpod_batch_set_pass_stages(batch, stages)
 
 
 def rpod_batch_configure(batch, streams, split_pct):
@@ -521,6 +527,9 @@ class Batch:
                                   colmajor_ld(R) if R is not None else 0, U.data_ptr(),
                                   colmajor_ld(U), sg.data_ptr(), C.data_ptr(), colmajor_ld(C)))
         self.s_dtype = dtype_code(self.S[0].dtype)
+        self.flags = flags
+        self.shapes = [[int(S.shape[0]), int(S.shape[1]), int(ks[b]), int(p), int(q)]
+                       for b, S in enumerate(self.S)]
         self.handle = rpod_batch_create(insts, self.compute, flags, self.s_dtype)
         self.ws_bytes = rpod_batch_workspace_bytes(self.handle)
         self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
@@ -542,11 +551,52 @@ class Batch:
         _check(rpod_batch_run(self.handle, self.ws_ptr, self.ws_bytes, self._stream()),
                "rpod_batch_run")
 
-    def tune(self, trials=2):
-        return rpod_batch_tune(self.handle, self.ws_ptr, self.ws_bytes, self._stream(), trials)
+    def tune(self, trials=3, cache=None):
+        """Autotunes the launch configuration (rpod_batch_tune) and returns
+        (streams, split_pct, stages).  With `cache` (a JSON file path) a
+        configuration tuned before for the same instance shapes, form, GPU
+        and library build is applied without timing, and a new one is
+        stored."""
+        key = self._tune_key() if cache else None
+        if cache:
+            import json
+            try:
+                with open(cache) as f:
+                    hit = json.load(f).get(key)
+            except (OSError, ValueError):
+                hit = None
+            if hit:
+                self.configure(hit[0], hit[1], hit[2])
+                return tuple(hit)
+        best = rpod_batch_tune(self.handle, self.ws_ptr, self.ws_bytes, self._stream(), trials)
+        if cache:
+            import json
+            try:
+                with open(cache) as f:
+                    db = json.load(f)
+            except (OSError, ValueError):
+                db = {}
+            db[key] = list(best)
+            tmp = f"{cache}.tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(db, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return best
 
-    def configure(self, streams, split_pct):
+    def _tune_key(self):
+        import hashlib
+        import json
+        torch = _torch()
+        with open(LIB_PATH, "rb") as f:
+            lib = hashlib.sha256(f.read()).hexdigest()[:16]
+        desc = {"compute": self.compute, "flags": self.flags, "s_dtype": self.s_dtype,
+                "shapes": self.shapes, "gpu": torch.cuda.get_device_name(self.device), "lib": lib}
+        return hashlib.sha256(json.dumps(desc, sort_keys=True).encode()).hexdigest()[:24]
+
+    def configure(self, streams, split_pct, stages=None):
         _check(rpod_batch_configure(self.handle, streams, split_pct), "rpod_batch_configure")
+        if stages is not None:
+            _check(rpod_batch_set_pass_stages(self.handle, stages), "rpod_batch_set_pass_stages")
 
     def status(self):
         return rpod_batch_status_sync(self.handle, self.ws_ptr, self._stream())

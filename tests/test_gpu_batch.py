@@ -67,9 +67,10 @@ def test_batch_replay_tracks_data_and_tuning_keeps_results():
     torch.cuda.synchronize()
     for a, b in zip(first, B.sigma):
         assert torch.allclose(b, 2.0 * a, rtol=1e-5, atol=0)
-    streams, split = B.tune(trials=1)
-    # the tuner's own candidate sets (worker streams up to the instance count)
-    assert streams in (1, 2, 4) and split in (25, 50, 100, 200)
+    streams, split, stages = B.tune(trials=1)
+    # the tuner's own candidate sets (worker streams up to the instance count;
+    # the FP32 form has no tensor-core passes, so the stage count stays 0)
+    assert streams in (1, 2, 4) and split in (25, 50, 100, 200) and stages == 0
     B.run()
     assert B.status()[0] == R.RPOD_OK
     torch.cuda.synchronize()
@@ -153,3 +154,31 @@ def test_batch_64_instances_full_size():
         Ub = B.U[b].double().cpu().numpy()
         keep = sg[:k] > 1e-4 * sg[0]           # directions FP32 resolves
         assert orth_err(Ub[:, keep]) <= 5e-5
+
+
+def test_tuning_cache_and_pass_stages(tmp_path):
+    """The BF16 form's tuner searches the passes' pipeline depth too; a
+    second batch of the same shapes takes the configuration from the JSON
+    cache without timing, and every configuration gives the same results
+    up to FP32 summation order."""
+    import time
+    recs, ks, S_cpu, S = small_batch(count=4, seed=6)
+    p, q = 10, 1
+    cache = str(tmp_path / "tune.json")
+    B1 = R.Batch(S, ks, p, q, list(range(4)), compute="bf16", flags=R.RPOD_FLAG_REFINE_FP32)
+    best = B1.tune(trials=3, cache=cache)
+    assert best[2] in (2, 4)
+    B1.run()
+    assert B1.status()[0] == R.RPOD_OK
+    B2 = R.Batch(S, ks, p, q, list(range(4)), compute="bf16", flags=R.RPOD_FLAG_REFINE_FP32)
+    t0 = time.perf_counter()
+    assert tuple(B2.tune(trials=3, cache=cache)) == tuple(best)
+    assert time.perf_counter() - t0 < 0.5          # a cache hit times nothing
+    for stages in (2, 4):
+        B2.configure(best[0], best[1], stages)
+        B2.run()
+        assert B2.status()[0] == R.RPOD_OK
+        torch.cuda.synchronize()
+        for a, b in zip(B1.sigma, B2.sigma):
+            assert torch.allclose(a, b, rtol=1e-5, atol=1e-6 * a[0].item())
+    assert R.rpod_batch_set_pass_stages(B2.handle, 3) == R.RPOD_ERR_INVALID_ARG
