@@ -357,12 +357,11 @@ def time_basis(dev, S, k, p, q, compute, flags, warmup, steps, seed=0):
     odt = torch.float64 if compute == "f64" else torch.float32
     out = (R.empty_colmajor(n, k, odt, dev), torch.empty(l, dtype=torch.float64, device=dev),
            R.empty_colmajor(k, m, odt, dev))
-    for _ in range(warmup):
+    for _ in range(max(warmup, 3)):
         plan.basis(S, out=out)
     rc, _ = plan.status()
     if rc != R.RPOD_OK:
         raise RuntimeError(f"{compute}: device status {R.rpod_strerror(rc)}")
-    plan.profile(True)
     stream = torch.cuda.current_stream(dev)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -370,6 +369,11 @@ def time_basis(dev, S, k, p, q, compute, flags, warmup, steps, seed=0):
     for _ in range(steps):
         plan.basis(S, out=out)
     e1.record(stream)
+    torch.cuda.synchronize()
+    # pass times from a profiled repeat (direct launches, events per pass)
+    plan.profile(True)
+    for _ in range(steps):
+        plan.basis(S, out=out)
     torch.cuda.synchronize()
     passes, pass_ms, pbytes, _ = plan.profile_read()
     plan.profile(False)
@@ -584,7 +588,6 @@ def main():
         if rc != R.RPOD_OK:
             raise RuntimeError(f"{form}: device status {R.rpod_strerror(rc)}")
         steps = args.steps if form == head else max(3, min(args.steps, 5))
-        plan.profile(True)
         stream = torch.cuda.current_stream(dev)
         barrier()
         torch.cuda.synchronize()
@@ -602,9 +605,16 @@ def main():
         barrier()
         ms = e0.elapsed_time(e1) / steps
         clocks = clk.stop() if clk else None
+        launches = plan.launches()
+        # the same steps again with CUDA events around every pass (a profiled
+        # plan launches its kernels directly; the timed steps above replay the
+        # plan's CUDA graph)
+        plan.profile(True)
+        for _ in range(steps):
+            plan.basis(S, out=out)
+        torch.cuda.synchronize()
         passes, pass_ms, pbytes, pflops = plan.profile_read()
         plan.profile(False)
-        launches = plan.launches()
         rc, _ = plan.status()
         if rc != R.RPOD_OK:
             raise RuntimeError(f"{form}: device status {R.rpod_strerror(rc)}")
@@ -715,7 +725,8 @@ def main():
         def e2e_step():
             plan.basis(S_host.t(), out=(U_h.t(), s_h, C_h.t()))
 
-        e2e_step()
+        for _ in range(2):  # the second call records the plan's graph
+            e2e_step()
         torch.cuda.synchronize()
         barrier()
         a0 = torch.cuda.Event(enable_timing=True)
@@ -779,6 +790,9 @@ def main():
         "cpu_baseline": cpu if cpu else ({"value": None, "error": cpu_err} if cpu_err else None),
         "e2e": e2e,
         "gpu_launches": hr["launches"] * hr["steps"],
+        "launch_mode": ("each timed call replays the plan's CUDA graph of its kernels "
+                        "(rpod_plan_set_graph); pass times from a profiled repeat of the "
+                        "same steps with CUDA events around every pass"),
         "clocks": hr["clocks"],
         "throughput_rpod_per_s": world / (hr["ms"] / 1e3),
         "batched": batched,

@@ -116,6 +116,23 @@ int rpod_plan_create(rpod_plan** out, int64_t n, int64_t m, int32_t k, int32_t p
  * is not RPOD_F64 (those forms take no Jacobi sweeps). */
 int rpod_plan_set_svd_sweeps(rpod_plan* plan, int32_t max_sweeps);
 
+/* Graph replay of repeated rpod_basis calls (on by default).  The second
+ * consecutive call with the same S, S_refine, U, sigma, C and workspace
+ * pointers, leading dimensions, s_dtype and workspace size records the
+ * call's kernel sequence into one CUDA graph (captured on a stream the plan
+ * creates), and later calls with those arguments launch that graph on their
+ * stream instead of launching each kernel: the same kernels, arguments and
+ * results, without the host work and the gaps between kernels.  A call with
+ * other arguments launches directly and starts the count again.  Direct
+ * launches are also used while pass profiling is enabled, for row-sharded
+ * plans, and when the caller's stream is itself being captured.  The graph
+ * reads the buffers at their addresses when it runs, so new contents of S
+ * are seen; freeing and reallocating a buffer at the same address is safe.
+ * enable = 0 drops the graph and launches directly from then on.  If a
+ * capture fails the plan falls back to direct launches for good.
+ * Errors: RPOD_ERR_INVALID_ARG for a NULL plan or enable not 0 or 1. */
+int rpod_plan_set_graph(rpod_plan* plan, int32_t enable);
+
 /* Bytes of device workspace the plan needs (for any of its calls). */
 int rpod_workspace_bytes(const rpod_plan* plan, size_t* bytes);
 

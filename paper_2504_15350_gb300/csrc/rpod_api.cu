@@ -58,6 +58,15 @@ struct rpod_plan {
   // round runs beside the refinement pass); null when they could not be made
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_join;
+  // graph replay of repeated basis calls: the second call with the same
+  // buffers captures the launch sequence (on gcap) into gexec, later calls
+  // with those buffers launch the graph on the caller's stream
+  int graph_on;
+  int graph_calls;  // consecutive calls seen with gkey
+  uintptr_t gkey[12];
+  cudaStream_t gcap;
+  cudaGraphExec_t gexec;
+  int graph_launches;  // kernels in the captured graph
 };
 
 namespace rpod {
@@ -701,6 +710,7 @@ static int plan_create_impl(rpod_plan** out, int64_t n, int64_t m, int32_t k, in
   P->last_launches = 0;
   P->svd_sweeps = 30;
   P->pass_stages = 0;
+  P->graph_on = 1;
   *out = P;
   return RPOD_OK;
 }
@@ -729,10 +739,24 @@ int rpod_rows_plan_create(rpod_plan** out, int64_t n_total, int64_t row0, int64_
   return RPOD_OK;
 }
 
+static void drop_plan_graph(rpod_plan* P) {
+  if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  P->gexec = nullptr;
+  P->graph_calls = 0;
+}
+
 int rpod_plan_set_svd_sweeps(rpod_plan* P, int32_t max_sweeps) {
   if (!P || max_sweeps < 1 || max_sweeps > 1000) return RPOD_ERR_INVALID_ARG;
   if (P->compute != RPOD_F64) return RPOD_ERR_UNSUPPORTED;
   P->svd_sweeps = max_sweeps;
+  drop_plan_graph(P);
+  return RPOD_OK;
+}
+
+int rpod_plan_set_graph(rpod_plan* P, int32_t enable) {
+  if (!P || (enable != 0 && enable != 1)) return RPOD_ERR_INVALID_ARG;
+  P->graph_on = enable;
+  drop_plan_graph(P);
   return RPOD_OK;
 }
 
@@ -746,6 +770,8 @@ int rpod_profile_enable(rpod_plan* P, int enable);
 
 void rpod_plan_destroy(rpod_plan* P) {
   if (P && P->prof_on) rpod_profile_enable(P, 0);
+  if (P) drop_plan_graph(P);
+  if (P && P->gcap) cudaStreamDestroy(P->gcap);
   if (P && P->side) {
     cudaEventDestroy(P->ev_fork);
     cudaEventDestroy(P->ev_join);
@@ -816,7 +842,83 @@ int rpod_basis(rpod_plan* P, const void* S, int64_t lds, int32_t s_dtype, const 
   return RPOD_OK;
 }
 
+static int basis_direct(rpod_plan* P, const void* S, int64_t lds, int32_t s_dtype,
+                        const float* S_refine, int64_t ldr, void* U, int64_t ldu, double* sigma,
+                        void* C, int64_t ldc, void* workspace, size_t workspace_bytes,
+                        void* stream);
+
+// A repeated basis call with unchanged buffers replays one CUDA graph of its
+// launches (no host work per kernel, no launch gaps).  Direct launches for:
+// the first call with a set of buffers, row-sharded plans (their exchange
+// callback runs on the host between kernels), profiled plans (their events
+// time each pass), and a caller's stream that is itself being captured.
 static int basis_device(rpod_plan* P, const void* S, int64_t lds, int32_t s_dtype,
+                        const float* S_refine, int64_t ldr, void* U, int64_t ldu, double* sigma,
+                        void* C, int64_t ldc, void* workspace, size_t workspace_bytes,
+                        void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (!P->graph_on || P->rows_mode || P->prof_on || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return basis_direct(P, S, lds, s_dtype, S_refine, ldr, U, ldu, sigma, C, ldc, workspace,
+                        workspace_bytes, stream);
+  }
+  const uintptr_t key[12] = {(uintptr_t)S, (uintptr_t)lds, (uintptr_t)s_dtype, (uintptr_t)S_refine,
+                             (uintptr_t)ldr, (uintptr_t)U, (uintptr_t)ldu, (uintptr_t)sigma,
+                             (uintptr_t)C, (uintptr_t)ldc, (uintptr_t)workspace,
+                             (uintptr_t)workspace_bytes};
+  const bool same = P->graph_calls > 0 && std::equal(key, key + 12, P->gkey);
+  if (same && P->gexec) {
+    if (cudaGraphLaunch(P->gexec, st) != cudaSuccess) return RPOD_ERR_CUDA;
+    P->last_launches = P->graph_launches;
+    return RPOD_OK;
+  }
+  if (!same) {
+    drop_plan_graph(P);
+    std::copy(key, key + 12, P->gkey);
+    P->graph_calls = 1;
+    return basis_direct(P, S, lds, s_dtype, S_refine, ldr, U, ldu, sigma, C, ldc, workspace,
+                        workspace_bytes, stream);
+  }
+  // second call with these buffers: capture on the plan's own stream (the
+  // caller's may be the legacy default stream, which cannot capture)
+  if (!P->gcap && cudaStreamCreateWithFlags(&P->gcap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    P->gcap = nullptr;
+    P->graph_on = 0;
+    return basis_direct(P, S, lds, s_dtype, S_refine, ldr, U, ldu, sigma, C, ldc, workspace,
+                        workspace_bytes, stream);
+  }
+  int rc = RPOD_ERR_CUDA;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(P->gcap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    rc = basis_direct(P, S, lds, s_dtype, S_refine, ldr, U, ldu, sigma, C, ldc, workspace,
+                      workspace_bytes, P->gcap);
+    const cudaError_t ec = cudaStreamEndCapture(P->gcap, &g);
+    if (rc == RPOD_OK && ec != cudaSuccess) rc = RPOD_ERR_CUDA;
+  }
+  cudaGraphExec_t ex = nullptr;
+  if (rc == RPOD_OK && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+    ex = nullptr;
+    rc = RPOD_ERR_CUDA;
+  }
+  if (g) cudaGraphDestroy(g);
+  if (rc == RPOD_OK) {
+    P->gexec = ex;
+    P->graph_launches = P->last_launches;
+    if (cudaGraphLaunch(P->gexec, st) != cudaSuccess) return RPOD_ERR_CUDA;
+    return RPOD_OK;
+  }
+  cudaGetLastError();  // leave no capture error behind
+  if (rc != RPOD_ERR_CUDA) return rc;  // an argument error: the same as a direct call
+  // the launch sequence could not be captured: direct launches from now on
+  P->graph_on = 0;
+  return basis_direct(P, S, lds, s_dtype, S_refine, ldr, U, ldu, sigma, C, ldc, workspace,
+                      workspace_bytes, stream);
+}
+
+static int basis_direct(rpod_plan* P, const void* S, int64_t lds, int32_t s_dtype,
                         const float* S_refine, int64_t ldr, void* U, int64_t ldu, double* sigma,
                         void* C, int64_t ldc, void* workspace, size_t workspace_bytes,
                         void* stream) {

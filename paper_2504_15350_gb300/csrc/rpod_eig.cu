@@ -10,8 +10,10 @@
 //      keeps its small eigenvalues' relative accuracy).
 //   2. Eigenvalues of the tridiagonal T by multisection on Sturm counts
 //      (the number of negative pivots of the LDL^T factorization of T - x I
-//      is the number of eigenvalues below x), 8 points per step and per
-//      eigenvalue, stopped at a relative width of two ulps.  The counts use
+//      is the number of eigenvalues below x): one pass of 1024 counts at
+//      geometrically spaced points brackets every eigenvalue to a few
+//      percent, then 4 points per step and per eigenvalue narrow each
+//      bracket to a relative width of two ulps.  The counts use
 //      IEEE infinities in place of a pivot threshold (a zero pivot gives an
 //      infinite next pivot, counted by its sign bit), with e_k^2 kept at or
 //      above the smallest normal number so that no 0/0 arises.
@@ -77,6 +79,28 @@ __device__ __forceinline__ float dot4(const float4& a, const float4& b) {
   return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
 }
 
+// Number of eigenvalues of the tridiagonal T below x: the negative pivots
+// of the LDL^T factorization of T - x I (de[k] = (d_k, e_{k-1}^2)).
+__device__ __forceinline__ unsigned sturm_count(const float2* de, int l, float x) {
+  float q = de[0].x - x;
+  unsigned c = __float_as_uint(q) >> 31;
+#pragma unroll 4
+  for (int k = 1; k < l; ++k) {
+    const float2 p = de[k];
+    q = fmaf(-p.y, __fdividef(1.f, q), p.x - x);
+    c += __float_as_uint(q) >> 31;
+  }
+  return c;
+}
+
+constexpr int kBrk = 1024;  // bracketing points (one per thread)
+constexpr int kMs = 4;      // threads (points) per eigenvalue in the multisection
+static_assert(kBrk == kEigThreads, "one bracketing point per thread");
+
+__device__ __forceinline__ float brk_point(float bn, int i) {
+  return bn * exp2f(40.f * ((float)i * (1.f / (kBrk - 1)) - 1.f));
+}
+
 __device__ __forceinline__ uint32_t mix32(uint32_t x) {
   x ^= x >> 16; x *= 0x7feb352du; x ^= x >> 15; x *= 0x846ca68bu; x ^= x >> 16;
   return x;
@@ -140,6 +164,7 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
   float* const Ws = Xs + (size_t)l * ldx;          // forward pivots per eigenvalue
   __shared__ double s_red[32];
   __shared__ float s_bnd[3];
+  __shared__ unsigned s_cnt[kBrk];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
   const float pivmin = 1e-30f;
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -190,17 +215,24 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
   __syncthreads();
 
   // ---- 2. Householder tridiagonalization.  Warp w owns rows 4w..4w+3 of
-  // the trailing matrix; lane q holds columns 4q..4q+3 of a row.  Step j:
+  // the trailing matrix and keeps them in registers for the whole
+  // reduction (lane q holds columns 4q..4q+3 of a row).  Step j:
   // p = tau A22 v on the owned rows, then A22 -= v w^T + w v^T with
   // w = p - (tau/2)(p.v) v; the owner of row j+1 forms the next reflector
-  // from the updated row while it is still in registers.  Columns up to j
-  // of v and p are zero, so whole rows are processed.
+  // from the updated row while it is still in registers and stores it (the
+  // full vector, zeros included) as row j+1 of A for the back-transformation.
+  // Columns up to j of v and p are zero, so whole rows are processed; the
+  // register copies of rows already reduced are no longer read.
   const int c0 = 4 * lane;
   const bool lact = c0 < lda;
-  if (l >= 2 && warp == 0) {
-    const float4 x = lact ? *reinterpret_cast<const float4*>(A + c0) : z4;
-    reflector(0, lda, x, lane, A, vs, psb, tau, dd, ee);
+  const int rb = 4 * warp;
+  float4 rw[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int r = rb + u;
+    rw[u] = (r < l && lact) ? *reinterpret_cast<const float4*>(A + r * lda + c0) : z4;
   }
+  if (l >= 2 && warp == 0) reflector(0, lda, rw[0], lane, A, vs, psb, tau, dd, ee);
   for (int j = 0; j + 1 < l; ++j) {
     __syncthreads();
     const float t = tau[j];
@@ -208,7 +240,8 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
     const bool mk_next = nxt + 1 < l && warp == (nxt >> 2);
     if (t == 0.f) {
       if (mk_next) {
-        const float4 x = lact ? *reinterpret_cast<const float4*>(A + nxt * lda + c0) : z4;
+        const int u = nxt & 3;
+        const float4 x = u == 0 ? rw[0] : (u == 1 ? rw[1] : (u == 2 ? rw[2] : rw[3]));
         reflector(nxt, lda, x, lane, A + nxt * lda, vs + (nxt & 1) * kMaxL,
                   psb + (nxt & 1) * kMaxL, tau, dd, ee);
       }
@@ -216,18 +249,13 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
     }
     const float* const v = vs + (j & 1) * kMaxL;
     float* const ps = psb + (j & 1) * kMaxL;
-    const int rb = 4 * warp;
     const bool owns = rb + 3 >= j + 1 && rb < l;
-    float4 v4 = z4, rw[4];
+    float4 v4 = z4;
     if (owns) {
       v4 = lact ? *reinterpret_cast<const float4*>(v + c0) : z4;
       float s[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int r = rb + u;
-        rw[u] = (r >= j + 1 && r < l && lact) ? *reinterpret_cast<const float4*>(A + r * lda + c0) : z4;
-        s[u] = dot4(rw[u], v4);
-      }
+      for (int u = 0; u < 4; ++u) s[u] = dot4(rw[u], v4);
       // four row sums at once: lanes 8u..8u+7 end with the sum of row rb+u
       const bool hi16 = lane & 16, hi8 = lane & 8;
       float k0 = hi16 ? s[2] : s[0], k1 = hi16 ? s[3] : s[1];
@@ -258,15 +286,19 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
         a.y = fmaf(-wr, v4.y, fmaf(-vr, w4.y, a.y));
         a.z = fmaf(-wr, v4.z, fmaf(-vr, w4.z, a.z));
         a.w = fmaf(-wr, v4.w, fmaf(-vr, w4.w, a.w));
-        if (lact) *reinterpret_cast<float4*>(A + r * lda + c0) = a;
+        rw[u] = a;
         if (r == nxt && mk_next)
           reflector(nxt, lda, a, lane, A + nxt * lda, vs + (nxt & 1) * kMaxL,
                     psb + (nxt & 1) * kMaxL, tau, dd, ee);
       }
     }
   }
-  __syncthreads();
-  if (tid == 0) dd[l - 1] = A[(l - 1) * lda + l - 1];
+  // the last diagonal entry, from the registers of its row's owner
+  if (warp == ((l - 1) >> 2) && lane == ((l - 1) >> 2)) {
+    const int u = (l - 1) & 3;
+    const float4 x = u == 0 ? rw[0] : (u == 1 ? rw[1] : (u == 2 ? rw[2] : rw[3]));
+    dd[l - 1] = pick(x, (l - 1) & 3);
+  }
   __syncthreads();
 
   // ---- 3. eigenvalues of T (ascending) by multisection
@@ -290,33 +322,42 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
     if (lane == 0) { s_bnd[0] = lo - pad; s_bnd[1] = hi + pad; s_bnd[2] = bn; }
   }
   __syncthreads();
+  // bracketing pass: every thread counts the eigenvalues below one of
+  // kBrk points spaced geometrically over 2^-40 bn .. bn (the eigenvalues of
+  // a power-iterated Gram spread over decades; ratio 1.028 between points)
   {
-    const int g = tid / kGrp, t8 = tid % kGrp;
-    const unsigned gmask = 0xFFu << (lane & 24);
+    const float bn = s_bnd[2];
+    s_cnt[tid] = tid < kBrk ? sturm_count(de, l, brk_point(bn, tid)) : 0u;
+  }
+  __syncthreads();
+  {
+    const int g = tid / kMs, t4 = tid % kMs;
+    const unsigned gmask = 0xFu << (lane & 28);
     if (g < l) {
-      float lo = s_bnd[0], hi = s_bnd[1];
-      const float atol = 1e-14f * s_bnd[2];
-      for (int it = 0; it < 20; ++it) {
+      // first point whose count exceeds g (binary search: the points on
+      // either side of the result were both probed, so lambda_g lies
+      // between them even where rounding makes the counts non-monotone)
+      int bl = 0, bh = kBrk;
+      while (bl < bh) {
+        const int md = (bl + bh) >> 1;
+        if (s_cnt[md] > (unsigned)g) bh = md; else bl = md + 1;
+      }
+      const float bn = s_bnd[2];
+      float lo = bl == 0 ? s_bnd[0] : brk_point(bn, bl - 1);
+      float hi = bl == kBrk ? s_bnd[1] : brk_point(bn, bl);
+      const float atol = 1e-14f * bn;
+      for (int it = 0; it < 40; ++it) {
         if (hi - lo <= fmaf(2.4e-7f, fmaxf(fabsf(lo), fabsf(hi)), atol)) break;
-        const float h = (hi - lo) * (1.f / 9.f);
-        const float x = fmaf(h, (float)(t8 + 1), lo);
-        // number of negative pivots of T - x I = eigenvalues below x
-        float q = de[0].x - x;
-        unsigned c = __float_as_uint(q) >> 31;
-#pragma unroll 4
-        for (int k = 1; k < l; ++k) {
-          const float2 p = de[k];
-          q = fmaf(-p.y, __fdividef(1.f, q), p.x - x);
-          c += __float_as_uint(q) >> 31;
-        }
-        const unsigned bits = (__ballot_sync(gmask, c > (unsigned)g) >> (lane & 24)) & 0xFFu;
-        const int tt = bits ? __ffs(bits) - 1 : kGrp;
+        const float h = (hi - lo) * (1.f / (kMs + 1));
+        const unsigned c = sturm_count(de, l, fmaf(h, (float)(t4 + 1), lo));
+        const unsigned bits = (__ballot_sync(gmask, c > (unsigned)g) >> (lane & 28)) & 0xFu;
+        const int tt = bits ? __ffs(bits) - 1 : kMs;
         const float nlo = tt == 0 ? lo : fmaf(h, (float)tt, lo);
-        const float nhi = tt == kGrp ? hi : fmaf(h, (float)(tt + 1), lo);
+        const float nhi = tt == kMs ? hi : fmaf(h, (float)(tt + 1), lo);
         lo = nlo;
         hi = nhi;
       }
-      if (t8 == 0) lam[g] = 0.5f * (lo + hi);
+      if (t4 == 0) lam[g] = 0.5f * (lo + hi);
     }
   }
   __syncthreads();
@@ -334,6 +375,7 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
         float q = dd[0] - lm;
         if (fabsf(q) < pivmin) q = -pivmin;
         Dp[0] = q;
+        #pragma unroll 4
         for (int k = 1; k < l; ++k) {
           q = (dd[k] - lm) - __fdividef(de[k].y, q);
           if (fabsf(q) < pivmin) q = -pivmin;
@@ -343,6 +385,7 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
         float q = dd[l - 1] - lm;
         if (fabsf(q) < pivmin) q = -pivmin;
         Xc[(l - 1) * ldx] = q;
+        #pragma unroll 4
         for (int k = l - 2; k >= 0; --k) {
           q = (dd[k] - lm) - __fdividef(de[k + 1].y, q);
           if (fabsf(q) < pivmin) q = -pivmin;
@@ -355,6 +398,7 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
       const int h = l >> 1;
       float gb = FLT_MAX;
       int r = l;
+      #pragma unroll 4
       for (int k = fwd ? 0 : h; k < (fwd ? h : l); ++k) {
         const float gk = k + 1 < l ? Dp[k * ldx] - __fdividef(de[k + 1].y, Xc[(k + 1) * ldx])
                                    : Dp[k * ldx];
@@ -370,12 +414,14 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
       if (fwd) {
         Xc[r * ldx] = 1.f;
         n2 = 1.f;
+        #pragma unroll 4
         for (int k = r - 1; k >= 0; --k) {
           xv = -__fdividef(ee[k], Dp[k * ldx]) * xv;
           Xc[k * ldx] = xv;
           n2 = fmaf(xv, xv, n2);
         }
       } else {
+        #pragma unroll 4
         for (int k = r; k + 1 < l; ++k) {
           xv = -__fdividef(ee[k], Xc[(k + 1) * ldx]) * xv;
           Xc[(k + 1) * ldx] = xv;
@@ -389,8 +435,10 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
       } else {
         const float s = rsqrtf(n2);
         if (fwd) {
+          #pragma unroll 4
           for (int k = 0; k <= r; ++k) Xc[k * ldx] *= s;
         } else {
+          #pragma unroll 4
           for (int k = r + 1; k < l; ++k) Xc[k * ldx] *= s;
         }
       }
@@ -564,53 +612,73 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
     if (tid == 0) status[4] = (unsigned)nrep;
   }
 
-  // ---- 6. back-transformation X = H_0 ... H_{l-2} Z: 8 threads per column,
-  // thread t8 holding rows 32u + 4 t8 + i (u, i < 4) in registers; row j of
-  // A is the full vector v_j
+  // ---- 6. back-transformation X = H_0 ... H_{l-2} Z: 16 threads per pair
+  // of columns, thread t16 holding rows 64u + 4 t16 + i (u < 2, i < 4) of
+  // both in registers, so that each reflector row read from shared memory
+  // serves two columns; row j of A is the full vector v_j.  The two dot
+  // products are summed over the 16 threads with one transposed exchange
+  // (lanes with bit 3 set carry column 1 on, the others column 0) and two
+  // broadcasts.
   {
-    const int c = tid / kGrp, t8 = tid % kGrp;
-    const unsigned gmask = 0xFFu << (lane & 24);
+    const int cp = tid >> 4, t16 = tid & 15;
+    const int c = 2 * cp;
+    const unsigned gmask = 0xFFFFu << (lane & 16);
     if (c < l) {
-      float xr[16];
+      const bool two = c + 1 < l;
+      float xa[8], xb[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < 2; ++u)
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const int r = 32 * u + 4 * t8 + i;
-          xr[4 * u + i] = r < l ? Xs[r * ldx + c] : 0.f;
+          const int r = 64 * u + 4 * t16 + i;
+          xa[4 * u + i] = r < l ? Xs[r * ldx + c] : 0.f;
+          xb[4 * u + i] = (r < l && two) ? Xs[r * ldx + c + 1] : 0.f;
         }
+      const bool hi8 = lane & 8;
+      const int base = lane & 16;
       for (int j = l - 2; j >= 0; --j) {
         const float t = tau[j];
         if (t == 0.f) continue;
         const float* vj = A + j * lda;
-        float4 vv[4];
-        float s0 = 0.f, s1 = 0.f;
+        float4 vv[2];
+        float sa = 0.f, sb = 0.f;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int cc = 32 * u + 4 * t8;
+        for (int u = 0; u < 2; ++u) {
+          const int cc = 64 * u + 4 * t16;
           vv[u] = cc < lda ? *reinterpret_cast<const float4*>(vj + cc) : z4;
-          s0 = fmaf(vv[u].x, xr[4 * u + 0], fmaf(vv[u].y, xr[4 * u + 1], s0));
-          s1 = fmaf(vv[u].z, xr[4 * u + 2], fmaf(vv[u].w, xr[4 * u + 3], s1));
+          sa = fmaf(vv[u].x, xa[4 * u + 0], fmaf(vv[u].y, xa[4 * u + 1],
+                    fmaf(vv[u].z, xa[4 * u + 2], fmaf(vv[u].w, xa[4 * u + 3], sa))));
+          sb = fmaf(vv[u].x, xb[4 * u + 0], fmaf(vv[u].y, xb[4 * u + 1],
+                    fmaf(vv[u].z, xb[4 * u + 2], fmaf(vv[u].w, xb[4 * u + 3], sb))));
         }
-        float s = s0 + s1;
-        s += __shfl_xor_sync(gmask, s, 1);
-        s += __shfl_xor_sync(gmask, s, 2);
-        s += __shfl_xor_sync(gmask, s, 4);
-        const float f = -t * s;
+        float k = hi8 ? sb : sa;
+        k += __shfl_xor_sync(gmask, hi8 ? sa : sb, 8);
+        k += __shfl_xor_sync(gmask, k, 4);
+        k += __shfl_xor_sync(gmask, k, 2);
+        k += __shfl_xor_sync(gmask, k, 1);
+        const float fa = -t * __shfl_sync(gmask, k, base);
+        const float fb = -t * __shfl_sync(gmask, k, base + 8);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          xr[4 * u + 0] = fmaf(f, vv[u].x, xr[4 * u + 0]);
-          xr[4 * u + 1] = fmaf(f, vv[u].y, xr[4 * u + 1]);
-          xr[4 * u + 2] = fmaf(f, vv[u].z, xr[4 * u + 2]);
-          xr[4 * u + 3] = fmaf(f, vv[u].w, xr[4 * u + 3]);
+        for (int u = 0; u < 2; ++u) {
+          xa[4 * u + 0] = fmaf(fa, vv[u].x, xa[4 * u + 0]);
+          xa[4 * u + 1] = fmaf(fa, vv[u].y, xa[4 * u + 1]);
+          xa[4 * u + 2] = fmaf(fa, vv[u].z, xa[4 * u + 2]);
+          xa[4 * u + 3] = fmaf(fa, vv[u].w, xa[4 * u + 3]);
+          xb[4 * u + 0] = fmaf(fb, vv[u].x, xb[4 * u + 0]);
+          xb[4 * u + 1] = fmaf(fb, vv[u].y, xb[4 * u + 1]);
+          xb[4 * u + 2] = fmaf(fb, vv[u].z, xb[4 * u + 2]);
+          xb[4 * u + 3] = fmaf(fb, vv[u].w, xb[4 * u + 3]);
         }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < 2; ++u)
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const int r = 32 * u + 4 * t8 + i;
-          if (r < l) Xout[r + (size_t)c * l] = (double)xr[4 * u + i];
+          const int r = 64 * u + 4 * t16 + i;
+          if (r < l) {
+            Xout[r + (size_t)c * l] = (double)xa[4 * u + i];
+            if (two) Xout[r + (size_t)(c + 1) * l] = (double)xb[4 * u + i];
+          }
         }
     }
   }

@@ -558,11 +558,24 @@ static cudaError_t launch_cholesky(cudaStream_t st, int l, const double* G, doub
 // owner of diagonal block (k, k) factors it (pivot test per column), the
 // owners of row block k solve R_kj = R_kk^{-T} A_kj, and the owners of the
 // upper trailing blocks apply A_ij -= R_ki^T R_kj: two barriers per block step
-// instead of per column.  The inverse X = R^{-1} follows by the blocked
-// column sweep X(:, k) = W(:, k) R_kk^{-1}, W(:, c) -= X(:, k) R_kc.  Pivot
+// instead of per column.  The inverse X = R^{-1} comes from the blocked
+// column sweep X(:, k) = W(:, k) R_kk^{-1}, W(:, c) -= X(:, k) R_kc, W = I,
+// run one block step behind the factorization in the same barrier
+// intervals (15 block steps in all for l = 120, not 30).  Pivot
 // semantics as k_cholesky: a column whose pivot falls to tol times its
 // original diagonal is dropped (zero row of R, zero column of X); in round 0
 // a pivot below 1e-4 of it raises the FP64 gate.
+// Eight consecutive values to a 16-byte aligned address as 16-byte stores.
+__device__ __forceinline__ void store8(float* p, const float* v) {
+  reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+  reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+__device__ __forceinline__ void store8(double* p, const float* v) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    reinterpret_cast<double2*>(p)[i] = make_double2((double)v[2 * i], (double)v[2 * i + 1]);
+}
+
 constexpr int kBlkLd = 132;  // row stride of the shared R (16-byte aligned rows)
 constexpr size_t kBlkSmem = (size_t)(128 * kBlkLd + 128 * 8) * sizeof(float);
 
@@ -612,6 +625,12 @@ k_cholesky_blk(int l, const float* __restrict__ G, float tol, int* gate, double*
 #pragma unroll
     for (int b = 0; b < 8; ++b) A[a][b] = s_R[(r0 + a) * kBlkLd + c0 + b];
   __syncthreads();
+  // One register block per thread: thread (ty, tx) holds block (ty, tx) of
+  // A until block step ty forms row block ty of R, then block (ty, tx) of W
+  // (zero; the identity for ty = tx), which becomes block (ty, tx) of
+  // X = R^{-1} at block step tx.  The inverse runs one block step behind the
+  // factorization in the same barrier intervals: step k of X needs R_kk and
+  // R_kc (c > k), both known after factorization step k.
   for (int k = 0; k < nb; ++k) {
     const int k0 = 8 * k;
     if (ty == k && tx == k) {
@@ -640,6 +659,22 @@ k_cholesky_blk(int l, const float* __restrict__ G, float tol, int* gate, double*
       for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int b = 0; b < 8; ++b) s_R[(k0 + a) * kBlkLd + k0 + b] = (b >= a) ? A[a][b] : 0.f;
+    } else if (k > 0 && ty < k && tx >= k && tx < nb) {
+      // inverse, second half of step k - 1: W(:, c) -= X(:, k-1) R_{k-1,c}
+      const int j0 = k0 - 8;
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const float4* rk4 = (const float4*)&s_R[(j0 + s) * kBlkLd + c0];
+        const float4 q0 = rk4[0], q1 = rk4[1];
+        const float rk[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+        float xs[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) xs[a] = s_X[(r0 + a) * 8 + s];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) A[a][b] -= xs[a] * rk[b];
+      }
     }
     __syncthreads();
     if (ty == k && tx > k && tx < nb) {
@@ -662,6 +697,40 @@ k_cholesky_blk(int l, const float* __restrict__ G, float tol, int* gate, double*
         dst[0] = make_float4(A[a][0], A[a][1], A[a][2], A[a][3]);
         dst[1] = make_float4(A[a][4], A[a][5], A[a][6], A[a][7]);
       }
+      // this block of R is in shared memory: the registers become W (zero
+      // off the diagonal)
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) A[a][b] = 0.f;
+    } else if (tx == k && ty <= k) {
+      // inverse, first half of step k: X(:, k) = W(:, k) R_kk^{-1} (rows of
+      // block column k above the diagonal and the diagonal block, whose W
+      // is the identity)
+      if (ty == k) {
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) A[a][b] = (a == b) ? 1.f : 0.f;
+      }
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const float rinv = s_ri[k0 + b];
+#pragma unroll
+        for (int s = 0; s < b; ++s) {
+          const float rsb = s_R[(k0 + s) * kBlkLd + k0 + b];
+#pragma unroll
+          for (int a = 0; a < 8; ++a) A[a][b] -= A[a][s] * rsb;
+        }
+#pragma unroll
+        for (int a = 0; a < 8; ++a) A[a][b] *= rinv;
+      }
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        float4* dst = (float4*)&s_X[(r0 + a) * 8];
+        dst[0] = make_float4(A[a][0], A[a][1], A[a][2], A[a][3]);
+        dst[1] = make_float4(A[a][4], A[a][5], A[a][6], A[a][7]);
+      }
     }
     __syncthreads();
     if (ty > k && tx >= ty && tx < nb) {
@@ -679,69 +748,38 @@ k_cholesky_blk(int l, const float* __restrict__ G, float tol, int* gate, double*
           for (int b = 0; b < 8; ++b) A[a][b] -= ri[a] * rj[b];
       }
     }
-    // block step k + 1 writes rows k0 + 8.. only; no barrier needed here
+    // block step k + 1 writes rows k0 + 8.. of s_R and reads s_X after its
+    // first barrier only; no barrier needed here
   }
   __syncthreads();
-  // inverse: W = I; for each block column k, X(:, k) = W(:, k) R_kk^{-1}
-  // (rows 0..k0+7), then W(:, c) -= X(:, k) R_kc for c > k
-  float W[8][8];
+  float (&W)[8][8] = A;
+  // X straight from the register blocks: column c0 + b, rows r0 .. r0 + 7,
+  // as 16-byte stores (zero below the diagonal); few wide store requests
+  // instead of one request per 32 elements
+  const bool vec = ((uintptr_t)Xw & 15) == 0 && ((size_t)ldxw * sizeof(TW)) % 16 == 0 &&
+                   (!Xout || ((l & 1) == 0 && ((uintptr_t)Xout & 15) == 0));
+  if (r0 < l && c0 < l) {
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
+    for (int b = 0; b < 8; ++b) {
+      const int j = c0 + b;
+      if (j < l) {
+        float col[8];
 #pragma unroll
-    for (int b = 0; b < 8; ++b) W[a][b] = (r0 + a == c0 + b) ? 1.f : 0.f;
-  for (int k = 0; k < nb; ++k) {
-    const int k0 = 8 * k;
-    if (tx == k && ty <= k) {
+        for (int a = 0; a < 8; ++a) col[a] = (r0 + a <= j) ? W[a][b] : 0.f;
+        if (vec && r0 + 8 <= l) {
+          store8(Xw + r0 + (int64_t)j * ldxw, col);
+          if (Xout) store8(Xout + r0 + (int64_t)j * l, col);
+        } else {
 #pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        const float rinv = s_ri[k0 + b];
-#pragma unroll
-        for (int s = 0; s < b; ++s) {
-          const float rsb = s_R[(k0 + s) * kBlkLd + k0 + b];
-#pragma unroll
-          for (int a = 0; a < 8; ++a) W[a][b] -= W[a][s] * rsb;
+          for (int a = 0; a < 8; ++a)
+            if (r0 + a < l) {
+              Xw[r0 + a + (int64_t)j * ldxw] = (TW)col[a];
+              if (Xout) Xout[r0 + a + (int64_t)j * l] = (double)col[a];
+            }
         }
-#pragma unroll
-        for (int a = 0; a < 8; ++a) W[a][b] *= rinv;
-      }
-#pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        float4* dst = (float4*)&s_X[(r0 + a) * 8];
-        dst[0] = make_float4(W[a][0], W[a][1], W[a][2], W[a][3]);
-        dst[1] = make_float4(W[a][4], W[a][5], W[a][6], W[a][7]);
       }
     }
-    __syncthreads();
-    if (tx > k && tx < nb && ty <= k) {
-#pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        const float4* rk4 = (const float4*)&s_R[(k0 + s) * kBlkLd + c0];
-        const float4 q0 = rk4[0], q1 = rk4[1];
-        const float rk[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-        float xs[8];
-#pragma unroll
-        for (int a = 0; a < 8; ++a) xs[a] = s_X[(r0 + a) * 8 + s];
-#pragma unroll
-        for (int a = 0; a < 8; ++a)
-#pragma unroll
-          for (int b = 0; b < 8; ++b) W[a][b] -= xs[a] * rk[b];
-      }
-    }
-    __syncthreads();
   }
-  // X (upper block triangle of W) through shared memory for coalesced stores
-#pragma unroll
-  for (int a = 0; a < 8; ++a)
-#pragma unroll
-    for (int b = 0; b < 8; ++b) s_R[(c0 + b) * kBlkLd + r0 + a] = (r0 + a <= c0 + b) ? W[a][b] : 0.f;
-  __syncthreads();
-  // column j by warp j % 8 (no index division); the FP64 copy only when asked
-  for (int j = tid >> 5; j < l; j += 8)
-    for (int i = tid & 31; i < l; i += 32) {
-      const float v = s_R[j * kBlkLd + i];
-      if (Xout) Xout[i + j * l] = (double)v;
-      Xw[i + (int64_t)j * ldxw] = (TW)v;
-    }
   if (tid == 0) {
     int ndropped = 0;
     for (int j = 0; j < l; ++j) ndropped += s_keep[j] ? 0 : 1;

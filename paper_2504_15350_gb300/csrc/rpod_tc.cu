@@ -53,6 +53,18 @@ __device__ __forceinline__ float tf32_rna(float x) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
   return __uint_as_float(u);
 }
+// 1024-byte aligned start within the dynamic shared memory.  Offset
+// arithmetic on the shared array keeps every pointer derived from it in the
+// shared address space, so that accesses through it compile to shared-memory
+// loads and stores (a round trip of the address through an integer would
+// leave the compiler generic accesses, which take the slower generic path).
+__device__ __forceinline__ uint8_t* align_smem1024(uint8_t* base) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(base);
+  return base + ((1024u - (a & 1023u)) & 1023u);
+}
+__device__ __forceinline__ float pick4(const float4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
 __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -194,7 +206,7 @@ k_wpass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
   // memory by warps 2-5 before the MMA reads it, so that the tensor core's
   // truncation of the low mantissa bits adds no bias.  Warps 0-3 drain TMEM.
   constexpr bool RND = (KIND == 2);
-  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* smem = align_smem1024(smem_raw);
   uint64_t* full = (uint64_t*)(smem + L::BARS);
   uint64_t* empty = full + STAGES;
   uint64_t* conv = empty + STAGES;
@@ -324,7 +336,7 @@ k_ypass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
         int64_t ysplit) {
   using L = Smem<BN, STAGES>;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* smem = align_smem1024(smem_raw);
   uint64_t* full = (uint64_t*)(smem + L::BARS);
   uint64_t* empty = full + STAGES;
   uint64_t* done = empty + STAGES;
@@ -436,7 +448,7 @@ k_gram3(const __grid_constant__ CUtensorMap tmY, int64_t rows, int l, int kchunk
         double* __restrict__ part, unsigned* status) {
   using L = GramSmem<STAGES>;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* smem = align_smem1024(smem_raw);
   uint64_t* full = (uint64_t*)(smem + L::BARS);
   uint64_t* empty = full + STAGES;
   uint64_t* conv = empty + STAGES;
@@ -574,7 +586,7 @@ k_gram_x(const __grid_constant__ CUtensorMap tmY, int64_t rows, int l, int kchun
          double* __restrict__ part, unsigned* status) {
   using L = GramXSmem<STAGES>;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* smem = align_smem1024(smem_raw);
   float* acc = (float*)(smem + STAGES * L::STAGE);
   uint64_t* full = (uint64_t*)(smem + L::BARS);
   uint64_t* empty = full + STAGES;
@@ -762,7 +774,7 @@ k_ypass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   using TH = typename std::conditional<KIND == 0, __nv_bfloat16, __half>::type;
   constexpr int BN = 128;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* smem = align_smem1024(smem_raw);
   uint64_t* full = (uint64_t*)(smem + L::BARS);
   uint64_t* empty = full + STAGES;
   uint64_t* conv = empty + STAGES;
@@ -911,38 +923,46 @@ k_ypass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 // either rounded to BF16 for the next pass or re-orthonormalised by a
 // CholeskyQR round on an exact FP32 Gram, so one TF32 product suffices.
 // Persistent CTAs over 128-row tiles: warp 0 TMA-loads 128 x 32 column-major
-// FP32 tiles of Y (one per 32-column k-block), warps 2-5 round them and
-// transpose them into the K-major SW128 operand layout, warp 1 issues the
+// FP32 tiles of Y (one per 32-column k-block) into a ring of NR raw slots,
+// warps 2-9 round them and transpose them into one of NC K-major SW128
+// operand tiles (a raw slot is released once read, so up to NR k-blocks
+// stay in flight from HBM), warp 1 issues the
 // MMAs against X (resident in shared memory as the B operand) into one of two
-// TMEM accumulators, and warps 6-9 drain the other accumulator and write any
-// of: Q (FP32), Q rounded to the 16-bit type (the next W-pass operand), Q
-// rounded to TF32 (the refinement pass operand).
+// TMEM accumulators, and warps 10-17 drain the other accumulator (two warps
+// per TMEM lane quarter, one per column half) through shared memory into
+// 16-byte stores of any of: Q (FP32), Q rounded to the 16-bit type (the next
+// W-pass operand), Q rounded to TF32 (the refinement pass operand).
 // SPLIT = 2 (the lift U = Q1 (X2 Uhat) of the returned basis): both operands
 // split into TF32 hi and lo parts and three products (lo hi, hi lo, hi hi),
 // about 2^-21 relative error per entry.
-template <int STAGES, int SPLIT>
+template <int NR, int NC, int SPLIT>
 struct ApplySmem {
   static constexpr uint32_t KB = 128 * 32 * 4;   // 128 rows x 32 columns of FP32
-  static constexpr uint32_t STAGE = (1 + SPLIT) * KB;  // raw TMA tile + converted parts
+  static constexpr uint32_t RAW = NR * KB;       // TMA ring of raw Y tiles
+  static constexpr uint32_t CONV = SPLIT * KB;   // one converted operand tile (all parts)
   static constexpr uint32_t XOP = SPLIT * 4 * KB;  // X parts: 4 k-blocks x 128 (j) x 32 (k)
-  static constexpr uint32_t BARS = STAGES * STAGE + XOP;
+  static constexpr uint32_t STG = 32 * 32 * 4;     // one epilogue warp's 32 x 32 staging block
+  static constexpr uint32_t BARS = RAW + NC * CONV + XOP + 8 * STG;
   static constexpr size_t TOTAL = 1024 + (size_t)BARS + 256;
 };
 
-template <int KIND16, int STAGES, int SPLIT>
-__global__ void __launch_bounds__(320, 1)
+template <int KIND16, int NR, int NC, int SPLIT>
+__global__ void __launch_bounds__(576, 1)
 k_apply_tf32(const __grid_constant__ CUtensorMap tmY, const float* __restrict__ X, int64_t ldx,
              int64_t n, int l, int ncol, float* __restrict__ Q, int64_t ldq, void* __restrict__ Qh,
              int64_t ldh, float* __restrict__ Qt, int64_t ldt, unsigned* status) {
-  using L = ApplySmem<STAGES, SPLIT>;
+  using L = ApplySmem<NR, NC, SPLIT>;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* xop = smem + STAGES * L::STAGE;
-  uint64_t* full = (uint64_t*)(smem + L::BARS);
-  uint64_t* empty = full + STAGES;
-  uint64_t* conv = empty + STAGES;
-  uint64_t* tfull = conv + STAGES;   // [2]
-  uint64_t* tempty = tfull + 2;      // [2]
+  uint8_t* smem = align_smem1024(smem_raw);
+  uint8_t* conv_buf = smem + L::RAW;
+  uint8_t* xop = conv_buf + NC * L::CONV;
+  uint8_t* stage = xop + L::XOP;
+  uint64_t* rfull = (uint64_t*)(smem + L::BARS);
+  uint64_t* rempty = rfull + NR;
+  uint64_t* cfull = rempty + NR;
+  uint64_t* cempty = cfull + NC;
+  uint64_t* tfull = cempty + NC;    // [2]
+  uint64_t* tempty = tfull + 2;     // [2]
   uint64_t* mdone = tempty + 2;
   uint32_t* tslot = (uint32_t*)(mdone + 1);
   volatile int* abort_flag = (volatile int*)(tslot + 1);
@@ -954,14 +974,17 @@ k_apply_tf32(const __grid_constant__ CUtensorMap tmY, const float* __restrict__ 
   const int nlt = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
-      mbar_init(&conv[s], 4);
+    for (int s = 0; s < NR; ++s) {
+      mbar_init(&rfull[s], 1);
+      mbar_init(&rempty[s], 4);
+    }
+    for (int c = 0; c < NC; ++c) {
+      mbar_init(&cfull[c], 4);
+      mbar_init(&cempty[c], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 4);
+      mbar_init(&tempty[b], 8);
     }
     mbar_init(mdone, 1);
     *abort_flag = 0;
@@ -969,15 +992,15 @@ k_apply_tf32(const __grid_constant__ CUtensorMap tmY, const float* __restrict__ 
   }
   // X as the B operand (N = j, K = k), K-major SW128, rounded to TF32, zero
   // outside l x l; eight loads per thread in flight before their stores
-  if (warp >= 2 && warp < 6) {
+  if (warp >= 2 && warp < 10) {
     const int ct = threadIdx.x - 64;
     const bool vec = (ldx & 3) == 0 && ((uintptr_t)X & 15) == 0;
 #pragma unroll 1
-    for (int e0 = 0; e0 < 4 * 128 * 8; e0 += 128 * 8) {
+    for (int e0 = 0; e0 < 4 * 128 * 8; e0 += 256 * 8) {
       float4 v[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int e = e0 + u * 128 + ct;
+        const int e = e0 + u * 256 + ct;
         const int j = (e >> 3) & 127, k = (e >> 10) * 32 + 4 * (e & 7);
         v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (j < ncol && k < l) {
@@ -994,7 +1017,7 @@ k_apply_tf32(const __grid_constant__ CUtensorMap tmY, const float* __restrict__ 
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int e = e0 + u * 128 + ct;
+        const int e = e0 + u * 256 + ct;
         const int kb = e >> 10, j = (e >> 3) & 127, c4 = e & 7;
         const float4 r = make_float4(tf32_rna(v[u].x), tf32_rna(v[u].y), tf32_rna(v[u].z),
                                      tf32_rna(v[u].w));
@@ -1020,47 +1043,71 @@ k_apply_tf32(const __grid_constant__ CUtensorMap tmY, const float* __restrict__ 
     for (int lt = 0; lt < nlt && go; ++lt) {
       const int64_t t = blockIdx.x + (int64_t)lt * gridDim.x;
       for (int kb = 0; kb < nkb; ++kb) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (it >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, abort_flag)) { go = false; break; }
-        mbar_expect_tx(&full[s], L::KB);
-        tma_load_2d(smem + s * L::STAGE, &tmY, &full[s], (int)(t * 128), kb * 32);
+        const int s = it % NR;
+        const uint32_t ph = (uint32_t)(it / NR) & 1u;
+        if (it >= NR && !mbar_wait(&rempty[s], ph ^ 1u, abort_flag)) { go = false; break; }
+        mbar_expect_tx(&rfull[s], L::KB);
+        tma_load_2d(smem + s * L::KB, &tmY, &rfull[s], (int)(t * 128), kb * 32);
         ++it;
       }
     }
     // on an abort, wait (bounded) for the copies still in flight
     if (*abort_flag)
-      for (int i2 = it > STAGES ? it - STAGES : 0; i2 < it; ++i2)
-        mbar_wait_drain(&full[i2 % STAGES], (uint32_t)(i2 / STAGES) & 1u);
-  } else if (warp >= 2 && warp < 6) {
+      for (int i2 = it > NR ? it - NR : 0; i2 < it; ++i2)
+        mbar_wait_drain(&rfull[i2 % NR], (uint32_t)(i2 / NR) & 1u);
+  } else if (warp >= 2 && warp < 10) {
+    // converters (eight warps): raw tile s of the ring -> operand tile c;
+    // the raw slot is released as soon as it is read, so the loads run NR
+    // k-blocks ahead of the conversions and the MMAs.  Thread (c4, mq)
+    // takes the 4 x 4 block of rows 4 mq .. + 3 and columns 4 c4 .. + 3:
+    // four 16-byte loads down the columns, a transpose in registers, four
+    // 16-byte stores along the rows of the K-major operand.  The rows are
+    // stored in a lane-rotated order, so that the eight lanes of each store
+    // phase cover all eight row residues mod 8 and hence eight distinct
+    // swizzled 16-byte bank groups.
+    // Two groups of four warps take alternate k-blocks, so that two
+    // conversions are in flight; each thread converts two 4 x 4 blocks.
     const int ct = threadIdx.x - 64;
+    const int grp = ct >> 7, gt = ct & 127;
+    const int c4 = gt >> 5, mq = gt & 31;
     bool go = true;
     for (int lt = 0, it = 0; lt < nlt && go; ++lt)
       for (int kb = 0; kb < nkb; ++kb, ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[s], ph, abort_flag));
-        if (!ok) { go = false; break; }
-        const float* raw = (const float*)(smem + s * L::STAGE);  // column k at k * 128
-        uint8_t* aop = smem + s * L::STAGE + L::KB;
-#pragma unroll 2
-        for (int e = ct; e < 128 * 8; e += 128) {
-          const int m = e & 127, c4 = e >> 7;
-          float4 x, v;
-          x.x = raw[(4 * c4 + 0) * 128 + m];
-          x.y = raw[(4 * c4 + 1) * 128 + m];
-          x.z = raw[(4 * c4 + 2) * 128 + m];
-          x.w = raw[(4 * c4 + 3) * 128 + m];
-          v.x = tf32_rna(x.x); v.y = tf32_rna(x.y); v.z = tf32_rna(x.z); v.w = tf32_rna(x.w);
-          const uint32_t off = (m >> 3) * 1024 + (m & 7) * 128 + ((c4 ^ (m & 7)) << 4);
-          *(float4*)(aop + off) = v;
-          if (SPLIT == 2)
-            *(float4*)(aop + L::KB + off) = make_float4(tf32_rna(x.x - v.x), tf32_rna(x.y - v.y),
-                                                        tf32_rna(x.z - v.z), tf32_rna(x.w - v.w));
+        if ((it & 1) != grp) continue;
+        const int s = it % NR, c = it % NC;
+        const uint32_t ph = (uint32_t)(it / NR) & 1u, phc = (uint32_t)(it / NC) & 1u;
+        bool ok = mbar_wait(&rfull[s], ph, abort_flag);
+        if (ok && it >= NC) ok = mbar_wait(&cempty[c], phc ^ 1u, abort_flag);
+        if (!__all_sync(0xffffffffu, ok)) { go = false; break; }
+        const float* raw = (const float*)(smem + s * L::KB);  // column k at k * 128
+        uint8_t* aop = conv_buf + c * L::CONV;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int cb = c4 + 4 * h;  // column block 4 cb .. 4 cb + 3
+          float4 col[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            col[i] = *reinterpret_cast<const float4*>(raw + (4 * cb + i) * 128 + 4 * mq);
+#pragma unroll
+          for (int rr = 0; rr < 4; ++rr) {
+            const int r = (rr + (lane >> 1)) & 3;
+            const float4 x = make_float4(pick4(col[0], r), pick4(col[1], r), pick4(col[2], r),
+                                         pick4(col[3], r));
+            const int m = 4 * mq + r;
+            const float4 v = make_float4(tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w));
+            const uint32_t off = (m >> 3) * 1024 + (m & 7) * 128 + ((cb ^ (m & 7)) << 4);
+            *(float4*)(aop + off) = v;
+            if (SPLIT == 2)
+              *(float4*)(aop + L::KB + off) = make_float4(tf32_rna(x.x - v.x), tf32_rna(x.y - v.y),
+                                                          tf32_rna(x.z - v.z), tf32_rna(x.w - v.w));
+          }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(&conv[s]);
+        if (lane == 0) {
+          mbar_arrive(&rempty[s]);
+          mbar_arrive(&cfull[c]);
+        }
       }
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t id = idesc(2, false, 128, 128);
@@ -1071,11 +1118,11 @@ k_apply_tf32(const __grid_constant__ CUtensorMap tmY, const float* __restrict__ 
       tc_after();
       const uint32_t d = tmem + (uint32_t)(buf * 128);
       for (int kb = 0; kb < nkb; ++kb, ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!mbar_wait(&conv[s], ph, abort_flag)) { go = false; break; }
+        const int c = it % NC;
+        const uint32_t phc = (uint32_t)(it / NC) & 1u;
+        if (!mbar_wait(&cfull[c], phc, abort_flag)) { go = false; break; }
         tc_after();
-        const uint32_t a = su32(smem + s * L::STAGE + L::KB), b = su32(xop + kb * L::KB);
+        const uint32_t a = su32(conv_buf + c * L::CONV), b = su32(xop + kb * L::KB);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
           const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
@@ -1088,7 +1135,7 @@ k_apply_tf32(const __grid_constant__ CUtensorMap tmY, const float* __restrict__ 
             mma<2>(d, sdesc(a + 32 * kk, 16, 1024), sdesc(b + 32 * kk, 16, 1024), id, acc0);
           }
         }
-        mma_commit(&empty[s]);
+        mma_commit(&cempty[c]);
         issued = true;
       }
       if (go) mma_commit(&tfull[buf]);
@@ -1098,30 +1145,91 @@ k_apply_tf32(const __grid_constant__ CUtensorMap tmY, const float* __restrict__ 
       mma_commit(mdone);
       mbar_wait_drain(mdone, 0);
     }
-  } else if (warp >= 6) {
-    const int q = warp & 3;  // TMEM lane quarter this warp may read
+  } else if (warp >= 10) {
+    // eight epilogue warps: warp w reads TMEM lane quarter w % 4 (rows
+    // 32 (w % 4) .. + 31 of the tile) and one half of the columns.  Each
+    // 32 x 32 block goes through this warp's staging buffer (column j of the
+    // block at j * 32) and leaves as 16-byte stores along the rows of a
+    // column: 4 (FP32) or 8 (16-bit) rows per lane, so one store instruction
+    // writes 4 or 8 whole 128- or 64-byte column segments instead of 32
+    // two- or four-byte pieces
+    const int q = warp & 3;
+    const int half = (warp - 10) >> 2;
+    float* stg = reinterpret_cast<float*>(stage + (warp - 10) * L::STG);
+    __nv_bfloat16* stgb = reinterpret_cast<__nv_bfloat16*>(stg);
+    __half* stgh = reinterpret_cast<__half*>(stg);
+    // 16-byte stores need 16-byte aligned columns
+    const bool vq = Q && ((uintptr_t)Q & 15) == 0 && (ldq & 3) == 0;
+    const bool vt = Qt && ((uintptr_t)Qt & 15) == 0 && (ldt & 3) == 0;
+    const bool vh = Qh && ((uintptr_t)Qh & 15) == 0 && (ldh & 7) == 0;
     for (int lt = 0; lt < nlt; ++lt) {
       const int buf = lt & 1;
       const bool ok = __all_sync(0xffffffffu, mbar_wait(&tfull[buf], (uint32_t)(lt >> 1) & 1u, abort_flag));
       if (!ok) break;
       tc_after();
       const int64_t t = blockIdx.x + (int64_t)lt * gridDim.x;
-      const int64_t m = t * 128 + q * 32 + lane;
-      for (int cc = 0; cc < ncol; cc += 32) {
+      const int64_t m0 = t * 128 + q * 32;  // first row of this warp's block
+      const int64_t m = m0 + lane;
+      const bool full = m0 + 32 <= n;
+      for (int cc = 64 * half; cc < ncol && cc < 64 * half + 64; cc += 32) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 128 + cc), v);
-        if (m < n) {
+        const int nc = ncol - cc < 32 ? ncol - cc : 32;
+        // FP32 outputs: Q, then Q rounded to TF32
+#pragma unroll 1
+        for (int o = 0; o < 2; ++o) {
+          float* out = o == 0 ? Q : Qt;
+          const int64_t ld = o == 0 ? ldq : ldt;
+          if (!out) continue;
+          if (full && (o == 0 ? vq : vt)) {
+            __syncwarp();
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const int j = cc + i;
-            if (j < ncol) {
-              if (Q) Q[m + j * ldq] = v[i];
-              if (Qt) Qt[m + j * ldt] = tf32_rna(v[i]);
-              if (Qh) {
+            for (int i = 0; i < 32; ++i) stg[i * 32 + lane] = o == 0 ? v[i] : tf32_rna(v[i]);
+            __syncwarp();
+            // lane: column cl = lane / 8 + 4 u, rows 4 (lane % 8) .. + 3
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int cl = (lane >> 3) + 4 * u;
+              if (cl < nc)
+                *reinterpret_cast<float4*>(out + m0 + 4 * (lane & 7) + (int64_t)(cc + cl) * ld) =
+                    *reinterpret_cast<const float4*>(stg + cl * 32 + 4 * (lane & 7));
+            }
+          } else if (m < n) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (i < nc) out[m + (int64_t)(cc + i) * ld] = o == 0 ? v[i] : tf32_rna(v[i]);
+          }
+        }
+        // Q rounded to the 16-bit type
+        if (Qh) {
+          if (full && vh) {
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              if (KIND16 == 0)
+                stgb[i * 32 + lane] = __float2bfloat16_rn(v[i]);
+              else
+                stgh[i * 32 + lane] = __float2half_rn(v[i]);
+            }
+            __syncwarp();
+            // lane: column cl = lane / 4 + 8 u, rows 8 (lane % 4) .. + 7
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int cl = (lane >> 2) + 8 * u;
+              if (cl < nc)
+                *reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(Qh) + m0 + 8 * (lane & 3) +
+                                          (int64_t)(cc + cl) * ldh) =
+                    *reinterpret_cast<const uint4*>(reinterpret_cast<const uint16_t*>(stg) +
+                                                    cl * 32 + 8 * (lane & 3));
+            }
+          } else if (m < n) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              if (i < nc) {
                 if (KIND16 == 0)
-                  ((__nv_bfloat16*)Qh)[m + j * ldh] = __float2bfloat16_rn(v[i]);
+                  ((__nv_bfloat16*)Qh)[m + (int64_t)(cc + i) * ldh] = __float2bfloat16_rn(v[i]);
                 else
-                  ((__half*)Qh)[m + j * ldh] = __float2half_rn(v[i]);
+                  ((__half*)Qh)[m + (int64_t)(cc + i) * ldh] = __float2half_rn(v[i]);
               }
             }
           }
@@ -1203,8 +1311,10 @@ constexpr size_t kSmallPassBytes = (size_t)1 << 30;
 constexpr int kGramStages = 3;  // 96 KB: two CTAs per SM
 constexpr int kYcvtStages = 3;  // 192 KB
 constexpr int kGramXStages = 3;  // 144 KB of stages + 33 KB of sums
-constexpr int kApplyStages = 4;  // 128 KB of stages + 64 KB for X
-constexpr int kApply2Stages = 2;  // two-part form: 96 KB of stages + 128 KB for X
+// apply: raw TMA slots and operand tiles (224 KB with X and the epilogue's
+// 32 KB of staging in both forms)
+constexpr int kApplyRaw = 6, kApplyConv = 2;    // 96 + 32 KB + 64 KB for X
+constexpr int kApply2Raw = 2, kApply2Conv = 1;  // two-part form: 32 + 32 KB + 128 KB for X
 
 int sm_count() {
   static int n = 0;
@@ -1244,11 +1354,14 @@ void prepare_kernels_tc() {
     const int yc = (int)tc::YcvtSmem<kYcvtStages>::TOTAL;
     cudaFuncSetAttribute(tc::k_ypass_cvt<0, kYcvtStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, yc);
     cudaFuncSetAttribute(tc::k_ypass_cvt<1, kYcvtStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, yc);
-    const int ap = (int)tc::ApplySmem<kApplyStages, 1>::TOTAL;
-    cudaFuncSetAttribute(tc::k_apply_tf32<0, kApplyStages, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ap);
-    cudaFuncSetAttribute(tc::k_apply_tf32<1, kApplyStages, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ap);
-    const int ap2 = (int)tc::ApplySmem<kApply2Stages, 2>::TOTAL;
-    cudaFuncSetAttribute(tc::k_apply_tf32<0, kApply2Stages, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, ap2);
+    const int ap = (int)tc::ApplySmem<kApplyRaw, kApplyConv, 1>::TOTAL;
+    cudaFuncSetAttribute(tc::k_apply_tf32<0, kApplyRaw, kApplyConv, 1>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, ap);
+    cudaFuncSetAttribute(tc::k_apply_tf32<1, kApplyRaw, kApplyConv, 1>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, ap);
+    const int ap2 = (int)tc::ApplySmem<kApply2Raw, kApply2Conv, 2>::TOTAL;
+    cudaFuncSetAttribute(tc::k_apply_tf32<0, kApply2Raw, kApply2Conv, 2>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, ap2);
   });
 }
 
@@ -1441,14 +1554,16 @@ int tc_apply(cudaStream_t st, const float* Y, int64_t ldy, int64_t n, int l, con
   const int64_t ntiles = (n + 127) / 128;
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, sm_count());
   prepare_kernels_tc();
+  using L1 = tc::ApplySmem<kApplyRaw, kApplyConv, 1>;
+  using L2 = tc::ApplySmem<kApply2Raw, kApply2Conv, 2>;
   if (precise)
-    tc::k_apply_tf32<0, kApply2Stages, 2><<<grid, 320, tc::ApplySmem<kApply2Stages, 2>::TOTAL, st>>>(
+    tc::k_apply_tf32<0, kApply2Raw, kApply2Conv, 2><<<grid, 576, L2::TOTAL, st>>>(
         ty, X, ldx, n, l, ncol, Q, ldq, Qh, ldh, Qt, ldt, status);
   else if (dt16 == RPOD_F16)
-    tc::k_apply_tf32<1, kApplyStages, 1><<<grid, 320, tc::ApplySmem<kApplyStages, 1>::TOTAL, st>>>(
+    tc::k_apply_tf32<1, kApplyRaw, kApplyConv, 1><<<grid, 576, L1::TOTAL, st>>>(
         ty, X, ldx, n, l, ncol, Q, ldq, Qh, ldh, Qt, ldt, status);
   else
-    tc::k_apply_tf32<0, kApplyStages, 1><<<grid, 320, tc::ApplySmem<kApplyStages, 1>::TOTAL, st>>>(
+    tc::k_apply_tf32<0, kApplyRaw, kApplyConv, 1><<<grid, 576, L1::TOTAL, st>>>(
         ty, X, ldx, n, l, ncol, Q, ldq, Qh, ldh, Qt, ldt, status);
   note_launch();
   return cudaGetLastError() == cudaSuccess ? RPOD_OK : RPOD_ERR_CUDA;

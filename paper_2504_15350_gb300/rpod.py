@@ -85,6 +85,7 @@ SIGNATURES = {
                                         _c_u64, _c_i32, _c_u32]),
     "rpod_workspace_bytes": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_size_t)]),
     "rpod_plan_set_svd_sweeps": (ctypes.c_int, [_p, _c_i32]),
+    "rpod_plan_set_graph": (ctypes.c_int, [_p, _c_i32]),
     "rpod_rows_plan_create": (ctypes.c_int, [ctypes.POINTER(_p), _c_i64, _c_i64, _c_i64, _c_i64, _c_i32,
                                              _c_i32, _c_i32, _c_u64, _c_i32, _c_u32]),
     "rpod_basis_rows": (ctypes.c_int, [_p, _p, _c_i64, _c_i32, _p, _c_i64, _p, _p, _c_i64, _p,
@@ -162,6 +163,10 @@ def rpod_workspace_bytes(plan) -> int:
 
 def rpod_plan_set_svd_sweeps(plan, max_sweeps):
     return load().rpod_plan_set_svd_sweeps(plan, max_sweeps)
+
+
+def rpod_plan_set_graph(plan, enable):
+    return load().rpod_plan_set_graph(plan, enable)
 
 
 def rpod_basis(plan, S, lds, s_dtype, S_refine, ldr, U, ldu, sigma, C, ldc, ws, ws_bytes, stream):
@@ -465,6 +470,11 @@ class Plan:
 
     def launches(self):
         return rpod_last_launch_count(self.handle)
+
+    def set_graph(self, enable):
+        """Graph replay of repeated basis calls with unchanged buffers
+        (rpod_plan_set_graph; on by default)."""
+        _check(rpod_plan_set_graph(self.handle, 1 if enable else 0), "rpod_plan_set_graph")
 
     def set_svd_sweeps(self, max_sweeps):
         """Caps the FP64 form's one-sided Jacobi sweeps (rpod_plan_set_svd_sweeps)."""

@@ -400,3 +400,66 @@ def test_host_io_plan_matches_device_plan(compute):
     assert np.abs(s1.numpy() - s0.cpu().numpy()).max() <= tol * float(s0[0])
     assert np.abs(U1.double().numpy() - U0.double().cpu().numpy()).max() <= 1e3 * tol
     assert np.abs(C1.double().numpy() - C0.double().cpu().numpy()).max() <= tol * 10 * float(s0[0])
+
+
+@pytest.mark.parametrize("compute", ["f64", "f32", "bf16"])
+def test_graph_replay_matches_direct_launches(compute):
+    """rpod_plan_set_graph: the second call with the same buffers records the
+    plan's kernels into one CUDA graph and later calls replay it.  Replays
+    give bit-identical outputs to direct launches, see new contents of S,
+    launch the same kernel count, and a call with other buffers launches
+    directly (and is still correct)."""
+    rng = np.random.default_rng(31)
+    n, m, k, p, q = 4100, 700, 20, 10, 2
+    dt = torch.float64 if compute == "f64" else torch.float32
+    S0, _, _ = lowrank(n, m, 60, seed=5, decay=0.9)
+    S1 = S0 * torch.from_numpy(rng.uniform(0.5, 1.5, size=(1, m)))
+    flags = R.RPOD_FLAG_REFINE_FP32 if compute == "bf16" else 0
+    Sd = dev(S0, dt)
+    direct = R.Plan(n, m, k, p, q, seed=4, compute=compute, flags=flags)
+    direct.set_graph(False)
+    ref0 = [t.clone() for t in direct.basis(Sd)]
+    plan = R.Plan(n, m, k, p, q, seed=4, compute=compute, flags=flags)
+    odt = torch.float64 if compute == "f64" else torch.float32
+    out = (R.empty_colmajor(n, k, odt, "cuda"), torch.empty(k + p, dtype=torch.float64, device="cuda"),
+           R.empty_colmajor(k, m, odt, "cuda"))
+    counts = []
+    for _ in range(4):   # direct, capture + launch, replay, replay
+        for t in out:
+            t.fill_(float("nan"))
+        plan.basis(Sd, out=out)
+        torch.cuda.synchronize()
+        counts.append(plan.launches())
+        assert plan.status()[0] == R.RPOD_OK
+        for a, b in zip(out, ref0):
+            assert torch.equal(a, b)
+    assert len(set(counts)) == 1 and counts[0] > 10
+    # new contents of S at the same address: the replay sees them
+    Sd.copy_(dev(S1, dt))
+    ref1 = [t.clone() for t in direct.basis(Sd)]
+    plan.basis(Sd, out=out)
+    torch.cuda.synchronize()
+    for a, b in zip(out, ref1):
+        assert torch.equal(a, b)
+    # other buffers: a direct call with the right result
+    U2, s2, C2 = plan.basis(Sd)
+    torch.cuda.synchronize()
+    for a, b in zip((U2, s2, C2), ref1):
+        assert torch.equal(a, b)
+    # inside a caller's own capture the plan launches directly into it
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        plan.basis(Sd, out=out)
+    torch.cuda.current_stream().wait_stream(side)
+    Sd.copy_(dev(S0, dt))
+    with torch.cuda.graph(g):
+        plan.basis(Sd, out=out)
+    for t in out:
+        t.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    assert plan.status()[0] == R.RPOD_OK
+    for a, b in zip(out, ref0):
+        assert torch.equal(a, b)
