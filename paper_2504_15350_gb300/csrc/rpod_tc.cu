@@ -328,12 +328,14 @@ k_wpass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
 // (BN rows as BN/64 boxes of 64 rows x 64 snapshots).  blockIdx.y takes the
 // 64-snapshot k-tiles kchunk * y .. kchunk * (y + 1) - 1 and writes its sum
 // to Y + y * ysplit (a split over snapshots for matrices with few rows; the
-// caller sums the slices).
+// caller sums the slices).  Row tile blockIdx.x is tile tile0 + blockIdx.x of
+// S; its rows i go to row i - yrow0 of Y (a launch over the last row tiles
+// alone writes a compact slice).
 template <int KIND, int BN, int STAGES>
 __global__ void __launch_bounds__(128, 1)
 k_ypass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmS, int64_t n,
         int64_t m, int l, float* __restrict__ Y, int64_t ldy, unsigned* status, int kchunk,
-        int64_t ysplit) {
+        int64_t ysplit, int64_t tile0, int64_t yrow0) {
   using L = Smem<BN, STAGES>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align_smem1024(smem_raw);
@@ -344,7 +346,7 @@ k_ypass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
   volatile int* abort_flag = (volatile int*)(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t i0 = (int64_t)blockIdx.x * BN;
+  const int64_t i0 = (tile0 + (int64_t)blockIdx.x) * BN;
   // this CTA's k-tiles (the host sizes the chunks so that none is empty)
   const int nk_all = (int)((m + 63) / 64);
   const int kt0 = (int)blockIdx.y * kchunk;
@@ -411,12 +413,12 @@ k_ypass(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     if (c < l) {
       const int64_t ib = i0 + cc;
       if (((ldy & 3) == 0) && ib + 32 <= n) {
-        float4* d4 = (float4*)(ycol + ib);
+        float4* d4 = (float4*)(ycol + (ib - yrow0));
 #pragma unroll
         for (int i = 0; i < 8; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
       } else {
         for (int i = 0; i < 32; ++i)
-          if (ib + i < n) ycol[ib + i] = v[i];
+          if (ib + i < n) ycol[ib - yrow0 + i] = v[i];
       }
     }
   }
@@ -769,7 +771,8 @@ template <int KIND, int STAGES>
 __global__ void __launch_bounds__(192, 1)
 k_ypass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmF,
             int64_t n, int64_t m, int l, float* __restrict__ Y, int64_t ldy, void* __restrict__ Sh,
-            int64_t ldh, unsigned* status, int kchunk, int64_t ysplit) {
+            int64_t ldh, unsigned* status, int kchunk, int64_t ysplit, int64_t tile0,
+            int64_t yrow0) {
   using L = YcvtSmem<STAGES>;
   using TH = typename std::conditional<KIND == 0, __nv_bfloat16, __half>::type;
   constexpr int BN = 128;
@@ -783,7 +786,7 @@ k_ypass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   volatile int* abort_flag = (volatile int*)(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t i0 = (int64_t)blockIdx.x * BN;
+  const int64_t i0 = (tile0 + (int64_t)blockIdx.x) * BN;
   const int nk_all = (int)((m + 63) / 64);
   const int kt0 = (int)blockIdx.y * kchunk;
   const int nk = min(nk_all, kt0 + kchunk) - kt0;
@@ -898,12 +901,12 @@ k_ypass_cvt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       if (c < l) {
         const int64_t ib = i0 + cc;
         if (((ldy & 3) == 0) && ib + 32 <= n) {
-          float4* d4 = (float4*)(ycol + ib);
+          float4* d4 = (float4*)(ycol + (ib - yrow0));
 #pragma unroll
           for (int i = 0; i < 8; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
         } else {
           for (int i = 0; i < 32; ++i)
-            if (ib + i < n) ycol[ib + i] = v[i];
+            if (ib + i < n) ycol[ib - yrow0 + i] = v[i];
         }
       }
     }
@@ -974,12 +977,14 @@ k_apply_tf32(const __grid_constant__ CUtensorMap tmY, const float* __restrict__ 
   const int nlt = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
 
   if (threadIdx.x == 0) {
+    // converter warps per k-block: four of two groups, or all eight
+    constexpr uint32_t CW = NC >= 2 ? 4 : 8;
     for (int s = 0; s < NR; ++s) {
       mbar_init(&rfull[s], 1);
-      mbar_init(&rempty[s], 4);
+      mbar_init(&rempty[s], CW);
     }
     for (int c = 0; c < NC; ++c) {
-      mbar_init(&cfull[c], 4);
+      mbar_init(&cfull[c], CW);
       mbar_init(&cempty[c], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -1065,15 +1070,22 @@ k_apply_tf32(const __grid_constant__ CUtensorMap tmY, const float* __restrict__ 
     // stored in a lane-rotated order, so that the eight lanes of each store
     // phase cover all eight row residues mod 8 and hence eight distinct
     // swizzled 16-byte bank groups.
-    // Two groups of four warps take alternate k-blocks, so that two
-    // conversions are in flight; each thread converts two 4 x 4 blocks.
+    // With two operand tiles (NC = 2) two groups of four warps take
+    // alternate k-blocks, so that two conversions are in flight, and each
+    // thread converts two 4 x 4 blocks; each operand tile and raw slot then
+    // belongs to one group, whose waits on its barriers follow the phases in
+    // order.  With one operand tile a single group of eight warps converts
+    // every k-block (two groups waiting on one barrier could each see a phase
+    // two ahead of the barrier as complete).
+    constexpr int NG = NC >= 2 ? 2 : 1;
+    static_assert(NG == 1 || (NC % 2 == 0 && NR % 2 == 0), "a slot per converter group");
     const int ct = threadIdx.x - 64;
-    const int grp = ct >> 7, gt = ct & 127;
+    const int grp = ct / (256 / NG), gt = ct % (256 / NG);
     const int c4 = gt >> 5, mq = gt & 31;
     bool go = true;
     for (int lt = 0, it = 0; lt < nlt && go; ++lt)
       for (int kb = 0; kb < nkb; ++kb, ++it) {
-        if ((it & 1) != grp) continue;
+        if (it % NG != grp) continue;
         const int s = it % NR, c = it % NC;
         const uint32_t ph = (uint32_t)(it / NR) & 1u, phc = (uint32_t)(it / NC) & 1u;
         bool ok = mbar_wait(&rfull[s], ph, abort_flag);
@@ -1082,8 +1094,8 @@ k_apply_tf32(const __grid_constant__ CUtensorMap tmY, const float* __restrict__ 
         const float* raw = (const float*)(smem + s * L::KB);  // column k at k * 128
         uint8_t* aop = conv_buf + c * L::CONV;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int cb = c4 + 4 * h;  // column block 4 cb .. 4 cb + 3
+        for (int h = 0; h < NG; ++h) {
+          const int cb = c4 + (8 / NG) * h;  // column block 4 cb .. 4 cb + 3
           float4 col[4];
 #pragma unroll
           for (int i = 0; i < 4; ++i)
@@ -1453,6 +1465,42 @@ void ypass_chunks(int64_t m, int want, size_t slice_elems, size_t part_elems, in
   *kchunk = kc;
 }
 
+// Work layout of a Y-pass over `tiles` row tiles that is not split over the
+// snapshots: whole waves of tiles in one launch, and -- when the last wave
+// would fill at most 60 % of the GPU, so that fewer than that many SMs draw
+// on HBM while it runs -- the last tiles alone in a second launch, each split
+// over the snapshots into the chunk count that leaves the fewest partly
+// filled waves (partials in `part`, summed into Y after).
+struct YTail {
+  int64_t full = 0;  // tiles of the first launch (all tiles when no tail launch)
+  int nst = 1;       // snapshot chunks of each tail tile (1: no tail launch)
+  int kchunk = 0;    // 64-snapshot k-tiles per chunk
+};
+
+YTail ypass_tail(int64_t tiles, int64_t m, int64_t rows_per_tile, int64_t n, int l, int per_wave,
+                 const float* part, size_t part_elems) {
+  YTail t;
+  t.full = tiles;
+  const int64_t full = tiles / per_wave * per_wave, tail = tiles - full;
+  if (!part || full == 0 || tail == 0 || tail * 10 > (int64_t)per_wave * 6) return t;
+  const int nk = (int)((m + 63) / 64);
+  int best = 1;
+  double best_w = 1.0;
+  for (int s = 2; s <= 8 && s <= nk; ++s) {
+    const double w = (double)((tail * s + per_wave - 1) / per_wave) / s;
+    if (w < best_w - 1e-9) { best_w = w; best = s; }
+  }
+  if (best == 1) return t;
+  const int kc = (nk + best - 1) / best;
+  best = (nk + kc - 1) / kc;
+  const int64_t trows = n - full * rows_per_tile;
+  if ((size_t)best * (size_t)trows * (size_t)l > part_elems) return t;
+  t.full = full;
+  t.nst = best;
+  t.kchunk = kc;
+  return t;
+}
+
 int tc_ypass(cudaStream_t st, int dt, const void* A, int64_t lda, const void* S, int64_t lds,
              int64_t n, int64_t m, int l, float* Y, int64_t ldy, unsigned* status, float* part,
              size_t part_elems, int stages) {
@@ -1464,29 +1512,44 @@ int tc_ypass(cudaStream_t st, int dt, const void* A, int64_t lda, const void* S,
   const size_t bytes = (size_t)n * (size_t)m * 2;
   int ns = 1, kchunk = 0;
   ypass_chunks(m, part ? ypass_split(tiles, m, bytes, 1) : 1, (size_t)n * l, part_elems, &ns, &kchunk);
-  float* out = ns > 1 ? part : Y;
-  const int64_t ldo = ns > 1 ? n : ldy;
-  const int64_t ysplit = ns > 1 ? n * l : 0;
-  dim3 grid((unsigned)tiles, (unsigned)ns);
   prepare_kernels_tc();
   const bool small = stages == 2 || (stages != 4 && bytes < kSmallPassBytes);
   using L = tc::Smem<kBN, kStages>;
   using Ls = tc::Smem<kBN, kStagesSmall>;
-  if (small) {
-    if (dt == RPOD_BF16)
-      tc::k_ypass<0, kBN, kStagesSmall><<<grid, 128, Ls::TOTAL, st>>>(ta, ts, n, m, l, out, ldo, status, kchunk, ysplit);
-    else
-      tc::k_ypass<1, kBN, kStagesSmall><<<grid, 128, Ls::TOTAL, st>>>(ta, ts, n, m, l, out, ldo, status, kchunk, ysplit);
-  } else {
-    if (dt == RPOD_BF16)
-      tc::k_ypass<0, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, out, ldo, status, kchunk, ysplit);
-    else
-      tc::k_ypass<1, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(ta, ts, n, m, l, out, ldo, status, kchunk, ysplit);
+  auto launch = [&](int64_t ntile, int nsy, int64_t tile0, float* out, int64_t ldo, int64_t ysplit,
+                    int kc) {
+    dim3 grid((unsigned)ntile, (unsigned)nsy);
+    if (small) {
+      if (dt == RPOD_BF16)
+        tc::k_ypass<0, kBN, kStagesSmall><<<grid, 128, Ls::TOTAL, st>>>(
+            ta, ts, n, m, l, out, ldo, status, kc, ysplit, tile0, tile0 * kBN);
+      else
+        tc::k_ypass<1, kBN, kStagesSmall><<<grid, 128, Ls::TOTAL, st>>>(
+            ta, ts, n, m, l, out, ldo, status, kc, ysplit, tile0, tile0 * kBN);
+    } else {
+      if (dt == RPOD_BF16)
+        tc::k_ypass<0, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(
+            ta, ts, n, m, l, out, ldo, status, kc, ysplit, tile0, tile0 * kBN);
+      else
+        tc::k_ypass<1, kBN, kStages><<<grid, 128, L::TOTAL, st>>>(
+            ta, ts, n, m, l, out, ldo, status, kc, ysplit, tile0, tile0 * kBN);
+    }
+    note_launch();
+    return cudaGetLastError() == cudaSuccess;
+  };
+  if (ns > 1) {
+    if (!launch(tiles, ns, 0, part, n, n * l, kchunk)) return RPOD_ERR_CUDA;
+    if (reduce_splits<float, float>(st, n, l, ns, part, Y, 1, ldy) != cudaSuccess) return RPOD_ERR_CUDA;
+    return RPOD_OK;
   }
-  note_launch();
-  if (cudaGetLastError() != cudaSuccess) return RPOD_ERR_CUDA;
-  if (ns > 1 && reduce_splits<float, float>(st, n, l, ns, part, Y, 1, ldy) != cudaSuccess)
-    return RPOD_ERR_CUDA;
+  const YTail t = ypass_tail(tiles, m, kBN, n, l, sm_count() * (small ? 2 : 1), part, part_elems);
+  if (!launch(t.full, 1, 0, Y, ldy, 0, kchunk)) return RPOD_ERR_CUDA;
+  if (t.nst > 1) {
+    const int64_t trows = n - t.full * kBN;
+    if (!launch(tiles - t.full, t.nst, t.full, part, trows, trows * l, t.kchunk)) return RPOD_ERR_CUDA;
+    if (reduce_splits<float, float>(st, trows, l, t.nst, part, Y + t.full * kBN, 1, ldy) != cudaSuccess)
+      return RPOD_ERR_CUDA;
+  }
   return RPOD_OK;
 }
 
@@ -1516,26 +1579,38 @@ int tc_ypass_cvt(cudaStream_t st, int dt, const void* A, int64_t lda, const floa
   CUtensorMap ta, tf;
   if (int rc = make_map(&ta, A, dt, m, l, lda, 64, 128)) return rc;
   if (int rc = make_map(&tf, S, RPOD_F32, n, m, lds, 32, 64)) return rc;
-  const int64_t tiles = (n + 127) / 128;
+  constexpr int64_t BN = 128;
+  const int64_t tiles = (n + BN - 1) / BN;
   int ns = 1, kchunk = 0;
   ypass_chunks(m, part ? ypass_split(tiles, m, (size_t)n * (size_t)m * 4, 1) : 1, (size_t)n * l,
                part_elems, &ns, &kchunk);
-  float* out = ns > 1 ? part : Y;
-  const int64_t ldo = ns > 1 ? n : ldy;
-  const int64_t ysplit = ns > 1 ? n * l : 0;
-  dim3 grid((unsigned)tiles, (unsigned)ns);
   using L = tc::YcvtSmem<kYcvtStages>;
   prepare_kernels_tc();
-  if (dt == RPOD_BF16)
-    tc::k_ypass_cvt<0, kYcvtStages><<<grid, 192, L::TOTAL, st>>>(ta, tf, n, m, l, out, ldo, Sh, ldh, status,
-                                                                  kchunk, ysplit);
-  else
-    tc::k_ypass_cvt<1, kYcvtStages><<<grid, 192, L::TOTAL, st>>>(ta, tf, n, m, l, out, ldo, Sh, ldh, status,
-                                                                  kchunk, ysplit);
-  note_launch();
-  if (cudaGetLastError() != cudaSuccess) return RPOD_ERR_CUDA;
-  if (ns > 1 && reduce_splits<float, float>(st, n, l, ns, part, Y, 1, ldy) != cudaSuccess)
-    return RPOD_ERR_CUDA;
+  auto launch = [&](int64_t ntile, int nsy, int64_t tile0, float* out, int64_t ldo, int64_t ysplit,
+                    int kc) {
+    dim3 grid((unsigned)ntile, (unsigned)nsy);
+    if (dt == RPOD_BF16)
+      tc::k_ypass_cvt<0, kYcvtStages><<<grid, 192, L::TOTAL, st>>>(
+          ta, tf, n, m, l, out, ldo, Sh, ldh, status, kc, ysplit, tile0, tile0 * BN);
+    else
+      tc::k_ypass_cvt<1, kYcvtStages><<<grid, 192, L::TOTAL, st>>>(
+          ta, tf, n, m, l, out, ldo, Sh, ldh, status, kc, ysplit, tile0, tile0 * BN);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess;
+  };
+  if (ns > 1) {
+    if (!launch(tiles, ns, 0, part, n, n * l, kchunk)) return RPOD_ERR_CUDA;
+    if (reduce_splits<float, float>(st, n, l, ns, part, Y, 1, ldy) != cudaSuccess) return RPOD_ERR_CUDA;
+    return RPOD_OK;
+  }
+  const YTail t = ypass_tail(tiles, m, BN, n, l, sm_count(), part, part_elems);
+  if (!launch(t.full, 1, 0, Y, ldy, 0, kchunk)) return RPOD_ERR_CUDA;
+  if (t.nst > 1) {
+    const int64_t trows = n - t.full * BN;
+    if (!launch(tiles - t.full, t.nst, t.full, part, trows, trows * l, t.kchunk)) return RPOD_ERR_CUDA;
+    if (reduce_splits<float, float>(st, trows, l, t.nst, part, Y + t.full * BN, 1, ldy) != cudaSuccess)
+      return RPOD_ERR_CUDA;
+  }
   return RPOD_OK;
 }
 

@@ -191,6 +191,35 @@ def test_basis_bf16_refine_65536_rows_matches_oracle():
     assert orth_err(U) <= 1e-5
 
 
+def test_basis_bf16_refine_tail_tiles_split_over_snapshots():
+    """Y-passes whose last wave of row tiles would fill at most 60 % of the
+    GPU run their whole waves in one launch and the last tiles, split over
+    the snapshots, in a second (partials summed into Y): n = 100352 rows
+    (392 tiles of 256 in the S Z passes, two CTAs per SM, 88 in the tail;
+    784 tiles of 128 in the first pass, 24 in the tail), m = 2000, k = 20,
+    p = 10, q = 2.  BF16 bounds against both oracles."""
+    # amplitudes j^-1.5 (the config-1 spectrum): sigma_20 / sigma_21 = 1.08,
+    # so span(U_k) is well separated at the BF16 error level
+    rec = make_recipe(256, 392, 2000, 400, ("power", 1.5), seed=3, noise=1e-6)
+    S = snapshot_matrix(rec, device="cuda", dtype=torch.float32)
+    k, p, q = 20, 10, 2
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert 0 < (rec.n // 256) % (2 * sms) <= 0.6 * 2 * sms
+    assert 0 < (rec.n // 128) % sms <= 0.6 * sms
+    plan = R.Plan(rec.n, rec.m, k, p, q, seed=0, compute="bf16", flags=R.RPOD_FLAG_REFINE_FP32)
+    U, sig, C = plan.basis(S)
+    assert plan.status()[0] == R.RPOD_OK
+    sig = sig.cpu().numpy()
+    U = U.double().cpu().numpy()
+    assert orth_err(U) <= 1e-5
+    S64 = S.cpu().double().numpy()
+    lowp, orig = _oracles(S64, k, p, q, "bf16")
+    for name, o in (("rounded-input", lowp), ("FP32-input", orig)):
+        err = np.abs(sig[:k] - o.sigma[:k]) / o.sigma[:k]
+        assert err.max() <= 1e-4, (name, err.max())
+        assert max_angle(o.U[:, :k], U) <= 1e-2, name
+
+
 def test_basis_bf16_refine_paper_shape_split_ypass():
     """The paper's own snapshot-matrix shape (Sec. 4.2, Table tab:cpu_time):
     n = 8192 grid cells (64 x 128), m = 90225 snapshots, k = 10, p = 75,
