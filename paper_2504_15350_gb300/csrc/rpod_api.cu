@@ -154,11 +154,12 @@ struct Run {
     if (sizeof(W) == 4) {
       // the exact kernel holds one CTA per SM: one wave of partials
       const int ns = fast ? nsplit : std::min(nsplit, tc_sm_count());
-      int rc = tc_gram(st, (const float*)A, lda, rows, l, dbuf(P->off_gpart), ns, status, !fast);
-      // FP32 working type: partials summed in FP64, the Gram stored in FP32
-      // for the FP32 Cholesky
+      float* fpart = (float*)dbuf(P->off_gpart);
+      int rc = tc_gram(st, (const float*)A, lda, rows, l, fpart, ns, status, !fast);
+      // FP32 working type: FP32 partials summed in FP64, the Gram stored in
+      // FP32 for the FP32 Cholesky
       if (rc == RPOD_OK) {
-        CK((reduce_splits<double, float>(st, l, l, ns, dbuf(P->off_gpart), (float*)G, 1, l)));
+        CK((reduce_splits<float, float>(st, l, l, ns, fpart, (float*)G, 1, l)));
         return RPOD_OK;
       }
       if (rc == RPOD_ERR_CUDA) return rc;
@@ -290,12 +291,14 @@ struct Run {
       CK(jacobi_svd(st, l, GT, Uhat, sigma, status, P->svd_sweeps));
     } else {
       // FP32 and 16-bit forms: FP32 start from the tridiagonal reduction
-      // (eigenvectors to about 1e-5), then two FP64 refinement passes, each
-      // of which squares the eigenvector error outside clusters
-      // (orthogonality near 1e-9); the cluster threshold of a pass scales
-      // with the norm of all remaining off-diagonal terms, so eigenvalues
-      // closer than that are separated only by a later pass
-      CK((sym_eig(st, l, GT, sigma, Uhat, dbuf(P->off_eig), status, 2)));
+      // (eigenvectors to about 1e-5), then FP64 refinement passes, each of
+      // which squares the eigenvector error outside clusters and restores
+      // orthogonality; the cluster threshold of a pass scales with the norm
+      // of all remaining off-diagonal terms, so eigenvalues closer than that
+      // are separated only by a later pass.  The 16-bit forms, whose passes
+      // over S hold sigma to 1e-4 (BF16) or 1e-5 (FP16), take one pass
+      // (eigenvector error near 1e-10); the FP32 form takes two.
+      CK((sym_eig(st, l, GT, sigma, Uhat, dbuf(P->off_eig), status, is16(P->compute) ? 1 : 2)));
     }
     CK((check_finite_vec(st, l, sigma, status)));
     // Alg. 1: lift U = Q Uhat (first k or all l columns), then the sign rule

@@ -2,45 +2,48 @@
 // left singular vectors of T are the eigenvectors of its l x l Gram matrix
 // G = T T^T, and the eigensolver refines a starting basis X in FP64
 // (Ogita-Aishima passes, rpod_simt.cu).  This file computes that start in
-// FP32 with one CTA:
+// FP32 in four launches:
 //
-//   1. G / max_i G_ii in FP32; Householder reduction to tridiagonal form
-//      A = H T H^T (lower variant: column 0 first, so a matrix whose large
-//      entries sit at the top left -- the Gram of a power-iterated basis --
-//      keeps its small eigenvalues' relative accuracy).
-//   2. Eigenvalues of the tridiagonal T by multisection on Sturm counts
-//      (the number of negative pivots of the LDL^T factorization of T - x I
-//      is the number of eigenvalues below x): one pass of 1024 counts at
-//      geometrically spaced points brackets every eigenvalue to a few
-//      percent, then 4 points per step and per eigenvalue narrow each
-//      bracket to a relative width of two ulps.  The counts use
-//      IEEE infinities in place of a pivot threshold (a zero pivot gives an
+//   1. (one CTA) G / max_i G_ii in FP32; Householder reduction to
+//      tridiagonal form A = H T H^T (lower variant: column 0 first, so a
+//      matrix whose large entries sit at the top left -- the Gram of a
+//      power-iterated basis -- keeps its small eigenvalues' relative
+//      accuracy).  The diagonal and off-diagonal of T, the reflector
+//      vectors and their factors go to a scratch buffer.
+//   2. (one CTA per eight eigenvalues) Eigenvalues of T by multisection on
+//      Sturm counts (the number of negative pivots of the LDL^T
+//      factorization of T - x I is the number of eigenvalues below x): one
+//      pass of 256 counts at geometrically spaced points brackets every
+//      eigenvalue, then a warp per eigenvalue narrows its bracket with 32
+//      points per step to a relative width of two ulps.  The counts use IEEE
+//      infinities in place of a pivot threshold (a zero pivot gives an
 //      infinite next pivot, counted by its sign bit), with e_k^2 kept at or
 //      above the smallest normal number so that no 0/0 arises.
-//   3. Eigenvectors of T from twisted factorizations (Dhillon and Parlett,
+//      Eigenvectors of T from twisted factorizations (Dhillon and Parlett,
 //      "Multiple representations to compute orthogonal eigenvectors of
 //      symmetric tridiagonal matrices", Lin. Alg. Appl. 387, 2004): with the
 //      forward pivots D+ and backward pivots D- of T - lambda I, the twist
 //      index r minimising |gamma_r|, gamma_r = D+_r - e_r^2 / D-_{r+1},
 //      gives the vector with x_r = 1 by two one-term recurrences.  Two
-//      threads per eigenvalue: one runs the forward recurrences, one the
-//      backward ones.
-//   4. Vectors of eigenvalues closer than 1e-5 ||T|| are orthogonalised
-//      against each other (Gram-Schmidt in ascending order); a
-//      vector that loses more than half its norm there (a multiple
+//      threads per eigenvalue, in different warps: one runs the forward
+//      recurrences, one the backward ones.
+//   3. (one CTA) Vectors of eigenvalues closer than 1e-5 ||T|| are
+//      orthogonalised against each other (Gram-Schmidt in ascending order);
+//      a vector that loses more than half its norm there (a multiple
 //      eigenvalue) is replaced by inverse iteration with T - lambda I from
 //      a pseudo-random vector, orthogonalised against the cluster's other
-//      vectors.  Vectors of eigenvalues further apart come out
-//      of step 3 orthogonal to a few 1e-5 at most, which the refinement
-//      removes.
-//   5. Back-transformation X = H Z, column by column, each column held in
-//      the registers of 8 threads.
+//      vectors.  Vectors of eigenvalues further apart come out of step 2
+//      orthogonal to a few 1e-5 at most, which the refinement removes;
+//      without a cluster this launch ends after the gap test.
+//   4. (one CTA per 32 columns) Back-transformation X = H Z, each pair of
+//      columns held in the registers of 16 threads.
 //
 // Step 1 keeps the rows of A as float4 (four consecutive rows per warp, the
 // reduced rows replaced by the full reflector vectors, zeros included), so
 // that the matrix-vector product, the rank-2 update and the
 // back-transformation run on 16-byte shared-memory accesses without
-// per-element bounds tests.
+// per-element bounds tests.  Steps 2 and 4 spread the independent
+// per-eigenvalue and per-column work over many SMs.
 //
 // The FP64 refinement that follows squares the error of this start per
 // pass; its accuracy, not this one's, sets the final result.
@@ -52,18 +55,24 @@
 namespace rpod {
 namespace {
 
-constexpr int kEigThreads = 1024;
-constexpr int kGrp = 8;  // threads per eigenvalue (multisection) and per column (back-transform)
+constexpr int kEigThreads = 1024;  // tridiagonalization and cluster kernels
+constexpr int kVecThreads = 256;   // eigenvalue / eigenvector kernel
+constexpr int kEpb = 8;            // eigenvalues per CTA of that kernel
+constexpr int kBackThreads = 256;  // back-transformation: 16 column pairs per CTA
+constexpr int kBackCols = 32;
 
-// Rows of A start on 16-byte boundaries; Xs/Ws use a leading dimension of
-// 1 mod 32, so that a column, a row and the back-transform's 4 columns x 8
-// row groups each fall in distinct banks.
+// Rows of A start on 16-byte boundaries; the cluster pass's Z uses a leading
+// dimension of 1 mod 32, so that a column and a row each fall in distinct
+// banks.
 __host__ __device__ inline int eig_lda(int l) { return (l + 3) & ~3; }
 __host__ __device__ inline int eig_ldx(int l) { return ((l + 31) & ~31) + 1; }
 
-size_t eig_smem_bytes(int l) {
-  return sizeof(float) * ((size_t)l * eig_lda(l) + 12 * (size_t)kMaxL + 2 * (size_t)l * eig_ldx(l));
-}
+// Shared memory of the tridiagonalization (A, reflector and p buffers, d, e,
+// tau), the cluster pass (Z and the dot-product buffer) and the
+// back-transformation (the reflector rows).
+size_t tri_smem_bytes(int l) { return sizeof(float) * ((size_t)l * eig_lda(l) + 7 * (size_t)kMaxL); }
+size_t clu_smem_bytes(int l) { return sizeof(float) * ((size_t)l * eig_ldx(l) + (size_t)kMaxL); }
+size_t back_smem_bytes(int l) { return sizeof(float) * (size_t)l * eig_lda(l); }
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -93,9 +102,11 @@ __device__ __forceinline__ unsigned sturm_count(const float2* de, int l, float x
   return c;
 }
 
-constexpr int kBrk = 1024;  // bracketing points (one per thread)
-constexpr int kMs = 4;      // threads (points) per eigenvalue in the multisection
-static_assert(kBrk == kEigThreads, "one bracketing point per thread");
+constexpr int kBrk = 256;  // bracketing points (one per thread)
+constexpr int kMs = 32;    // points per eigenvalue and multisection step (a warp)
+static_assert(kBrk == kVecThreads, "one bracketing point per thread");
+static_assert(kEpb * kMs <= kVecThreads, "multisection threads");
+static_assert(kEpb <= 32, "one lane per eigenvalue in the vector recurrences");
 
 __device__ __forceinline__ float brk_point(float bn, int i) {
   return bn * exp2f(40.f * ((float)i * (1.f / (kBrk - 1)) - 1.f));
@@ -147,26 +158,22 @@ __device__ __forceinline__ void reflector(int j, int lda, const float4& x, int l
   }
 }
 
+// Step 1: G scaled to FP32, Householder tridiagonalization; T's diagonal
+// and off-diagonal, the reflector rows (row j = v_j) and their factors tau_j
+// are written to the scratch buffer.
 __global__ void __launch_bounds__(kEigThreads)
-k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
-                unsigned* __restrict__ status) {
+k_eig_tri(int l, const double* __restrict__ G, float* __restrict__ sA, float* __restrict__ sd,
+          float* __restrict__ se, float* __restrict__ stau) {
   extern __shared__ float4 sm4[];
-  const int lda = eig_lda(l), ldx = eig_ldx(l);
+  const int lda = eig_lda(l);
   float* const A = reinterpret_cast<float*>(sm4);  // l x lda
   float* const vs = A + (size_t)l * lda;           // [2][kMaxL] reflector vectors
   float* const psb = vs + 2 * kMaxL;               // [2][kMaxL] p = tau A22 v
-  float2* const de = reinterpret_cast<float2*>(psb + 2 * kMaxL);  // (d_k, e_{k-1}^2)
-  float* const dd = psb + 4 * kMaxL;               // diagonal of T
+  float* const dd = psb + 2 * kMaxL;               // diagonal of T
   float* const ee = dd + kMaxL;                    // off-diagonal of T
   float* const tau = ee + kMaxL;
-  float* const lam = tau + kMaxL;
-  float* const Xs = lam + kMaxL;                   // eigenvectors of T: row r at r*ldx
-  float* const Ws = Xs + (size_t)l * ldx;          // forward pivots per eigenvalue
   __shared__ double s_red[32];
-  __shared__ float s_bnd[3];
-  __shared__ unsigned s_cnt[kBrk];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
-  const float pivmin = 1e-30f;
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
 
   // ---- 1. A = G / max_i G_ii (FP32, zero padding columns); p buffers
@@ -301,7 +308,36 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
   }
   __syncthreads();
 
-  // ---- 3. eigenvalues of T (ascending) by multisection
+  // T and the reflectors to the scratch buffer
+  for (int e = tid; e < l * lda / 4; e += nt)
+    reinterpret_cast<float4*>(sA)[e] = reinterpret_cast<const float4*>(A)[e];
+  for (int k = tid; k < l; k += nt) {
+    sd[k] = dd[k];
+    se[k] = k + 1 < l ? ee[k] : 0.f;
+    stau[k] = k + 1 < l ? tau[k] : 0.f;
+  }
+}
+
+// Step 2: eigenvalues g0 .. g0 + kEpb - 1 of T (g0 = kEpb blockIdx.x) and
+// their eigenvectors, written as columns of Z (ld l) and to lam.
+__global__ void __launch_bounds__(kVecThreads)
+k_eig_vec(int l, const float* __restrict__ sd, const float* __restrict__ se, float* __restrict__ Z,
+          float* __restrict__ slam) {
+  __shared__ float dd[kMaxL], ee[kMaxL];
+  __shared__ float2 de[kMaxL];
+  __shared__ float lam[kEpb];
+  __shared__ float s_bnd[3];
+  __shared__ unsigned s_cnt[kBrk];
+  constexpr int ldx = kEpb + 1;  // pivots and vectors of the CTA's eigenvalues: row k at k * ldx
+  __shared__ float Ws[kMaxL * ldx], Xs[kMaxL * ldx];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+  const int g0 = kEpb * blockIdx.x;
+  const float pivmin = 1e-30f;
+  for (int k = tid; k < l; k += blockDim.x) {
+    dd[k] = sd[k];
+    ee[k] = se[k];
+  }
+  __syncthreads();
   for (int k = tid; k < l; k += nt)
     de[k] = make_float2(dd[k], k > 0 ? fmaxf(ee[k - 1] * ee[k - 1], FLT_MIN) : 0.f);
   if (warp == 0) {
@@ -324,16 +360,16 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
   __syncthreads();
   // bracketing pass: every thread counts the eigenvalues below one of
   // kBrk points spaced geometrically over 2^-40 bn .. bn (the eigenvalues of
-  // a power-iterated Gram spread over decades; ratio 1.028 between points)
+  // a power-iterated Gram spread over decades; ratio 1.115 between points)
   {
     const float bn = s_bnd[2];
     s_cnt[tid] = tid < kBrk ? sturm_count(de, l, brk_point(bn, tid)) : 0u;
   }
   __syncthreads();
   {
-    const int g = tid / kMs, t4 = tid % kMs;
-    const unsigned gmask = 0xFu << (lane & 28);
-    if (g < l) {
+    // one warp per eigenvalue: kMs = 32 points per step (5 bits)
+    const int gl = warp, g = g0 + gl;
+    if (gl < kEpb && g < l) {
       // first point whose count exceeds g (binary search: the points on
       // either side of the result were both probed, so lambda_g lies
       // between them even where rounding makes the counts non-monotone)
@@ -349,33 +385,38 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
       for (int it = 0; it < 40; ++it) {
         if (hi - lo <= fmaf(2.4e-7f, fmaxf(fabsf(lo), fabsf(hi)), atol)) break;
         const float h = (hi - lo) * (1.f / (kMs + 1));
-        const unsigned c = sturm_count(de, l, fmaf(h, (float)(t4 + 1), lo));
-        const unsigned bits = (__ballot_sync(gmask, c > (unsigned)g) >> (lane & 28)) & 0xFu;
+        const unsigned c = sturm_count(de, l, fmaf(h, (float)(lane + 1), lo));
+        const unsigned bits = __ballot_sync(0xffffffffu, c > (unsigned)g);
         const int tt = bits ? __ffs(bits) - 1 : kMs;
         const float nlo = tt == 0 ? lo : fmaf(h, (float)tt, lo);
         const float nhi = tt == kMs ? hi : fmaf(h, (float)(tt + 1), lo);
         lo = nlo;
         hi = nhi;
       }
-      if (t4 == 0) lam[g] = 0.5f * (lo + hi);
+      if (lane == 0) lam[gl] = 0.5f * (lo + hi);
     }
   }
   __syncthreads();
 
-  // ---- 4. eigenvectors of T by twisted factorizations: threads 2i (forward
-  // pivots D+, into Ws) and 2i+1 (backward pivots D-, into Xs) for lambda_i
+  // eigenvectors of T by twisted factorizations: lane il of warp 0 runs the
+  // forward pivots D+ (into Ws) and the vector above the twist index, lane
+  // il of warp 1 the backward pivots D- (into Xs) and the vector below it,
+  // for lambda_il (two warps, so the two recurrences run side by side)
   {
-    const int i = tid >> 1;
-    const bool fwd = !(tid & 1);
-    if (i < l) {
-      const float lm = lam[i];
-      float* const Dp = Ws + i;
-      float* const Xc = Xs + i;
+    __shared__ float s_gb[2][kEpb], s_n2[2][kEpb];
+    __shared__ int s_r[2][kEpb];
+    const bool fwd = warp == 0;
+    const int il = lane;
+    const bool act = warp < 2 && il < kEpb && g0 + il < l;
+    float* const Dp = Ws + il;
+    float* const Xc = Xs + il;
+    const float lm = act ? lam[il] : 0.f;
+    if (act) {
       if (fwd) {
         float q = dd[0] - lm;
         if (fabsf(q) < pivmin) q = -pivmin;
         Dp[0] = q;
-        #pragma unroll 4
+#pragma unroll 4
         for (int k = 1; k < l; ++k) {
           q = (dd[k] - lm) - __fdividef(de[k].y, q);
           if (fabsf(q) < pivmin) q = -pivmin;
@@ -385,68 +426,119 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
         float q = dd[l - 1] - lm;
         if (fabsf(q) < pivmin) q = -pivmin;
         Xc[(l - 1) * ldx] = q;
-        #pragma unroll 4
+#pragma unroll 4
         for (int k = l - 2; k >= 0; --k) {
           q = (dd[k] - lm) - __fdividef(de[k + 1].y, q);
           if (fabsf(q) < pivmin) q = -pivmin;
           Xc[k * ldx] = q;
         }
       }
-      __syncwarp(3u << (lane & 30));
-      // twist index: gamma_k = D+_k - e_k^2 / D-_{k+1} (gamma_{l-1} = D+_{l-1});
-      // the forward thread scans k < l/2, the backward one the rest
+    }
+    __syncthreads();
+    // twist index: gamma_k = D+_k - e_k^2 / D-_{k+1} (gamma_{l-1} = D+_{l-1});
+    // the forward lane scans k < l/2, the backward one the rest
+    if (act) {
       const int h = l >> 1;
       float gb = FLT_MAX;
       int r = l;
-      #pragma unroll 4
+#pragma unroll 4
       for (int k = fwd ? 0 : h; k < (fwd ? h : l); ++k) {
         const float gk = k + 1 < l ? Dp[k * ldx] - __fdividef(de[k + 1].y, Xc[(k + 1) * ldx])
                                    : Dp[k * ldx];
         if (fabsf(gk) < gb) { gb = fabsf(gk); r = k; }
       }
-      const unsigned pmask = 3u << (lane & 30);
-      const float gbo = __shfl_xor_sync(pmask, gb, 1);
-      const int ro = __shfl_xor_sync(pmask, r, 1);
-      if (gbo < gb || (gbo == gb && ro < r)) r = ro;
+      s_gb[warp][il] = gb;
+      s_r[warp][il] = r;
+    }
+    __syncthreads();
+    int r = l;
+    if (act) {
+      const float g0v = s_gb[0][il], g1v = s_gb[1][il];
+      const int r0 = s_r[0][il], r1 = s_r[1][il];
+      r = (g1v < g0v || (g1v == g0v && r1 < r0)) ? r1 : r0;
       if (r >= l) r = 0;  // every gamma non-finite: any twist index will do
-      __syncwarp(pmask);
-      float xv = 1.f, n2 = 0.f;
+    }
+    __syncthreads();  // the pivots read by the twist scan are overwritten below
+    float n2 = 0.f;
+    if (act) {
+      float xv = 1.f;
       if (fwd) {
         Xc[r * ldx] = 1.f;
         n2 = 1.f;
-        #pragma unroll 4
         for (int k = r - 1; k >= 0; --k) {
           xv = -__fdividef(ee[k], Dp[k * ldx]) * xv;
           Xc[k * ldx] = xv;
           n2 = fmaf(xv, xv, n2);
         }
       } else {
-        #pragma unroll 4
         for (int k = r; k + 1 < l; ++k) {
           xv = -__fdividef(ee[k], Xc[(k + 1) * ldx]) * xv;
           Xc[(k + 1) * ldx] = xv;
           n2 = fmaf(xv, xv, n2);
         }
       }
-      n2 += __shfl_xor_sync(pmask, n2, 1);
-      __syncwarp(pmask);
+      s_n2[warp][il] = n2;
+    }
+    __syncthreads();
+    if (act) {
+      n2 = s_n2[0][il] + s_n2[1][il];
       if (!(n2 <= FLT_MAX)) {  // overflow: e_r instead (the cluster pass may replace it)
         for (int k = fwd ? 0 : 1; k < l; k += 2) Xc[k * ldx] = k == r ? 1.f : 0.f;
       } else {
-        const float s = rsqrtf(n2);
+        const float sc = rsqrtf(n2);
         if (fwd) {
-          #pragma unroll 4
-          for (int k = 0; k <= r; ++k) Xc[k * ldx] *= s;
+          for (int k = 0; k <= r; ++k) Xc[k * ldx] *= sc;
         } else {
-          #pragma unroll 4
-          for (int k = r + 1; k < l; ++k) Xc[k * ldx] *= s;
+          for (int k = r + 1; k < l; ++k) Xc[k * ldx] *= sc;
         }
       }
     }
   }
   __syncthreads();
 
-  // ---- 5. orthogonalise vectors of close eigenvalues.  Per vector a of a
+  // the CTA's vectors to Z and its eigenvalues to lam
+  for (int e = tid; e < kEpb * l; e += blockDim.x) {
+    const int el = e / l, r = e - el * l;
+    if (g0 + el < l) Z[r + (size_t)(g0 + el) * l] = Xs[r * ldx + el];
+  }
+  if (tid < kEpb && g0 + tid < l) slam[g0 + tid] = lam[tid];
+}
+
+// Step 3: vectors of clustered eigenvalues (Z in place); without a cluster
+// the kernel ends after the gap test.
+__global__ void __launch_bounds__(kEigThreads)
+k_eig_cluster(int l, const float* __restrict__ sd, const float* __restrict__ se,
+              const float* __restrict__ slam, float* __restrict__ Z, unsigned* __restrict__ status) {
+  extern __shared__ float4 sm4[];
+  const int ldx = eig_ldx(l);
+  float* const Xs = reinterpret_cast<float*>(sm4);  // Z: row r at r * ldx
+  float* const Ws = Xs + (size_t)l * ldx;           // dot products
+  __shared__ float lam[kMaxL], dd[kMaxL], ee[kMaxL];
+  __shared__ int s_any;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+  if (tid == 0) s_any = 0;
+  for (int k = tid; k < l; k += nt) {
+    lam[k] = slam[k];
+    dd[k] = sd[k];
+    ee[k] = se[k];
+  }
+  __syncthreads();
+  {
+    const float ctol = fmaxf(1e-5f * fmaxf(fabsf(lam[0]), fabsf(lam[l - 1])), 1e-15f);
+    for (int i = tid + 1; i < l; i += nt)
+      if (lam[i] - lam[i - 1] <= ctol) s_any = 1;
+  }
+  __syncthreads();
+  if (!s_any) {
+    if (tid == 0) status[4] = 0u;
+    return;
+  }
+  for (int e = tid; e < l * l; e += nt) {
+    const int g = e / l, r = e - g * l;
+    Xs[r * ldx + g] = Z[e];
+  }
+  __syncthreads();
+  // orthogonalise vectors of close eigenvalues.  Per vector a of a
   // cluster, two classical Gram-Schmidt passes against the cluster's
   // earlier (already orthonormal) vectors: the dots by one warp each, the
   // update by 16 threads per row.  A vector that loses more than half its
@@ -612,7 +704,29 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
     if (tid == 0) status[4] = (unsigned)nrep;
   }
 
-  // ---- 6. back-transformation X = H_0 ... H_{l-2} Z: 16 threads per pair
+  __syncthreads();
+  for (int e = tid; e < l * l; e += nt) {
+    const int g = e / l, r = e - g * l;
+    Z[e] = Xs[r * ldx + g];
+  }
+}
+
+// Step 4: X = H_0 ... H_{l-2} Z for columns kBackCols blockIdx.x .. + 31,
+// with the reflector rows in shared memory.
+__global__ void __launch_bounds__(kBackThreads)
+k_eig_back(int l, const float* __restrict__ sA, const float* __restrict__ stau,
+           const float* __restrict__ Z, double* __restrict__ Xout) {
+  extern __shared__ float4 sm4[];
+  const int lda = eig_lda(l);
+  float* const A = reinterpret_cast<float*>(sm4);  // reflector rows, row j at j * lda
+  __shared__ float tau[kMaxL];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int e = tid; e < l * lda / 4; e += blockDim.x)
+    reinterpret_cast<float4*>(A)[e] = reinterpret_cast<const float4*>(sA)[e];
+  for (int k = tid; k < l; k += blockDim.x) tau[k] = stau[k];
+  __syncthreads();
+  // back-transformation X = H_0 ... H_{l-2} Z: 16 threads per pair
   // of columns, thread t16 holding rows 64u + 4 t16 + i (u < 2, i < 4) of
   // both in registers, so that each reflector row read from shared memory
   // serves two columns; row j of A is the full vector v_j.  The two dot
@@ -621,7 +735,7 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
   // broadcasts.
   {
     const int cp = tid >> 4, t16 = tid & 15;
-    const int c = 2 * cp;
+    const int c = kBackCols * blockIdx.x + 2 * cp;
     const unsigned gmask = 0xFFFFu << (lane & 16);
     if (c < l) {
       const bool two = c + 1 < l;
@@ -631,8 +745,8 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int r = 64 * u + 4 * t16 + i;
-          xa[4 * u + i] = r < l ? Xs[r * ldx + c] : 0.f;
-          xb[4 * u + i] = (r < l && two) ? Xs[r * ldx + c + 1] : 0.f;
+          xa[4 * u + i] = r < l ? Z[r + (size_t)c * l] : 0.f;
+          xb[4 * u + i] = (r < l && two) ? Z[r + (size_t)(c + 1) * l] : 0.f;
         }
       const bool hi8 = lane & 8;
       const int base = lane & 16;
@@ -686,16 +800,38 @@ k_tridiag_eig32(int l, const double* __restrict__ G, double* __restrict__ Xout,
 
 }  // namespace
 
-cudaError_t tridiag_eig32(cudaStream_t st, int l, const double* G, double* X, unsigned* status) {
+size_t eig_scratch_floats(int l) {
+  return (size_t)l * eig_lda(l) + (size_t)l * l + 4 * (size_t)kMaxL;
+}
+
+cudaError_t tridiag_eig32(cudaStream_t st, int l, const double* G, double* X, float* scratch,
+                          unsigned* status) {
   if (l < 1 || l > kMaxL) return cudaErrorInvalidValue;
-  k_tridiag_eig32<<<1, kEigThreads, eig_smem_bytes(l), st>>>(l, G, X, status);
+  float* const sA = scratch;                        // l x lda reflector rows
+  float* const sZ = sA + (size_t)l * eig_lda(l);    // l x l eigenvectors of T
+  float* const sd = sZ + (size_t)l * l;
+  float* const se = sd + kMaxL;
+  float* const stau = se + kMaxL;
+  float* const slam = stau + kMaxL;
+  k_eig_tri<<<1, kEigThreads, tri_smem_bytes(l), st>>>(l, G, sA, sd, se, stau);
+  note_launch();
+  k_eig_vec<<<(l + kEpb - 1) / kEpb, kVecThreads, 0, st>>>(l, sd, se, sZ, slam);
+  note_launch();
+  k_eig_cluster<<<1, kEigThreads, clu_smem_bytes(l), st>>>(l, sd, se, slam, sZ, status);
+  note_launch();
+  k_eig_back<<<(l + kBackCols - 1) / kBackCols, kBackThreads, back_smem_bytes(l), st>>>(l, sA, stau,
+                                                                                      sZ, X);
   note_launch();
   return cudaGetLastError();
 }
 
 void prepare_eig_kernels() {
-  cudaFuncSetAttribute(k_tridiag_eig32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)eig_smem_bytes(kMaxL));
+  cudaFuncSetAttribute(k_eig_tri, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)tri_smem_bytes(kMaxL));
+  cudaFuncSetAttribute(k_eig_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)clu_smem_bytes(kMaxL));
+  cudaFuncSetAttribute(k_eig_back, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)back_smem_bytes(kMaxL));
 }
 
 }  // namespace rpod

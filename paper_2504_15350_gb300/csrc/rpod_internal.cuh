@@ -103,7 +103,9 @@ cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma,
 // one CTA: Householder tridiagonalization, multisection, twisted
 // factorizations.  Writes the number of replaced vectors of multiple
 // eigenvalues to status[4] (diagnostic).
-cudaError_t tridiag_eig32(cudaStream_t st, int l, const double* G, double* X, unsigned* status);
+cudaError_t tridiag_eig32(cudaStream_t st, int l, const double* G, double* X, float* scratch,
+                          unsigned* status);
+size_t eig_scratch_floats(int l);
 size_t sym_eig_work_doubles(int l);
 
 // Relatively accurate small SVD from the Gram G = T T^T (l x l, FP64) of a

@@ -306,29 +306,54 @@ INST_GEMM(float, __nv_bfloat16, float, float)
 // FP64 form) in FP64, FP32 partials in FP32 (GB300 issues FP64 adds at
 // 1/64 of the FP32 rate, which made an FP64-accumulating FP32 reduction
 // arithmetic-bound).
+// Knuth's TwoSum: s + x = t + err exactly; used to carry the rounding error
+// of FP32 sums in a second word (FP64 sums of many FP32 values would run at
+// GB300's narrow FP64 rate, and so would the conversions to FP64).
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+  const float t = s + x;
+  const float bp = t - s;
+  c += (s - (t - bp)) + (x - bp);
+  s = t;
+}
+
 template <typename TP, typename TO>
 __global__ void __launch_bounds__(256)
 k_reduce(int64_t M, int64_t N, int nsplit, const TP* __restrict__ part, TO* __restrict__ out,
          int64_t oi, int64_t oj) {
-  __shared__ TP acc[8][33];
+  // FP64 partials: FP64 sums; FP32 partials: compensated FP32 sums (about
+  // as accurate as FP64 ones for these counts), combined in FP64
+  __shared__ double acc[8][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t idx = (int64_t)blockIdx.x * 32 + tx;
   const int64_t MN = M * N;
-  TP s0 = TP(0), s1 = TP(0), s2 = TP(0), s3 = TP(0);
+  double tot = 0.0;
   if (idx < MN) {
-    int z = ty;
-    for (; z + 24 < nsplit; z += 32) {
-      s0 += part[(int64_t)z * MN + idx];
-      s1 += part[(int64_t)(z + 8) * MN + idx];
-      s2 += part[(int64_t)(z + 16) * MN + idx];
-      s3 += part[(int64_t)(z + 24) * MN + idx];
+    if (sizeof(TP) == 8) {
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int z = ty;
+      for (; z + 24 < nsplit; z += 32) {
+        s0 += (double)part[(int64_t)z * MN + idx];
+        s1 += (double)part[(int64_t)(z + 8) * MN + idx];
+        s2 += (double)part[(int64_t)(z + 16) * MN + idx];
+        s3 += (double)part[(int64_t)(z + 24) * MN + idx];
+      }
+      for (; z < nsplit; z += 8) s0 += (double)part[(int64_t)z * MN + idx];
+      tot = (s0 + s1) + (s2 + s3);
+    } else {
+      float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+      int z = ty;
+      for (; z + 8 < nsplit; z += 16) {
+        two_sum_acc(s0, c0, (float)part[(int64_t)z * MN + idx]);
+        two_sum_acc(s1, c1, (float)part[(int64_t)(z + 8) * MN + idx]);
+      }
+      for (; z < nsplit; z += 8) two_sum_acc(s0, c0, (float)part[(int64_t)z * MN + idx]);
+      tot = ((double)s0 + (double)s1) + ((double)c0 + (double)c1);
     }
-    for (; z < nsplit; z += 8) s0 += part[(int64_t)z * MN + idx];
   }
-  acc[ty][tx] = (s0 + s1) + (s2 + s3);
+  acc[ty][tx] = tot;
   __syncthreads();
   if (ty == 0 && idx < MN) {
-    TP t = TP(0);
+    double t = 0.0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) t += acc[k][tx];
     const int64_t j = idx / M, i = idx - j * M;
@@ -337,8 +362,8 @@ k_reduce(int64_t M, int64_t N, int nsplit, const TP* __restrict__ part, TO* __re
 }
 
 // Up to 32 splits (the W-pass partials): each thread sums four consecutive
-// elements over z in order (16-byte loads of FP32 partials when aligned),
-// with eight splits in flight.
+// elements over z in order (16-byte loads of FP32 partials when aligned,
+// compensated FP32 sums), with eight splits in flight.
 template <typename TP, typename TO>
 __global__ void __launch_bounds__(256)
 k_reduce_flat(int64_t M, int64_t N, int nsplit, const TP* __restrict__ part, TO* __restrict__ out,
@@ -348,8 +373,10 @@ k_reduce_flat(int64_t M, int64_t N, int nsplit, const TP* __restrict__ part, TO*
   if (idx0 >= MN) return;
   TP s[4] = {TP(0), TP(0), TP(0), TP(0)};
   if (vec && idx0 + 4 <= MN) {
+    // FP32 partials: compensated FP32 sums (TwoSum), the error words added
+    // at the end
     const float* pf = reinterpret_cast<const float*>(part);
-    float f[4] = {0.f, 0.f, 0.f, 0.f};
+    float f[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
     int z = 0;
     for (; z + 8 <= nsplit; z += 8) {
       float4 v[8];
@@ -357,15 +384,21 @@ k_reduce_flat(int64_t M, int64_t N, int nsplit, const TP* __restrict__ part, TO*
       for (int u = 0; u < 8; ++u) v[u] = *(const float4*)(pf + (int64_t)(z + u) * MN + idx0);
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        f[0] += v[u].x; f[1] += v[u].y; f[2] += v[u].z; f[3] += v[u].w;
+        two_sum_acc(f[0], c[0], v[u].x);
+        two_sum_acc(f[1], c[1], v[u].y);
+        two_sum_acc(f[2], c[2], v[u].z);
+        two_sum_acc(f[3], c[3], v[u].w);
       }
     }
     for (; z < nsplit; ++z) {
       const float4 v = *(const float4*)(pf + (int64_t)z * MN + idx0);
-      f[0] += v.x; f[1] += v.y; f[2] += v.z; f[3] += v.w;
+      two_sum_acc(f[0], c[0], v.x);
+      two_sum_acc(f[1], c[1], v.y);
+      two_sum_acc(f[2], c[2], v.z);
+      two_sum_acc(f[3], c[3], v.w);
     }
 #pragma unroll
-    for (int e = 0; e < 4; ++e) s[e] = (TP)f[e];
+    for (int e = 0; e < 4; ++e) s[e] = (TP)(f[e] + c[e]);
   } else {
     for (int z = 0; z < nsplit; ++z)
 #pragma unroll
@@ -1138,8 +1171,9 @@ static unsigned oa_blocks(int l) {
 }
 
 size_t sym_eig_work_doubles(int l) {
-  // V/X, XtX, AX, S, E, XE, lam, normA, split partials (8 splits of l*l)
-  return (size_t)l * l * (6 + 8) + 2 * (size_t)l + 8;
+  // V/X, XtX, AX, S, E, XE, lam, normA, split partials (8 splits of l*l),
+  // then the FP32 scratch of the starting eigenvectors
+  return (size_t)l * l * (6 + 8) + 2 * (size_t)l + 8 + (eig_scratch_floats(l) + 1) / 2 + 2;
 }
 
 cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma, double* Uhat,
@@ -1154,10 +1188,13 @@ cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma, doub
   double* part = XE + ll;  // 8 * ll
   double* lam = part + 8 * ll;
   double* normA = lam + l;
+  // 16-byte aligned FP32 scratch after normA (the work buffer is aligned)
+  const size_t esc_off = (size_t)(normA + 8 - work + 1) & ~(size_t)1;
+  float* esc = reinterpret_cast<float*>(work + esc_off);
   prepare_kernels();
-  cudaError_t e = tridiag_eig32(st, l, G, X, status);
+  cudaError_t e = tridiag_eig32(st, l, G, X, esc, status);
   if (e != cudaSuccess) return e;
-  k_frob<<<1, 256, 0, st>>>((int64_t)ll, G, normA); note_launch();
+  k_frob<<<1, 1024, 0, st>>>((int64_t)ll, G, normA); note_launch();
   // normA is needed on the device only: pass through a tiny kernel chain
   const int nsp = l > 64 ? 8 : 4;
   for (int it = 0; it < refine_iters; ++it) {

@@ -447,7 +447,7 @@ struct GramSmem {
 template <int STAGES>
 __global__ void __launch_bounds__(192, 1)
 k_gram3(const __grid_constant__ CUtensorMap tmY, int64_t rows, int l, int kchunk,
-        double* __restrict__ part, unsigned* status) {
+        float* __restrict__ part, unsigned* status) {
   using L = GramSmem<STAGES>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align_smem1024(smem_raw);
@@ -539,7 +539,7 @@ k_gram3(const __grid_constant__ CUtensorMap tmY, int64_t rows, int l, int kchunk
     tc_after();
     const int q = warp & 3;  // TMEM lane quarter this warp may read
     const int c = q * 32 + lane;
-    double* pz = part + (int64_t)blockIdx.x * l * l;
+    float* pz = part + (int64_t)blockIdx.x * l * l;
     for (int cc = 0; cc < 128; cc += 32) {
       float v[32];
       if (nk > 0 && ok) {
@@ -551,7 +551,7 @@ k_gram3(const __grid_constant__ CUtensorMap tmY, int64_t rows, int l, int kchunk
       if (c < l) {
 #pragma unroll
         for (int i = 0; i < 32; ++i)
-          if (cc + i < l) pz[c + (int64_t)(cc + i) * l] = (double)v[i];
+          if (cc + i < l) pz[c + (int64_t)(cc + i) * l] = v[i];
       }
     }
   }
@@ -585,7 +585,7 @@ struct GramXSmem {
 template <int STAGES>
 __global__ void __launch_bounds__(320, 1)
 k_gram_x(const __grid_constant__ CUtensorMap tmY, int64_t rows, int l, int kchunk,
-         double* __restrict__ part, unsigned* status) {
+         float* __restrict__ part, unsigned* status) {
   using L = GramXSmem<STAGES>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align_smem1024(smem_raw);
@@ -722,10 +722,10 @@ k_gram_x(const __grid_constant__ CUtensorMap tmY, int64_t rows, int l, int kchun
       if (lane == 0) mbar_arrive(&tempty[buf]);
     }
     // upper triangle only (coalesced); the lower one is left unset
-    double* pz = part + (int64_t)blockIdx.x * l * l;
+    float* pz = part + (int64_t)blockIdx.x * l * l;
     if (c < l)
       for (int j = c; j < l; ++j)
-        pz[c + (int64_t)j * l] = *abort_flag ? 0.0 : (double)acc[j * (j + 1) / 2 + c];
+        pz[c + (int64_t)j * l] = *abort_flag ? 0.f : acc[j * (j + 1) / 2 + c];
   }
   __syncwarp();
   if (threadIdx.x == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
@@ -1553,7 +1553,7 @@ int tc_ypass(cudaStream_t st, int dt, const void* A, int64_t lda, const void* S,
   return RPOD_OK;
 }
 
-int tc_gram(cudaStream_t st, const float* Y, int64_t ldy, int64_t rows, int l, double* part,
+int tc_gram(cudaStream_t st, const float* Y, int64_t ldy, int64_t rows, int l, float* part,
             int nsplit, unsigned* status, bool exact) {
   if (l < 1 || l > 128 || rows < 1 || nsplit < 1) return RPOD_ERR_INVALID_ARG;
   CUtensorMap ty;

@@ -34,7 +34,7 @@ int tc_ypass_cvt(cudaStream_t st, int dt, const void* A, int64_t lda, const floa
                  int64_t n, int64_t m, int l, float* Y, int64_t ldy, void* Sh, int64_t ldh,
                  unsigned* status, float* part = nullptr, size_t part_elems = 0);
 
-// Gram partials part[z][c + j l] (FP64) = sum over rows of split z of
+// Gram partials part[z][c + j l] (FP32 sums) = sum over rows of split z of
 // Y(i, c) Y(i, j) for c, j < l <= 128, on the TF32 tensor path with FP32
 // accumulation; nsplit CTAs, each a contiguous run of 32-row tiles.  Every
 // element is split into TF32 parts: hi/lo with three products (about 2^-21
@@ -43,7 +43,7 @@ int tc_ypass_cvt(cudaStream_t st, int dt, const void* A, int64_t lda, const floa
 // The exact form writes only the upper triangle (c <= j) of each partial.
 // Y FP32 column-major (ld ldy); base 16-byte aligned and ldy a multiple of
 // 4, else RPOD_ERR_UNSUPPORTED.
-int tc_gram(cudaStream_t st, const float* Y, int64_t ldy, int64_t rows, int l, double* part,
+int tc_gram(cudaStream_t st, const float* Y, int64_t ldy, int64_t rows, int l, float* part,
             int nsplit, unsigned* status, bool exact = false);
 
 // CholeskyQR apply Q = Y X for Y n x l FP32 (column-major, ld ldy; base
