@@ -194,6 +194,7 @@ struct Run {
     float* tf;
     bool f32;
     bool used;
+    int64_t ldo = 0;  // leading dimension of h16 and tf (P->n_ld when 0)
   };
 
   // `ld`: leading dimension of in and tmp (rows when 0).
@@ -232,8 +233,9 @@ struct Run {
       int rc = RPOD_ERR_UNSUPPORTED;
       if (sizeof(W) == 4 && tco && last_apply)
         rc = tc_apply(st, (const float*)src, ld, rows, l, (const float*)buf(P->off_xw), l,
-                      tco->f32 ? (float*)dst : nullptr, rows, P->compute, tco->h16, P->n_ld,
-                      tco->tf, P->n_ld, status);
+                      tco->f32 ? (float*)dst : nullptr, rows, P->compute, tco->h16,
+                      tco->ldo ? tco->ldo : P->n_ld, tco->tf, tco->ldo ? tco->ldo : P->n_ld,
+                      status);
       if (rc == RPOD_ERR_CUDA) return rc;
       if (tco && last_apply) tco->used = rc == RPOD_OK;
       if (rc != RPOD_OK)
@@ -264,8 +266,17 @@ struct Run {
   int fold_t(const W* Tt1, W* out) {
     const int64_t m = P->m;
     const int l = P->l;
-    CK((gemm<W, W, W, W>(st, false, m, l, l, 1, Tt1, m, buf(P->off_xw), l, out, 1, m, 0, status,
-                         false)));
+    // 16-bit forms: the two-part TF32 tensor-core product (about 2^-21
+    // relative error per entry, as the lift); else, or when Tt1 is not
+    // addressable by TMA, the SIMT product
+    int rc = RPOD_ERR_UNSUPPORTED;
+    if (sizeof(W) == 4 && is16(P->compute))
+      rc = tc_apply(st, (const float*)Tt1, m, m, l, (const float*)buf(P->off_xw), l, (float*)out, m,
+                    0, nullptr, 0, nullptr, 0, status, 0, true);
+    if (rc == RPOD_ERR_CUDA) return rc;
+    if (rc != RPOD_OK)
+      CK((gemm<W, W, W, W>(st, false, m, l, l, 1, Tt1, m, buf(P->off_xw), l, out, 1, m, 0, status,
+                           false)));
     return RPOD_OK;
   }
 
@@ -482,9 +493,13 @@ struct Run {
         // takes the tensor-core path at any m
         const int64_t m4 = round_up(m, 4);
         CK((reduce_splits<float, float>(st, m, l, P->nsplit_w, wpart, Z, 1, m4)));
+        // the orthonormal Z goes straight to its 16-bit copy for the Y-pass
+        // (the tensor-core apply; the SIMT product and a conversion when Z
+        // is not addressable by TMA)
         float* Zo = nullptr;
-        CR(orth(Z, Zq, m, 1, &Zo, false, false, nullptr, m4));
-        CK(to16(Zo, m, m4, Zh, mld));
+        TcOut tz{Zh, nullptr, false, false, mld};
+        CR(orth(Z, Zq, m, 1, &Zo, false, false, &tz, m4));
+        if (!tz.used) CK(to16(Zo, m, m4, Zh, mld));
         prof_begin(P, st);
         CR(tc_ypass(st, dt, Zh, mld, Sh, ldh, n, m, l, Y, n, status, wpart, P->wpart_elems, P->pass_stages));
         prof_end(P, st, pb16, pass_flops);

@@ -266,7 +266,7 @@ cudaError_t gemm_ex(cudaStream_t st, bool akc, bool bkc, int64_t M, int64_t N, i
     // small FP64 products (the l x l steps of the eigensolver) on 32 x 32
     // tiles: GB300 issues about two FP64 FMAs per clock per SM, so the tile
     // count, not the tile efficiency, sets their time
-    if ((M <= 32 && N <= 32) || (M <= 128 && N <= 128))
+    if ((M <= 32 && N <= 32) || (M <= 128 && N <= 256))
       return launch_gemm<TA, TB, TC, TO, 32, 32, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
     if (N <= 32) return launch_gemm<TA, TB, TC, TO, 64, 32, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
     return launch_gemm<TA, TB, TC, TO, 64, 64, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
@@ -1058,173 +1058,186 @@ template cudaError_t cholesky<float>(cudaStream_t, int, const void*, double, int
 // |lambda_i - lambda_j| > delta, else R_ij / 2, E_ii = R_ii / 2,
 // X <- X + X E; each pass squares the error.
 
-__global__ void k_frob(int64_t n, const double* __restrict__ A, double* out) {
-  __shared__ double rs[32];
-  double s = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int64_t i = threadIdx.x;
-  for (; i + 3 * blockDim.x < n; i += 4 * blockDim.x) {
-    const double a0 = A[i], a1 = A[i + blockDim.x], a2 = A[i + 2 * blockDim.x], a3 = A[i + 3 * blockDim.x];
-    s += a0 * a0; s1 += a1 * a1; s2 += a2 * a2; s3 += a3 * a3;
-  }
-  for (; i < n; i += blockDim.x) s += A[i] * A[i];
-  s = (s + s1) + (s2 + s3);
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) rs[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) a += rs[k];
-    *out = sqrt(a);
-  }
-}
-
-// Sort eigenpairs by descending eigenvalue (stable), sigma = sqrt(max(lambda, 0)).
-__global__ void __launch_bounds__(1024)
-k_sort_eig(int l, const double* __restrict__ lam, const double* __restrict__ X,
-           double* __restrict__ sigma, double* __restrict__ U) {
-  __shared__ int rank[kMaxL];
-  __shared__ double sl[kMaxL];
-  const int tid = threadIdx.x;
-  if (tid < l) sl[tid] = lam[tid];
-  __syncthreads();
-  if (tid < l) {
-    const double li = sl[tid];
-    int r = 0;
-    for (int j = 0; j < l; ++j) r += (sl[j] > li) || (sl[j] == li && j < tid);
-    rank[tid] = r;
-    sigma[r] = sqrt(fmax(li, 0.0));
-  }
-  __syncthreads();
-  for (int e0 = 0; e0 < l * l; e0 += 8 * (int)blockDim.x) {
-    double v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * (int)blockDim.x + tid;
-      v[u] = e < l * l ? X[e] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * (int)blockDim.x + tid;
-      if (e < l * l) U[e % l + rank[e / l] * l] = v[u];
-    }
-  }
-}
-
-// Ogita-Aishima update: from XtX = X^T X and S = X^T A X (l x l) write the
-// eigenvalue estimates lambda and I + E, E the correction (FP64), so that
-// the next basis is X (I + E); ||A||_F is read from the device.  Every
-// block recomputes the two norms of delta (l^2 reads from L2, summed in
-// FP32: delta is only a threshold) and then fills its share of I + E, so
-// the FP64 divisions spread over the grid.
+// Ogita-Aishima pass, part 1: per block, FP64 partial sums over its columns
+// of ||I - X^T X||_F^2, ||X^T A X - diag(lambda)||_F^2 and ||A||_F^2
+// (lambda_i = (X^T A X)_ii / (X^T X)_ii); the last block to finish (a ticket
+// counter, reset for the next call) adds the partials in block order -- the
+// result does not depend on the blocks' timing -- and writes the separation
+// threshold delta and lambda.  XS = [X^T X | X^T A X] (l x 2l, ld l).
 __global__ void __launch_bounds__(256)
-k_oa_update_dev(int l, const double* __restrict__ XtX, const double* __restrict__ S,
-                const double* __restrict__ normA, double* __restrict__ lam, double* __restrict__ E) {
-  extern __shared__ double sml[];
-  double* lm = sml;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < l; i += nt) lm[i] = S[i + i * l] / XtX[i + i * l];
-  __syncthreads();
-  float so = 0.f, sr = 0.f;
-  for (int e = tid; e < l * l; e += nt) {
-    const int i = e % l, j = e / l;
-    const float rij = (float)((i == j ? 1.0 : 0.0) - XtX[e]);
-    const float sij = (float)(S[e] - (i == j ? lm[i] : 0.0));
-    so = fmaf(sij, sij, so);
-    sr = fmaf(rij, rij, sr);
+k_oa_norm(int l, const double* __restrict__ XS, const double* __restrict__ A,
+          double* __restrict__ part3, unsigned* __restrict__ ticket, double* __restrict__ lam,
+          double* __restrict__ delta) {
+  const double* XtX = XS;
+  const double* S = XS + (size_t)l * l;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  double sr = 0.0, so = 0.0, sa = 0.0;
+  for (int j = blockIdx.x; j < l; j += gridDim.x) {
+    const double lj = S[j + (size_t)j * l] / XtX[j + (size_t)j * l];
+    for (int i = tid; i < l; i += blockDim.x) {
+      const size_t e = i + (size_t)j * l;
+      const double rij = (i == j ? 1.0 : 0.0) - XtX[e];
+      const double sij = S[e] - (i == j ? lj : 0.0);
+      sr = fma(rij, rij, sr);
+      so = fma(sij, sij, so);
+      sa = fma(A[e], A[e], sa);
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
-    so += __shfl_xor_sync(0xffffffffu, so, o);
     sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    so += __shfl_xor_sync(0xffffffffu, so, o);
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
   }
-  __shared__ float rs[2][32];
-  __shared__ double s_delta;
-  const int w = tid >> 5, lane = tid & 31;
-  if (lane == 0) { rs[0][w] = so; rs[1][w] = sr; }
+  __shared__ double rs[3][8];
+  __shared__ bool s_last;
+  if (lane == 0) { rs[0][w] = sr; rs[1][w] = so; rs[2][w] = sa; }
   __syncthreads();
   if (tid == 0) {
-    float a = 0.f, b = 0.f;
-    for (int k = 0; k < (nt >> 5); ++k) { a += rs[0][k]; b += rs[1][k]; }
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a0 += rs[0][k]; a1 += rs[1][k]; a2 += rs[2][k]; }
+    part3[blockIdx.x] = a0;
+    part3[gridDim.x + blockIdx.x] = a1;
+    part3[2 * gridDim.x + blockIdx.x] = a2;
+    __threadfence();
+    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // the partials in parallel (L2 loads: other blocks wrote them), then
+  // added by one thread in block order
+  __shared__ double s_p[3][64];
+  for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
+    s_p[0][b] = __ldcg(part3 + b);
+    s_p[1][b] = __ldcg(part3 + gridDim.x + b);
+    s_p[2][b] = __ldcg(part3 + 2 * gridDim.x + b);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double r = 0.0, o = 0.0, g = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) {
+      r += s_p[0][b];
+      o += s_p[1][b];
+      g += s_p[2][b];
+    }
+    const double normA = sqrt(g);
     // floor: once the passes have converged, delta falls to the rounding
     // level, where the Rayleigh quotients of an exactly multiple eigenvalue
     // differ by rounding alone; without the floor such a pair counts as
     // separated and E divides by that difference
-    s_delta = fmax(2.0 * (sqrt((double)a) + (*normA) * sqrt((double)b)),
-                   64.0 * DBL_EPSILON * (double)l * (*normA));
+    *delta = fmax(2.0 * (sqrt(o) + normA * sqrt(r)), 64.0 * DBL_EPSILON * (double)l * normA);
+    *ticket = 0u;
+  }
+  for (int i = tid; i < l; i += blockDim.x)
+    lam[i] = S[i + (size_t)i * l] / XtX[i + (size_t)i * l];
+}
+
+// Ogita-Aishima pass, part 2: I + E from XS, lambda and delta, so that the
+// next basis is X (I + E); the FP64 divisions spread over the grid.
+__global__ void __launch_bounds__(256)
+k_oa_e(int l, const double* __restrict__ XS, const double* __restrict__ lam,
+       const double* __restrict__ delta, double* __restrict__ E) {
+  extern __shared__ double lm[];
+  const double* XtX = XS;
+  const double* S = XS + (size_t)l * l;
+  for (int i = threadIdx.x; i < l; i += blockDim.x) lm[i] = lam[i];
+  __syncthreads();
+  const double dl = *delta;
+  for (int j = blockIdx.x; j < l; j += gridDim.x)
+    for (int i = threadIdx.x; i < l; i += blockDim.x) {
+      const size_t e = i + (size_t)j * l;
+      const double rij = (i == j ? 1.0 : 0.0) - XtX[e];
+      double v;
+      if (i == j) v = 1.0 + 0.5 * rij;
+      else if (fabs(lm[i] - lm[j]) > dl) v = (S[e] + lm[j] * rij) / (lm[j] - lm[i]);
+      else v = 0.5 * rij;
+      E[e] = v;
+    }
+}
+
+// Sort eigenpairs by descending eigenvalue (stable), sigma = sqrt(max(lambda,
+// 0)): one CTA per eigenpair c finds its rank and copies its column.
+__global__ void __launch_bounds__(128)
+k_sort_eig(int l, const double* __restrict__ lam, const double* __restrict__ X,
+           double* __restrict__ sigma, double* __restrict__ U) {
+  __shared__ int s_rank;
+  const int c = blockIdx.x, tid = threadIdx.x;
+  const double lc = lam[c];
+  if (tid < 32) {
+    int r = 0;
+    for (int j = tid; j < l; j += 32) {
+      const double lj = lam[j];
+      r += (lj > lc) || (lj == lc && j < c);
+    }
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (tid == 0) {
+      s_rank = r;
+      sigma[r] = sqrt(fmax(lc, 0.0));
+    }
   }
   __syncthreads();
-  const double delta = s_delta;
-  for (int e = blockIdx.x * nt + tid; e < l * l; e += gridDim.x * nt) {
-    const int i = e % l, j = e / l;
-    const double rij = (i == j ? 1.0 : 0.0) - XtX[e];
-    double v;
-    if (i == j) v = 1.0 + 0.5 * rij;
-    else if (fabs(lm[i] - lm[j]) > delta) v = (S[e] + lm[j] * rij) / (lm[j] - lm[i]);
-    else v = 0.5 * rij;
-    E[e] = v;
-  }
-  if (blockIdx.x == 0)
-    for (int i = tid; i < l; i += nt) lam[i] = lm[i];
+  const int r = s_rank;
+  for (int i = tid; i < l; i += blockDim.x) U[i + (size_t)r * l] = X[i + (size_t)c * l];
 }
 
-static unsigned oa_blocks(int l) {
-  return (unsigned)std::min(64, std::max(1, (l * l + 255) / 256));
-}
 
 size_t sym_eig_work_doubles(int l) {
-  // V/X, XtX, AX, S, E, XE, lam, normA, split partials (8 splits of l*l),
-  // then the FP32 scratch of the starting eigenvectors
-  return (size_t)l * l * (6 + 8) + 2 * (size_t)l + 8 + (eig_scratch_floats(l) + 1) / 2 + 2;
+  // [X0 | AX0], [X1 | AX1], [X^T X | X^T A X], E, split partials (4 splits
+  // of l x 2l), lambda, norm partials and delta, then the FP32 scratch of
+  // the starting eigenvectors
+  return (size_t)l * l * 15 + (size_t)l + 3 * 64 + 8 + (eig_scratch_floats(l) + 1) / 2 + 2;
 }
 
 cudaError_t sym_eig(cudaStream_t st, int l, const double* G, double* sigma, double* Uhat,
                     double* work, unsigned* status, int refine_iters) {
   const size_t ll = (size_t)l * l;
-  double* X = work;
-  double* XtX = X + ll;
-  double* AX = XtX + ll;
-  double* S = AX + ll;
-  double* E = S + ll;
-  double* XE = E + ll;
-  double* part = XE + ll;  // 8 * ll
+  double* XA[2] = {work, work + 2 * ll};  // [X | G X], ld l
+  double* XS = work + 4 * ll;             // [X^T X | X^T G X]
+  double* E = XS + 2 * ll;
+  double* part = E + ll;                  // 4 * 2 ll
   double* lam = part + 8 * ll;
-  double* normA = lam + l;
-  // 16-byte aligned FP32 scratch after normA (the work buffer is aligned)
-  const size_t esc_off = (size_t)(normA + 8 - work + 1) & ~(size_t)1;
+  double* part3 = lam + l;                // 3 x (at most 64) norm partials
+  double* delta = part3 + 3 * 64;
+  // 16-byte aligned FP32 scratch after delta (the work buffer is aligned)
+  const size_t esc_off = (size_t)(delta + 8 - work + 1) & ~(size_t)1;
   float* esc = reinterpret_cast<float*>(work + esc_off);
+  // the ticket of k_oa_norm sits in the status block (cleared at every basis
+  // call; the kernel's last block resets it)
+  unsigned* ticket = status + 8;
   prepare_kernels();
-  cudaError_t e = tridiag_eig32(st, l, G, X, esc, status);
+  cudaError_t e = tridiag_eig32(st, l, G, XA[0], esc, status);
   if (e != cudaSuccess) return e;
-  k_frob<<<1, 1024, 0, st>>>((int64_t)ll, G, normA); note_launch();
-  // normA is needed on the device only: pass through a tiny kernel chain
   const int nsp = l > 64 ? 8 : 4;
+  const unsigned nb = (unsigned)std::min(64, l);
+  int cur = 0;
+  // lambda and E from the basis in XA[cur]: G X, then [X^T X | X^T G X] as
+  // one product, then the two pass kernels
+  auto oa_step = [&]() -> cudaError_t {
+    double* X = XA[cur];
+    double* AX = X + ll;
+    cudaError_t r;
+    if ((r = gemm<double, double, double, double>(st, false, l, l, l, nsp, G, l, X, l, part, 1, l, ll, status, false))) return r;
+    if ((r = reduce_splits<double, double>(st, l, l, nsp, part, AX, 1, l))) return r;
+    if ((r = gemm<double, double, double, double>(st, true, l, 2 * l, l, 4, X, l, X, l, part, 1, l, 2 * ll, status, false))) return r;
+    if ((r = reduce_splits<double, double>(st, l, 2 * l, 4, part, XS, 1, l))) return r;
+    k_oa_norm<<<nb, 256, 0, st>>>(l, XS, G, part3, ticket, lam, delta);
+    note_launch();
+    k_oa_e<<<nb, 256, l * sizeof(double), st>>>(l, XS, lam, delta, E);
+    note_launch();
+    return cudaGetLastError();
+  };
   for (int it = 0; it < refine_iters; ++it) {
-    // XtX = X^T X
-    if ((e = gemm<double, double, double, double>(st, true, l, l, l, nsp, X, l, X, l, part, 1, l, ll, status, false))) return e;
-    if ((e = reduce_splits<double, double>(st, l, l, nsp, part, XtX, 1, l))) return e;
-    // AX = G X
-    if ((e = gemm<double, double, double, double>(st, false, l, l, l, nsp, G, l, X, l, part, 1, l, ll, status, false))) return e;
-    if ((e = reduce_splits<double, double>(st, l, l, nsp, part, AX, 1, l))) return e;
-    // S = X^T AX
-    if ((e = gemm<double, double, double, double>(st, true, l, l, l, nsp, X, l, AX, l, part, 1, l, ll, status, false))) return e;
-    if ((e = reduce_splits<double, double>(st, l, l, nsp, part, S, 1, l))) return e;
-    k_oa_update_dev<<<oa_blocks(l), 256, l * sizeof(double), st>>>(l, XtX, S, normA, lam, E); note_launch();
-    if ((e = cudaGetLastError())) return e;
+    if ((e = oa_step())) return e;
     // X <- X (I + E), into the other buffer
-    if ((e = gemm<double, double, double, double>(st, false, l, l, l, nsp, X, l, E, l, part, 1, l, ll, status, false))) return e;
-    if ((e = reduce_splits<double, double>(st, l, l, nsp, part, XE, 1, l))) return e;
-    double* t = X; X = XE; XE = t;
+    if ((e = gemm<double, double, double, double>(st, false, l, l, l, nsp, XA[cur], l, E, l, part, 1, l, ll, status, false))) return e;
+    if ((e = reduce_splits<double, double>(st, l, l, nsp, part, XA[cur ^ 1], 1, l))) return e;
+    cur ^= 1;
   }
-  if (refine_iters == 0) {
-    // eigenvalues from the Rayleigh quotients of the starting vectors
-    if ((e = gemm<double, double, double, double>(st, false, l, l, l, nsp, G, l, X, l, part, 1, l, ll, status, false))) return e;
-    if ((e = reduce_splits<double, double>(st, l, l, nsp, part, AX, 1, l))) return e;
-    if ((e = gemm<double, double, double, double>(st, true, l, l, l, nsp, X, l, AX, l, part, 1, l, ll, status, false))) return e;
-    if ((e = reduce_splits<double, double>(st, l, l, nsp, part, S, 1, l))) return e;
-    if ((e = gemm<double, double, double, double>(st, true, l, l, l, nsp, X, l, X, l, part, 1, l, ll, status, false))) return e;
-    if ((e = reduce_splits<double, double>(st, l, l, nsp, part, XtX, 1, l))) return e;
-    k_oa_update_dev<<<oa_blocks(l), 256, l * sizeof(double), st>>>(l, XtX, S, normA, lam, E); note_launch();
-  }
-  k_sort_eig<<<1, 1024, 0, st>>>(l, lam, X, sigma, Uhat); note_launch();
+  // eigenvalues: Rayleigh quotients of the final basis (refine_iters = 0:
+  // of the starting vectors)
+  if (refine_iters == 0 && (e = oa_step())) return e;
+  k_sort_eig<<<l, 128, 0, st>>>(l, lam, XA[cur], sigma, Uhat);
+  note_launch();
   return cudaGetLastError();
 }
 
