@@ -227,7 +227,8 @@ struct Run {
       double* xd = (sizeof(W) == 8 || (defer && r == rounds - 1)) ? dbuf(P->off_x) : nullptr;
       CK((cholesky<W>(st, l, G, tol, r, xd, buf(P->off_xw), l, status,
                       sizeof(W) == 4 ? (const float*)src : nullptr, rows, dbuf(P->off_gpart), ns, ld,
-                      r == 0 ? shift_coef : 0.0, sizeof(W) == 8 && r > 0)));
+                      r == 0 ? shift_coef : 0.0, sizeof(W) == 8 && r > 0,
+                      P->compute == RPOD_F32 && r == 1)));
       if (defer && r == rounds - 1) break;
       const bool last_apply = r == rounds - 1 - (defer ? 1 : 0);
       int rc = RPOD_ERR_UNSUPPORTED;
@@ -306,7 +307,8 @@ struct Run {
       // which squares the eigenvector error outside clusters and restores
       // orthogonality; the cluster threshold of a pass scales with the norm
       // of all remaining off-diagonal terms, so eigenvalues closer than that
-      // are separated only by a later pass.  The 16-bit forms, whose passes
+      // are separated only by a later pass, and never below the rounding
+      // level of the FP32 Gram (100 u_32 ||A||).  The 16-bit forms, whose passes
       // over S hold sigma to 1e-4 (BF16) or 1e-5 (FP16), take one pass
       // (eigenvector error near 1e-10); the FP32 form takes two.
       CK((sym_eig(st, l, GT, sigma, Uhat, dbuf(P->off_eig), status, is16(P->compute) ? 1 : 2)));

@@ -85,11 +85,13 @@ cudaError_t sketch(cudaStream_t st, uint64_t seed, uint64_t stream_id, int64_t m
 // exactly vanishing columns are dropped), and flag_tiny raises
 // ST_RANK_DEF, without dropping, for columns of squared norm below 1e-16
 // (rounds after a shifted one, whose basis is near orthonormal).
+// gate_second (FP32 working type, round 1): the second round takes the same
+// gated FP64 factorization when its FP32 pivots show kappa(Q1)^2 > 2.
 template <typename TW>
 cudaError_t cholesky(cudaStream_t st, int l, const void* G, double tol, int round,
                      double* X, TW* Xw, int ldxw, unsigned* status, const float* Y = nullptr,
                      int64_t rows = 0, double* part = nullptr, int nsplit = 0, int64_t ldy = 0,
-                     double shift_coef = 0.0, bool flag_tiny = false);
+                     double shift_coef = 0.0, bool flag_tiny = false, bool gate_second = false);
 
 // Symmetric eigen-decomposition of G (l x l, FP64): an FP32 start from the
 // tridiagonal reduction, then FP64 Ogita-Aishima refinement.  Outputs

@@ -596,8 +596,8 @@ static cudaError_t launch_cholesky(cudaStream_t st, int l, const double* G, doub
 // run one block step behind the factorization in the same barrier
 // intervals (15 block steps in all for l = 120, not 30).  Pivot
 // semantics as k_cholesky: a column whose pivot falls to tol times its
-// original diagonal is dropped (zero row of R, zero column of X); in round 0
-// a pivot below 1e-4 of it raises the FP64 gate.
+// original diagonal is dropped (zero row of R, zero column of X); with a
+// gate word, a pivot below ill_tol of it raises the FP64 gate.
 // Eight consecutive values to a 16-byte aligned address as 16-byte stores.
 __device__ __forceinline__ void store8(float* p, const float* v) {
   reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
@@ -614,7 +614,8 @@ constexpr size_t kBlkSmem = (size_t)(128 * kBlkLd + 128 * 8) * sizeof(float);
 
 template <typename TW>
 __global__ void __launch_bounds__(256)
-k_cholesky_blk(int l, const float* __restrict__ G, float tol, int* gate, double* __restrict__ Xout,
+k_cholesky_blk(int l, const float* __restrict__ G, float tol, int* gate, float ill_tol,
+               double* __restrict__ Xout,
                TW* __restrict__ Xw, int ldxw, unsigned* status) {
   extern __shared__ __align__(16) float s_R[];  // [128][kBlkLd]: G, then R rows, then X
   float* s_X = s_R + 128 * kBlkLd;              // [128][8]: one block column of X
@@ -674,7 +675,7 @@ k_cholesky_blk(int l, const float* __restrict__ G, float tol, int* gate, double*
         const int j = k0 + t;
         const float d = A[t][t], d0 = s_d0[j];
         const bool keep = (j < l) && (d0 > 1e-30f) && (d0 > 1e-30f * gmax) && (d > tol * d0);
-        if (j < l && d < 1e-4f * d0) ill = 1;
+        if (j < l && d < ill_tol * d0) ill = 1;
         const float rinv = keep ? rsqrtf(d) : 0.f;
         const float rd = d * rinv;
 #pragma unroll
@@ -822,12 +823,16 @@ k_cholesky_blk(int l, const float* __restrict__ G, float tol, int* gate, double*
   }
 }
 
-// FP64 factorization that runs only when the FP32 attempt raised the gate.
+// FP64 factorization that runs only when the FP32 attempt raised the gate;
+// its dynamic shared memory for an l x l Gram matrix.
+constexpr size_t gated_smem_bytes(int l) {
+  return (size_t)l * (l + 1) * (sizeof(double) + sizeof(float)) + (size_t)l * (sizeof(double) + sizeof(float));
+}
 template <typename TW>
 __global__ void __launch_bounds__(256)
 k_cholesky64_gated(int l, const double* __restrict__ G, double tol, int* gate,
                    double* __restrict__ Xout, TW* __restrict__ Xw, int ldxw, unsigned* status,
-                   const double* __restrict__ part, int nsplit);
+                   double* __restrict__ part, int nsplit, unsigned* ticket);
 
 // Gram partials of an FP32 matrix with exact products, run only when the
 // gate is raised (an FP32 Gram cannot resolve pivots below about 1e-9 of the
@@ -920,7 +925,8 @@ k_gram_df_gated(int64_t rows, int l, const float* __restrict__ Y, int64_t ldy, i
 template <typename TW>
 cudaError_t cholesky(cudaStream_t st, int l, const void* Gv, double tol, int round, double* X,
                      TW* Xw, int ldxw, unsigned* status, const float* Y, int64_t rows,
-                     double* part, int nsplit, int64_t ldy, double shift_coef, bool flag_tiny) {
+                     double* part, int nsplit, int64_t ldy, double shift_coef, bool flag_tiny,
+                     bool gate_second) {
   if (ldy == 0) ldy = rows;
   if (sizeof(TW) == 8)
     return launch_cholesky<double, double, TW>(st, l, (const double*)Gv, tol, X, Xw, ldxw, status,
@@ -929,13 +935,21 @@ cudaError_t cholesky(cudaStream_t st, int l, const void* Gv, double tol, int rou
   // the gate word sits next to the status word (same 256-byte status block)
   int* gate = (int*)(status + 2);
   prepare_kernels();
-  k_cholesky_blk<TW><<<1, 256, kBlkSmem, st>>>(l, G, (float)tol, round == 0 ? gate : nullptr, X, Xw, ldxw,
-                                       status);
+  // round 0: the gate rises where a pivot shows a condition number beyond
+  // FP32 reach; second round (gate_second): where the first round's basis
+  // Q1 has kappa(Q1)^2 > 2 (a pivot below half its column's norm) -- the
+  // FP32 Gram and factorization of Q1 leave an orthogonality error of about
+  // sqrt(rows) * u * kappa(Q1)^2, the FP64 ones about u * kappa(Q1) (the
+  // rounding of the apply).  Only a first round that took the FP64 path
+  // on a sampled matrix near FP32's noise level leaves such a Q1.
+  const bool gated = round == 0 || (round == 1 && gate_second);
+  k_cholesky_blk<TW><<<1, 256, kBlkSmem, st>>>(l, G, (float)tol, gated ? gate : nullptr,
+                                               round == 0 ? 1e-4f : 0.5f, X, Xw, ldxw, status);
   note_launch();
-  if (round != 0) return cudaGetLastError();
+  if (!gated) return cudaGetLastError();
   // the FP64 refactorization needs the exact-product Gram of Y
   if (!(Y && part && nsplit > 0)) return cudaGetLastError();
-  const double* gp = nullptr;
+  double* gp = nullptr;
   if (Y && part && nsplit > 0) {
     int64_t chunk = (rows + nsplit - 1) / nsplit;
     chunk = (chunk + 31) / 32 * 32;
@@ -946,8 +960,10 @@ cudaError_t cholesky(cudaStream_t st, int l, const void* Gv, double tol, int rou
     note_launch();
     gp = part;
   }
-  const size_t sm64 = (size_t)l * (l + 1) * sizeof(double) + 16 + (size_t)l * (sizeof(double) + sizeof(float));
-  k_cholesky64_gated<TW><<<1, 256, sm64, st>>>(l, nullptr, 1e-13, gate, X, Xw, ldxw, status, gp, nsplit);
+  const size_t sm64 = gated_smem_bytes(l);
+  const unsigned grid = gp && nsplit > 1 ? (unsigned)(((int64_t)l * l + 63) / 64) : 1u;
+  k_cholesky64_gated<TW><<<grid, 256, sm64, st>>>(l, nullptr, 1e-13, gate, X, Xw, ldxw, status, gp,
+                                                  nsplit, status + 9);
   note_launch();
   return cudaGetLastError();
 }
@@ -956,31 +972,64 @@ template <typename TW>
 __global__ void __launch_bounds__(256)
 k_cholesky64_gated(int l, const double* __restrict__ G, double tol, int* gate,
                    double* __restrict__ Xout, TW* __restrict__ Xw, int ldxw, unsigned* status,
-                   const double* __restrict__ part, int nsplit) {
-  __shared__ int s_go;
+                   double* __restrict__ part, int nsplit, unsigned* ticket) {
+  __shared__ int s_go, s_last;
+  __shared__ double s_zs[8][32];
   if (threadIdx.x == 0) s_go = *gate;
   __syncthreads();
   if (!s_go) return;
-  // FP64 factorization of the Gram matrix; with `part`, the Gram matrix is
-  // the sum of the exact-product partials written by k_gram_df_gated
-  extern __shared__ double sm[];
-  const int ld = l + 1;
-  double* A = sm;
-  double* d0 = sm + (((size_t)l * ld + 1) / 2) * 2;
-  float* tmp = (float*)(d0 + l);
-  __shared__ double red[32];
-  __shared__ double s_rinv;
-  __shared__ int s_keep[kMaxL];
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (part && nsplit > 1) {
+    // The Gram matrix is the sum of the nsplit exact-product partials of
+    // k_gram_df_gated (element e = i + j*l, i <= j, of split z at
+    // part[z*l*l + e]).  GB300 adds about two FP64 numbers per clock per
+    // SM, so the sums are spread over the grid: CTA b sums elements
+    // [64 b, 64 b + 64) into split 0, warps w and w + 4k (k < 4) take the
+    // splits z = k, k + 4, ... of one 32-element group, and their four sums
+    // are added in warp order; the last CTA to finish (a ticket counter,
+    // reset for the next call) factors.  The result does not depend on
+    // the CTAs' timing.
+    const int lane = tid & 31, w = tid >> 5, grp = w >> 2, wz = w & 3;
+    const int64_t nel = (int64_t)l * l;
+    const int64_t e = (int64_t)blockIdx.x * 64 + grp * 32 + lane;
+    const bool up = e < nel && (e % l) <= (e / l);
+    double zs = 0.0;
+    if (up) {
+#pragma unroll 4
+      for (int z = wz; z < nsplit; z += 4) zs += part[(int64_t)z * nel + e];
+    }
+    s_zs[w][lane] = zs;
+    __syncthreads();
+    if (wz == 0 && up) {
+      part[e] = ((s_zs[w][lane] + s_zs[w + 1][lane]) + s_zs[w + 2][lane]) + s_zs[w + 3][lane];
+      __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (tid == 0) *ticket = 0u;
+  }
+  // FP64 factorization of the Gram matrix, then the FP32 inverse of the
+  // factor.  Dynamic shared memory: A (l x ld doubles), d0 (l doubles), Rf
+  // (l x ld floats), rf (l floats); Xf (l x ldx floats) reuses A once R is
+  // in Rf.
+  extern __shared__ double sm[];
+  const int ld = l + 1, ldx = (l + 1) & ~1;
+  double* A = sm;
+  double* d0 = sm + (size_t)l * ld;
+  float* Rf = (float*)(d0 + l);
+  float* rf = Rf + (size_t)l * ld;
+  float* Xf = (float*)sm;
+  __shared__ double red[32];
+  __shared__ double s_ri[kMaxL];
+  __shared__ int s_keep[kMaxL];
   for (int e = tid; e < l * l; e += nt) {
     const int i = e % l, j = e / l;
     if (i > j) continue;
-    double g = 0.0;
-    if (part) {
-      for (int z = 0; z < nsplit; ++z) g += part[(int64_t)z * l * l + e];
-    } else {
-      g = G[e];
-    }
+    // split 0 holds the sums (written by other CTAs: read through L2)
+    const double g = part ? (nsplit > 1 ? __ldcg(part + e) : part[e]) : G[e];
     A[i + j * ld] = g;
     if (i == j) d0[j] = g;
   }
@@ -988,61 +1037,79 @@ k_cholesky64_gated(int l, const double* __restrict__ G, double tol, int* gate,
   double dm = 0.0;
   for (int j = tid; j < l; j += nt) dm = fmax(dm, d0[j]);
   const double gmax = block_max(dm, red);
-  int ndropped = 0;
+  // Right-looking factorization with unscaled rows: after step j, row j
+  // holds r_jj times row j of R, the trailing block loses the outer product
+  // of that row with itself times 1/r_jj^2, and the rows are scaled once at
+  // the end.  Thread 0 makes the last update of the next diagonal entry in
+  // each step and takes that pivot's decision and square root while the
+  // other threads finish the step, so a column costs one barrier.
   const int cb = tid & 127, rg = tid >> 7, ng = nt >> 7;
-  for (int j = 0; j < l; ++j) {
-    if (tid == 0) {
-      const double d = A[j + j * ld];
-      const bool keep = (d0[j] > 1e-300) && (d0[j] > 1e-30 * gmax) && (d > 1e-13 * d0[j]);
-      s_keep[j] = keep ? 1 : 0;
-      const double r = keep ? sqrt(d) : 0.0;
-      s_rinv = keep ? 1.0 / r : 0.0;
-      A[j + j * ld] = r;
-    }
-    __syncthreads();
-    const double rinv = s_rinv;
-    if (!s_keep[j]) ++ndropped;
-    for (int c = j + 1 + tid; c < l; c += nt) A[j + c * ld] *= rinv;
-    __syncthreads();
+  auto pivot = [&](int j, double d) {
+    const bool keep = (d0[j] > 1e-300) && (d0[j] > 1e-30 * gmax) && (d > 1e-13 * d0[j]);
+    const double ri = keep ? rsqrt(d) : 0.0;
+    s_keep[j] = keep ? 1 : 0;
+    s_ri[j] = ri;
+    A[j + j * ld] = keep ? d * ri : 0.0;
+  };
+  if (tid == 0) pivot(0, A[0]);
+  __syncthreads();
+  for (int j = 0; j + 1 < l; ++j) {
+    const double ri = s_ri[j];
     const int b = j + 1 + cb;
     if (b < l) {
-      const double rb = A[j + b * ld];
+      const double rb = A[j + b * ld] * (ri * ri);
       for (int a = j + 1 + rg; a <= b; a += ng) A[a + b * ld] -= A[j + a * ld] * rb;
     }
+    // thread 0 (b = j + 1, a = j + 1) has just updated the next pivot
+    if (tid == 0) pivot(j + 1, A[(j + 1) + (j + 1) * ld]);
     __syncthreads();
   }
-  for (int j = 0; j < l; ++j) {
-    const bool keep = s_keep[j] != 0;
-    for (int i = tid; i < j; i += nt) tmp[i] = keep ? (float)A[i + j * ld] : 0.f;
-    __syncthreads();
-    if (keep) {
-      const float ajj = 1.f / (float)A[j + j * ld];
-      for (int i = tid; i < j; i += nt) {
-        float s = 0.f;
-        for (int t2 = i; t2 < j; ++t2) s += (float)A[i + t2 * ld] * tmp[t2];
-        A[i + j * ld] = (double)(-ajj * s);
-      }
-      __syncthreads();
-      if (tid == 0) A[j + j * ld] = (double)ajj;
-    } else {
-      for (int i = tid; i <= j; i += nt) A[i + j * ld] = 0.0;
-    }
-    __syncthreads();
-  }
+  // R with scaled rows (a dropped row is zero), in FP32, and 1 / r_jj
   for (int e = tid; e < l * l; e += nt) {
     const int i = e % l, j = e / l;
-    const double v = (i <= j) ? A[i + j * ld] : 0.0;
-    if (Xout) Xout[e] = v;
+    if (i > j) continue;
+    const double v = (i == j) ? A[i + j * ld] : A[i + j * ld] * s_ri[i];
+    Rf[i + j * ld] = (float)v;
+  }
+  for (int j = tid; j < l; j += nt) rf[j] = s_keep[j] ? 1.f / (float)A[j + j * ld] : 0.f;
+  __syncthreads();
+  // X = R^{-1} by rows, without barriers: thread i forms row i (stored
+  // contiguously, Xf[i * ldx + j]), X_ii = 1 / r_ii and, for j > i,
+  // X_ij = -(sum_{t=i}^{j-1} X_it R_tj) / r_jj.  A dropped direction j gives
+  // a zero column j and, through X_jj = 0, a zero row j.
+  if (tid < l) {
+    const int i = tid;
+    float* xr = Xf + (size_t)i * ldx;
+    xr[i] = rf[i];
+    for (int j = i + 1; j < l; ++j) {
+      const float* rc = Rf + (size_t)j * ld;
+      float s0 = 0.f, s1 = 0.f;
+      int t = i;
+      for (; t + 1 < j; t += 2) {
+        s0 = fmaf(xr[t], rc[t], s0);
+        s1 = fmaf(xr[t + 1], rc[t + 1], s1);
+      }
+      if (t < j) s0 = fmaf(xr[t], rc[t], s0);
+      xr[j] = -rf[j] * (s0 + s1);
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < l * l; e += nt) {
+    const int i = e % l, j = e / l;
+    const float v = (i <= j) ? Xf[(size_t)i * ldx + j] : 0.f;
+    if (Xout) Xout[e] = (double)v;
     Xw[i + (int64_t)j * ldxw] = (TW)v;
   }
   if (tid == 0) {
+    int ndropped = 0;
+    for (int j = 0; j < l; ++j) ndropped += s_keep[j] ? 0 : 1;
     *gate = 0;
     if (ndropped > 0) atomicOr(status, ndropped == l ? (ST_RANK_DEF | ST_BREAKDOWN) : ST_RANK_DEF);
   }
   (void)tol;
 }
-template cudaError_t cholesky<double>(cudaStream_t, int, const void*, double, int, double*, double*, int, unsigned*, const float*, int64_t, double*, int, int64_t, double, bool);
-template cudaError_t cholesky<float>(cudaStream_t, int, const void*, double, int, double*, float*, int, unsigned*, const float*, int64_t, double*, int, int64_t, double, bool);
+template cudaError_t cholesky<double>(cudaStream_t, int, const void*, double, int, double*, double*, int, unsigned*, const float*, int64_t, double*, int, int64_t, double, bool, bool);
+template cudaError_t cholesky<float>(cudaStream_t, int, const void*, double, int, double*, float*, int, unsigned*, const float*, int64_t, double*, int, int64_t, double, bool, bool);
 
 // ------------------------------------------------------------------------
 // Symmetric eigensolver for the small SVD.  T T^T = Uhat Sigma^2 Uhat^T, so
@@ -1122,10 +1189,18 @@ k_oa_norm(int l, const double* __restrict__ XS, const double* __restrict__ A,
     }
     const double normA = sqrt(g);
     // floor: once the passes have converged, delta falls to the rounding
-    // level, where the Rayleigh quotients of an exactly multiple eigenvalue
-    // differ by rounding alone; without the floor such a pair counts as
-    // separated and E divides by that difference
-    *delta = fmax(2.0 * (sqrt(o) + normA * sqrt(r)), 64.0 * DBL_EPSILON * (double)l * normA);
+    // level, where the Rayleigh quotients of a multiple eigenvalue differ by
+    // rounding alone; without the floor such a pair counts as separated and
+    // E divides by that difference.  The Gram comes from FP32 products of
+    // the FP32 matrix T and the start from FP32 arithmetic: neither
+    // determines the eigenvectors of a pair closer than about
+    // 100 u_32 ||A|| (u_32 = 2^-24), whose start keeps an arbitrary rotation
+    // within the pair -- a pass that took such a pair as separated would
+    // apply an O(1) first-order rotation and lose orthogonality, so the pair
+    // keeps the orthonormalizing update (its span is still refined)
+    const double floor64 = 64.0 * DBL_EPSILON * (double)l * normA;
+    const double floor32 = 100.0 * (double)(FLT_EPSILON / 2) * normA;
+    *delta = fmax(2.0 * (sqrt(o) + normA * sqrt(r)), fmax(floor64, floor32));
     *ticket = 0u;
   }
   for (int i = tid; i < l; i += blockDim.x)
@@ -1697,7 +1772,8 @@ void prepare_kernels() {
   std::call_once(once, [] {
     const int big = 160 * 1024;
     cudaFuncSetAttribute(k_cholesky<double, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_cholesky64_gated<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_cholesky64_gated<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)gated_smem_bytes(kMaxL));
     prepare_eig_kernels();
     prepare_jacobi_kernels();
     cudaFuncSetAttribute(k_cholesky_blk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlkSmem);

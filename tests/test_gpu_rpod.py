@@ -228,6 +228,27 @@ def test_f32_config1_matches_oracle():
         assert d <= 1e-5 * o.sigma[0]
 
 
+def test_f32_steep_spectrum_through_fp64_factorization():
+    """Amplitudes exp(-j/5), k = 50, p = 10, q = 1 (l = 60): the Grams of the
+    sampled and power-iterated matrices span condition numbers near 1e10,
+    beyond the FP32 Cholesky's pivot test, so the first CholeskyQR round of
+    every orthonormalization refactors the exact-product Gram in FP64 (the
+    gated path).  FP32 form against the oracle on the same FP32 snapshots:
+    sigma_i within 2e-5 where sigma_i >= 1e-2 sigma_1 and within 1e-6
+    sigma_1 below, the top-10 span within 1e-4, U orthonormal to 1e-5 and
+    no direction dropped."""
+    rec = make_recipe(64, 64, 1500, 200, ("exp", 5.0), seed=4, noise=1e-6)
+    S = snapshot_matrix(rec)
+    k, p, q = 50, 10, 1
+    o = oracle_rpod(S.float().double().numpy(), k, p, q, seed=3)
+    _, U, sig, C, rc, warn = run_gpu(dev(S, torch.float32), k, p, q, 3, "f32")
+    assert rc == R.RPOD_OK and warn == 0
+    ok, er, ea = sigma_close(sig[:k], o.sigma[:k], 2e-5, 1e-6, floor=1e-2)
+    assert ok, (er, ea)
+    assert max_angle(o.U[:, :10], U[:, :10]) <= 1e-4
+    assert orth_err(U) <= 1e-5
+
+
 def test_project_matches_oracle():
     rec = make_recipe(32, 64, 300, 100, ("power", 1.5), seed=3)
     S = snapshot_matrix(rec)
