@@ -3,6 +3,7 @@
 // reductions, the one-block Cholesky (CholeskyQR), the symmetric
 // eigensolver of the small SVD, and the column sign convention.
 #include <float.h>
+#include <type_traits>
 #include <math.h>
 
 #include <algorithm>
@@ -224,6 +225,183 @@ k_gemm(int64_t M, int64_t N, int64_t K, int64_t kchunk, const TA* __restrict__ A
     }
 }
 
+// FP32 pass GEMM for the plain FP32 form's products over S (M or K in the
+// hundreds of thousands, N = l > 64): C_z = sum_{k in split z} A(i, k) B(k, j)
+// with B(k, j) = B[k + j*ldb] and A(i, k) = A[i + k*lda] (AKC false) or
+// A[k + i*lda] (AKC true).  128 x 128 x 16 tiles, 256 threads; thread
+// (tx, ty) = (tid % 16, tid / 16) owns rows {4 ty .. 4 ty + 3} and
+// {64 + 4 ty ..} and the same pattern of columns, so each inner step reads
+// its eight A and eight B values with four 16-byte shared loads and global
+// tiles move as float4 (16-byte aligned operands, leading dimensions
+// multiples of four).  The shared tiles are double-buffered: the next
+// tile's global loads are in flight during the current tile's 1024 FMAs per
+// thread and one barrier per tile separates the buffers.  `check` flags
+// non-finite A entries in *status.
+namespace {
+constexpr int kSgBM = 128, kSgBN = 128, kSgBK = 16, kSgLd = 132;
+
+template <bool AKC>
+__global__ void __launch_bounds__(256, 2)
+k_sgemm(int64_t M, int64_t N, int64_t K, int64_t kchunk, const float* __restrict__ A, int64_t lda,
+        const float* __restrict__ B, int64_t ldb, float* __restrict__ C, int64_t ci, int64_t cj,
+        int64_t csplit, unsigned* status, int check) {
+  __shared__ __align__(16) float As[2][kSgBK][kSgLd];
+  __shared__ __align__(16) float Bs[2][kSgBK][kSgLd];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t i0 = (int64_t)blockIdx.x * kSgBM, j0 = (int64_t)blockIdx.y * kSgBN;
+  const int64_t kb = (int64_t)blockIdx.z * kchunk;
+  const int64_t ke = (K < kb + kchunk) ? K : kb + kchunk;
+  float acc[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+  bool bad = false;
+  float4 ra[2], rb[2];
+  // A tile: AKC false -- float4 along i (32 per k row), AKC true -- float4
+  // along k (4 per row i); B tile: float4 along k (4 per column j)
+  auto load = [&](int64_t k0) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int idx = tid + 256 * u;
+      float v[4];
+      if (!AKC) {
+        const int kk = idx >> 5, i4 = idx & 31;
+        const int64_t gi = i0 + 4 * i4, gk = k0 + kk;
+        const float* p = A + gi + gk * lda;
+        if (gk < ke && gi + 3 < M) {
+          const float4 q = *reinterpret_cast<const float4*>(p);
+          v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) v[e] = (gk < ke && gi + e < M) ? p[e] : 0.f;
+        }
+      } else {
+        const int k4 = idx & 3, ii = idx >> 2;
+        const int64_t gi = i0 + ii, gk = k0 + 4 * k4;
+        const float* p = A + gk + gi * lda;
+        if (gi < M && gk + 3 < ke) {
+          const float4 q = *reinterpret_cast<const float4*>(p);
+          v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) v[e] = (gi < M && gk + e < ke) ? p[e] : 0.f;
+        }
+      }
+      ra[u] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int idx = tid + 256 * u;
+      const int k4 = idx & 3, jj = idx >> 2;
+      const int64_t gj = j0 + jj, gk = k0 + 4 * k4;
+      const float* p = B + gk + gj * ldb;
+      float v[4];
+      if (gj < N && gk + 3 < ke) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = (gj < N && gk + e < ke) ? p[e] : 0.f;
+      }
+      rb[u] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int idx = tid + 256 * u;
+      if (check && !(isfinite(ra[u].x) && isfinite(ra[u].y) && isfinite(ra[u].z) && isfinite(ra[u].w)))
+        bad = true;
+      if (!AKC) {
+        *reinterpret_cast<float4*>(&As[buf][idx >> 5][4 * (idx & 31)]) = ra[u];
+      } else {
+        const int k4 = idx & 3, ii = idx >> 2;
+        As[buf][4 * k4 + 0][ii] = ra[u].x;
+        As[buf][4 * k4 + 1][ii] = ra[u].y;
+        As[buf][4 * k4 + 2][ii] = ra[u].z;
+        As[buf][4 * k4 + 3][ii] = ra[u].w;
+      }
+      const int k4 = idx & 3, jj = idx >> 2;
+      Bs[buf][4 * k4 + 0][jj] = rb[u].x;
+      Bs[buf][4 * k4 + 1][jj] = rb[u].y;
+      Bs[buf][4 * k4 + 2][jj] = rb[u].z;
+      Bs[buf][4 * k4 + 3][jj] = rb[u].w;
+    }
+  };
+  const int64_t ntiles = kb < ke ? (ke - kb + kSgBK - 1) / kSgBK : 0;
+  if (ntiles > 0) {
+    load(kb);
+    store(0);
+  }
+  __syncthreads();
+  for (int64_t t = 0; t < ntiles; ++t) {
+    const int cur = (int)(t & 1);
+    if (t + 1 < ntiles) load(kb + (t + 1) * kSgBK);
+#pragma unroll
+    for (int kk = 0; kk < kSgBK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][4 * ty]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][64 + 4 * ty]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][4 * tx]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][64 + 4 * tx]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+    }
+    if (t + 1 < ntiles) store(cur ^ 1);
+    __syncthreads();
+  }
+  if (check && bad) atomicOr(status, ST_NONFINITE);
+  float* Cz = C + (int64_t)blockIdx.z * csplit;
+  const bool vec = ci == 1 && (cj & 3) == 0 && ((uintptr_t)Cz & 15) == 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int64_t gj = j0 + (c < 4 ? 4 * tx + c : 64 + 4 * tx + c - 4);
+    if (gj >= N) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t gi = i0 + 64 * h + 4 * ty;
+      float* p = Cz + gi * ci + gj * cj;
+      if (vec && gi + 3 < M) {
+        *reinterpret_cast<float4*>(p) =
+            make_float4(acc[4 * h][c], acc[4 * h + 1][c], acc[4 * h + 2][c], acc[4 * h + 3][c]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (gi + e < M) p[e * ci] = acc[4 * h + e][c];
+      }
+    }
+  }
+}
+}  // namespace
+
+// The FP32 pass GEMM when it applies (FP32 operands and output, a product
+// over S, 16-byte aligned operands): returns false to leave the product to
+// the generic kernel.
+static bool launch_sgemm(cudaStream_t st, bool akc, int64_t M, int64_t N, int64_t K, int nsplit,
+                         const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
+                         int64_t ci, int64_t cj, int64_t csplit, unsigned* status, bool check,
+                         cudaError_t* err) {
+  if (N <= 64 || M < 128 || K < 128 || M * K < ((int64_t)1 << 22)) return false;
+  if (((uintptr_t)A & 15) || ((uintptr_t)B & 15) || (lda & 3) || (ldb & 3)) return false;
+  int64_t kchunk = (K + nsplit - 1) / nsplit;
+  kchunk = ((kchunk + kSgBK - 1) / kSgBK) * kSgBK;
+  dim3 grid((unsigned)((M + kSgBM - 1) / kSgBM), (unsigned)((N + kSgBN - 1) / kSgBN),
+            (unsigned)nsplit);
+  if (akc)
+    k_sgemm<true><<<grid, 256, 0, st>>>(M, N, K, kchunk, A, lda, B, ldb, C, ci, cj, csplit, status,
+                                        check ? 1 : 0);
+  else
+    k_sgemm<false><<<grid, 256, 0, st>>>(M, N, K, kchunk, A, lda, B, ldb, C, ci, cj, csplit, status,
+                                         check ? 1 : 0);
+  note_launch();
+  *err = cudaGetLastError();
+  return true;
+}
+
 template <typename TA, typename TB, typename TC, typename TO, int BM, int BN, int BK>
 static cudaError_t launch_gemm(cudaStream_t st, bool akc, bool bkc, int64_t M, int64_t N,
                                int64_t K, int nsplit, const TA* A, int64_t lda, const TB* B,
@@ -249,6 +427,13 @@ cudaError_t gemm_ex(cudaStream_t st, bool akc, bool bkc, int64_t M, int64_t N, i
                     int nsplit, const TA* A, int64_t lda, const TB* B, int64_t ldb, TO* C,
                     int64_t ci, int64_t cj, int64_t csplit, unsigned* status, bool check) {
   if (nsplit < 1) nsplit = 1;
+  if constexpr (std::is_same<TA, float>::value && std::is_same<TB, float>::value &&
+                std::is_same<TC, float>::value && std::is_same<TO, float>::value) {
+    cudaError_t e = cudaSuccess;
+    if (bkc && launch_sgemm(st, akc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status,
+                            check, &e))
+      return e;
+  }
   if (sizeof(TC) == 4) {
     if (N <= 32) return launch_gemm<TA, TB, TC, TO, 128, 32, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);
     if (N <= 64) return launch_gemm<TA, TB, TC, TO, 128, 64, 16>(st, akc, bkc, M, N, K, nsplit, A, lda, B, ldb, C, ci, cj, csplit, status, check);

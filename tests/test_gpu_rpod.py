@@ -228,6 +228,36 @@ def test_f32_config1_matches_oracle():
         assert d <= 1e-5 * o.sigma[0]
 
 
+def test_f32_wide_basis_matches_oracle():
+    """FP32 form with l = 80 > 64, where the products over S take the
+    128 x 128 FP32 pass kernel: n = 4160 and m = 1001 leave ragged row,
+    snapshot and column tiles, and the S^T Q passes split over rows.
+    Against the oracle on the same FP32 snapshots: sigma_i within 1e-5
+    relative (1e-6 sigma_1 below 1e-3 sigma_1); span(U_k) within the
+    Davis-Kahan scale 10 u_32 sigma_1 / (sigma_k - sigma_{k+1}) of FP32
+    rounding (this spectrum's gap at k = 70 is 5e-5 sigma_1, and a pair
+    inside U_k lies 8e-6 sigma_1 apart, so single vectors are not compared);
+    U orthonormal to 1e-5; C and the projection of new snapshots equal
+    U^T S with the returned U to 1e-5 sigma_1."""
+    rec = make_recipe(64, 65, 1001, 400, ("power", 1.2), seed=6, noise=1e-6)
+    S = snapshot_matrix(rec)
+    k, p, q = 70, 10, 1
+    S64 = S.float().double().numpy()
+    o = oracle_rpod(S64, k, p, q, seed=5)
+    plan, U, sig, C, rc, warn = run_gpu(dev(S, torch.float32), k, p, q, 5, "f32")
+    assert rc == R.RPOD_OK
+    ok, er, ea = sigma_close(sig[:k], o.sigma[:k], 1e-5, 1e-6)
+    assert ok, (er, ea)
+    gap = o.sigma[k - 1] - o.sigma[k]
+    assert max_angle(o.U[:, :k], U) <= 10 * 2.0**-24 * o.sigma[0] / gap
+    assert orth_err(U) <= 1e-5
+    assert np.abs(C - U.T @ S64).max() <= 1e-5 * o.sigma[0]
+    Snew = S[:, 500:777].float()
+    Cn = plan.project(dev(torch.from_numpy(U), torch.float32), dev(Snew, torch.float32))
+    ref = oracle_project(U, Snew.double().numpy())
+    assert np.abs(Cn.double().cpu().numpy() - ref).max() <= 1e-5 * o.sigma[0]
+
+
 def test_f32_steep_spectrum_through_fp64_factorization():
     """Amplitudes exp(-j/5), k = 50, p = 10, q = 1 (l = 60): the Grams of the
     sampled and power-iterated matrices span condition numbers near 1e10,
