@@ -91,6 +91,35 @@ def test_zero_weights_special_case():
     assert np.allclose(y, H * s(bo) * np.tanh(cT), rtol=1e-14)
 
 
+def test_rollout_zero_weights_closed_form():
+    """Rollout of a two-layer network whose weights are zero and whose gate
+    biases are (b_i, b_f, b_g, b_o) in both layers: each unit of each layer
+    follows c_t = s(b_f) c_{t-1} + s(b_i) tanh(b_g) whatever its input, so
+    every step predicts H s(b_o) tanh(c_T) + b_y for each output (W_y = ones)
+    -- the same value at all steps, from any window; the rollout's output
+    has one row per step and output."""
+    I, H, Ly, O, T, B, mu = 5, 3, 2, 3, 4, 2, 2
+    theta = np.zeros(L.param_count(I, H, Ly, O))
+    bi, bf, bg, bo, by = -0.4, 0.8, 0.6, 0.3, -0.25
+    b = np.concatenate([np.full(H, bi), np.full(H, bf), np.full(H, bg), np.full(H, bo)])
+    off = 0
+    for l in range(Ly):
+        il = I if l == 0 else H
+        off += 4 * H * il + 4 * H * H
+        theta[off:off + 4 * H] = b
+        off += 4 * H
+    theta[off:off + O * H] = 1.0                  # W_y = ones
+    theta[off + O * H:off + O * H + O] = by       # b_y
+    s = lambda x: 1 / (1 + np.exp(-x))
+    a, r = s(bi) * np.tanh(bg), s(bf)
+    cT = a * (1 - r ** T) / (1 - r)
+    expect = H * s(bo) * np.tanh(cT) + by
+    win = np.random.default_rng(4).standard_normal((B, T, I)) * 3.0
+    out = L.rollout(theta, win, mu, 7, H, Ly, O)
+    assert out.shape == (B, 7, O)
+    assert np.allclose(out, expect, rtol=1e-14, atol=1e-15)
+
+
 def test_adam_hand_example():
     theta = np.array([1.0, -2.0])
     g = np.array([0.5, -0.25])

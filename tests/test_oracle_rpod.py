@@ -59,6 +59,25 @@ def test_modes_discretely_orthogonal():
     assert np.abs(G - np.eye(rec.J) * rec.n / 4).max() < 1e-11
 
 
+def test_project_recovers_recipe_coefficients():
+    """Galerkin projection against the recipe's closed form: the sine modes
+    satisfy Phi^T Phi = (n/4) I, so with U = (2/sqrt(n)) Phi and the
+    noise-free S = Phi (amp * A)^T the projection U^T S is
+    (sqrt(n)/2) amp_j cos(omega_j t_p + theta_j); a transposed operand or a
+    missing scale fails it."""
+    rec = make_recipe(16, 24, 37, 30, ("power", 1.0), seed=3, noise=0.0)
+    S = snapshot_matrix(rec, noise=False).numpy()
+    U = mode_matrix(rec) * (2.0 / np.sqrt(rec.n))
+    t = rec.times()
+    closed = (np.sqrt(rec.n) / 2) * rec.amp[:, None] * np.cos(
+        np.outer(rec.omega, t) + rec.theta[:, None])
+    C = project(U, S)
+    assert C.shape == (rec.J, rec.m)
+    assert np.abs(C - closed).max() <= 1e-12 * np.abs(closed).max()
+    # a subset of snapshots projects to the same columns
+    assert np.abs(project(U, S[:, 5:9]) - closed[:, 5:9]).max() <= 1e-12 * np.abs(closed).max()
+
+
 def test_closed_form_spectrum_with_truncation():
     # more modes than l: the leading sigma still converge to the closed form
     rec = make_recipe(32, 32, 400, 200, ("exp", 10.0), seed=1, noise=1e-6)
