@@ -51,10 +51,15 @@ extern "C" {
  *                CholeskyQR3); the small SVD is one-sided Jacobi in FP64 on
  *                the transposed Cholesky factor of T T^T (relative accuracy
  *                of small singular values).
- *   F32, 16-bit: FP64 sums of the Gram partials, an FP32 Cholesky factor with
- *                a device-gated FP64 refactorization when a pivot shows a
- *                condition number beyond FP32 reach; the small SVD is the FP32
- *                eigen start of the FP64 Gram T T^T refined in FP64. */
+ *   F32, 16-bit: Gram partials added as compensated FP32 sums, an FP32
+ *                Cholesky factor with a device-gated FP64 refactorization of
+ *                an exact-product Gram when a pivot shows a condition number
+ *                beyond FP32 reach (F32 form: also in the second CholeskyQR
+ *                round when its basis has kappa^2 > 2); the small SVD is the
+ *                FP32 eigen start of the Gram T T^T (FP32 products, FP64
+ *                sums) refined in FP64, where eigenvalue pairs closer than
+ *                the FP32 Gram's rounding level (100 u_32 ||T T^T||_F) keep
+ *                an orthonormal basis of their common span. */
 typedef enum { RPOD_F64 = 0, RPOD_F32 = 1, RPOD_BF16 = 2, RPOD_F16 = 3 } rpod_dtype;
 
 typedef enum {
