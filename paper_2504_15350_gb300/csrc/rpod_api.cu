@@ -83,12 +83,16 @@ __attribute__((visibility("hidden"))) void plan_shape(const rpod_plan* P, int64_
   *nsplit = P->nsplit_z;
 }
 
-// Pass profiling hooks used by the pipelines.
+// Pass profiling hooks used by the pipelines; each pass over S is also an
+// NVTX range named "pass" (one left open by an error return is closed by the
+// entry point's range).
 void prof_begin(rpod_plan* P, cudaStream_t st) {
+  nvtx_pass_push();
   if (!P->prof_on || P->prof_n >= kProfPasses) return;
   cudaEventRecord(P->prof_ev[2 * P->prof_n], st);
 }
 void prof_end(rpod_plan* P, cudaStream_t st, double bytes, double flops) {
+  nvtx_pass_pop();
   if (!P->prof_on || P->prof_n >= kProfPasses) return;
   cudaEventRecord(P->prof_ev[2 * P->prof_n + 1], st);
   ++P->prof_n;
@@ -815,6 +819,7 @@ static int basis_device(rpod_plan* P, const void* S, int64_t lds, int32_t s_dtyp
 int rpod_basis_rows(rpod_plan* P, const void* S, int64_t lds, int32_t s_dtype, void* U, int64_t ldu,
                     double* sigma, void* C, int64_t ldc, void* workspace, size_t workspace_bytes,
                     void* stream, rpod_exchange_fn exchange, void* ctx) {
+  rpod::NvtxRange nv("rpod_basis_rows");
   if (!P || !P->rows_mode || !S || !U || !sigma || !C || !exchange) return RPOD_ERR_INVALID_ARG;
   if (s_dtype != P->compute) return RPOD_ERR_INVALID_ARG;
   P->xch = exchange;
@@ -829,6 +834,7 @@ int rpod_basis_rows(rpod_plan* P, const void* S, int64_t lds, int32_t s_dtype, v
 int rpod_basis(rpod_plan* P, const void* S, int64_t lds, int32_t s_dtype, const float* S_refine,
                int64_t ldr, void* U, int64_t ldu, double* sigma, void* C, int64_t ldc,
                void* workspace, size_t workspace_bytes, void* stream) {
+  rpod::NvtxRange nv("rpod_basis");
   if (!P || !S || !U || !sigma || !C) return RPOD_ERR_INVALID_ARG;
   if (P->rows_mode) return RPOD_ERR_INVALID_ARG;  // needs the exchange: rpod_basis_rows
   if (!(P->flags & RPOD_FLAG_HOST_IO))
@@ -981,6 +987,7 @@ static int basis_direct(rpod_plan* P, const void* S, int64_t lds, int32_t s_dtyp
 int rpod_project(const rpod_plan* P, const void* U, int64_t ldu, int32_t kc, const void* S_new,
                  int64_t lds, int64_t m_new, int32_t s_dtype, void* C, int64_t ldc, void* workspace,
                  size_t workspace_bytes, void* stream) {
+  rpod::NvtxRange nv("rpod_project");
   if (!P || !U || !S_new || !C || kc < 1 || kc > P->l || m_new < 1) return RPOD_ERR_INVALID_ARG;
   if (P->rows_mode || ldu < P->n || lds < P->n || ldc < kc) return RPOD_ERR_INVALID_ARG;
   if (int rc = check_ws(P, workspace, workspace_bytes)) return rc;
@@ -1273,6 +1280,7 @@ int rpod_batch_set_pass_stages(rpod_batch* B, int32_t stages) {
 }
 
 int rpod_batch_run(rpod_batch* B, void* workspace, size_t workspace_bytes, void* stream) {
+  rpod::NvtxRange nv("rpod_batch_run");
   if (!B) return RPOD_ERR_INVALID_ARG;
   if (!workspace || workspace_bytes < B->total || ((uintptr_t)workspace & 255))
     return RPOD_ERR_WORKSPACE;
@@ -1285,6 +1293,7 @@ int rpod_batch_run(rpod_batch* B, void* workspace, size_t workspace_bytes, void*
 int rpod_batch_tune(rpod_batch* B, void* workspace, size_t workspace_bytes, void* stream,
                     int32_t trials, int32_t* best_streams, int32_t* best_split_pct,
                     int32_t* best_stages) {
+  rpod::NvtxRange nv("rpod_batch_tune");
   if (!B || trials < 1) return RPOD_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   const int stream_opts[7] = {1, 2, 4, 8, 16, 32, 64};

@@ -6,9 +6,30 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/rpod.h"
 
 namespace rpod {
+
+// NVTX ranges for profilers (ncu --nvtx, nsys): the kernels a call launches
+// are attributed to the range open on the calling thread; without a
+// profiler attached a push or pop does nothing.  Pass ranges are counted so
+// that an entry point's range closes any left open by an error return.
+inline thread_local int g_nvtx_passes = 0;
+inline void nvtx_pass_push() { nvtxRangePushA("pass"); ++g_nvtx_passes; }
+inline void nvtx_pass_pop() {
+  if (g_nvtx_passes > 0) { nvtxRangePop(); --g_nvtx_passes; }
+}
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() {
+    while (g_nvtx_passes > 0) nvtx_pass_pop();
+    nvtxRangePop();
+  }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Device status word bits (first 32-bit word of the workspace).
 enum : unsigned {

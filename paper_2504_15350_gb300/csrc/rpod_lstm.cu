@@ -592,6 +592,7 @@ int rpod_lstm_loss_grad(rpod_lstm* N, const float* X, const float* Yt, int32_t B
 
 int rpod_lstm_train_step(rpod_lstm* N, const float* X, const float* Yt, int32_t B, float lr,
                          float weight_decay, float* loss, void* ws, size_t bytes, void* stream) {
+  rpod::NvtxRange nv("rpod_lstm_train_step");
   if (int rc = rpod_lstm_loss_grad(N, X, Yt, B, loss, nullptr, ws, bytes, stream)) return rc;
   const int launches = N->last_launches;
   cudaStream_t st = (cudaStream_t)stream;
@@ -632,6 +633,7 @@ static bool rollout_fits(const rpod_lstm* N, int B, int sms) {
 
 int rpod_lstm_rollout(rpod_lstm* N, const float* window, int32_t B, int32_t mu_cols, int32_t steps,
                       float* out, void* ws, size_t bytes, void* stream) {
+  rpod::NvtxRange nv("rpod_lstm_rollout");
   if (!N || !window || !out || B < 1 || B > N->Bmax || steps < 1 || mu_cols < 0 ||
       mu_cols + N->O != N->I)
     return RPOD_ERR_INVALID_ARG;
@@ -681,6 +683,7 @@ int rpod_lstm_train_epoch(rpod_lstm* N, const float* series, const float* mu, in
                           int32_t t_len, int32_t d, const int32_t* idx, int32_t n_windows,
                           int32_t batch, float lr, float weight_decay, float* loss_out, void* ws,
                           size_t bytes, void* stream) {
+  rpod::NvtxRange nv("rpod_lstm_train_epoch");
   if (!N || !series || !idx || n_windows < 1 || batch < 1 || batch > N->Bmax || d < 0 ||
       d + N->O != N->I || t_len <= N->T || n_series < 1 || (d > 0 && !mu))
     return RPOD_ERR_INVALID_ARG;
