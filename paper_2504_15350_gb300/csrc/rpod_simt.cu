@@ -1,7 +1,10 @@
-// SIMT kernels of librpod: the Philox sketch, the generic tall-skinny GEMM
-// used by the FP64/FP32 passes and by the small dense steps, split-K
-// reductions, the one-block Cholesky (CholeskyQR), the symmetric
-// eigensolver of the small SVD, and the column sign convention.
+// SIMT kernels of librpod (Alg. 1, Sec. 4.2): the Philox sketch Lambda
+// (first step); the tall-skinny GEMMs of the FP64 and FP32 passes over S --
+// P = S Lambda (second step), the subspace iterations S (S^T Q) (third) and
+// T = Q^T S (fifth) -- and of the small dense steps; split-K reductions; the
+// Cholesky factors of CholeskyQR (the QR of the fourth step); the symmetric
+// eigensolver of the small SVD (sixth step); and the column sign convention
+// of the lift (last step).
 #include <float.h>
 #include <type_traits>
 #include <math.h>
@@ -225,7 +228,8 @@ k_gemm(int64_t M, int64_t N, int64_t K, int64_t kchunk, const TA* __restrict__ A
     }
 }
 
-// FP32 pass GEMM for the plain FP32 form's products over S (M or K in the
+// FP32 pass GEMM for the plain FP32 form's passes over S of Alg. 1
+// (P = S Lambda and S Z: AKC false; S^T Q and T = Q^T S: AKC true; M or K in the
 // hundreds of thousands, N = l > 64): C_z = sum_{k in split z} A(i, k) B(k, j)
 // with B(k, j) = B[k + j*ldb] and A(i, k) = A[i + k*lda] (AKC false) or
 // A[k + i*lda] (AKC true).  128 x 128 x 16 tiles, 256 threads; thread
@@ -1008,8 +1012,9 @@ k_cholesky_blk(int l, const float* __restrict__ G, float tol, int* gate, float i
   }
 }
 
-// FP64 factorization that runs only when the FP32 attempt raised the gate;
-// its dynamic shared memory for an l x l Gram matrix.
+// CholeskyQR factor (the QR of Alg. 1's fourth step) in FP64, run only when
+// the FP32 attempt raised the gate; its dynamic shared memory for an l x l
+// Gram matrix.
 constexpr size_t gated_smem_bytes(int l) {
   return (size_t)l * (l + 1) * (sizeof(double) + sizeof(float)) + (size_t)l * (sizeof(double) + sizeof(float));
 }
