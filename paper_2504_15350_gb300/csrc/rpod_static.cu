@@ -1,4 +1,5 @@
-// Allocation-free Galerkin projection: the rpod_project computation with its
+// Allocation-free Galerkin projection (C' = U^T S', the coefficients of new
+// snapshots on the basis, Sec. 4.3): the rpod_project computation with its
 // split-K partial sums kept in a fixed device array of this library instead
 // of a caller-provided workspace.
 //

@@ -1,7 +1,8 @@
 """Host-side sharding across ranks.
 
-Instances of the batched form share nothing, so N ranks (one GPU each) split
-them with no collective on the data path: instance b goes to the rank with the
+Instances of the batched form (one rPOD of Alg. 1 per field and parameter
+sample, Sec. 4.1) share nothing, so N ranks (one GPU each) split them with no
+collective on the data path: instance b goes to the rank with the
 least accumulated cost, largest instances first (longest-processing-time
 greedy).  The cost of an instance is its streamed work, (2q + 2) n m_b l_b.
 
